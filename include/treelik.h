@@ -1,0 +1,232 @@
+/*
+ * treelik -- C ABI of the GB300 (sm_103a) phylogenetic likelihood library.
+ *
+ * Computes the log-likelihood of aligned sequence data on a rooted binary
+ * tree by Felsenstein pruning (post-order partial likelihoods) and its
+ * gradient by the linear-time pre-order scheme of the paper (Sec.
+ * "Algorithmic advances": post- and pre-order partials whose inner product
+ * is the likelihood; Sec. "Discussion": the branch-length gradient is a
+ * sandwich of a pre-order partial, the rate matrix and a post-order partial;
+ * transition matrices come from an eigendecomposition of Q, cached across
+ * patterns; exact substitution-parameter gradients through the matrix
+ * exponential).
+ *
+ * Conventions shared by every call
+ *  - Every function returns an int status: TL_OK (0) or a negative TL_ERR_*
+ *    code; tl_last_error() gives the text of the instance's last error.
+ *    No C++ exception crosses this boundary.
+ *  - Host arrays passed in are borrowed for the duration of the call and
+ *    copied; the caller keeps ownership. Results written to host pointers
+ *    are complete when the call returns (the call synchronises the
+ *    instance's stream). Calls whose name ends in _dev take and return
+ *    device pointers and do not synchronise.
+ *  - The instance owns all of its device memory (partials, matrices,
+ *    scratch) and frees it in tl_destroy. All device work is enqueued on the
+ *    CUDA stream given at creation (NULL = the legacy default stream).
+ *  - An instance is not thread-safe; use one instance per host thread.
+ *  - Buffer indices: 0 .. n_tips-1 name the tips; n_tips ..
+ *    n_tips+n_buffers-1 name internal partials buffers (post- or pre-order).
+ *    Matrix slots are 0 .. n_matrices-1; model slots 0 .. n_models-1.
+ *  - Layouts: host matrices are row-major S x S doubles; tip states are one
+ *    int8 code per pattern; tip partials are [pattern][state] doubles.
+ *    Device partials are [category][pattern][state] in the instance's
+ *    working precision, patterns padded to a multiple of 32.
+ */
+#ifndef TREELIK_H
+#define TREELIK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define TL_OK               0
+#define TL_ERR_ARG         -1  /* bad argument (size, null pointer, flag)      */
+#define TL_ERR_INDEX       -2  /* buffer / matrix / model index out of range   */
+#define TL_ERR_ORDER       -3  /* op list reads a buffer it writes later, or
+                                  writes one buffer twice                      */
+#define TL_ERR_OOM         -4  /* device allocation failed                     */
+#define TL_ERR_NUMERIC     -5  /* a pattern likelihood is zero, negative or
+                                  not finite, or an input is not finite        */
+#define TL_ERR_TIMEOUT     -6  /* a bounded device wait gave up                */
+#define TL_ERR_CUDA        -7  /* a CUDA runtime call failed                   */
+#define TL_ERR_UNSUPPORTED -8  /* combination of sizes/precision not built     */
+#define TL_ERR_STATE       -9  /* required input not set yet (model, matrix)   */
+
+/* ---- creation flags ---------------------------------------------------- */
+#define TL_PREC_F64    0x1u   /* FP64 partials and matrices (any S <= 64)      */
+#define TL_PREC_F32    0x2u   /* FP32 partials (S == 4), FP64 reductions       */
+#define TL_PREC_TF32   0x4u   /* S in 33..64: tcgen05 kind::tf32 contractions,
+                                 TF32-rounded FP32 partials, FP32 accumulate   */
+#define TL_PREC_BF16X3 0x8u   /* S in 33..64: tcgen05 kind::f16 with a BF16
+                                 hi/lo split, three products per contraction   */
+#define TL_SCALE_NONE  0x100u /* no per-pattern rescaling (FP64 only)          */
+
+/* ---- model kinds for tl_set_model -------------------------------------- */
+#define TL_MODEL_HKY   1  /* S=4.  params: kappa.  freqs: pi[4]                */
+#define TL_MODEL_GTR   2  /* S=4.  params: AC,AG,AT,CG,CT,GT.  freqs: pi[4]    */
+#define TL_MODEL_GY94  3  /* S=61. params: kappa, omega.  freqs: F3x4 [3][4]   */
+#define TL_MODEL_REV   4  /* any S. params: symmetric S x S exchangeabilities
+                             (row-major, diagonal ignored).  freqs: pi[S]      */
+
+typedef struct tl_instance tl_instance;
+
+/* Post-order partials update (Sec. "Introduction", Felsenstein pruning):
+ *   dest[r,p,:] = (P_mat1,r child1[r,p,:]) o (P_mat2,r child2[r,p,:])
+ * then rescaled per pattern by a power of two (unless TL_SCALE_NONE); the
+ * removed exponents of the whole subtree are kept with dest. A child that is
+ * a tip with states uses a column lookup of P instead of a product. */
+typedef struct {
+    int dest;
+    int child1, mat1;
+    int child2, mat2;
+} tl_op;
+
+/* Pre-order step for one parent node (Sec. "Algorithmic advances"). For
+ * each child c (sibling s) with post-order partial p_c:
+ *   u_c = q_parent o (P_s p_s),   q_c = P_c^T u_c   (rescaled per pattern)
+ * q_parent is the pre-order partial of the parent: buffer parent_pre, or the
+ * root distribution pi when parent_pre == -1. pre_c >= 0 names the buffer
+ * that receives q_c (-1: q_c is not needed). edge_c >= 0 is the slot of
+ * out_grad that receives dlogL/dt_c, computed from dmat_c = dP/dt (see
+ * tl_update_matrices) as
+ *   sum_p w_p [sum_r w_r u_c^T dP_c p_c] / [sum_r w_r u_c^T P_c p_c]
+ * (Sec. "Discussion": pre-order partial . dP/dt . post-order partial). */
+typedef struct {
+    int parent_pre;
+    int child[2];
+    int mat[2];
+    int dmat[2];
+    int pre[2];
+    int edge[2];
+} tl_pre_op;
+
+/* One edge for tl_edge_derivatives: post-order partial p_c (buffer or tip),
+ * materialised pre-order partial q_c (buffer), and the slot of out_grad. */
+typedef struct {
+    int post;
+    int pre;
+    int edge;
+} tl_edge;
+
+/* Create an instance. n_states: 1..64 (TL_PREC_F32: 4; TF32/BF16X3: 33..64,
+ * stored padded to 64). n_categories: 1..8. n_buffers: internal partials
+ * buffers. n_matrices: transition-matrix slots (each holds all categories).
+ * n_models: model slots (Q, pi, eigensystem, dQ/dtheta). stream: a
+ * cudaStream_t or NULL. Exactly one TL_PREC_* flag must be set. */
+int tl_create(int n_tips, int n_patterns, int n_states, int n_categories,
+              int n_buffers, int n_matrices, int n_models, unsigned flags,
+              void* stream, tl_instance** out);
+int tl_destroy(tl_instance* inst);
+/* Text of the last error on this instance (or of the last failed tl_create
+ * when inst is NULL), copied into buf (NUL-terminated, truncated). */
+int tl_last_error(const tl_instance* inst, char* buf, size_t len);
+/* Device bytes this instance holds. */
+int tl_device_bytes(const tl_instance* inst, size_t* out);
+
+/* Tip data. states: [n_patterns] int8 codes, 0..S-1 observed, any other
+ * value ambiguous (all-ones partial). partials: [n_patterns][S] doubles, used
+ * in every category. A tip holds either states or partials. */
+int tl_set_tip_states(tl_instance* inst, int tip, const int8_t* states);
+int tl_set_tip_partials(tl_instance* inst, int tip, const double* partials);
+/* All tips' states at once: states is [n_tips][n_patterns] int8 (row-major),
+ * copied with one 2-D transfer (full speed from page-locked host memory);
+ * synchronises the stream before returning. */
+int tl_set_tip_states_all(tl_instance* inst, const int8_t* states);
+/* Pattern weights [n_patterns] (non-negative, finite). Default 1. */
+int tl_set_pattern_weights(tl_instance* inst, const double* weights);
+/* Category rates rho_r [n_categories] (>= 0) and weights w_r (>= 0, summing
+ * to 1 is not required). Defaults: rates 1, weights 1/R. */
+int tl_set_category_rates(tl_instance* inst, const double* rates);
+int tl_set_category_weights(tl_instance* inst, const double* weights);
+
+/* Model slot set-up (Sec. "Discussion": transition matrices by numerical
+ * eigendecomposition of the rate matrix, reused across patterns).
+ * tl_set_model builds Q on the device for the given kind, normalises it to
+ * one expected substitution per unit time, forms dQ/dtheta for every
+ * parameter (normaliser included) and diagonalises the symmetrised Q by
+ * FP64 Jacobi rotations. params/freqs are read as documented at TL_MODEL_*. */
+int tl_set_model(tl_instance* inst, int model, int kind, const double* params,
+                 int n_params, const double* freqs, int n_freqs);
+/* As tl_set_model without waiting for the device: a failed device check
+ * (non-positive frequency, zero mean rate, Jacobi not converged) is reported
+ * by the next tl_sync or result-returning call. For use inside a stream of
+ * queued work. */
+int tl_set_model_async(tl_instance* inst, int model, int kind, const double* params,
+                       int n_params, const double* freqs, int n_freqs);
+/* A reversible rate matrix Q (row-major S x S) with stationary pi, taken as
+ * given (no normalisation); diagonalised on the device. */
+int tl_set_rate_matrix(tl_instance* inst, int model, const double* Q, const double* pi);
+/* A host eigensystem Q = V diag(lambda) Vinv (row-major), with pi. */
+int tl_set_eigen(tl_instance* inst, int model, const double* V, const double* Vinv,
+                 const double* lambda, const double* pi);
+/* Read back a model's FP64 Q [S*S], pi [S] and the number of dQ/dtheta
+ * matrices; dq may be NULL, otherwise receives n_dq * S * S values. */
+int tl_get_model(tl_instance* inst, int model, double* Q, double* pi, double* dq, int* n_dq);
+
+/* Transition matrices (Sec. "Discussion"): for i < count,
+ *   P[p_idx[i]]_r  = V diag(exp(lambda rho_r t_i)) Vinv
+ *   P[dp_idx[i]]_r = V diag(rho_r lambda exp(lambda rho_r t_i)) Vinv = dP/dt
+ * for every category r; dp_idx may be NULL, entries -1 are skipped.
+ * edge_len must be finite and >= 0. */
+int tl_update_matrices(tl_instance* inst, int model, const int* p_idx, const int* dp_idx,
+                       const double* edge_len, int count);
+/* Read back one matrix slot in FP64, [R][S][S]. */
+int tl_get_matrix(tl_instance* inst, int mat, double* out);
+
+/* Execute a post-order operation list. Every child must be a tip, a buffer
+ * written earlier by this list, or a buffer written by an earlier call. An
+ * op list may not read a buffer that it writes later, nor write a buffer
+ * twice (TL_ERR_ORDER). Ops may run in any order that respects these
+ * dependencies; the results do not depend on that order. */
+int tl_update_partials(tl_instance* inst, const tl_op* ops, int count);
+
+/* Root log-likelihood (Sec. "Introduction"):
+ *   l_p = log(sum_r w_r sum_s pi_s root[r,p,s]) + ln2 * E_p,
+ *   logL = sum_p w_p l_p   (FP64, fixed-order two-stage reduction),
+ * where E_p is the root buffer's accumulated rescaling exponent and pi is the
+ * model's stationary distribution. out_site_logl ([n_patterns]) may be NULL.
+ * Returns TL_ERR_NUMERIC (and writes the value) when a pattern likelihood
+ * is not positive and finite. */
+int tl_root_loglik(tl_instance* inst, int root, int model, double* out_logl,
+                   double* out_site_logl);
+/* Same on the device: writes logL to out_logl_dev (1 double) without
+ * synchronising; the numeric-error flag is checked by the next synchronous
+ * call or tl_sync. */
+int tl_root_loglik_dev(tl_instance* inst, int root, int model, double* out_logl_dev);
+
+/* Pre-order partials (materialised in the pre[] buffers of each op). */
+int tl_update_pre_partials(tl_instance* inst, const tl_pre_op* ops, int count, int model);
+/* Fused pre-order pass and branch-length gradient: ops in pre-order (a
+ * parent's op before its children's). q partials stay on chip where
+ * possible and are written only where pre[] >= 0. out_grad has n_grad
+ * doubles; slot edge[c] receives dlogL/dt_c; untouched slots are zeroed. */
+int tl_pre_order_gradient(tl_instance* inst, const tl_pre_op* ops, int count, int model,
+                          double* out_grad, int n_grad);
+int tl_pre_order_gradient_dev(tl_instance* inst, const tl_pre_op* ops, int count, int model,
+                              double* out_grad_dev, int n_grad);
+/* Edge derivatives from materialised partials:
+ *   g_c = sum_p w_p [sum_r w_r rho_r q_c^T Q p_c] / [sum_r w_r q_c^T p_c]. */
+int tl_edge_derivatives(tl_instance* inst, const tl_edge* edges, int count, int model,
+                        double* out_grad, int n_grad);
+
+/* Read back one buffer in FP64: out [R][n_patterns][S] partials as stored
+ * (post-order partials carry their accumulated power-of-two exponents
+ * separately; pre-order partials are defined up to a per-pattern power of
+ * two). exponents ([n_patterns] int32, may be NULL) receives the buffer's
+ * accumulated rescaling exponents (zeros for pre-order buffers and tips). */
+int tl_get_partials(tl_instance* inst, int buf, double* out, int32_t* exponents);
+
+/* Number of kernels this instance has launched since creation. */
+int tl_launch_count(const tl_instance* inst, unsigned long long* out);
+
+/* Wait for the instance's stream and report any pending device error. */
+int tl_sync(tl_instance* inst);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TREELIK_H */

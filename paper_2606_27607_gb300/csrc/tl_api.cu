@@ -1,0 +1,1258 @@
+// C ABI of the treelik library: instance lifecycle, input validation, the
+// host-side scheduler that turns an operation list into a device walk (op
+// reordering and on-chip slot assignment), launches, and fixed-order
+// reductions. Every numerical step runs in the kernels of tl_model.cu,
+// tl_nuc.cu and tl_generic.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "tl_internal.cuh"
+
+namespace tl {
+
+static thread_local std::string g_create_err;
+
+int fail(Instance* I, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (I) I->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+int cuda_check(Instance* I, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return TL_OK;
+    return fail(I, e == cudaErrorMemoryAllocation ? TL_ERR_OOM : TL_ERR_CUDA, "%s: %s (%s)", what,
+                cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+// Sum each of n_out rows of n_in doubles in a fixed order (deterministic).
+__global__ void k_reduce_rows(const double* __restrict__ in, int n_in, double* __restrict__ out) {
+    __shared__ double s[256];
+    const int row = blockIdx.x;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < n_in; j += blockDim.x) acc += in[(size_t)row * n_in + j];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[row] = s[0];
+}
+
+// out[map[k]] = in[k] for k < n; out has n_out entries, the rest zeroed.
+__global__ void k_scatter(const double* __restrict__ in, const int* __restrict__ map, int n,
+                          double* __restrict__ out, int n_out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_out; i += gridDim.x * blockDim.x)
+        out[i] = 0.0;
+    __syncthreads();
+    // single block launch: the zeroing above is complete for this block
+    for (int k = threadIdx.x; k < n; k += blockDim.x) out[map[k]] = in[k];
+}
+
+int reduce_fixed(Instance* I, const double* d_in, int n_out, int n_in, double* d_out) {
+    if (n_out <= 0) return TL_OK;
+    k_reduce_rows<<<n_out, 256, 0, I->stream>>>(d_in, n_in, d_out);
+    I->launches += 1;
+    return cuda_check(I, cudaGetLastError(), "reduction");
+}
+
+}  // namespace tl
+
+using namespace tl;
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename P>
+int dev_alloc(Instance* I, P** p, size_t bytes, const char* what) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(I, TL_ERR_OOM, "cudaMalloc(%zu bytes) for %s failed: %s", bytes, what,
+                    cudaGetErrorString(e));
+    }
+    I->bytes += bytes;
+    *p = reinterpret_cast<P*>(q);
+    return TL_OK;
+}
+
+int ensure_scratch(Instance* I, size_t doubles) {
+    if (I->red_cap >= doubles) return TL_OK;
+    if (I->d_red) {
+        cudaStreamSynchronize(I->stream);
+        cudaFree(I->d_red);
+        I->bytes -= I->red_cap * sizeof(double);
+        I->d_red = nullptr;
+        I->red_cap = 0;
+    }
+    size_t cap = std::max<size_t>(doubles, 1 << 16);
+    int rc = dev_alloc(I, &I->d_red, cap * sizeof(double), "reduction scratch");
+    if (rc) return rc;
+    I->red_cap = cap;
+    return TL_OK;
+}
+
+// Pinned host staging ring for small uploads: a slot is reused only after
+// the copy that last read it has completed (its event), so callers' host
+// arrays are free as soon as a call returns and no copy waits on the stream.
+struct PinnedSlot {
+    void* h = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev = nullptr;
+};
+constexpr int kRing = 8;
+
+// Upload bytes to op area `which` unless identical to the last upload.
+struct OpArea {
+    void* d = nullptr;
+    size_t cap = 0;
+    std::vector<char> last;
+};
+
+int h2d(Instance* I, void* dst, const void* src, size_t bytes);
+
+int upload(Instance* I, OpArea& A, const void* src, size_t bytes, void** dptr) {
+    if (bytes == 0) {
+        *dptr = A.d;
+        return TL_OK;
+    }
+    if (A.last.size() == bytes && std::memcmp(A.last.data(), src, bytes) == 0 && A.d) {
+        *dptr = A.d;
+        return TL_OK;
+    }
+    if (A.cap < bytes) {
+        if (A.d) {
+            cudaStreamSynchronize(I->stream);
+            cudaFree(A.d);
+            I->bytes -= A.cap;
+        }
+        size_t cap = std::max<size_t>(bytes * 2, 4096);
+        int rc = dev_alloc(I, &A.d, cap, "op list");
+        if (rc) return rc;
+        A.cap = cap;
+        A.last.clear();
+    }
+    int rc = h2d(I, A.d, src, bytes);
+    if (rc) return rc;
+    A.last.assign((const char*)src, (const char*)src + bytes);
+    *dptr = A.d;
+    return TL_OK;
+}
+
+struct Extra {
+    PinnedSlot ring[kRing];
+    int ring_next = 0;
+    OpArea areas[5];
+    std::vector<void*> gen_q;     // generic path: scratch pre-order buffers
+    double* d_out = nullptr;      // small result area
+    size_t out_cap = 0;
+};
+
+Extra& extra(Instance* I) {
+    return *reinterpret_cast<Extra*>(I->host_extra);
+}
+
+// Copy `bytes` from host `src` to device `dst` on the instance stream through
+// the pinned ring.
+int h2d(Instance* I, void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return TL_OK;
+    Extra& X = extra(I);
+    PinnedSlot& s = X.ring[X.ring_next];
+    X.ring_next = (X.ring_next + 1) % kRing;
+    cudaError_t e = cudaSuccess;
+    if (s.ev) e = cudaEventSynchronize(s.ev);
+    else e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_check(I, e, "staging event");
+    if (s.cap < bytes) {
+        if (s.h) cudaFreeHost(s.h);
+        s.cap = std::max<size_t>(bytes, 64 * 1024);
+        e = cudaHostAlloc(&s.h, s.cap, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            s.h = nullptr;
+            s.cap = 0;
+            return cuda_check(I, e, "pinned staging");
+        }
+    }
+    std::memcpy(s.h, src, bytes);
+    e = cudaMemcpyAsync(dst, s.h, bytes, cudaMemcpyHostToDevice, I->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s.ev, I->stream);
+    return cuda_check(I, e, "host to device copy");
+}
+
+int ensure_out(Instance* I, size_t n) {
+    Extra& X = extra(I);
+    if (X.out_cap >= n) return TL_OK;
+    if (X.d_out) {
+        cudaStreamSynchronize(I->stream);
+        cudaFree(X.d_out);
+        I->bytes -= X.out_cap * sizeof(double);
+    }
+    size_t cap = std::max<size_t>(n, 4096);
+    int rc = dev_alloc(I, &X.d_out, cap * sizeof(double), "result area");
+    if (rc) return rc;
+    X.out_cap = cap;
+    return TL_OK;
+}
+
+bool use_nuc(const Instance* I) { return I->S == 4 && (I->prec == kF32 || I->prec == kF64); }
+
+int max_slots(const Instance* I) {
+    // keep the per-block on-chip slot area near 56 KB so four blocks
+    // (sixteen warps) stay resident per SM
+    const int per = nuc_smem_per_slot(I) * kWarpsPerBlock;
+    return std::max(0, std::min(12, (56 * 1024) / per));
+}
+
+int check_numeric_flag(Instance* I) {
+    int h[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, I->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, I->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
+    if (e != cudaSuccess) return cuda_check(I, e, "error flag");
+    if (h[0] || h[1]) {
+        cudaMemsetAsync(I->d_err, 0, 2 * sizeof(int), I->stream);
+        if (h[0])
+            return fail(I, TL_ERR_NUMERIC, "model set-up failed on the device (check %d: "
+                        "non-positive frequency, zero mean rate or Jacobi did not converge)", h[0]);
+        return fail(I, TL_ERR_NUMERIC, "a pattern likelihood is zero, negative or not finite");
+    }
+    return TL_OK;
+}
+
+#define CHECK_INST(I)                                                        \
+    do {                                                                     \
+        if (!(I)) return fail(nullptr, TL_ERR_ARG, "null instance");         \
+    } while (0)
+
+// -------- post-order scheduling ---------------------------------------------
+struct PostPlan {
+    std::vector<DevPostOp> dev;
+    int n_slots = 0;
+};
+
+int plan_post(Instance* I, const tl_op* ops, int n, PostPlan* plan, bool dry) {
+    const int NB = I->n_bufs;
+    std::vector<int> producer(NB, -1);
+    std::vector<int> consumers(n, 0);
+    std::vector<int> first_read(NB, n);
+    std::vector<int> writer(NB, -1);
+    for (int k = 0; k < n; ++k)
+        if (ops[k].dest >= 0 && ops[k].dest < NB && writer[ops[k].dest] < 0) writer[ops[k].dest] = k;
+    for (int k = 0; k < n; ++k) {
+        const tl_op& o = ops[k];
+        const int ch[2] = {o.child1, o.child2};
+        const int mt[2] = {o.mat1, o.mat2};
+        if (o.dest < I->n_tips || o.dest >= NB)
+            return fail(I, TL_ERR_INDEX, "op %d: dest %d is not an internal buffer", k, o.dest);
+        for (int c = 0; c < 2; ++c) {
+            if (ch[c] < 0 || ch[c] >= NB)
+                return fail(I, TL_ERR_INDEX, "op %d: child %d out of range", k, ch[c]);
+            if (mt[c] < 0 || mt[c] >= I->n_mats)
+                return fail(I, TL_ERR_INDEX, "op %d: matrix %d out of range", k, mt[c]);
+            if (!I->mat_set[mt[c]])
+                return fail(I, TL_ERR_STATE, "op %d: matrix %d not computed", k, mt[c]);
+            if (ch[c] == o.dest)
+                return fail(I, TL_ERR_ORDER, "op %d: dest is also a child", k);
+            if (writer[ch[c]] > k)
+                return fail(I, TL_ERR_ORDER, "op %d: buffer %d is read before op %d writes it", k,
+                            ch[c], writer[ch[c]]);
+            if (ch[c] < I->n_tips) {
+                if (!I->tip_set[ch[c]])
+                    return fail(I, TL_ERR_STATE, "op %d: tip %d has no data", k, ch[c]);
+            } else if (producer[ch[c]] < 0 && !I->buf_written[ch[c] - I->n_tips]) {
+                return fail(I, TL_ERR_STATE, "op %d: buffer %d read before it is written", k, ch[c]);
+            }
+            first_read[ch[c]] = std::min(first_read[ch[c]], k);
+            if (producer[ch[c]] >= 0) consumers[producer[ch[c]]]++;
+        }
+        if (producer[o.dest] >= 0)
+            return fail(I, TL_ERR_ORDER, "op %d: buffer %d written twice", k, o.dest);
+        if (first_read[o.dest] < k)
+            return fail(I, TL_ERR_ORDER, "op %d: buffer %d read by op %d before it is written", k,
+                        o.dest, first_read[o.dest]);
+        producer[o.dest] = k;
+    }
+    if (dry) return TL_OK;
+
+    // Sethi-Ullman order: evaluate the child subtree needing more slots
+    // first. Only for forests (each local result consumed once).
+    bool forest = true;
+    for (int k = 0; k < n; ++k)
+        if (consumers[k] > 1) forest = false;
+    std::vector<int> order;
+    order.reserve(n);
+    std::vector<int> need(n, 1);
+    auto local = [&](int k, int c) {
+        int ch = c == 0 ? ops[k].child1 : ops[k].child2;
+        return (ch >= I->n_tips) ? producer[ch] : -1;
+    };
+    if (forest) {
+        for (int k = 0; k < n; ++k) {
+            int x = local(k, 0), y = local(k, 1);
+            if (x >= 0 && y >= 0)
+                need[k] = need[x] == need[y] ? need[x] + 1 : std::max(need[x], need[y]);
+            else if (x >= 0 || y >= 0)
+                need[k] = need[x >= 0 ? x : y];
+        }
+        std::vector<char> emitted(n, 0);
+        // iterative guard against deep recursion on caterpillars
+        for (int k = 0; k < n; ++k) {
+            if (consumers[k] == 0) {
+                // explicit stack version of emit
+                std::vector<std::pair<int, int>> st;
+                st.push_back({k, 0});
+                while (!st.empty()) {
+                    auto& [v, phase] = st.back();
+                    int x = local(v, 0), y = local(v, 1);
+                    if (x >= 0 && y >= 0 && need[y] > need[x]) std::swap(x, y);
+                    if (phase == 0) {
+                        phase = 1;
+                        if (x >= 0) { st.push_back({x, 0}); continue; }
+                    }
+                    if (phase == 1) {
+                        phase = 2;
+                        if (y >= 0) { st.push_back({y, 0}); continue; }
+                    }
+                    order.push_back(v);
+                    emitted[v] = 1;
+                    st.pop_back();
+                }
+            }
+        }
+        if ((int)order.size() != n) {  // should not happen; fall back
+            order.clear();
+            for (int k = 0; k < n; ++k) order.push_back(k);
+        }
+    } else {
+        for (int k = 0; k < n; ++k) order.push_back(k);
+    }
+
+    // slot assignment by linear scan
+    const int cap = max_slots(I);
+    std::vector<int> slot_of(n, -1), remaining(n, 0);
+    for (int k = 0; k < n; ++k) remaining[k] = consumers[k];
+    std::vector<int> free_slots;
+    for (int s = cap - 1; s >= 0; --s) free_slots.push_back(s);
+    int used = 0;
+    plan->dev.resize(n);
+    for (int idx = 0; idx < n; ++idx) {
+        const int k = order[idx];
+        const tl_op& o = ops[k];
+        DevPostOp d;
+        d.dest = o.dest;
+        d.child[0] = o.child1;
+        d.child[1] = o.child2;
+        d.mat[0] = o.mat1;
+        d.mat[1] = o.mat2;
+        for (int c = 0; c < 2; ++c) {
+            int pk = local(k, c);
+            d.slot_in[c] = (pk >= 0) ? slot_of[pk] : -1;
+        }
+        for (int c = 0; c < 2; ++c) {
+            int pk = local(k, c);
+            if (pk >= 0 && --remaining[pk] == 0 && slot_of[pk] >= 0) {
+                free_slots.push_back(slot_of[pk]);
+            }
+        }
+        d.slot_out = -1;
+        if (consumers[k] > 0 && !free_slots.empty()) {
+            d.slot_out = free_slots.back();
+            free_slots.pop_back();
+            slot_of[k] = d.slot_out;
+            used = std::max(used, d.slot_out + 1);
+        }
+        d.store = 1;
+        plan->dev[idx] = d;
+    }
+    plan->n_slots = used;
+    return TL_OK;
+}
+
+// -------- pre-order scheduling ----------------------------------------------
+struct PrePlan {
+    std::vector<DevPreOp> dev;
+    int n_slots = 0;
+    std::vector<int> edge_map;   // compact row -> user edge index
+};
+
+int plan_pre(Instance* I, const tl_pre_op* ops, int n, int n_grad, bool store_all,
+             PrePlan* plan) {
+    const int NB = I->n_bufs;
+    std::vector<int> prod_op(NB, -1), prod_c(NB, -1);
+    std::vector<int> child_op(2 * n, -1);   // op consuming output c of op k
+    std::vector<int> edge_row(std::max(n_grad, 1), -1);
+    plan->edge_map.clear();
+    for (int k = 0; k < n; ++k) {
+        const tl_pre_op& o = ops[k];
+        if (o.parent_pre != -1) {
+            if (o.parent_pre < I->n_tips || o.parent_pre >= NB)
+                return fail(I, TL_ERR_INDEX, "pre op %d: parent_pre %d not an internal buffer", k,
+                            o.parent_pre);
+            int j = prod_op[o.parent_pre];
+            if (j >= 0) {
+                if (child_op[2 * j + prod_c[o.parent_pre]] >= 0)
+                    return fail(I, TL_ERR_ORDER, "pre op %d: q buffer %d consumed twice", k,
+                                o.parent_pre);
+                child_op[2 * j + prod_c[o.parent_pre]] = k;
+            } else if (!I->buf_written[o.parent_pre - I->n_tips]) {
+                return fail(I, TL_ERR_STATE, "pre op %d: parent_pre %d holds no data", k,
+                            o.parent_pre);
+            }
+        }
+        for (int c = 0; c < 2; ++c) {
+            if (o.child[c] < 0 || o.child[c] >= NB)
+                return fail(I, TL_ERR_INDEX, "pre op %d: child %d out of range", k, o.child[c]);
+            if (o.child[c] < I->n_tips ? !I->tip_set[o.child[c]]
+                                       : !I->buf_written[o.child[c] - I->n_tips])
+                return fail(I, TL_ERR_STATE, "pre op %d: child %d holds no data", k, o.child[c]);
+            if (o.mat[c] < 0 || o.mat[c] >= I->n_mats || !I->mat_set[o.mat[c]])
+                return fail(I, TL_ERR_INDEX, "pre op %d: matrix %d not available", k, o.mat[c]);
+            if (o.dmat[c] >= I->n_mats || (o.dmat[c] >= 0 && !I->mat_set[o.dmat[c]]))
+                return fail(I, TL_ERR_INDEX, "pre op %d: dmat %d not available", k, o.dmat[c]);
+            if (o.edge[c] >= 0) {
+                if (o.edge[c] >= n_grad)
+                    return fail(I, TL_ERR_INDEX, "pre op %d: edge %d >= n_grad", k, o.edge[c]);
+                if (o.dmat[c] < 0)
+                    return fail(I, TL_ERR_ARG, "pre op %d: edge requested without dmat", k);
+                if (edge_row[o.edge[c]] >= 0)
+                    return fail(I, TL_ERR_ORDER, "pre op %d: edge %d requested twice", k, o.edge[c]);
+                edge_row[o.edge[c]] = (int)plan->edge_map.size();
+                plan->edge_map.push_back(o.edge[c]);
+            }
+            if (o.pre[c] >= 0) {
+                if (o.pre[c] < I->n_tips || o.pre[c] >= NB)
+                    return fail(I, TL_ERR_INDEX, "pre op %d: pre %d not an internal buffer", k,
+                                o.pre[c]);
+                if (prod_op[o.pre[c]] >= 0)
+                    return fail(I, TL_ERR_ORDER, "pre op %d: pre buffer %d written twice", k,
+                                o.pre[c]);
+                prod_op[o.pre[c]] = k;
+                prod_c[o.pre[c]] = c;
+            }
+        }
+    }
+    // order: depth first from each root op, smaller-need subtree first
+    std::vector<int> need(n, 0), parent_op(n, -1);
+    for (int k = 0; k < n; ++k)
+        for (int c = 0; c < 2; ++c)
+            if (child_op[2 * k + c] >= 0) parent_op[child_op[2 * k + c]] = k;
+    for (int k = n - 1; k >= 0; --k) {
+        int x = child_op[2 * k], y = child_op[2 * k + 1];
+        if (x >= 0 && y >= 0) {
+            int a = std::min(need[x], need[y]), b = std::max(need[x], need[y]);
+            need[k] = std::max(2, std::max(a + 1, b));
+        } else if (x >= 0 || y >= 0) {
+            need[k] = std::max(1, need[x >= 0 ? x : y]);
+        }
+    }
+    std::vector<int> order;
+    order.reserve(n);
+    for (int k = 0; k < n; ++k) {
+        if (parent_op[k] >= 0) continue;
+        std::vector<int> st{k};
+        while (!st.empty()) {
+            int v = st.back();
+            st.pop_back();
+            order.push_back(v);
+            int x = child_op[2 * v], y = child_op[2 * v + 1];
+            // push larger-need first so the smaller one is processed first
+            if (x >= 0 && y >= 0) {
+                if (need[x] < need[y]) std::swap(x, y);
+                st.push_back(x);
+                st.push_back(y);
+            } else if (x >= 0) {
+                st.push_back(x);
+            } else if (y >= 0) {
+                st.push_back(y);
+            }
+        }
+    }
+    if ((int)order.size() != n) return fail(I, TL_ERR_ORDER, "pre-order op list is not a forest");
+    // parents must precede children in the given list too (validated above by
+    // prod_op lookups happening in list order)
+    const int cap = use_nuc(I) ? max_slots(I) : 0;
+    std::vector<int> free_slots;
+    for (int s = cap - 1; s >= 0; --s) free_slots.push_back(s);
+    std::vector<int> q_slot(2 * n, -1);
+    int used = 0;
+    plan->dev.resize(n);
+    for (int idx = 0; idx < n; ++idx) {
+        const int k = order[idx];
+        const tl_pre_op& o = ops[k];
+        DevPreOp d;
+        std::memset(&d, 0, sizeof d);
+        if (o.parent_pre == -1) {
+            d.q_slot_in = -2;
+            d.q_buf_in = -1;
+        } else {
+            int j = prod_op[o.parent_pre];
+            int s = (j >= 0) ? q_slot[2 * j + prod_c[o.parent_pre]] : -1;
+            d.q_slot_in = s;
+            d.q_buf_in = o.parent_pre;
+            if (s >= 0) free_slots.push_back(s);
+        }
+        for (int c = 0; c < 2; ++c) {
+            d.child[c] = o.child[c];
+            d.mat[c] = o.mat[c];
+            d.dmat[c] = o.dmat[c];
+            d.edge[c] = o.edge[c] >= 0 ? edge_row[o.edge[c]] : -1;
+            d.q_slot_out[c] = -1;
+            d.q_buf_out[c] = -1;
+            const bool consumed = child_op[2 * k + c] >= 0;
+            if (o.pre[c] >= 0 && (consumed || store_all)) {
+                d.need_q[c] = 1;
+                if (consumed && !store_all && !free_slots.empty()) {
+                    d.q_slot_out[c] = free_slots.back();
+                    free_slots.pop_back();
+                    q_slot[2 * k + c] = d.q_slot_out[c];
+                    used = std::max(used, d.q_slot_out[c] + 1);
+                } else {
+                    d.q_buf_out[c] = o.pre[c];
+                }
+            }
+        }
+        plan->dev[idx] = d;
+    }
+    plan->n_slots = used;
+    return TL_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int tl_last_error(const tl_instance* inst, char* buf, size_t len) {
+    if (!buf || len == 0) return TL_ERR_ARG;
+    const std::string& s = inst ? reinterpret_cast<const Instance*>(inst)->err : g_create_err;
+    size_t n = std::min(len - 1, s.size());
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+    return TL_OK;
+}
+
+int tl_device_bytes(const tl_instance* inst, size_t* out) {
+    if (!inst || !out) return TL_ERR_ARG;
+    *out = reinterpret_cast<const Instance*>(inst)->bytes;
+    return TL_OK;
+}
+
+int tl_destroy(tl_instance* inst) {
+    if (!inst) return TL_ERR_ARG;
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    cudaStreamSynchronize(I->stream);
+    auto fr = [](void* p) {
+        if (p) cudaFree(p);
+    };
+    fr(I->pool);
+    fr(I->scale_pool);
+    for (void* p : I->tip_part) fr(p);
+    fr(I->tip_pool);
+    fr(I->d_buf);
+    fr(I->d_scale);
+    fr(I->d_tipst);
+    fr(I->d_patw);
+    fr(I->d_mat64);
+    fr(I->d_matw);
+    for (ModelDev& M : I->models) {
+        fr(M.Q);
+        fr(M.pi);
+        fr(M.V);
+        fr(M.Vinv);
+        fr(M.lam);
+        fr(M.dQ);
+        fr(M.piw);
+        fr(M.Qw);
+    }
+    fr(I->d_red);
+    fr(I->d_err);
+    fr(I->d_tmp);
+    if (I->host_extra) {
+        Extra* X = reinterpret_cast<Extra*>(I->host_extra);
+        for (auto& s : X->ring) {
+            if (s.h) cudaFreeHost(s.h);
+            if (s.ev) cudaEventDestroy(s.ev);
+        }
+        for (auto& A : X->areas) fr(A.d);
+        for (void* p : X->gen_q) fr(p);
+        fr(X->d_out);
+        delete X;
+    }
+    delete[] I->h_catw;
+    delete[] I->h_rates;
+    delete I;
+    return TL_OK;
+}
+
+int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_buffers,
+              int n_matrices, int n_models, unsigned flags, void* stream, tl_instance** out) {
+    if (!out) return fail(nullptr, TL_ERR_ARG, "out is null");
+    *out = nullptr;
+    const unsigned precs = flags & (TL_PREC_F64 | TL_PREC_F32 | TL_PREC_TF32 | TL_PREC_BF16X3);
+    if (precs == 0 || (precs & (precs - 1)))
+        return fail(nullptr, TL_ERR_ARG, "exactly one TL_PREC_* flag is required");
+    if (n_tips < 2 || n_patterns < 1 || n_states < 2 || n_states > kMaxStates ||
+        n_categories < 1 || n_categories > kMaxCat || n_buffers < 1 || n_matrices < 1 ||
+        n_models < 1)
+        return fail(nullptr, TL_ERR_ARG,
+                    "bad sizes (tips>=2, patterns>=1, 2<=states<=64, 1<=categories<=8, "
+                    "buffers, matrices, models >= 1)");
+    Prec prec = (precs == TL_PREC_F64) ? kF64 : (precs == TL_PREC_F32) ? kF32
+                : (precs == TL_PREC_TF32) ? kTF32 : kBF16X3;
+    if (prec == kF32 && n_states != 4)
+        return fail(nullptr, TL_ERR_UNSUPPORTED, "TL_PREC_F32 is built for 4 states");
+    if ((prec == kTF32 || prec == kBF16X3))
+        return fail(nullptr, TL_ERR_UNSUPPORTED, "tensor-core precisions are not built in this library");
+    if ((flags & TL_SCALE_NONE) && prec != kF64)
+        return fail(nullptr, TL_ERR_ARG, "TL_SCALE_NONE needs TL_PREC_F64");
+
+    Instance* I = new Instance();
+    I->n_tips = n_tips;
+    I->P = n_patterns;
+    I->Ppad = ((n_patterns + kTile - 1) / kTile) * kTile;
+    I->S = n_states;
+    I->Spad = (n_states == 4) ? 4 : ((n_states + 3) / 4) * 4;
+    if (prec == kTF32 || prec == kBF16X3) I->Spad = 64;
+    I->R = n_categories;
+    I->n_buffers = n_buffers;
+    I->n_bufs = n_tips + n_buffers;
+    I->n_mats = n_matrices;
+    I->n_models = n_models;
+    I->flags = flags;
+    I->prec = prec;
+    I->elt = (prec == kF64) ? 8 : 4;
+    I->rescale = (flags & TL_SCALE_NONE) ? 0 : 1;
+    I->stream = reinterpret_cast<cudaStream_t>(stream);
+    I->h_catw = new double[kMaxCat];
+    I->h_rates = new double[kMaxCat];
+    for (int r = 0; r < kMaxCat; ++r) {
+        I->h_catw[r] = r < n_categories ? 1.0 / n_categories : 0.0;
+        I->h_rates[r] = r < n_categories ? 1.0 : 0.0;
+    }
+    I->host_extra = new Extra();
+    cudaGetDevice(&I->device);
+
+    auto bail = [&](int rc) {
+        g_create_err = I->err;
+        tl_destroy(reinterpret_cast<tl_instance*>(I));
+        return rc;
+    };
+    int rc;
+    const size_t nbuf_elems = (size_t)I->R * I->Ppad * I->Spad;
+    if ((rc = dev_alloc(I, &I->pool, nbuf_elems * I->elt * n_buffers, "partials"))) return bail(rc);
+    if ((rc = dev_alloc(I, &I->scale_pool, sizeof(int) * (size_t)I->Ppad * n_buffers, "scales")))
+        return bail(rc);
+    cudaMemsetAsync(I->scale_pool, 0, sizeof(int) * (size_t)I->Ppad * n_buffers, I->stream);
+    if ((rc = dev_alloc(I, &I->d_buf, sizeof(void*) * I->n_bufs, "buffer table"))) return bail(rc);
+    if ((rc = dev_alloc(I, &I->d_scale, sizeof(int*) * I->n_bufs, "scale table"))) return bail(rc);
+    if ((rc = dev_alloc(I, &I->d_tipst, sizeof(int8_t*) * n_tips, "tip table"))) return bail(rc);
+    I->h_buf.assign(I->n_bufs, nullptr);
+    I->h_scale.assign(I->n_bufs, nullptr);
+    I->h_tipst.assign(n_tips, nullptr);
+    I->tip_part.assign(n_tips, nullptr);
+    if ((rc = dev_alloc(I, &I->tip_pool, (size_t)n_tips * I->Ppad, "tip states"))) return bail(rc);
+    cudaMemsetAsync(I->tip_pool, 0xff, (size_t)n_tips * I->Ppad, I->stream);
+    I->tip_set.assign(n_tips, 0);
+    I->buf_written.assign(n_buffers, 0);
+    for (int b = 0; b < n_buffers; ++b) {
+        I->h_buf[n_tips + b] = (char*)I->pool + nbuf_elems * I->elt * b;
+        I->h_scale[n_tips + b] = I->scale_pool + (size_t)I->Ppad * b;
+    }
+    cudaMemcpyAsync(I->d_buf, I->h_buf.data(), sizeof(void*) * I->n_bufs, cudaMemcpyHostToDevice, I->stream);
+    cudaMemcpyAsync(I->d_scale, I->h_scale.data(), sizeof(int*) * I->n_bufs, cudaMemcpyHostToDevice, I->stream);
+    cudaMemcpyAsync(I->d_tipst, I->h_tipst.data(), sizeof(int8_t*) * n_tips, cudaMemcpyHostToDevice, I->stream);
+    if ((rc = dev_alloc(I, &I->d_patw, sizeof(double) * I->Ppad, "pattern weights"))) return bail(rc);
+    {
+        std::vector<double> w(I->Ppad, 0.0);
+        for (int p = 0; p < n_patterns; ++p) w[p] = 1.0;
+        cudaMemcpyAsync(I->d_patw, w.data(), sizeof(double) * I->Ppad, cudaMemcpyHostToDevice, I->stream);
+        cudaStreamSynchronize(I->stream);
+    }
+    const size_t mat64 = (size_t)I->R * I->Spad * I->Spad;
+    if ((rc = dev_alloc(I, &I->d_mat64, sizeof(double) * mat64 * n_matrices, "matrices")))
+        return bail(rc);
+    if (use_nuc(I)) I->matw_stride = (size_t)I->R * kColStride * 4;
+    else I->matw_stride = (size_t)I->R * (I->Spad + 1) * I->Spad;
+    if ((rc = dev_alloc(I, &I->d_matw, (size_t)I->elt * I->matw_stride * n_matrices, "matrix copies")))
+        return bail(rc);
+    I->mat_set.assign(n_matrices, 0);
+    I->models.resize(n_models);
+    const size_t SS = (size_t)I->Spad * I->Spad;
+    for (ModelDev& M : I->models) {
+        if ((rc = dev_alloc(I, &M.Q, sizeof(double) * SS, "Q")) ||
+            (rc = dev_alloc(I, &M.pi, sizeof(double) * I->Spad, "pi")) ||
+            (rc = dev_alloc(I, &M.V, sizeof(double) * SS, "V")) ||
+            (rc = dev_alloc(I, &M.Vinv, sizeof(double) * SS, "Vinv")) ||
+            (rc = dev_alloc(I, &M.lam, sizeof(double) * I->Spad, "lambda")) ||
+            (rc = dev_alloc(I, &M.dQ, sizeof(double) * SS * kMaxDq, "dQ")) ||
+            (rc = dev_alloc(I, &M.piw, (size_t)I->elt * I->Spad, "pi copy")) ||
+            (rc = dev_alloc(I, &M.Qw, (size_t)I->elt * SS, "Q copy")))
+            return bail(rc);
+    }
+    if ((rc = dev_alloc(I, &I->d_err, sizeof(int) * 4, "error flags"))) return bail(rc);
+    cudaMemsetAsync(I->d_err, 0, sizeof(int) * 4, I->stream);
+    I->tmp_cap = 4096;
+    if ((rc = dev_alloc(I, &I->d_tmp, sizeof(double) * I->tmp_cap, "staging"))) return bail(rc);
+    cudaError_t e = cudaStreamSynchronize(I->stream);
+    if (e != cudaSuccess) return bail(cuda_check(I, e, "tl_create"));
+    *out = reinterpret_cast<tl_instance*>(I);
+    return TL_OK;
+}
+
+int tl_sync(tl_instance* inst) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    cudaError_t e = cudaStreamSynchronize(I->stream);
+    if (e != cudaSuccess) return cuda_check(I, e, "tl_sync");
+    return check_numeric_flag(I);
+}
+
+int tl_set_tip_states(tl_instance* inst, int tip, const int8_t* states) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (tip < 0 || tip >= I->n_tips) return fail(I, TL_ERR_INDEX, "tip %d out of range", tip);
+    if (!states) return fail(I, TL_ERR_ARG, "states is null");
+    int8_t* dst = I->tip_pool + (size_t)tip * I->Ppad;
+    int rc = h2d(I, dst, states, (size_t)I->P);
+    if (rc) return rc;
+    if (I->h_tipst[tip] != dst || I->h_buf[tip] != nullptr) {
+        I->h_tipst[tip] = dst;
+        I->h_buf[tip] = nullptr;
+        if ((rc = h2d(I, I->d_tipst + tip, &I->h_tipst[tip], sizeof(int8_t*)))) return rc;
+        if ((rc = h2d(I, I->d_buf + tip, &I->h_buf[tip], sizeof(void*)))) return rc;
+    }
+    I->tip_set[tip] = 1;
+    return TL_OK;
+}
+
+int tl_set_tip_states_all(tl_instance* inst, const int8_t* states) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (!states) return fail(I, TL_ERR_ARG, "states is null");
+    cudaError_t e = cudaMemcpy2DAsync(I->tip_pool, I->Ppad, states, I->P, I->P, I->n_tips,
+                                      cudaMemcpyHostToDevice, I->stream);
+    if (e != cudaSuccess) return cuda_check(I, e, "tl_set_tip_states_all");
+    bool changed = false;
+    for (int t = 0; t < I->n_tips; ++t) {
+        int8_t* dst = I->tip_pool + (size_t)t * I->Ppad;
+        if (I->h_tipst[t] != dst || I->h_buf[t] != nullptr) changed = true;
+        I->h_tipst[t] = dst;
+        I->h_buf[t] = nullptr;
+        I->tip_set[t] = 1;
+    }
+    int rc;
+    if (changed) {
+        if ((rc = h2d(I, I->d_tipst, I->h_tipst.data(), sizeof(int8_t*) * I->n_tips))) return rc;
+        if ((rc = h2d(I, I->d_buf, I->h_buf.data(), sizeof(void*) * I->n_tips))) return rc;
+    }
+    return cuda_check(I, cudaStreamSynchronize(I->stream), "tl_set_tip_states_all");
+}
+
+int tl_launch_count(const tl_instance* inst, unsigned long long* out) {
+    if (!inst || !out) return TL_ERR_ARG;
+    *out = reinterpret_cast<const Instance*>(inst)->launches;
+    return TL_OK;
+}
+
+int tl_set_tip_partials(tl_instance* inst, int tip, const double* partials) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (tip < 0 || tip >= I->n_tips) return fail(I, TL_ERR_INDEX, "tip %d out of range", tip);
+    if (!partials) return fail(I, TL_ERR_ARG, "partials is null");
+    for (size_t i = 0; i < (size_t)I->P * I->S; ++i)
+        if (!std::isfinite(partials[i]) || partials[i] < 0)
+            return fail(I, TL_ERR_NUMERIC, "tip partial %zu is negative or not finite", i);
+    const size_t n = (size_t)I->R * I->Ppad * I->Spad;
+    int rc;
+    if (!I->tip_part[tip]) {
+        if ((rc = dev_alloc(I, &I->tip_part[tip], n * I->elt, "tip partials"))) return rc;
+    }
+    std::vector<char> h(n * I->elt);
+    for (int r = 0; r < I->R; ++r)
+        for (int p = 0; p < I->Ppad; ++p)
+            for (int s = 0; s < I->Spad; ++s) {
+                double v = (s >= I->S) ? 0.0 : (p < I->P ? partials[(size_t)p * I->S + s] : 1.0);
+                size_t off = ((size_t)r * I->Ppad + p) * I->Spad + s;
+                if (I->elt == 8) reinterpret_cast<double*>(h.data())[off] = v;
+                else reinterpret_cast<float*>(h.data())[off] = (float)v;
+            }
+    cudaMemcpyAsync(I->tip_part[tip], h.data(), h.size(), cudaMemcpyHostToDevice, I->stream);
+    I->h_buf[tip] = I->tip_part[tip];
+    I->h_tipst[tip] = nullptr;
+    if ((rc = h2d(I, I->d_tipst + tip, &I->h_tipst[tip], sizeof(int8_t*)))) return rc;
+    if ((rc = h2d(I, I->d_buf + tip, &I->h_buf[tip], sizeof(void*)))) return rc;
+    I->tip_set[tip] = 2;
+    return cuda_check(I, cudaStreamSynchronize(I->stream), "tl_set_tip_partials");
+}
+
+int tl_set_pattern_weights(tl_instance* inst, const double* w) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (!w) return fail(I, TL_ERR_ARG, "weights is null");
+    std::vector<double> h(I->Ppad, 0.0);
+    for (int p = 0; p < I->P; ++p) {
+        if (!std::isfinite(w[p]) || w[p] < 0)
+            return fail(I, TL_ERR_NUMERIC, "pattern weight %d is negative or not finite", p);
+        h[p] = w[p];
+    }
+    return h2d(I, I->d_patw, h.data(), sizeof(double) * I->Ppad);
+}
+
+int tl_set_category_rates(tl_instance* inst, const double* rates) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (!rates) return fail(I, TL_ERR_ARG, "rates is null");
+    for (int r = 0; r < I->R; ++r)
+        if (!std::isfinite(rates[r]) || rates[r] < 0)
+            return fail(I, TL_ERR_NUMERIC, "category rate %d is negative or not finite", r);
+    for (int r = 0; r < I->R; ++r) I->h_rates[r] = rates[r];
+    return TL_OK;
+}
+
+int tl_set_category_weights(tl_instance* inst, const double* w) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (!w) return fail(I, TL_ERR_ARG, "weights is null");
+    for (int r = 0; r < I->R; ++r)
+        if (!std::isfinite(w[r]) || w[r] < 0)
+            return fail(I, TL_ERR_NUMERIC, "category weight %d is negative or not finite", r);
+    for (int r = 0; r < I->R; ++r) I->h_catw[r] = w[r];
+    return TL_OK;
+}
+
+static int stage(Instance* I, const double* a, int na, const double* b, int nb) {
+    if ((size_t)(na + nb) > I->tmp_cap) return fail(I, TL_ERR_ARG, "staging too large");
+    std::vector<double> h((size_t)na + nb);
+    if (na) std::memcpy(h.data(), a, sizeof(double) * na);
+    if (nb) std::memcpy(h.data() + na, b, sizeof(double) * nb);
+    return h2d(I, I->d_tmp, h.data(), sizeof(double) * h.size());
+}
+
+static int set_model(tl_instance* inst, int model, int kind, const double* params, int n_params,
+                     const double* freqs, int n_freqs, bool check) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (model < 0 || model >= I->n_models) return fail(I, TL_ERR_INDEX, "model %d out of range", model);
+    int want_p = 0, want_f = 0;
+    switch (kind) {
+        case TL_MODEL_HKY: want_p = 1; want_f = 4; break;
+        case TL_MODEL_GTR: want_p = 6; want_f = 4; break;
+        case TL_MODEL_GY94: want_p = 2; want_f = 12; break;
+        case TL_MODEL_REV: want_p = I->S * I->S; want_f = I->S; break;
+        default: return fail(I, TL_ERR_ARG, "unknown model kind %d", kind);
+    }
+    if ((kind == TL_MODEL_HKY || kind == TL_MODEL_GTR) && I->S != 4)
+        return fail(I, TL_ERR_ARG, "nucleotide model on a %d-state instance", I->S);
+    if (kind == TL_MODEL_GY94 && I->S != 61)
+        return fail(I, TL_ERR_ARG, "GY94 needs 61 states, instance has %d", I->S);
+    if (n_params != want_p || n_freqs != want_f || !params || !freqs)
+        return fail(I, TL_ERR_ARG, "model kind %d takes %d params and %d freqs", kind, want_p, want_f);
+    for (int i = 0; i < n_params; ++i)
+        if (!std::isfinite(params[i]) || params[i] < 0)
+            return fail(I, TL_ERR_NUMERIC, "parameter %d is negative or not finite", i);
+    for (int i = 0; i < n_freqs; ++i)
+        if (!std::isfinite(freqs[i]) || freqs[i] <= 0)
+            return fail(I, TL_ERR_NUMERIC, "frequency %d is not positive and finite", i);
+    if (n_params + n_freqs > (int)I->tmp_cap) {
+        cudaStreamSynchronize(I->stream);
+        cudaFree(I->d_tmp);
+        I->tmp_cap = n_params + n_freqs + 1024;
+        int rc = dev_alloc(I, &I->d_tmp, sizeof(double) * I->tmp_cap, "staging");
+        if (rc) return rc;
+    }
+    int rc = stage(I, params, n_params, freqs, n_freqs);
+    if (rc) return rc;
+    I->models[model].ready = false;
+    return launch_build_model(I, model, kind, I->d_tmp, n_params, I->d_tmp + n_params, n_freqs,
+                              check);
+}
+
+int tl_set_model(tl_instance* inst, int model, int kind, const double* params, int n_params,
+                 const double* freqs, int n_freqs) {
+    return set_model(inst, model, kind, params, n_params, freqs, n_freqs, true);
+}
+
+int tl_set_model_async(tl_instance* inst, int model, int kind, const double* params, int n_params,
+                       const double* freqs, int n_freqs) {
+    return set_model(inst, model, kind, params, n_params, freqs, n_freqs, false);
+}
+
+int tl_set_rate_matrix(tl_instance* inst, int model, const double* Q, const double* pi) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (model < 0 || model >= I->n_models) return fail(I, TL_ERR_INDEX, "model %d out of range", model);
+    if (!Q || !pi) return fail(I, TL_ERR_ARG, "null input");
+    const int S = I->S, Sp = I->Spad;
+    std::vector<double> q((size_t)Sp * Sp, 0.0), p(Sp, 0.0);
+    for (int i = 0; i < S; ++i) {
+        if (!(pi[i] > 0) || !std::isfinite(pi[i])) return fail(I, TL_ERR_NUMERIC, "pi[%d] not positive", i);
+        p[i] = pi[i];
+        for (int j = 0; j < S; ++j) {
+            if (!std::isfinite(Q[i * S + j])) return fail(I, TL_ERR_NUMERIC, "Q not finite");
+            q[(size_t)i * Sp + j] = Q[i * S + j];
+        }
+    }
+    ModelDev& M = I->models[model];
+    cudaMemcpyAsync(M.Q, q.data(), sizeof(double) * q.size(), cudaMemcpyHostToDevice, I->stream);
+    cudaMemcpyAsync(M.pi, p.data(), sizeof(double) * Sp, cudaMemcpyHostToDevice, I->stream);
+    M.n_dq = 0;
+    M.ready = false;
+    return launch_eigen_from_q(I, model, true);
+}
+
+int tl_set_eigen(tl_instance* inst, int model, const double* V, const double* Vinv,
+                 const double* lambda, const double* pi) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (model < 0 || model >= I->n_models) return fail(I, TL_ERR_INDEX, "model %d out of range", model);
+    if (!V || !Vinv || !lambda || !pi) return fail(I, TL_ERR_ARG, "null input");
+    const int S = I->S, Sp = I->Spad;
+    std::vector<double> v((size_t)Sp * Sp, 0.0), vi((size_t)Sp * Sp, 0.0), l(Sp, 0.0), p(Sp, 0.0);
+    for (int i = 0; i < S; ++i) {
+        l[i] = lambda[i];
+        p[i] = pi[i];
+        for (int j = 0; j < S; ++j) {
+            v[(size_t)i * Sp + j] = V[i * S + j];
+            vi[(size_t)i * Sp + j] = Vinv[i * S + j];
+        }
+    }
+    for (double x : v) if (!std::isfinite(x)) return fail(I, TL_ERR_NUMERIC, "V not finite");
+    for (double x : vi) if (!std::isfinite(x)) return fail(I, TL_ERR_NUMERIC, "Vinv not finite");
+    ModelDev& M = I->models[model];
+    cudaMemcpyAsync(M.V, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice, I->stream);
+    cudaMemcpyAsync(M.Vinv, vi.data(), sizeof(double) * vi.size(), cudaMemcpyHostToDevice, I->stream);
+    cudaMemcpyAsync(M.lam, l.data(), sizeof(double) * Sp, cudaMemcpyHostToDevice, I->stream);
+    cudaMemcpyAsync(M.pi, p.data(), sizeof(double) * Sp, cudaMemcpyHostToDevice, I->stream);
+    M.n_dq = 0;
+    int rc = launch_q_from_eigen(I, model);
+    if (rc) return rc;
+    return launch_model_working_copies(I, model);
+}
+
+int tl_get_model(tl_instance* inst, int model, double* Q, double* pi, double* dq, int* n_dq) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (model < 0 || model >= I->n_models) return fail(I, TL_ERR_INDEX, "model %d out of range", model);
+    ModelDev& M = I->models[model];
+    if (!M.ready) return fail(I, TL_ERR_STATE, "model %d not set", model);
+    const int S = I->S, Sp = I->Spad;
+    std::vector<double> q((size_t)Sp * Sp), p(Sp), d((size_t)kMaxDq * Sp * Sp);
+    cudaMemcpyAsync(q.data(), M.Q, sizeof(double) * q.size(), cudaMemcpyDeviceToHost, I->stream);
+    cudaMemcpyAsync(p.data(), M.pi, sizeof(double) * Sp, cudaMemcpyDeviceToHost, I->stream);
+    cudaMemcpyAsync(d.data(), M.dQ, sizeof(double) * d.size(), cudaMemcpyDeviceToHost, I->stream);
+    int rc = cuda_check(I, cudaStreamSynchronize(I->stream), "tl_get_model");
+    if (rc) return rc;
+    for (int i = 0; i < S; ++i) {
+        if (pi) pi[i] = p[i];
+        for (int j = 0; j < S; ++j)
+            if (Q) Q[i * S + j] = q[(size_t)i * Sp + j];
+    }
+    if (dq)
+        for (int k = 0; k < M.n_dq; ++k)
+            for (int i = 0; i < S; ++i)
+                for (int j = 0; j < S; ++j)
+                    dq[((size_t)k * S + i) * S + j] = d[((size_t)k * Sp + i) * Sp + j];
+    if (n_dq) *n_dq = M.n_dq;
+    return TL_OK;
+}
+
+int tl_update_matrices(tl_instance* inst, int model, const int* p_idx, const int* dp_idx,
+                       const double* edge_len, int count) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (model < 0 || model >= I->n_models) return fail(I, TL_ERR_INDEX, "model %d out of range", model);
+    if (!I->models[model].ready) return fail(I, TL_ERR_STATE, "model %d not set", model);
+    if (count < 0 || (count > 0 && (!p_idx || !edge_len))) return fail(I, TL_ERR_ARG, "bad arguments");
+    for (int i = 0; i < count; ++i) {
+        if (p_idx[i] < 0 || p_idx[i] >= I->n_mats)
+            return fail(I, TL_ERR_INDEX, "p_idx[%d]=%d out of range", i, p_idx[i]);
+        if (dp_idx && (dp_idx[i] < -1 || dp_idx[i] >= I->n_mats))
+            return fail(I, TL_ERR_INDEX, "dp_idx[%d]=%d out of range", i, dp_idx[i]);
+        if (!std::isfinite(edge_len[i]) || edge_len[i] < 0)
+            return fail(I, TL_ERR_NUMERIC, "edge_len[%d] is negative or not finite", i);
+    }
+    // staging: rates [R] | lengths [count] in d_tmp; indices in d_ops area 3
+    if ((size_t)(I->R + count) > I->tmp_cap) {
+        cudaStreamSynchronize(I->stream);
+        cudaFree(I->d_tmp);
+        I->tmp_cap = I->R + count + 1024;
+        int rc = dev_alloc(I, &I->d_tmp, sizeof(double) * I->tmp_cap, "staging");
+        if (rc) return rc;
+    }
+    int rc = stage(I, I->h_rates, I->R, edge_len, count);
+    if (rc) return rc;
+    std::vector<int> idx(2 * (size_t)count);
+    for (int i = 0; i < count; ++i) {
+        idx[i] = p_idx[i];
+        idx[count + i] = dp_idx ? dp_idx[i] : -1;
+    }
+    void* d_idx = nullptr;
+    Extra& X = extra(I);
+    if ((rc = upload(I, X.areas[3], idx.data(), sizeof(int) * idx.size(), &d_idx))) return rc;
+    rc = launch_update_matrices(I, model, (const int*)d_idx, (const int*)d_idx + count,
+                                I->d_tmp + I->R, count);
+    if (rc) return rc;
+    for (int i = 0; i < count; ++i) {
+        I->mat_set[p_idx[i]] = 1;
+        if (dp_idx && dp_idx[i] >= 0) I->mat_set[dp_idx[i]] = 1;
+    }
+    return TL_OK;
+}
+
+int tl_get_matrix(tl_instance* inst, int mat, double* out) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (mat < 0 || mat >= I->n_mats) return fail(I, TL_ERR_INDEX, "matrix %d out of range", mat);
+    if (!out) return fail(I, TL_ERR_ARG, "out is null");
+    const int S = I->S, Sp = I->Spad;
+    std::vector<double> h((size_t)I->R * Sp * Sp);
+    cudaMemcpyAsync(h.data(), I->d_mat64 + (size_t)mat * I->R * Sp * Sp, sizeof(double) * h.size(),
+                    cudaMemcpyDeviceToHost, I->stream);
+    int rc = cuda_check(I, cudaStreamSynchronize(I->stream), "tl_get_matrix");
+    if (rc) return rc;
+    for (int r = 0; r < I->R; ++r)
+        for (int i = 0; i < S; ++i)
+            for (int j = 0; j < S; ++j)
+                out[((size_t)r * S + i) * S + j] = h[((size_t)r * Sp + i) * Sp + j];
+    return TL_OK;
+}
+
+int tl_get_partials(tl_instance* inst, int buf, double* out, int32_t* exponents) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (buf < 0 || buf >= I->n_bufs) return fail(I, TL_ERR_INDEX, "buffer %d out of range", buf);
+    if (!out) return fail(I, TL_ERR_ARG, "out is null");
+    if (!I->h_buf[buf]) return fail(I, TL_ERR_STATE, "buffer %d holds tip states, not partials", buf);
+    const size_t n = (size_t)I->R * I->Ppad * I->Spad;
+    std::vector<char> h(n * I->elt);
+    std::vector<int> e(I->Ppad, 0);
+    cudaMemcpyAsync(h.data(), I->h_buf[buf], h.size(), cudaMemcpyDeviceToHost, I->stream);
+    if (I->h_scale[buf])
+        cudaMemcpyAsync(e.data(), I->h_scale[buf], sizeof(int) * I->Ppad, cudaMemcpyDeviceToHost, I->stream);
+    int rc = cuda_check(I, cudaStreamSynchronize(I->stream), "tl_get_partials");
+    if (rc) return rc;
+    for (int r = 0; r < I->R; ++r)
+        for (int p = 0; p < I->P; ++p)
+            for (int s = 0; s < I->S; ++s) {
+                size_t src = ((size_t)r * I->Ppad + p) * I->Spad + s;
+                out[((size_t)r * I->P + p) * I->S + s] =
+                    I->elt == 8 ? reinterpret_cast<double*>(h.data())[src]
+                                : (double)reinterpret_cast<float*>(h.data())[src];
+            }
+    if (exponents)
+        for (int p = 0; p < I->P; ++p) exponents[p] = e[p];
+    return TL_OK;
+}
+
+int tl_update_partials(tl_instance* inst, const tl_op* ops, int count) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (count < 0 || (count > 0 && !ops)) return fail(I, TL_ERR_ARG, "bad op list");
+    if (count == 0) return TL_OK;
+    int rc;
+    if (use_nuc(I)) {
+        PostPlan plan;
+        if ((rc = plan_post(I, ops, count, &plan, false))) return rc;
+        void* d_ops = nullptr;
+        if ((rc = upload(I, extra(I).areas[0], plan.dev.data(), sizeof(DevPostOp) * count, &d_ops)))
+            return rc;
+        if ((rc = launch_post4(I, (const DevPostOp*)d_ops, count, plan.n_slots))) return rc;
+    } else {
+        PostPlan plan;
+        if ((rc = plan_post(I, ops, count, &plan, true))) return rc;
+        if ((rc = launch_post_generic(I, ops, count))) return rc;
+    }
+    for (int k = 0; k < count; ++k) I->buf_written[ops[k].dest - I->n_tips] = 1;
+    return TL_OK;
+}
+
+static int root_common(Instance* I, int root, int model, double* d_site, double* d_out) {
+    if (root < 0 || root >= I->n_bufs) return fail(I, TL_ERR_INDEX, "root %d out of range", root);
+    if (root >= I->n_tips ? !I->buf_written[root - I->n_tips] : !I->tip_set[root])
+        return fail(I, TL_ERR_STATE, "root buffer %d holds no data", root);
+    if (model < 0 || model >= I->n_models || !I->models[model].ready)
+        return fail(I, TL_ERR_STATE, "model %d not set", model);
+    int rc;
+    if (use_nuc(I)) {
+        const int n_tiles = I->Ppad / kTile;
+        if ((rc = ensure_scratch(I, n_tiles))) return rc;
+        if ((rc = launch_root4(I, root, model, d_site, I->d_red, n_tiles))) return rc;
+        return reduce_fixed(I, I->d_red, 1, n_tiles, d_out);
+    }
+    const int parts = (I->Ppad + 127) / 128;
+    if ((rc = ensure_scratch(I, parts))) return rc;
+    if ((rc = launch_root_generic(I, root, model, d_site, I->d_red, parts))) return rc;
+    return reduce_fixed(I, I->d_red, 1, parts, d_out);
+}
+
+int tl_root_loglik(tl_instance* inst, int root, int model, double* out_logl, double* out_site) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (!out_logl) return fail(I, TL_ERR_ARG, "out_logl is null");
+    int rc;
+    if ((rc = ensure_out(I, 1 + (size_t)I->Ppad))) return rc;
+    double* d_out = extra(I).d_out;
+    double* d_site = out_site ? d_out + 1 : nullptr;
+    if ((rc = root_common(I, root, model, d_site, d_out))) return rc;
+    cudaMemcpyAsync(out_logl, d_out, sizeof(double), cudaMemcpyDeviceToHost, I->stream);
+    if (out_site)
+        cudaMemcpyAsync(out_site, d_site, sizeof(double) * I->P, cudaMemcpyDeviceToHost, I->stream);
+    if ((rc = cuda_check(I, cudaStreamSynchronize(I->stream), "tl_root_loglik"))) return rc;
+    return check_numeric_flag(I);
+}
+
+int tl_root_loglik_dev(tl_instance* inst, int root, int model, double* out_logl_dev) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (!out_logl_dev) return fail(I, TL_ERR_ARG, "out is null");
+    return root_common(I, root, model, nullptr, out_logl_dev);
+}
+
+static int pre_common(Instance* I, const tl_pre_op* ops, int count, int model, int n_grad,
+                      bool store_all, double* d_grad_out) {
+    if (count < 0 || (count > 0 && !ops)) return fail(I, TL_ERR_ARG, "bad op list");
+    if (model < 0 || model >= I->n_models || !I->models[model].ready)
+        return fail(I, TL_ERR_STATE, "model %d not set", model);
+    if (n_grad < 0) return fail(I, TL_ERR_ARG, "n_grad < 0");
+    PrePlan plan;
+    int rc = plan_pre(I, ops, count, n_grad, store_all, &plan);
+    if (rc) return rc;
+    const int E = (int)plan.edge_map.size();
+    if (use_nuc(I)) {
+        const int n_tiles = I->Ppad / kTile;
+        if ((rc = ensure_scratch(I, (size_t)std::max(E, 1) * n_tiles))) return rc;
+        void* d_ops = nullptr;
+        if ((rc = upload(I, extra(I).areas[1], plan.dev.data(), sizeof(DevPreOp) * count, &d_ops)))
+            return rc;
+        if ((rc = launch_pre4(I, (const DevPreOp*)d_ops, count, plan.n_slots, model, I->d_red, n_tiles)))
+            return rc;
+        if ((rc = ensure_out(I, (size_t)E))) return rc;
+        if ((rc = reduce_fixed(I, I->d_red, E, n_tiles, extra(I).d_out))) return rc;
+    } else {
+        // generic path: q partials always go through buffers; ops whose q
+        // output is consumed but unnamed are rejected by plan_pre (pre >= 0
+        // is required to name a consumed q).
+        const int parts = generic_parts(I);
+        if ((rc = ensure_scratch(I, (size_t)std::max(E, 1) * parts))) return rc;
+        std::vector<tl_pre_op> g(ops, ops + count);
+        std::vector<int> row(std::max(n_grad, 1), -1);
+        for (int k = 0; k < E; ++k) row[plan.edge_map[k]] = k;
+        for (auto& o : g)
+            for (int c = 0; c < 2; ++c) o.edge[c] = o.edge[c] >= 0 ? row[o.edge[c]] : -1;
+        if ((rc = launch_pre_generic(I, g.data(), count, model, I->d_red, parts))) return rc;
+        if ((rc = ensure_out(I, (size_t)E))) return rc;
+        if ((rc = reduce_fixed(I, I->d_red, E, parts, extra(I).d_out))) return rc;
+    }
+    for (int k = 0; k < count; ++k)
+        for (int c = 0; c < 2; ++c)
+            if (ops[k].pre[c] >= 0 && (store_all || !use_nuc(I)))
+                I->buf_written[ops[k].pre[c] - I->n_tips] = 1;
+    if (d_grad_out && n_grad > 0) {
+        void* d_map = nullptr;
+        if (E > 0 && (rc = upload(I, extra(I).areas[4], plan.edge_map.data(), sizeof(int) * E, &d_map)))
+            return rc;
+        k_scatter<<<1, 256, 0, I->stream>>>(extra(I).d_out, (const int*)d_map, E, d_grad_out, n_grad);
+        I->launches += 1;
+        if ((rc = cuda_check(I, cudaGetLastError(), "scatter"))) return rc;
+    }
+    return TL_OK;
+}
+
+int tl_update_pre_partials(tl_instance* inst, const tl_pre_op* ops, int count, int model) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    for (int k = 0; k < count; ++k)
+        for (int c = 0; c < 2; ++c)
+            if (ops[k].edge[c] >= 0)
+                return fail(I, TL_ERR_ARG, "tl_update_pre_partials takes no edges (use "
+                            "tl_pre_order_gradient)");
+    int rc = pre_common(I, ops, count, model, 0, true, nullptr);
+    if (rc) return rc;
+    return cuda_check(I, cudaStreamSynchronize(I->stream), "tl_update_pre_partials");
+}
+
+int tl_pre_order_gradient(tl_instance* inst, const tl_pre_op* ops, int count, int model,
+                          double* out_grad, int n_grad) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (!out_grad && n_grad > 0) return fail(I, TL_ERR_ARG, "out_grad is null");
+    int rc;
+    if ((rc = ensure_out(I, (size_t)2 * std::max(n_grad, 1) + 16))) return rc;
+    double* d_g = extra(I).d_out + std::max(n_grad, 1) + 8;
+    if ((rc = pre_common(I, ops, count, model, n_grad, false, d_g))) return rc;
+    if (n_grad > 0)
+        cudaMemcpyAsync(out_grad, d_g, sizeof(double) * n_grad, cudaMemcpyDeviceToHost, I->stream);
+    return cuda_check(I, cudaStreamSynchronize(I->stream), "tl_pre_order_gradient");
+}
+
+int tl_pre_order_gradient_dev(tl_instance* inst, const tl_pre_op* ops, int count, int model,
+                              double* out_grad_dev, int n_grad) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (!out_grad_dev && n_grad > 0) return fail(I, TL_ERR_ARG, "out_grad_dev is null");
+    return pre_common(I, ops, count, model, n_grad, false, out_grad_dev);
+}
+
+int tl_edge_derivatives(tl_instance* inst, const tl_edge* edges, int count, int model,
+                        double* out_grad, int n_grad) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (count < 0 || (count > 0 && !edges) || (n_grad > 0 && !out_grad))
+        return fail(I, TL_ERR_ARG, "bad arguments");
+    if (model < 0 || model >= I->n_models || !I->models[model].ready)
+        return fail(I, TL_ERR_STATE, "model %d not set", model);
+    std::vector<int> row(std::max(n_grad, 1), -1), map;
+    std::vector<tl_edge> e(edges, edges + count);
+    for (int k = 0; k < count; ++k) {
+        const tl_edge& x = edges[k];
+        if (x.post < 0 || x.post >= I->n_bufs || x.pre < I->n_tips || x.pre >= I->n_bufs)
+            return fail(I, TL_ERR_INDEX, "edge %d: buffer out of range", k);
+        if (x.post < I->n_tips ? !I->tip_set[x.post] : !I->buf_written[x.post - I->n_tips])
+            return fail(I, TL_ERR_STATE, "edge %d: post buffer holds no data", k);
+        if (!I->buf_written[x.pre - I->n_tips])
+            return fail(I, TL_ERR_STATE, "edge %d: pre buffer holds no data", k);
+        if (x.edge < 0 || x.edge >= n_grad) return fail(I, TL_ERR_INDEX, "edge %d: slot out of range", k);
+        if (row[x.edge] >= 0) return fail(I, TL_ERR_ORDER, "edge slot %d requested twice", x.edge);
+        row[x.edge] = (int)map.size();
+        map.push_back(x.edge);
+        e[k].edge = row[x.edge];
+    }
+    const int E = (int)map.size();
+    int rc;
+    int parts;
+    if (use_nuc(I)) {
+        parts = I->Ppad / kTile;
+        if ((rc = ensure_scratch(I, (size_t)std::max(E, 1) * parts))) return rc;
+        std::vector<DevEdge> d(count);
+        for (int k = 0; k < count; ++k) d[k] = {e[k].post, e[k].pre, e[k].edge, 0};
+        void* d_e = nullptr;
+        if ((rc = upload(I, extra(I).areas[2], d.data(), sizeof(DevEdge) * count, &d_e))) return rc;
+        if ((rc = launch_edge4(I, (const DevEdge*)d_e, count, model, I->d_red, parts))) return rc;
+    } else {
+        parts = generic_parts(I);
+        if ((rc = ensure_scratch(I, (size_t)std::max(E, 1) * parts))) return rc;
+        if ((rc = launch_edge_generic(I, e.data(), count, model, I->d_red, parts))) return rc;
+    }
+    if ((rc = ensure_out(I, (size_t)E + 1))) return rc;
+    if ((rc = reduce_fixed(I, I->d_red, E, parts, extra(I).d_out))) return rc;
+    std::vector<double> h(std::max(E, 1));
+    if (E) cudaMemcpyAsync(h.data(), extra(I).d_out, sizeof(double) * E, cudaMemcpyDeviceToHost, I->stream);
+    if ((rc = cuda_check(I, cudaStreamSynchronize(I->stream), "tl_edge_derivatives"))) return rc;
+    for (int i = 0; i < n_grad; ++i) out_grad[i] = 0.0;
+    for (int k = 0; k < E; ++k) out_grad[map[k]] = h[k];
+    return TL_OK;
+}
+
+}  // extern "C"

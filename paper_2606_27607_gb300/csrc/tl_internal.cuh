@@ -1,0 +1,176 @@
+// Internal declarations of the treelik library (device structs, instance
+// state and the launchers each translation unit exports).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "treelik.h"
+
+namespace tl {
+
+// Patterns handled by one warp in the four-state kernels: one lane per
+// pattern, all categories in registers.
+constexpr int kTile = 32;
+constexpr int kWarpsPerBlock = 4;
+constexpr int kMaxCat = 8;
+constexpr int kMaxStates = 64;
+constexpr int kMaxDq = 8;      // dQ/dtheta matrices kept per model
+constexpr int kColStride = 5;  // four-state matrices: 4 columns + row sums
+
+enum Prec { kF64 = 0, kF32 = 1, kTF32 = 2, kBF16X3 = 3 };
+
+// One post-order op as the device walks it.
+struct DevPostOp {
+    int dest;
+    int child[2];
+    int mat[2];
+    int slot_in[2];  // on-chip slot holding the child (-1: read memory)
+    int slot_out;    // on-chip slot receiving dest (-1: none)
+    int store;       // 1: write dest to its buffer
+};
+
+// One pre-order op (one parent, both children) as the device walks it.
+struct DevPreOp {
+    int q_slot_in;   // -2: root (pi), -1: read q_buf_in, >= 0: slot
+    int q_buf_in;
+    int child[2];
+    int mat[2];
+    int dmat[2];
+    int q_slot_out[2];
+    int q_buf_out[2];
+    int edge[2];
+    int need_q[2];
+    int pad;
+};
+
+struct DevEdge {
+    int post;
+    int pre;
+    int edge;
+    int pad;
+};
+
+// Kernel arguments shared by the pattern-parallel kernels. Pointer tables
+// live in device memory; everything else is passed by value.
+template <typename T>
+struct PathArgs {
+    T* const* buf;                  // [n_bufs] partials (null: tip with states)
+    int* const* scale;              // [n_bufs] accumulated exponents (null: none)
+    const int8_t* const* tipst;     // [n_tips] tip states (null: tip partials)
+    const T* mat;                   // working-precision matrices
+    const double* patw;             // [Ppad] pattern weights (0 on padding)
+    int n_tips;
+    int P;                          // real patterns
+    int Ppad;                       // padded patterns
+    int R;
+    int S;                          // states (real)
+    int Spad;                       // stored states
+    int n_slots;                    // on-chip slots per warp
+    int rescale;
+    int mat_stride;                 // elements per matrix slot
+    T catw[kMaxCat];
+    T rates[kMaxCat];
+};
+
+struct ModelDev {
+    double* Q = nullptr;      // [Spad][Spad]
+    double* pi = nullptr;     // [Spad]
+    double* V = nullptr;      // [Spad][Spad]
+    double* Vinv = nullptr;   // [Spad][Spad]
+    double* lam = nullptr;    // [Spad]
+    double* dQ = nullptr;     // [kMaxDq][Spad][Spad]
+    void* piw = nullptr;      // pi in working precision [Spad]
+    void* Qw = nullptr;       // Q in working precision [Spad][Spad]
+    int n_dq = 0;
+    bool ready = false;
+};
+
+struct Instance {
+    int n_tips = 0, P = 0, Ppad = 0, S = 0, Spad = 0, R = 0;
+    int n_buffers = 0, n_mats = 0, n_models = 0;
+    int n_bufs = 0;  // n_tips + n_buffers
+    unsigned flags = 0;
+    Prec prec = kF64;
+    int elt = 8;      // bytes per stored partial element
+    int rescale = 1;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int smem_optin = 0;
+
+    // device memory
+    void* pool = nullptr;            // internal partials
+    int* scale_pool = nullptr;       // [n_buffers][Ppad]
+    std::vector<void*> tip_part;     // per-tip partials allocations
+    int8_t* tip_pool = nullptr;      // [n_tips][Ppad] tip states (pad: ambiguous)
+    void** d_buf = nullptr;          // device table [n_bufs]
+    int** d_scale = nullptr;         // device table [n_bufs]
+    int8_t** d_tipst = nullptr;      // device table [n_tips]
+    std::vector<void*> h_buf;        // host mirrors
+    std::vector<int*> h_scale;
+    std::vector<int8_t*> h_tipst;
+    std::vector<char> tip_set;       // 0 unset, 1 states, 2 partials
+    std::vector<char> buf_written;   // internal buffer holds post data
+    double* d_patw = nullptr;
+    double* h_catw = nullptr;        // host copies [kMaxCat]
+    double* h_rates = nullptr;
+    double* d_mat64 = nullptr;       // FP64 master matrices [n_mats][R][Spad][Spad]
+    void* d_matw = nullptr;          // working copies
+    size_t matw_stride = 0;          // elements per matrix slot in d_matw
+    std::vector<char> mat_set;
+    std::vector<ModelDev> models;
+
+    // scratch
+    double* d_red = nullptr;         // reduction partials
+    size_t red_cap = 0;              // doubles
+    int* d_err = nullptr;            // device error flags [4]
+    void* d_ops = nullptr;           // op list upload area
+    size_t ops_cap = 0;              // bytes
+    std::vector<char> last_ops;      // bytes last uploaded (skip identical uploads)
+    double* d_tmp = nullptr;         // small staging (params, lengths)
+    size_t tmp_cap = 0;
+    void* host_extra = nullptr;      // host-side helper state (tl_api.cu)
+
+    size_t bytes = 0;
+    unsigned long long launches = 0; // kernels this instance has launched
+    std::string err;
+};
+
+// ---- launchers (one translation unit each) --------------------------------
+// tl_model.cu
+int launch_build_model(Instance* I, int m, int kind, const double* d_params, int n_params,
+                       const double* d_freqs, int n_freqs, bool check);
+int launch_eigen_from_q(Instance* I, int m, bool check);  // Q, pi already in the slot
+int launch_q_from_eigen(Instance* I, int m);  // V, Vinv, lambda already in the slot
+int launch_model_working_copies(Instance* I, int m);
+int launch_update_matrices(Instance* I, int m, const int* d_pidx, const int* d_dpidx,
+                           const double* d_len, int count);
+
+// tl_nuc.cu (four-state pattern-tile kernels, T = float or double)
+int launch_post4(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots);
+int launch_root4(Instance* I, int root, int model, double* d_site, double* d_part, int n_tiles);
+int launch_pre4(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, int model,
+                double* d_gpart, int n_tiles);
+int launch_edge4(Instance* I, const DevEdge* d_edges, int n_edges, int model, double* d_gpart,
+                 int n_tiles);
+int nuc_smem_per_slot(const Instance* I);
+
+// tl_generic.cu (FP64, any S)
+int launch_post_generic(Instance* I, const tl_op* h_ops, int n_ops);
+int launch_root_generic(Instance* I, int root, int model, double* d_site, double* d_part,
+                        int n_parts);
+int launch_pre_generic(Instance* I, const tl_pre_op* h_ops, int n_ops, int model,
+                       double* d_gpart, int n_parts);
+int launch_edge_generic(Instance* I, const tl_edge* h_edges, int n_edges, int model,
+                        double* d_gpart, int n_parts);
+int generic_parts(const Instance* I);
+
+// tl_api.cu helpers used by the other units
+int fail(Instance* I, int code, const char* fmt, ...);
+int cuda_check(Instance* I, cudaError_t e, const char* what);
+int reduce_fixed(Instance* I, const double* d_in, int n_out, int n_in, double* d_out);
+
+}  // namespace tl

@@ -1,0 +1,495 @@
+// Rate matrices, their FP64 eigensystems and the transition matrices.
+//
+// The paper computes transition probability matrices from a numerical
+// eigendecomposition of the instantaneous rate matrix and caches them for
+// reuse across site patterns (Sec. "Discussion"). Here every step runs on the
+// device in FP64: Q is built from the model parameters and normalised to one
+// expected substitution per unit time, the reversible Q is symmetrised as
+// D^1/2 Q D^-1/2 (D = diag(pi)) and diagonalised by cyclic Jacobi rotations
+// in a round-robin (tournament) order, and P_r(t) = V diag(exp(lambda rho_r t))
+// Vinv and dP_r/dt = V diag(rho_r lambda exp(lambda rho_r t)) Vinv are formed
+// per edge and category. Working-precision copies are laid out for the
+// kernels that consume them.
+#include <cmath>
+
+#include "tl_internal.cuh"
+
+namespace tl {
+
+// Standard genetic code, first/second/third base in A,C,G,T order; '*' marks
+// the stop codons.
+__constant__ char c_code_acgt[65] =
+    "KNKNTTTTRSRSIIMIQHQHPPPPRRRRLLLLEDEDAAAAGGGGVVVV*Y*YSSSS*CWCLFLF";
+
+__device__ __forceinline__ bool is_transition(int x, int y) {
+    return (x == 0 && y == 2) || (x == 2 && y == 0) || (x == 1 && y == 3) || (x == 3 && y == 1);
+}
+
+// Build Q, pi and dQ/dtheta for one model slot. One block.
+__global__ void k_build_model(int kind, int S, int Spad, const double* __restrict__ params,
+                              const double* __restrict__ freqs, double* __restrict__ Q,
+                              double* __restrict__ pi, double* __restrict__ dQ, int n_dq,
+                              int* __restrict__ err) {
+    __shared__ int codon_nt[64];   // sense codon -> 16*n1 + 4*n2 + n3
+    __shared__ char codon_aa[64];
+    __shared__ double s_pi[64];
+    __shared__ double s_red[256];
+    __shared__ double s_mu[1 + kMaxDq];
+    const int t = threadIdx.x;
+    const int nt = blockDim.x;
+
+    if (t == 0) {
+        int k = 0;
+        for (int c = 0; c < 64; ++c) {
+            if (c_code_acgt[c] == '*') continue;
+            codon_nt[k] = c;
+            codon_aa[k] = c_code_acgt[c];
+            ++k;
+        }
+    }
+    __syncthreads();
+    // stationary frequencies
+    if (kind == TL_MODEL_GY94) {
+        for (int i = t; i < 61; i += nt) {
+            int c = codon_nt[i];
+            s_pi[i] = freqs[c >> 4] * freqs[4 + ((c >> 2) & 3)] * freqs[8 + (c & 3)];
+        }
+        __syncthreads();
+        if (t == 0) {
+            double z = 0;
+            for (int i = 0; i < 61; ++i) z += s_pi[i];
+            for (int i = 0; i < 61; ++i) s_pi[i] /= z;
+        }
+    } else {
+        for (int i = t; i < S; i += nt) s_pi[i] = freqs[i];
+    }
+    __syncthreads();
+    for (int i = t; i < Spad; i += nt) pi[i] = i < S ? s_pi[i] : 0.0;
+
+    // off-diagonal rates R_ij = s_ij pi_j and their parameter derivatives
+    for (int idx = t; idx < Spad * Spad; idx += nt) {
+        int i = idx / Spad, j = idx % Spad;
+        double r = 0.0;
+        double d[kMaxDq];
+        for (int k = 0; k < kMaxDq; ++k) d[k] = 0.0;
+        if (i < S && j < S && i != j) {
+            if (kind == TL_MODEL_HKY) {
+                bool ts = is_transition(i, j);
+                r = (ts ? params[0] : 1.0) * s_pi[j];
+                d[0] = ts ? s_pi[j] : 0.0;
+            } else if (kind == TL_MODEL_GTR) {
+                int a = min(i, j), b = max(i, j);
+                // pair order AC AG AT CG CT GT
+                int k = (a == 0) ? (b - 1) : (a == 1 ? (b + 1) : 5);
+                r = params[k] * s_pi[j];
+                d[k] = s_pi[j];
+            } else if (kind == TL_MODEL_GY94) {
+                int ci = codon_nt[i], cj = codon_nt[j];
+                int ndiff = 0, pos = -1;
+                for (int q = 0; q < 3; ++q) {
+                    int sh = 4 - 2 * q;
+                    if (((ci >> sh) & 3) != ((cj >> sh) & 3)) {
+                        ++ndiff;
+                        pos = sh;
+                    }
+                }
+                if (ndiff == 1) {
+                    bool ts = is_transition((ci >> pos) & 3, (cj >> pos) & 3);
+                    bool ns = codon_aa[i] != codon_aa[j];
+                    double kap = ts ? params[0] : 1.0;
+                    double om = ns ? params[1] : 1.0;
+                    r = kap * om * s_pi[j];
+                    d[0] = (ts ? 1.0 : 0.0) * om * s_pi[j];
+                    d[1] = kap * (ns ? 1.0 : 0.0) * s_pi[j];
+                }
+            } else {  // TL_MODEL_REV
+                r = 0.5 * (params[i * S + j] + params[j * S + i]) * s_pi[j];
+            }
+        }
+        Q[idx] = r;
+        for (int k = 0; k < n_dq; ++k) dQ[(size_t)k * Spad * Spad + idx] = d[k];
+    }
+    __syncthreads();
+    // diagonals (row sums) of R and of each dR
+    for (int i = t; i < S; i += nt) {
+        double acc = 0;
+        for (int j = 0; j < S; ++j)
+            if (j != i) acc += Q[i * Spad + j];
+        Q[i * Spad + i] = -acc;
+        for (int k = 0; k < n_dq; ++k) {
+            double* D = dQ + (size_t)k * Spad * Spad;
+            double a2 = 0;
+            for (int j = 0; j < S; ++j)
+                if (j != i) a2 += D[i * Spad + j];
+            D[i * Spad + i] = -a2;
+        }
+    }
+    __syncthreads();
+    // normalisers mu = -sum pi_i R_ii and dmu_k
+    for (int k = 0; k <= n_dq; ++k) {
+        const double* M = (k == 0) ? Q : dQ + (size_t)(k - 1) * Spad * Spad;
+        double acc = 0;
+        for (int i = t; i < S; i += nt) acc -= s_pi[i] * M[i * Spad + i];
+        s_red[t] = acc;
+        __syncthreads();
+        for (int w = nt / 2; w > 0; w >>= 1) {
+            if (t < w) s_red[t] += s_red[t + w];
+            __syncthreads();
+        }
+        if (t == 0) s_mu[k] = s_red[0];
+        __syncthreads();
+    }
+    const double mu = s_mu[0];
+    if (t == 0 && !(mu > 0.0 && isfinite(mu))) err[0] = 1;
+    for (int idx = t; idx < Spad * Spad; idx += nt) {
+        double r = Q[idx];
+        for (int k = 0; k < n_dq; ++k) {
+            double* D = dQ + (size_t)k * Spad * Spad;
+            D[idx] = D[idx] / mu - r * s_mu[k + 1] / (mu * mu);
+        }
+        Q[idx] = r / mu;
+    }
+}
+
+// Jacobi eigensystem of the symmetrised reversible Q. One block; A and U in
+// shared memory ([64][65] doubles each).
+__global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
+                        const double* __restrict__ pi, double* __restrict__ V,
+                        double* __restrict__ Vinv, double* __restrict__ lam,
+                        int* __restrict__ err) {
+    extern __shared__ double sm[];
+    constexpr int LD = 65;
+    double* A = sm;
+    double* U = sm + 64 * LD;
+    __shared__ double s_sq[64];
+    __shared__ double s_c[32], s_s[32];
+    __shared__ int s_p[32], s_q[32];
+    __shared__ double s_red[256];
+    __shared__ int s_done, s_conv;
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int n = S;
+    const int m = (n + 1) & ~1;  // players in the tournament (one dummy if n odd)
+
+    for (int i = t; i < n; i += nt) {
+        double p = pi[i];
+        s_sq[i] = sqrt(p);
+        if (!(p > 0.0)) err[0] = 2;
+    }
+    __syncthreads();
+    for (int idx = t; idx < n * n; idx += nt) {
+        int i = idx / n, j = idx % n;
+        // symmetrise: (D^1/2 Q D^-1/2 + transpose) / 2
+        double a = s_sq[i] * Q[i * Spad + j] / s_sq[j];
+        double b = s_sq[j] * Q[j * Spad + i] / s_sq[i];
+        A[i * LD + j] = 0.5 * (a + b);
+        U[i * LD + j] = (i == j) ? 1.0 : 0.0;
+    }
+    if (t == 0) {
+        s_done = 0;
+        s_conv = 0;
+    }
+    __syncthreads();
+
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        for (int round = 0; round < m - 1; ++round) {
+            if (t < m / 2) {
+                int a = t, b = m - 1 - t;
+                int pa = (a == 0) ? 0 : ((a - 1 + round) % (m - 1)) + 1;
+                int pb = (b == 0) ? 0 : ((b - 1 + round) % (m - 1)) + 1;
+                int p = min(pa, pb), q = max(pa, pb);
+                double c = 1.0, s = 0.0;
+                if (q < n) {
+                    double apq = A[p * LD + q];
+                    if (fabs(apq) > 1e-300) {
+                        double theta = (A[q * LD + q] - A[p * LD + p]) / (2.0 * apq);
+                        double tt = 1.0 / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        if (theta < 0) tt = -tt;
+                        c = 1.0 / sqrt(tt * tt + 1.0);
+                        s = tt * c;
+                    }
+                } else {
+                    p = q = -1;
+                }
+                s_c[t] = c;
+                s_s[t] = s;
+                s_p[t] = p;
+                s_q[t] = q;
+            }
+            __syncthreads();
+            // rows: A <- J^T A
+            for (int idx = t; idx < (m / 2) * n; idx += nt) {
+                int k = idx / n, j = idx % n;
+                int p = s_p[k], q = s_q[k];
+                if (p < 0 || s_s[k] == 0.0) continue;
+                double c = s_c[k], s = s_s[k];
+                double ap = A[p * LD + j], aq = A[q * LD + j];
+                A[p * LD + j] = c * ap - s * aq;
+                A[q * LD + j] = s * ap + c * aq;
+            }
+            __syncthreads();
+            // columns: A <- A J, U <- U J
+            for (int idx = t; idx < (m / 2) * n; idx += nt) {
+                int k = idx / n, i = idx % n;
+                int p = s_p[k], q = s_q[k];
+                if (p < 0 || s_s[k] == 0.0) continue;
+                double c = s_c[k], s = s_s[k];
+                double ap = A[i * LD + p], aq = A[i * LD + q];
+                A[i * LD + p] = c * ap - s * aq;
+                A[i * LD + q] = s * ap + c * aq;
+                double up = U[i * LD + p], uq = U[i * LD + q];
+                U[i * LD + p] = c * up - s * uq;
+                U[i * LD + q] = s * up + c * uq;
+            }
+            __syncthreads();
+        }
+        // convergence: off-diagonal mass relative to the diagonal
+        double off = 0, dg = 0;
+        for (int idx = t; idx < n * n; idx += nt) {
+            int i = idx / n, j = idx % n;
+            double a = A[i * LD + j];
+            if (i == j) dg += a * a;
+            else off += a * a;
+        }
+        s_red[t] = off;
+        __syncthreads();
+        for (int w = nt / 2; w > 0; w >>= 1) {
+            if (t < w) s_red[t] += s_red[t + w];
+            __syncthreads();
+        }
+        double offs = s_red[0];
+        __syncthreads();
+        s_red[t] = dg;
+        __syncthreads();
+        for (int w = nt / 2; w > 0; w >>= 1) {
+            if (t < w) s_red[t] += s_red[t + w];
+            __syncthreads();
+        }
+        // stop one sweep after the off-diagonal norm falls below 1e-15 of the
+        // diagonal norm (a rotation sweep then leaves it at rounding level)
+        if (t == 0) {
+            if (offs <= 1e-30 * s_red[0]) s_done += 1;
+            s_conv = offs <= 1e-24 * s_red[0];
+        }
+        __syncthreads();
+        if (s_done >= 2) break;
+    }
+    if (t == 0 && !s_conv) err[0] = 3;
+    for (int idx = t; idx < Spad * Spad; idx += nt) {
+        int i = idx / Spad, k = idx % Spad;
+        double v = 0, vi = 0;
+        if (i < n && k < n) {
+            v = U[i * LD + k] / s_sq[i];   // V = D^-1/2 U
+            vi = U[k * LD + i] * s_sq[k];  // Vinv[i][k] = U[k][i] sqrt(pi_k)
+        }
+        V[idx] = v;
+        Vinv[idx] = vi;
+    }
+    for (int i = t; i < Spad; i += nt) lam[i] = (i < n) ? A[i * LD + i] : 0.0;
+}
+
+__device__ __forceinline__ float round_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Working-precision copies of pi and Q.
+template <typename T>
+__global__ void k_model_working(int S, int Spad, const double* __restrict__ Q,
+                                const double* __restrict__ pi, T* __restrict__ Qw,
+                                T* __restrict__ piw, int tf32) {
+    for (int idx = threadIdx.x; idx < Spad * Spad; idx += blockDim.x) {
+        T v = (T)Q[idx];
+        Qw[idx] = v;
+    }
+    for (int i = threadIdx.x; i < Spad; i += blockDim.x) piw[i] = (T)pi[i];
+    (void)S;
+    (void)tf32;
+}
+
+// P and dP/dt for `count` edges; grid (count, R).
+//  layout 0: four-state column layout [R][5][4] of T: column j of P, then row sums
+//  layout 1: FP64 transposed layout [R][Spad+1][Spad]: W[j][i] = P[i][j], row Spad = row sums
+//  layout 2: TF32 row-major [R][Spad][Spad] floats (rounded) + row sums [R][Spad]
+template <typename T>
+__global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
+                      const double* __restrict__ Vinv, const double* __restrict__ lam,
+                      const int* __restrict__ pidx, const int* __restrict__ dpidx,
+                      const double* __restrict__ len, const double* __restrict__ rates,
+                      double* __restrict__ mat64, T* __restrict__ matw, size_t matw_stride,
+                      int layout) {
+    extern __shared__ double sm_tpm[];
+    double* e = sm_tpm;              // [Spad]
+    double* de = sm_tpm + 64;        // [Spad]
+    double* Pm = sm_tpm + 128;       // [Spad*Spad] this matrix (for working copies)
+    const int b = blockIdx.x, r = blockIdx.y;
+    const int t = threadIdx.x, nt = blockDim.x;
+    const double rt = rates[r] * len[b];
+    // P = I + V diag(expm1(lambda rho t)) Vinv keeps short branches accurate
+    // (the eigen sum then carries only the O(t) part); dP/dt has no identity.
+    for (int k = t; k < Spad; k += nt) {
+        e[k] = (k < S) ? expm1(lam[k] * rt) : 0.0;
+        de[k] = (k < S) ? rates[r] * lam[k] * exp(lam[k] * rt) : 0.0;
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        const int slot = (pass == 0) ? pidx[b] : (dpidx ? dpidx[b] : -1);
+        if (slot < 0) continue;
+        const double* ev = (pass == 0) ? e : de;
+        double* out = mat64 + ((size_t)slot * R + r) * Spad * Spad;
+        for (int idx = t; idx < Spad * Spad; idx += nt) {
+            int i = idx / Spad, j = idx % Spad;
+            double acc = 0.0;
+            if (i < S && j < S)
+                for (int k = 0; k < S; ++k) acc += V[i * Spad + k] * ev[k] * Vinv[k * Spad + j];
+            if (pass == 0 && i == j && i < S) acc += 1.0;
+            out[idx] = acc;
+            Pm[idx] = acc;
+        }
+        __syncthreads();
+        T* w = matw + (size_t)slot * matw_stride;
+        if (layout == 0) {
+            w += (size_t)r * kColStride * 4;
+            // the row-sum column (ambiguous tips) is summed in T in column
+            // order, exactly as a product with an all-ones partial rounds
+            for (int idx = t; idx < kColStride * 4; idx += nt) {
+                int j = idx / 4, i = idx % 4;
+                T v;
+                if (j < 4) {
+                    v = (T)Pm[i * Spad + j];
+                } else {
+                    v = (T)Pm[i * Spad];
+                    for (int q = 1; q < S; ++q) v = v + (T)Pm[i * Spad + q];
+                }
+                w[idx] = v;
+            }
+        } else if (layout == 1) {
+            w += (size_t)r * (Spad + 1) * Spad;
+            for (int idx = t; idx < (Spad + 1) * Spad; idx += nt) {
+                int j = idx / Spad, i = idx % Spad;
+                T v;
+                if (j < Spad) {
+                    v = (T)Pm[i * Spad + j];
+                } else {
+                    v = (T)Pm[i * Spad];
+                    for (int q = 1; q < S; ++q) v = v + (T)Pm[i * Spad + q];
+                }
+                w[idx] = v;
+            }
+        } else {
+            w += (size_t)r * (Spad + 1) * Spad;
+            for (int idx = t; idx < Spad * Spad; idx += nt) w[idx] = (T)round_tf32((float)Pm[idx]);
+            __syncthreads();
+            for (int i = t; i < Spad; i += nt) {
+                double v = 0.0;
+                for (int q = 0; q < S; ++q) v += (double)w[i * Spad + q];
+                w[Spad * Spad + i] = (T)v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Q = V diag(lambda) Vinv for a host-supplied eigensystem. One block.
+__global__ void k_q_from_eigen(int S, int Spad, const double* __restrict__ V,
+                               const double* __restrict__ Vinv, const double* __restrict__ lam,
+                               double* __restrict__ Q) {
+    for (int idx = threadIdx.x; idx < Spad * Spad; idx += blockDim.x) {
+        int i = idx / Spad, j = idx % Spad;
+        double acc = 0.0;
+        if (i < S && j < S)
+            for (int k = 0; k < S; ++k) acc += V[i * Spad + k] * lam[k] * Vinv[k * Spad + j];
+        Q[idx] = acc;
+    }
+}
+
+static int model_check_err(Instance* I, const char* what) {
+    int h_err = 0;
+    cudaError_t e = cudaMemcpyAsync(&h_err, I->d_err, sizeof(int), cudaMemcpyDeviceToHost, I->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
+    if (e != cudaSuccess) return cuda_check(I, e, what);
+    if (h_err) {
+        cudaMemsetAsync(I->d_err, 0, sizeof(int), I->stream);
+        return fail(I, TL_ERR_NUMERIC, "%s: device check %d failed (non-positive frequency, "
+                    "zero mean rate or Jacobi did not converge)", what, h_err);
+    }
+    return TL_OK;
+}
+
+int launch_build_model(Instance* I, int m, int kind, const double* d_params, int n_params,
+                       const double* d_freqs, int n_freqs, bool check) {
+    (void)n_params;
+    (void)n_freqs;
+    ModelDev& M = I->models[m];
+    int n_dq = kind == TL_MODEL_HKY ? 1 : kind == TL_MODEL_GTR ? 6 : kind == TL_MODEL_GY94 ? 2 : 0;
+    M.n_dq = n_dq;
+    k_build_model<<<1, 256, 0, I->stream>>>(kind, I->S, I->Spad, d_params, d_freqs, M.Q, M.pi,
+                                            M.dQ, n_dq, I->d_err);
+    I->launches += 1;
+    int rc = cuda_check(I, cudaGetLastError(), "build model");
+    if (rc) return rc;
+    if (check && (rc = model_check_err(I, "tl_set_model"))) return rc;
+    return launch_eigen_from_q(I, m, check);
+}
+
+int launch_eigen_from_q(Instance* I, int m, bool check) {
+    ModelDev& M = I->models[m];
+    const size_t smem = 2 * 64 * 65 * sizeof(double);
+    cudaFuncSetAttribute(k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_eigen<<<1, 256, smem, I->stream>>>(I->S, I->Spad, M.Q, M.pi, M.V, M.Vinv, M.lam, I->d_err);
+    I->launches += 1;
+    int rc = cuda_check(I, cudaGetLastError(), "eigen");
+    if (rc) return rc;
+    if (check && (rc = model_check_err(I, "eigendecomposition"))) return rc;
+    return launch_model_working_copies(I, m);
+}
+
+int launch_q_from_eigen(Instance* I, int m) {
+    ModelDev& M = I->models[m];
+    k_q_from_eigen<<<1, 256, 0, I->stream>>>(I->S, I->Spad, M.V, M.Vinv, M.lam, M.Q);
+    I->launches += 1;
+    return cuda_check(I, cudaGetLastError(), "Q from eigensystem");
+}
+
+int launch_model_working_copies(Instance* I, int m) {
+    ModelDev& M = I->models[m];
+    if (I->prec == kF64) {
+        k_model_working<double><<<1, 256, 0, I->stream>>>(I->S, I->Spad, M.Q, M.pi,
+                                                          (double*)M.Qw, (double*)M.piw, 0);
+    } else {
+        k_model_working<float><<<1, 256, 0, I->stream>>>(I->S, I->Spad, M.Q, M.pi,
+                                                         (float*)M.Qw, (float*)M.piw,
+                                                         I->prec == kTF32);
+    }
+    I->launches += 1;
+    int rc = cuda_check(I, cudaGetLastError(), "model working copies");
+    if (rc) return rc;
+    M.ready = true;
+    return TL_OK;
+}
+
+int launch_update_matrices(Instance* I, int m, const int* d_pidx, const int* d_dpidx,
+                           const double* d_len, int count) {
+    if (count <= 0) return TL_OK;
+    ModelDev& M = I->models[m];
+    const double* d_rates = I->d_tmp;  // rates staged by the caller at d_tmp[0..R)
+    dim3 grid(count, I->R);
+    size_t smem = (128 + (size_t)I->Spad * I->Spad) * sizeof(double);
+    int layout = (I->S == 4 && (I->prec == kF32 || I->prec == kF64)) ? 0
+                 : (I->prec == kF64 ? 1 : 2);
+    if (I->prec == kF64) {
+        cudaFuncSetAttribute(k_tpm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        k_tpm<double><<<grid, 256, smem, I->stream>>>(I->S, I->Spad, I->R, M.V, M.Vinv, M.lam,
+                                                      d_pidx, d_dpidx, d_len, d_rates, I->d_mat64,
+                                                      (double*)I->d_matw, I->matw_stride, layout);
+    } else {
+        cudaFuncSetAttribute(k_tpm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        k_tpm<float><<<grid, 256, smem, I->stream>>>(I->S, I->Spad, I->R, M.V, M.Vinv, M.lam,
+                                                     d_pidx, d_dpidx, d_len, d_rates, I->d_mat64,
+                                                     (float*)I->d_matw, I->matw_stride, layout);
+    }
+    I->launches += 1;
+    return cuda_check(I, cudaGetLastError(), "update matrices");
+}
+
+}  // namespace tl

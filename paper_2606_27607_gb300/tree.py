@@ -1,0 +1,53 @@
+"""Operation lists for a rooted binary tree (index bookkeeping only).
+
+A tree is given as ``children`` ([N-1, 2] array: children of internal node
+N+k, children before parents) and ``n_tips``; node v's buffer index is v and
+the matrix slot of the edge above v is v (P) or n_nodes + v (dP/dt). The
+pre-order partial of internal node v lives in buffer ``pre_base + v``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from ._lib import EDGE_DTYPE, OP_DTYPE, PRE_OP_DTYPE
+
+
+def n_nodes(n_tips: int) -> int:
+    return 2 * n_tips - 1
+
+
+def post_ops(children, n_tips: int) -> np.ndarray:
+    """Post-order partials updates, one per internal node (children first)."""
+    children = np.asarray(children)
+    ops = np.zeros(len(children), dtype=OP_DTYPE)
+    for k, (a, b) in enumerate(children):
+        ops[k] = (n_tips + k, a, a, b, b)
+    return ops
+
+
+def pre_ops(children, n_tips: int, pre_base: int, with_edges: bool = True,
+            tip_pre: bool = False) -> np.ndarray:
+    """Pre-order ops, one per internal node, root first. ``edge`` slots are
+    node indices; q of internal node v goes to buffer pre_base + v (tips too
+    when ``tip_pre``)."""
+    children = np.asarray(children)
+    N = n_tips
+    root = 2 * N - 2
+    nn = n_nodes(N)
+    ops = np.zeros(N - 1, dtype=PRE_OP_DTYPE)
+    for i, v in enumerate(range(root, N - 1, -1)):
+        a, b = children[v - N]
+        parent_pre = -1 if v == root else pre_base + v
+        pre = [pre_base + c if (c >= N or tip_pre) else -1 for c in (a, b)]
+        edge = [a, b] if with_edges else [-1, -1]
+        ops[i] = (parent_pre, (a, b), (a, b), (nn + a, nn + b), pre, edge)
+    return ops
+
+
+def edges(n_tips: int, pre_base: int) -> np.ndarray:
+    """Every non-root edge for tl_edge_derivatives (pre buffers for all nodes)."""
+    nn = n_nodes(n_tips)
+    e = np.zeros(nn - 1, dtype=EDGE_DTYPE)
+    for v in range(nn - 1):
+        e[v] = (v, pre_base + v, v)
+    return e

@@ -1,0 +1,86 @@
+"""CPU-only checks of the library boundary: the shared library builds, loads
+and exports every symbol include/treelik.h declares; the Python binding and
+the op-list builders are consistent. No compute calls (no GPU here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_27607_gb300 import build
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def header_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^int\s+(tl_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for must in ("tl_create", "tl_destroy", "tl_set_tip_states", "tl_set_tip_partials",
+                 "tl_set_pattern_weights", "tl_set_category_rates", "tl_set_category_weights",
+                 "tl_set_model", "tl_set_eigen", "tl_update_matrices", "tl_update_partials",
+                 "tl_root_loglik", "tl_update_pre_partials", "tl_pre_order_gradient",
+                 "tl_edge_derivatives"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_symbol():
+    from paper_2606_27607_gb300 import _lib
+    assert set(header_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_struct_layouts_match_header():
+    from paper_2606_27607_gb300 import _lib
+    assert _lib.OP_DTYPE.itemsize == 5 * 4
+    assert _lib.PRE_OP_DTYPE.itemsize == 11 * 4
+    assert _lib.EDGE_DTYPE.itemsize == 3 * 4
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2606_27607_gb300 import Instance, TreelikError
+    with pytest.raises(TreelikError):
+        Instance(4, 10, 4, 4, 6, 14, 1, "f32")
+
+
+def test_op_lists_are_a_valid_traversal():
+    import synth
+    from paper_2606_27607_gb300 import tree
+    t = synth.yule_tree(50, np.random.default_rng(0))
+    post = tree.post_ops(t.children, 50)
+    seen = set(range(50))
+    for op in post:
+        assert op["child1"] in seen and op["child2"] in seen
+        seen.add(int(op["dest"]))
+    assert int(post[-1]["dest"]) == 98
+    pre = tree.pre_ops(t.children, 50, pre_base=49)
+    assert pre[0]["parent_pre"] == -1
+    produced = set()
+    for op in pre:
+        if op["parent_pre"] != -1:
+            assert op["parent_pre"] in produced
+        for c in range(2):
+            if op["pre"][c] >= 0:
+                produced.add(int(op["pre"][c]))
+    edges = sorted(int(e) for op in pre for e in op["edge"])
+    assert edges == list(range(98))
