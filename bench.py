@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 phylogenetic likelihood + gradient path.
+
+One step = one pass of the whole hot path on one batch of synthetic input
+(GTR+Gamma4, 512 taxa, 100,000 patterns, FP32 partials): device model set-up
+and FP64 eigensystem, transition matrices and their derivatives, post-order
+pruning with rescaling, root log-likelihood, fused pre-order pass with the
+branch-length gradient. The metric counts post-order (pattern, internal
+node) partials updates per second of that whole step.
+
+  python bench.py [--gpus N --steps K --warmup W]      # this library
+  python bench.py --impl reference                      # FP64 CPU oracle
+Under torchrun (N > 1) each rank evaluates its own block of patterns (weak
+scaling, no collective on the data path); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pattern-node partials/s (4 & 61 states), grad evals/s; serving p50/p99 latency"
+UNIT = "pattern-node/s"
+DEFAULT_WORKLOAD = "gtr_512x100k"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--taxa", type=int, default=0, help="override the workload's taxa")
+    ap.add_argument("--patterns", type=int, default=0, help="override the workload's patterns")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=0,
+                    help="patterns in the oracle sample (0: sized to ~15 s)")
+    ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (single-threaded subprocess)
+# ---------------------------------------------------------------------------
+
+def cpu_worker(workload: str, sample: int, steps: int) -> None:
+    """Time the FP64 oracle (logL + branch gradient) on the first ``sample``
+    patterns of the workload; prints one JSON line."""
+    import numpy as np
+
+    import synth
+    from oracle import gradient as og, model as om, pruning as op
+    w = synth.workload(workload)
+    tips = np.ascontiguousarray(w.tips[:, :sample])
+    wt = w.pattern_weights[:sample]
+    Q, pi, _ = om.build(w.model, w.params, w.freqs)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        op.loglik_chunked(w.tree, Q, pi, w.rates, w.cat_weights, wt, tips)
+        og.branch_gradient(w.tree, Q, pi, w.rates, w.cat_weights, wt, tips)
+        times.append(time.perf_counter() - t0)
+    print(json.dumps({"times": times, "patterns": sample, "internal_nodes": w.tree.n_tips - 1,
+                      "cores": 1}))
+
+
+def run_cpu(workload: str, sample: int, steps: int) -> dict:
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-worker", "--workload", workload,
+           "--cpu-sample", str(sample), "--steps", str(steps)]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True).stdout
+    return json.loads(out.strip().splitlines()[-1])
+
+
+def cpu_baseline(workload: str, sample: int) -> dict:
+    if sample <= 0:
+        probe = run_cpu(workload, 1000, 1)
+        per = probe["times"][0] / 1000
+        sample = int(max(1000, min(100_000, 15.0 / max(per, 1e-9))))
+        sample = (sample // 1000) * 1000
+    r = run_cpu(workload, sample, 1)
+    t = r["times"][0]
+    return {"value": r["patterns"] * r["internal_nodes"] / t, "unit": UNIT, "cores": r["cores"],
+            "kind": "oracle",
+            "sample": f"first {r['patterns']} patterns of {workload}, logL + branch gradient, "
+                      f"FP64 numpy/scipy, {t:.1f} s"}
+
+
+def reference_arm(args) -> None:
+    """The FP64 CPU oracle as it stands, same workload and metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample = args.cpu_sample or 2000
+    r = run_cpu(args.workload, sample, args.warmup + args.steps)
+    times = r["times"][args.warmup:]
+    t = statistics.median(times)
+    value = r["patterns"] * r["internal_nodes"] / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample_patterns": r["patterns"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
+                             "sample": f"first {r['patterns']} patterns of {args.workload} per "
+                                       "step, logL + branch gradient, FP64 numpy/scipy"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, enabled: bool, device_id: str | None):
+        self.proc = None
+        self.path = None
+        if not enabled:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if device_id:
+            cmd += ["-i", device_id]
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def device_id_for_smi() -> str | None:
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(0).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[0] if vis else None
+
+
+def peaks() -> tuple[float, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_for(kernel: str, per_launch_units: float) -> float | None:
+    """ncu DRAM bytes per launch recorded under profiles/, if the kernel source
+    is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    src = os.path.join(ROOT, "paper_2606_27607_gb300", "csrc", "tl_nuc.cu")
+    try:
+        rec = json.load(open(path))[kernel]
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") != h:
+            return None
+        return rec["bytes_per_pattern"] * per_launch_units
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def main() -> None:
+    args = parse()
+    if args.cpu_worker:
+        cpu_worker(args.workload, args.cpu_sample, max(1, args.steps))
+        return
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    if args.taxa or args.patterns:
+        args.no_cpu_baseline = True
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2606_27607_gb300 import TreeLikelihood, build
+    build.build()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    over = {}
+    if args.taxa:
+        over["n_tips"] = args.taxa
+    if args.patterns:
+        over["n_patterns"] = args.patterns
+    w = synth.workload(args.workload, **over)
+    N, P, S = w.tree.n_tips, w.n_patterns, w.n_states
+    R = len(w.rates)
+    stream = torch.cuda.current_stream()
+    tl = TreeLikelihood(N, P, S, R, "f32", stream=stream.cuda_stream)
+    inst = tl.inst
+    tl.set_tips(w.tips)
+    tl.set_model(w.model, w.params, w.freqs)
+    tl.set_rates(w.rates, w.cat_weights)
+    tl.set_pattern_weights(w.pattern_weights)
+    tl.set_tree(w.tree.children, w.tree.edge_len)
+    nn = tl.nn
+    v = np.arange(nn - 1, dtype=np.int32)
+    dp = (nn + v).astype(np.int32)
+    lengths = np.ascontiguousarray(w.tree.edge_len[: nn - 1])
+    d_out = torch.zeros(1 + nn, dtype=torch.float64, device="cuda")
+    post, pre = tl._post, tl._pre
+
+    ev = {k: [] for k in ("post", "pre")}
+
+    def step(timed: bool) -> None:
+        inst.set_model_async(0, w.model, w.params, w.freqs)            # a1
+        inst.update_matrices(0, v, lengths, dp)                        # a2, a6
+        if timed:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        inst.update_partials(post)                                     # a3, a4
+        if timed:
+            e1 = torch.cuda.Event(enable_timing=True)
+            e1.record(stream)
+            ev["post"].append((e0, e1))
+        inst.root_loglik_dev(nn - 1, 0, d_out.data_ptr())              # a5
+        if timed:
+            e2 = torch.cuda.Event(enable_timing=True)
+            e2.record(stream)
+        inst.pre_order_gradient_dev(pre, nn, 0, d_out.data_ptr() + 8)  # a7, a8
+        if timed:
+            e3 = torch.cuda.Event(enable_timing=True)
+            e3.record(stream)
+            ev["pre"].append((e2, e3))
+
+    clocks = Clocks(not args.no_clocks and rank == 0, device_id_for_smi() if rank == 0 else None)
+    t_w = time.perf_counter()
+    n_w = 0
+    while n_w < max(3, args.warmup) or (not args.no_clocks and time.perf_counter() - t_w < 1.0):
+        step(False)
+        n_w += 1
+        if n_w % 50 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    inst.sync()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = inst.launch_count()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = (inst.launch_count() - n0) // max(1, args.steps)
+    clk = clocks.stop()
+    inst.sync()
+    ms = start.elapsed_time(end) / args.steps
+    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms = float(t_max.item())
+    logl = float(d_out[0].item())
+    k_ms = {k: statistics.mean(a.elapsed_time(b) for a, b in ev[k]) for k in ev}
+
+    # e2e: the public API with host buffers; tips, weights and parameters go
+    # host -> device every step, logL and gradient come back
+    e2e = None
+    if not args.no_e2e:
+        tips_h = torch.from_numpy(np.ascontiguousarray(w.tips)).pin_memory()
+        tips_np = tips_h.numpy()
+        wts = np.ascontiguousarray(w.pattern_weights)
+
+        def e2e_step():
+            inst.set_tip_states_all(tips_np)
+            inst.set_pattern_weights(wts)
+            inst.set_model_async(0, w.model, w.params, w.freqs)
+            inst.update_matrices(0, v, lengths, dp)
+            inst.update_partials(post)
+            lg = inst.root_loglik(nn - 1, 0)
+            g = inst.pre_order_gradient(pre, nn, 0)
+            return lg, g
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ke = max(3, args.steps // 2)
+        for _ in range(ke):
+            e2e_step()
+        torch.cuda.synchronize()
+        t_e2e = (time.perf_counter() - t0) / ke
+        te = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        t_e2e = float(te.item())
+        # tips + padded weights + model parameters + (rates, branch lengths);
+        # op lists and matrix indices are unchanged between steps and stay
+        # resident (the library skips identical uploads)
+        h2d = (N * P + 8 * ((P + 31) // 32 * 32) + 8 * (len(w.params) + np.size(w.freqs))
+               + 8 * (R + nn - 1))
+        e2e = {"value": world * P * (N - 1) / t_e2e, "unit": UNIT, "ms_per_step": 1e3 * t_e2e,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 + 8 * nn)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (algorithmic bytes of one launch)
+    hbm, src = peaks()
+    RS = R * 4 * 4  # bytes of one pattern's FP32 partial, all categories
+    alg = {"post": P * ((N - 1) * (RS + 4) + N * 1),
+           "pre": P * ((N - 2) * RS + N * 1) + 8 * (2 * N - 2) * ((P + 31) // 32)}
+    dom = max(k_ms, key=k_ms.get)
+    ach = alg[dom] / (k_ms[dom] * 1e-3) / 1e9
+    kname = {"post": "k_post4<float,4>", "pre": "k_pre4<float,4>"}[dom]
+    traffic = traffic_for(kname, P)
+    roof = {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm, "peak_source": src, "traffic": traffic,
+            "algorithmic_bytes": alg[dom], "ms": k_ms[dom],
+            "other": {k: {"ms": k_ms[k], "GB/s": alg[k] / (k_ms[k] * 1e-3) / 1e9} for k in k_ms}}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline(args.workload, args.cpu_sample)
+        except Exception as exc:  # reported, not fatal
+            cpu = {"error": str(exc)[:200]}
+
+    value = world * P * (N - 1) / (ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "model": w.model.upper() + "+G4",
+                       "n_taxa": N, "n_patterns": P, "n_states": S, "n_categories": R,
+                       "precision": "f32 partials, f64 eigensystem/reductions",
+                       "step": "model+eigen, P and dP/dt, post-order, root logL, "
+                               "pre-order gradient",
+                       "l2": "no flush: partials working set "
+                             f"{(N - 1) * P * RS / 1e9:.1f} GB > 129 MB L2",
+                       "parallelism": f"patterns, weak x{world}"},
+            "grad_evals_per_s": world * 1e3 / ms, "logL": logl, "clocks": clk, "e2e": e2e,
+            "gpu_launches": int(launches) * args.steps, "gpu_launches_per_step": int(launches),
+            "roofline": roof, "cpu_baseline": cpu}
+    print(json.dumps(line), flush=True)
+    tl.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
