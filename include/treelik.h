@@ -220,6 +220,32 @@ int tl_edge_derivatives(tl_instance* inst, const tl_edge* edges, int count, int 
  * accumulated rescaling exponents (zeros for pre-order buffers and tips). */
 int tl_get_partials(tl_instance* inst, int buf, double* out, int32_t* exponents);
 
+/* Root log-likelihood without any device allocation (the paper has no
+ * counterpart; this exists for callers that cannot allocate device memory,
+ * such as code running inside someone else's stream capture, plug-ins whose
+ * host application owns the allocator, or loops that forbid allocation
+ * after start-up). Computes the same value as tl_root_loglik for caller-held
+ * FP32 four-state root partials:
+ *   root_partials    device, [n_categories][pattern_stride][4] float, 16-byte
+ *                    aligned (the layout of an FP32 instance buffer)
+ *   exponents        device, [n_patterns] int32 accumulated rescaling
+ *                    exponents, or NULL for none
+ *   pi               device, [4] doubles; cat_weights device, [n_categories]
+ *   pattern_weights  device, [n_patterns] doubles
+ *   out_logl         device, 1 double, written asynchronously on `stream`
+ * Scratch is a fixed array built into the library (one double per 32
+ * patterns): n_patterns above 2,097,152 returns TL_ERR_UNSUPPORTED. The
+ * first call on each device looks up that device's copy of the array with
+ * that device current; make the first call before any stream capture. All
+ * calls share the array, so calls that overlap on the GPU (other streams,
+ * other host threads) race; serialise them. A zero or non-finite pattern
+ * likelihood shows up as a non-finite *out_logl (no status is read back).
+ * Errors in arguments are reported through tl_last_error(NULL, ...). */
+int tl_root_loglik_static(const float* root_partials, const int32_t* exponents,
+                          const double* pi, const double* cat_weights,
+                          const double* pattern_weights, int n_patterns, int pattern_stride,
+                          int n_categories, double* out_logl, void* stream);
+
 /* Number of kernels this instance has launched since creation. */
 int tl_launch_count(const tl_instance* inst, unsigned long long* out);
 

@@ -68,6 +68,7 @@ SIGNATURES = {
     "tl_set_tip_states_all": [_VP, _VP],
     "tl_set_model_async": [_VP, _I, _I, _VP, _I, _VP, _I],
     "tl_launch_count": [_VP, C.POINTER(C.c_ulonglong)],
+    "tl_root_loglik_static": [_VP, _VP, _VP, _VP, _VP, _I, _I, _I, _VP, _VP],
     "tl_sync": [_VP],
 }
 
@@ -107,6 +108,18 @@ def last_error(handle) -> str:
 def _check(rc: int, handle) -> None:
     if rc != TL_OK:
         raise TreelikError(rc, last_error(handle))
+
+
+def root_loglik_static(root_ptr: int, exps_ptr: int | None, pi_ptr: int, catw_ptr: int,
+                       patw_ptr: int, n_patterns: int, stride: int, n_categories: int,
+                       out_ptr: int, stream: int | None = None) -> None:
+    """tl_root_loglik_static: all pointers are device addresses; the result
+    is written to out_ptr on ``stream`` without synchronising."""
+    rc = load().tl_root_loglik_static(C.c_void_p(root_ptr), C.c_void_p(exps_ptr or 0),
+                                      C.c_void_p(pi_ptr), C.c_void_p(catw_ptr),
+                                      C.c_void_p(patw_ptr), n_patterns, stride, n_categories,
+                                      C.c_void_p(out_ptr), C.c_void_p(stream or 0))
+    _check(rc, None)
 
 
 class Instance:
