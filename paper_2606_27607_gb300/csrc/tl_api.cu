@@ -337,7 +337,16 @@ int plan_post(Instance* I, const tl_op* ops, int n, PostPlan* plan, bool dry) {
         for (int k = 0; k < n; ++k) order.push_back(k);
     }
 
-    // slot assignment by linear scan
+    // The op just before hands its result over in registers when it is the
+    // only consumer; other in-list results get a shared-memory slot by linear
+    // scan (or are re-read from memory when no slot is free).
+    std::vector<int> pos(n), sole_consumer(n, -1);
+    for (int idx = 0; idx < n; ++idx) pos[order[idx]] = idx;
+    for (int k = 0; k < n; ++k)
+        for (int c = 0; c < 2; ++c) {
+            int pk = local(k, c);
+            if (pk >= 0 && consumers[pk] == 1) sole_consumer[pk] = k;
+        }
     const int cap = max_slots(I);
     std::vector<int> slot_of(n, -1), remaining(n, 0);
     for (int k = 0; k < n; ++k) remaining[k] = consumers[k];
@@ -349,23 +358,30 @@ int plan_post(Instance* I, const tl_op* ops, int n, PostPlan* plan, bool dry) {
         const int k = order[idx];
         const tl_op& o = ops[k];
         DevPostOp d;
-        d.dest = o.dest;
-        d.child[0] = o.child1;
-        d.child[1] = o.child2;
-        d.mat[0] = o.mat1;
-        d.mat[1] = o.mat2;
+        std::memset(&d, 0, sizeof d);
+        const int ch[2] = {o.child1, o.child2};
+        const int mt[2] = {o.mat1, o.mat2};
         for (int c = 0; c < 2; ++c) {
-            int pk = local(k, c);
-            d.slot_in[c] = (pk >= 0) ? slot_of[pk] : -1;
-        }
-        for (int c = 0; c < 2; ++c) {
-            int pk = local(k, c);
-            if (pk >= 0 && --remaining[pk] == 0 && slot_of[pk] >= 0) {
-                free_slots.push_back(slot_of[pk]);
+            d.mat[c] = mt[c];
+            if (ch[c] < I->n_tips) {
+                d.kind[c] = I->tip_set[ch[c]] == 1 ? kTipStates : kTipPartials;
+                d.child[c] = ch[c];
+            } else {
+                d.kind[c] = kInternal;
+                d.child[c] = ch[c] - I->n_tips;
             }
+            const int pk = local(k, c);
+            if (pk >= 0 && idx > 0 && order[idx - 1] == pk) d.slot_in[c] = kFromRegisters;
+            else d.slot_in[c] = (pk >= 0 && slot_of[pk] >= 0) ? slot_of[pk] : kFromMemory;
         }
+        for (int c = 0; c < 2; ++c) {
+            int pk = local(k, c);
+            if (pk >= 0 && --remaining[pk] == 0 && slot_of[pk] >= 0) free_slots.push_back(slot_of[pk]);
+        }
+        d.dest = o.dest - I->n_tips;
         d.slot_out = -1;
-        if (consumers[k] > 0 && !free_slots.empty()) {
+        const bool next_only = sole_consumer[k] >= 0 && pos[sole_consumer[k]] == idx + 1;
+        if (consumers[k] > 0 && !next_only && !free_slots.empty()) {
             d.slot_out = free_slots.back();
             free_slots.pop_back();
             slot_of[k] = d.slot_out;
@@ -441,6 +457,18 @@ int plan_pre(Instance* I, const tl_pre_op* ops, int n, int n_grad, bool store_al
             }
         }
     }
+    // a pre-order output may not overwrite a post-order child of this list
+    // (children are prefetched ahead of the ops that write q)
+    {
+        std::vector<char> is_child(NB, 0);
+        for (int k = 0; k < n; ++k)
+            for (int c = 0; c < 2; ++c) is_child[ops[k].child[c]] = 1;
+        for (int k = 0; k < n; ++k)
+            for (int c = 0; c < 2; ++c)
+                if (ops[k].pre[c] >= 0 && is_child[ops[k].pre[c]])
+                    return fail(I, TL_ERR_ORDER, "pre op %d: pre buffer %d is also a child", k,
+                                ops[k].pre[c]);
+    }
     // order: depth first from each root op, smaller-need subtree first
     std::vector<int> need(n, 0), parent_op(n, -1);
     for (int k = 0; k < n; ++k)
@@ -483,7 +511,8 @@ int plan_pre(Instance* I, const tl_pre_op* ops, int n, int n_grad, bool store_al
     const int cap = use_nuc(I) ? max_slots(I) : 0;
     std::vector<int> free_slots;
     for (int s = cap - 1; s >= 0; --s) free_slots.push_back(s);
-    std::vector<int> q_slot(2 * n, -1);
+    std::vector<int> q_slot(2 * n, -1), pos(n);
+    for (int idx = 0; idx < n; ++idx) pos[order[idx]] = idx;
     int used = 0;
     plan->dev.resize(n);
     for (int idx = 0; idx < n; ++idx) {
@@ -491,33 +520,52 @@ int plan_pre(Instance* I, const tl_pre_op* ops, int n, int n_grad, bool store_al
         const tl_pre_op& o = ops[k];
         DevPreOp d;
         std::memset(&d, 0, sizeof d);
+        d.q_buf_in = -1;
+        d.q_reg = -1;
         if (o.parent_pre == -1) {
-            d.q_slot_in = -2;
-            d.q_buf_in = -1;
+            d.q_src = kFromRoot;
         } else {
-            int j = prod_op[o.parent_pre];
-            int s = (j >= 0) ? q_slot[2 * j + prod_c[o.parent_pre]] : -1;
-            d.q_slot_in = s;
-            d.q_buf_in = o.parent_pre;
-            if (s >= 0) free_slots.push_back(s);
+            const int j = prod_op[o.parent_pre];
+            const int c = j >= 0 ? prod_c[o.parent_pre] : 0;
+            if (j >= 0 && pos[j] == idx - 1 && use_nuc(I)) {
+                d.q_src = kFromRegisters;
+            } else if (j >= 0 && q_slot[2 * j + c] >= 0) {
+                d.q_src = q_slot[2 * j + c];
+                free_slots.push_back(d.q_src);
+            } else {
+                d.q_src = kFromMemory;
+                d.q_buf_in = o.parent_pre - I->n_tips;
+            }
         }
         for (int c = 0; c < 2; ++c) {
-            d.child[c] = o.child[c];
+            if (o.child[c] < I->n_tips) {
+                d.kind[c] = I->tip_set[o.child[c]] == 1 ? kTipStates : kTipPartials;
+                d.child[c] = o.child[c];
+            } else {
+                d.kind[c] = kInternal;
+                d.child[c] = o.child[c] - I->n_tips;
+            }
             d.mat[c] = o.mat[c];
             d.dmat[c] = o.dmat[c];
             d.edge[c] = o.edge[c] >= 0 ? edge_row[o.edge[c]] : -1;
             d.q_slot_out[c] = -1;
             d.q_buf_out[c] = -1;
-            const bool consumed = child_op[2 * k + c] >= 0;
-            if (o.pre[c] >= 0 && (consumed || store_all)) {
+            const int cons = child_op[2 * k + c];
+            if (o.pre[c] >= 0 && (cons >= 0 || store_all)) {
                 d.need_q[c] = 1;
-                if (consumed && !store_all && !free_slots.empty()) {
+                const bool next = cons >= 0 && pos[cons] == idx + 1;
+                if (next) d.q_reg = c;  // the next op takes q_c from registers
+                if (store_all) {
+                    d.q_buf_out[c] = o.pre[c] - I->n_tips;
+                } else if (next) {
+                    // registers only
+                } else if (!free_slots.empty()) {
                     d.q_slot_out[c] = free_slots.back();
                     free_slots.pop_back();
                     q_slot[2 * k + c] = d.q_slot_out[c];
                     used = std::max(used, d.q_slot_out[c] + 1);
                 } else {
-                    d.q_buf_out[c] = o.pre[c];
+                    d.q_buf_out[c] = o.pre[c] - I->n_tips;
                 }
             }
         }
@@ -621,7 +669,7 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
     Instance* I = new Instance();
     I->n_tips = n_tips;
     I->P = n_patterns;
-    I->Ppad = ((n_patterns + kTile - 1) / kTile) * kTile;
+    I->Ppad = ((n_patterns + kPadPatterns - 1) / kPadPatterns) * kPadPatterns;
     I->S = n_states;
     I->Spad = (n_states == 4) ? 4 : ((n_states + 3) / 4) * 4;
     if (prec == kTF32 || prec == kBF16X3) I->Spad = 64;
@@ -1086,9 +1134,14 @@ static int root_common(Instance* I, int root, int model, double* d_site, double*
         return fail(I, TL_ERR_STATE, "model %d not set", model);
     int rc;
     if (use_nuc(I)) {
-        const int n_tiles = I->Ppad / kTile;
+        const int n_tiles = nuc_tiles(I);
         if ((rc = ensure_scratch(I, n_tiles))) return rc;
-        if ((rc = launch_root4(I, root, model, d_site, I->d_red, n_tiles))) return rc;
+        int kind = kInternal, idx = root - I->n_tips;
+        if (root < I->n_tips) {
+            kind = I->tip_set[root] == 1 ? kTipStates : kTipPartials;
+            idx = root;
+        }
+        if ((rc = launch_root4(I, kind, idx, model, d_site, I->d_red))) return rc;
         return reduce_fixed(I, I->d_red, 1, n_tiles, d_out);
     }
     const int parts = (I->Ppad + 127) / 128;
@@ -1131,12 +1184,12 @@ static int pre_common(Instance* I, const tl_pre_op* ops, int count, int model, i
     if (rc) return rc;
     const int E = (int)plan.edge_map.size();
     if (use_nuc(I)) {
-        const int n_tiles = I->Ppad / kTile;
+        const int n_tiles = nuc_tiles_main(I);
         if ((rc = ensure_scratch(I, (size_t)std::max(E, 1) * n_tiles))) return rc;
         void* d_ops = nullptr;
         if ((rc = upload(I, extra(I).areas[1], plan.dev.data(), sizeof(DevPreOp) * count, &d_ops)))
             return rc;
-        if ((rc = launch_pre4(I, (const DevPreOp*)d_ops, count, plan.n_slots, model, I->d_red, n_tiles)))
+        if ((rc = launch_pre4(I, (const DevPreOp*)d_ops, count, plan.n_slots, model, I->d_red)))
             return rc;
         if ((rc = ensure_out(I, (size_t)E))) return rc;
         if ((rc = reduce_fixed(I, I->d_red, E, n_tiles, extra(I).d_out))) return rc;
@@ -1233,13 +1286,18 @@ int tl_edge_derivatives(tl_instance* inst, const tl_edge* edges, int count, int 
     int rc;
     int parts;
     if (use_nuc(I)) {
-        parts = I->Ppad / kTile;
+        parts = nuc_tiles(I);
         if ((rc = ensure_scratch(I, (size_t)std::max(E, 1) * parts))) return rc;
         std::vector<DevEdge> d(count);
-        for (int k = 0; k < count; ++k) d[k] = {e[k].post, e[k].pre, e[k].edge, 0};
+        for (int k = 0; k < count; ++k) {
+            const int b = e[k].post;
+            const int kind = b < I->n_tips ? (I->tip_set[b] == 1 ? kTipStates : kTipPartials)
+                                           : kInternal;
+            d[k] = {b < I->n_tips ? b : b - I->n_tips, kind, e[k].pre - I->n_tips, e[k].edge};
+        }
         void* d_e = nullptr;
         if ((rc = upload(I, extra(I).areas[2], d.data(), sizeof(DevEdge) * count, &d_e))) return rc;
-        if ((rc = launch_edge4(I, (const DevEdge*)d_e, count, model, I->d_red, parts))) return rc;
+        if ((rc = launch_edge4(I, (const DevEdge*)d_e, count, model, I->d_red))) return rc;
     } else {
         parts = generic_parts(I);
         if ((rc = ensure_scratch(I, (size_t)std::max(E, 1) * parts))) return rc;

@@ -12,66 +12,73 @@
 
 namespace tl {
 
-// Patterns handled by one warp in the four-state kernels: one lane per
-// pattern, all categories in registers.
-constexpr int kTile = 32;
 constexpr int kWarpsPerBlock = 4;
 constexpr int kMaxCat = 8;
 constexpr int kMaxStates = 64;
 constexpr int kMaxDq = 8;      // dQ/dtheta matrices kept per model
 constexpr int kColStride = 5;  // four-state matrices: 4 columns + row sums
+constexpr int kPadPatterns = 32;  // patterns are padded to a multiple of this
 
 enum Prec { kF64 = 0, kF32 = 1, kTF32 = 2, kBF16X3 = 3 };
 
-// One post-order op as the device walks it.
-struct DevPostOp {
-    int dest;
+// Where a four-state kernel finds a child's partials.
+enum ChildKind { kInternal = 0, kTipStates = 1, kTipPartials = 2 };
+// On-chip sources of an op input (>= 0 is a shared-memory slot).
+constexpr int kFromMemory = -1;
+constexpr int kFromRegisters = -2;  // the result of the op just before
+constexpr int kFromRoot = -3;       // pre-order: q = pi
+
+// One post-order op as the device walks it. Buffer indices are relative to
+// the internal partials pool; tips are indexed 0..n_tips-1.
+struct __align__(16) DevPostOp {
     int child[2];
+    int kind[2];
     int mat[2];
-    int slot_in[2];  // on-chip slot holding the child (-1: read memory)
-    int slot_out;    // on-chip slot receiving dest (-1: none)
+    int slot_in[2];  // kFromMemory, kFromRegisters or a slot
+    int dest;
+    int slot_out;    // slot receiving dest (-1: none)
     int store;       // 1: write dest to its buffer
+    int pad;
 };
 
-// One pre-order op (one parent, both children) as the device walks it.
-struct DevPreOp {
-    int q_slot_in;   // -2: root (pi), -1: read q_buf_in, >= 0: slot
-    int q_buf_in;
+// One pre-order op (one parent, both children) as the device walks it. The
+// first 16 bytes (children and their kinds) are what the kernels prefetch.
+struct __align__(16) DevPreOp {
     int child[2];
+    int kind[2];
+    int q_src;       // kFromRoot, kFromRegisters, kFromMemory or a slot
+    int q_reg;       // which q output (0, 1) the next op takes from registers (-1: none)
+    int q_buf_in;    // with kFromMemory: pool index of q
     int mat[2];
-    int dmat[2];
+    int dmat[2];     // -1: no derivative
     int q_slot_out[2];
-    int q_buf_out[2];
-    int edge[2];
+    int q_buf_out[2];  // pool index or -1
+    int edge[2];     // row of the gradient partials or -1
     int need_q[2];
     int pad;
 };
 
-struct DevEdge {
-    int post;
-    int pre;
+struct __align__(16) DevEdge {
+    int post;        // pool index, or tip index
+    int kind;
+    int pre;         // pool index
     int edge;
-    int pad;
 };
 
-// Kernel arguments shared by the pattern-parallel kernels. Pointer tables
-// live in device memory; everything else is passed by value.
+// Arguments of the four-state kernels, passed by value. Partials of
+// internal buffer b live at pool + b * bstride as [R][Ppad][4]; its
+// accumulated exponents at epool + b * Ppad; tip t's states at
+// tips + t * Ppad.
 template <typename T>
-struct PathArgs {
-    T* const* buf;                  // [n_bufs] partials (null: tip with states)
-    int* const* scale;              // [n_bufs] accumulated exponents (null: none)
-    const int8_t* const* tipst;     // [n_tips] tip states (null: tip partials)
-    const T* mat;                   // working-precision matrices
+struct NucArgs {
+    T* pool;
+    int* epool;
+    const int8_t* tips;
+    T* const* tipbuf;               // device table: tip partials (kind 2)
+    const T* mat;                   // [mat][5 columns][R][4] working copies
     const double* patw;             // [Ppad] pattern weights (0 on padding)
-    int n_tips;
-    int P;                          // real patterns
-    int Ppad;                       // padded patterns
-    int R;
-    int S;                          // states (real)
-    int Spad;                       // stored states
-    int n_slots;                    // on-chip slots per warp
-    int rescale;
-    int mat_stride;                 // elements per matrix slot
+    size_t bstride;
+    int P, Ppad, R, n_slots, rescale, mat_stride, n_tiles;
     T catw[kMaxCat];
     T rates[kMaxCat];
 };
@@ -150,13 +157,17 @@ int launch_update_matrices(Instance* I, int m, const int* d_pidx, const int* d_d
                            const double* d_len, int count);
 
 // tl_nuc.cu (four-state pattern-tile kernels, T = float or double)
+int nuc_lanes(const Instance* I);            // lanes per pattern (root, edge kernels)
+int nuc_tiles(const Instance* I);            // their tiles
+int nuc_lanes_main(const Instance* I);       // lanes per pattern (post, pre kernels)
+int nuc_tiles_main(const Instance* I);       // their tiles (= gradient partial columns)
+int nuc_smem_per_slot(const Instance* I);    // bytes per slot per warp
 int launch_post4(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots);
-int launch_root4(Instance* I, int root, int model, double* d_site, double* d_part, int n_tiles);
+int launch_root4(Instance* I, int root_kind, int root, int model, double* d_site,
+                 double* d_part);
 int launch_pre4(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, int model,
-                double* d_gpart, int n_tiles);
-int launch_edge4(Instance* I, const DevEdge* d_edges, int n_edges, int model, double* d_gpart,
-                 int n_tiles);
-int nuc_smem_per_slot(const Instance* I);
+                double* d_gpart);
+int launch_edge4(Instance* I, const DevEdge* d_edges, int n_edges, int model, double* d_gpart);
 
 // tl_generic.cu (FP64, any S)
 int launch_post_generic(Instance* I, const tl_op* h_ops, int n_ops);

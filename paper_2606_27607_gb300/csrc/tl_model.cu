@@ -349,9 +349,9 @@ __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
         __syncthreads();
         T* w = matw + (size_t)slot * matw_stride;
         if (layout == 0) {
-            w += (size_t)r * kColStride * 4;
-            // the row-sum column (ambiguous tips) is summed in T in column
-            // order, exactly as a product with an all-ones partial rounds
+            // [5 columns][R][4]: column j of every category contiguous; the
+            // row-sum column (ambiguous tips) is summed in T in column order,
+            // exactly as a product with an all-ones partial rounds
             for (int idx = t; idx < kColStride * 4; idx += nt) {
                 int j = idx / 4, i = idx % 4;
                 T v;
@@ -361,7 +361,7 @@ __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
                     v = (T)Pm[i * Spad];
                     for (int q = 1; q < S; ++q) v = v + (T)Pm[i * Spad + q];
                 }
-                w[idx] = v;
+                w[((size_t)j * R + r) * 4 + i] = v;
             }
         } else if (layout == 1) {
             w += (size_t)r * (Spad + 1) * Spad;

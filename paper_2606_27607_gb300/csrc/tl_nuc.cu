@@ -4,17 +4,21 @@
 //
 // Design: patterns are independent given the tree (Sec. "Benchmarks on
 // NVIDIA and AMD GPUs": the alignment splits into conditionally independent
-// blocks), so one warp owns a tile of 32 patterns -- one lane per pattern,
-// all rate categories in registers -- and walks the WHOLE operation list for
-// its tile in a single launch. No warp ever waits for another. A child that
-// an earlier op of the same list produced is read from a warp-private
-// shared-memory slot (the host assigns slots); only results the caller asked
-// for go to HBM. Partials are [category][pattern][4] so each lane's float4 /
-// double2x2 accesses coalesce across the warp. Matrices are read through the
-// read-only path with warp-uniform addresses (one broadcast per load).
-// A tip with states uses a column of P (or the row sums for an ambiguous
-// code) instead of a product (the benchmark spec: tip-state lookups).
+// blocks), so a warp owns a tile of patterns and walks the WHOLE operation
+// list for it in a single launch; no warp ever waits for another. LPP lanes
+// share a pattern, one rate category each (LPP = 4 for four categories: a
+// warp tile is 8 patterns), so per-pattern maxima and sums over categories
+// are LPP-lane shuffles. The grid is persistent (sized by occupancy) and
+// warps stride over tiles. A child produced by the op just before is taken
+// from registers, one produced earlier in the same list from a warp-private
+// shared-memory slot (the host assigns both); only results the caller asked
+// for go to HBM. Partials are [category][pattern][4] so a warp's float4 /
+// double2x2 accesses cover LPP runs of consecutive patterns. A tip with
+// states uses a column of P (or the row sums for an ambiguous code) instead
+// of a product.
+#include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include "tl_internal.cuh"
 
@@ -64,10 +68,11 @@ __device__ __forceinline__ T vmax(V4<T> a) {
     return fmax(fmax(a.x, a.y), fmax(a.z, a.w));
 }
 
-// P x with P given by its columns c0..c3: x0 c0 + x1 c1 + x2 c2 + x3 c3.
+// P x with P given by its columns c0..c3 (column j at col + j * cs):
+// x0 c0 + x1 c1 + x2 c2 + x3 c3.
 template <typename T>
-__device__ __forceinline__ V4<T> matvec(const T* col, V4<T> x) {
-    V4<T> c0 = ldg4(col), c1 = ldg4(col + 4), c2 = ldg4(col + 8), c3 = ldg4(col + 12);
+__device__ __forceinline__ V4<T> matvec(const T* col, int cs, V4<T> x) {
+    V4<T> c0 = ld4(col), c1 = ld4(col + cs), c2 = ld4(col + 2 * cs), c3 = ld4(col + 3 * cs);
     V4<T> r;
     r.x = x.x * c0.x + x.y * c1.x + x.z * c2.x + x.w * c3.x;
     r.y = x.x * c0.y + x.y * c1.y + x.z * c2.y + x.w * c3.y;
@@ -77,8 +82,8 @@ __device__ __forceinline__ V4<T> matvec(const T* col, V4<T> x) {
 }
 // P^T u: component j is column j . u
 template <typename T>
-__device__ __forceinline__ V4<T> matTvec(const T* col, V4<T> u) {
-    V4<T> c0 = ldg4(col), c1 = ldg4(col + 4), c2 = ldg4(col + 8), c3 = ldg4(col + 12);
+__device__ __forceinline__ V4<T> matTvec(const T* col, int cs, V4<T> u) {
+    V4<T> c0 = ld4(col), c1 = ld4(col + cs), c2 = ld4(col + 2 * cs), c3 = ld4(col + 3 * cs);
     return {dot(c0, u), dot(c1, u), dot(c2, u), dot(c3, u)};
 }
 
@@ -129,313 +134,613 @@ __device__ __forceinline__ int tip_col(int8_t s) { return (s >= 0 && s < 4) ? (i
 // ---------------------------------------------------------------------------
 // post-order
 // ---------------------------------------------------------------------------
-template <typename T, int RM>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_post4(const DevPostOp* __restrict__ ops, int n_ops, PathArgs<T> a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * kWarpsPerBlock + warp;
-    if (tile * kTile >= a.Ppad) return;
-    const int p = tile * kTile + lane;
-    const int R = a.R;
-    V4<T>* slots = reinterpret_cast<V4<T>*>(smem_raw) + (size_t)warp * a.n_slots * RM * 32;
-    int* sexp = reinterpret_cast<int*>(reinterpret_cast<V4<T>*>(smem_raw) +
-                                       (size_t)kWarpsPerBlock * a.n_slots * RM * 32) +
-                warp * a.n_slots * 32;
+// Loads that feed op k are issued while op k-kAhead..k-1 compute: tip states
+// kAhead ops ahead, partials read from memory one op ahead. Without this
+// every op waits a full DRAM round trip for its inputs.
+constexpr int kAhead = 3;
 
-    for (int k = 0; k < n_ops; ++k) {
-        const DevPostOp op = ops[k];
-        V4<T> acc[RM];
-        int cum = 0;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int ch = op.child[c];
-            const T* mc = a.mat + (size_t)op.mat[c] * a.mat_stride;
-            const int8_t* ts = (ch < a.n_tips) ? a.tipst[ch] : nullptr;
-            if (ts != nullptr) {
-                const int col = tip_col(__ldg(ts + p));
-#pragma unroll
-                for (int r = 0; r < RM; ++r) {
-                    if (r < R) {
-                        V4<T> v = ldg4(mc + (r * kColStride + col) * 4);
-                        acc[r] = (c == 0) ? v : mul(acc[r], v);
-                    }
-                }
-            } else {
-                V4<T> x[RM];
-                if (op.slot_in[c] >= 0) {
-                    const V4<T>* s = slots + (size_t)op.slot_in[c] * RM * 32;
-#pragma unroll
-                    for (int r = 0; r < RM; ++r)
-                        if (r < R) x[r] = s[r * 32 + lane];
-                    cum += sexp[op.slot_in[c] * 32 + lane];
-                } else {
-                    const T* b = a.buf[ch];
-#pragma unroll
-                    for (int r = 0; r < RM; ++r)
-                        if (r < R) x[r] = ld4(b + ((size_t)r * a.Ppad + p) * 4);
-                    const int* sc = a.scale[ch];
-                    if (sc != nullptr) cum += sc[p];
-                }
-#pragma unroll
-                for (int r = 0; r < RM; ++r) {
-                    if (r < R) {
-                        V4<T> v = matvec(mc + r * kColStride * 4, x[r]);
-                        acc[r] = (c == 0) ? v : mul(acc[r], v);
-                    }
-                }
-            }
-        }
-        if (a.rescale) {
-            T m = T(0);
-#pragma unroll
-            for (int r = 0; r < RM; ++r)
-                if (r < R) m = fmax(m, vmax(acc[r]));
-            const int e = frexp_exp(m);
-            if (e != 0) {
-                scale_by_pow2(acc, R < RM ? R : RM, -e);
-                cum += e;
-            }
-        }
-        if (op.store) {
-            T* d = a.buf[op.dest];
-#pragma unroll
-            for (int r = 0; r < RM; ++r)
-                if (r < R) st4(d + ((size_t)r * a.Ppad + p) * 4, acc[r]);
-            a.scale[op.dest][p] = cum;
-        }
-        if (op.slot_out >= 0) {
-            V4<T>* s = slots + (size_t)op.slot_out * RM * 32;
-#pragma unroll
-            for (int r = 0; r < RM; ++r)
-                if (r < R) s[r * 32 + lane] = acc[r];
-            sexp[op.slot_out * 32 + lane] = cum;
-        }
-    }
+// Children and their kinds: the first 16 bytes of a post- or pre-order op.
+template <typename Op>
+__device__ __forceinline__ int4 op_head(const Op* ops, int k, int n) {
+    return (k < n) ? __ldg(reinterpret_cast<const int4*>(ops + k)) : make_int4(0, 0, -1, -1);
+}
+template <typename T>
+__device__ __forceinline__ int tip_state(const NucArgs<T>& a, int child, int kind, int p) {
+    return kind == kTipStates ? (int)__ldg(a.tips + (size_t)child * a.Ppad + p) : 0;
 }
 
 // ---------------------------------------------------------------------------
-// root log-likelihood: per-warp partial sums of w_p l_p
+// per-warp copy pipeline: op descriptors two ops ahead and the matrices of
+// the next op are copied into warp-private shared memory with cp.async while
+// the current op computes; completion is the hardware wait_group (no spin).
 // ---------------------------------------------------------------------------
-template <typename T, int RM>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_root4(int root, PathArgs<T> a, const double* __restrict__ pi, double* __restrict__ site,
-        double* __restrict__ part, int* __restrict__ err) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * kWarpsPerBlock + warp;
-    if (tile * kTile >= a.Ppad) return;
-    const int p = tile * kTile + lane;
-    double L = 0.0;
-    int cum = 0;
-    const int8_t* ts = (root < a.n_tips) ? a.tipst[root] : nullptr;
-    if (ts != nullptr) {
-        int s = ts[p];
-        double tot = 0;
-        for (int q = 0; q < 4; ++q) tot += pi[q];
-        L = (s >= 0 && s < 4) ? pi[s] : tot;
-        double cw = 0;
-        for (int r = 0; r < a.R; ++r) cw += (double)a.catw[r];
-        L *= cw;
-    } else {
-        const T* b = a.buf[root];
-#pragma unroll
-        for (int r = 0; r < RM; ++r) {
-            if (r < a.R) {
-                V4<T> x = ld4(b + ((size_t)r * a.Ppad + p) * 4);
-                double s = pi[0] * (double)x.x + pi[1] * (double)x.y + pi[2] * (double)x.z +
-                           pi[3] * (double)x.w;
-                L += (double)a.catw[r] * s;
-            }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ V4<T> lds4(const T* p) {
+    return ld4(p);
+}
+
+// NMAT matrices per op (post: P of both children; pre: P and dP of both),
+// each `matf` elements (all categories); obuf holds three descriptors.
+template <typename Op, typename T, int NMAT>
+struct WarpPipe {
+    Op* obuf;
+    T* mbuf;
+    int matf;
+    __device__ __forceinline__ void issue_op(const Op* ops, int j, int n, int lane) {
+        constexpr int chunks = sizeof(Op) / 16;
+        if (j < n && lane < chunks)
+            cp_async16(reinterpret_cast<char*>(obuf + j % 3) + lane * 16,
+                       reinterpret_cast<const char*>(ops + j) + lane * 16);
+    }
+    __device__ __forceinline__ void issue_mats(int j, int n, const int* idx, const T* mat,
+                                               int mat_stride, int lane) {
+        if (j >= n) return;
+        T* dst = mbuf + (j & 1) * NMAT * matf;
+        const int per = matf * (int)sizeof(T) / 16;
+        for (int q = lane; q < NMAT * per; q += 32) {
+            const int m = q / per, c = q % per;
+            const int slot = idx[m];
+            if (slot >= 0)
+                cp_async16(reinterpret_cast<char*>(dst + m * matf) + c * 16,
+                           reinterpret_cast<const char*>(mat + (size_t)slot * mat_stride) + c * 16);
         }
-        const int* sc = a.scale[root];
-        if (sc) cum = sc[p];
     }
-    double l = log(L) + 0.69314718055994530942 * (double)cum;
-    double contrib = 0.0;
-    if (p < a.P) {
-        if (!(L > 0.0) || !isfinite(l)) atomicOr(err, 1);
-        if (site) site[p] = l;
-        contrib = a.patw[p] * l;
+    __device__ __forceinline__ const T* mats(int k) const { return mbuf + (k & 1) * NMAT * matf; }
+};
+
+template <typename Op, typename T, int NMAT>
+__host__ __device__ constexpr size_t pipe_bytes(int R) {
+    return 3 * sizeof(Op) + 2 * (size_t)NMAT * kColStride * 4 * R * sizeof(T);
+}
+
+// Lane layout of the post- and pre-order kernels: LPP lanes share a
+// pattern and each holds CPL categories (r = r0 + j * LPP, j < CPL), so a
+// warp tile has 32 / LPP patterns. Fewer lanes per pattern amortise the
+// per-op work (op fetch, addressing, control) over more patterns; more lanes
+// lower the registers each lane needs.
+template <typename T, int LPP, int CPL, int NR>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_post4(const DevPostOp* __restrict__ ops, int n_ops, NucArgs<T> a) {
+    constexpr int TP = 32 / LPP;
+    // NR > 0: the category count is a compile-time constant
+    constexpr bool kFull = NR > 0 && LPP * CPL == NR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = lane % LPP, pp = lane / LPP;
+    const int R = NR > 0 ? NR : a.R;
+    const int cs = R * 4;  // matrix column stride (all categories of a column)
+    bool act[CPL];
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) act[j] = kFull || (r0 + j * LPP < R);
+    V4<T>* slots = reinterpret_cast<V4<T>*>(smem_raw) + (size_t)warp * a.n_slots * CPL * 32;
+    int* sexp = reinterpret_cast<int*>(reinterpret_cast<V4<T>*>(smem_raw) +
+                                       (size_t)kWarpsPerBlock * a.n_slots * CPL * 32) +
+                warp * a.n_slots * 32;
+    unsigned char* pipe_base = reinterpret_cast<unsigned char*>(
+        reinterpret_cast<int*>(reinterpret_cast<V4<T>*>(smem_raw) +
+                               (size_t)kWarpsPerBlock * a.n_slots * CPL * 32) +
+        kWarpsPerBlock * a.n_slots * 32);
+    WarpPipe<DevPostOp, T, 2> pipe;
+    pipe.obuf = reinterpret_cast<DevPostOp*>(pipe_base + (size_t)warp * pipe_bytes<DevPostOp, T, 2>(R));
+    pipe.mbuf = reinterpret_cast<T*>(pipe.obuf + 3);
+    pipe.matf = kColStride * 4 * R;
+    const V4<T> zero = {T(0), T(0), T(0), T(0)};
+    const int nw = gridDim.x * kWarpsPerBlock;
+    for (int tile = blockIdx.x * kWarpsPerBlock + warp; tile < a.n_tiles; tile += nw) {
+        const int p = tile * TP + pp;
+        const size_t off0 = ((size_t)r0 * a.Ppad + p) * 4;       // category r0
+        const size_t offj = (size_t)LPP * a.Ppad * 4;            // next category of this lane
+        V4<T> prev[CPL];
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) prev[j] = zero;
+        int prev_cum = 0;
+        int ts[kAhead][2];
+#pragma unroll
+        for (int j = 0; j < kAhead; ++j) {
+            const int4 h = op_head(ops, j, n_ops);
+            ts[j][0] = tip_state(a, h.x, h.z, p);
+            ts[j][1] = tip_state(a, h.y, h.w, p);
+        }
+        // pipeline prologue: descriptors 0 and 1, then matrices of op 0
+        __syncwarp();
+        pipe.issue_op(ops, 0, n_ops, lane);
+        pipe.issue_op(ops, 1, n_ops, lane);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncwarp();
+        pipe.issue_mats(0, n_ops, pipe.obuf[0].mat, a.mat, a.mat_stride, lane);
+        cp_async_commit();
+        for (int k = 0; k < n_ops; ++k) {
+            cp_async_wait_all();
+            __syncwarp();
+            pipe.issue_op(ops, k + 2, n_ops, lane);
+            if (k + 1 < n_ops)
+                pipe.issue_mats(k + 1, n_ops, pipe.obuf[(k + 1) % 3].mat, a.mat, a.mat_stride, lane);
+            cp_async_commit();
+            const int4 hn = op_head(ops, k + kAhead, n_ops);
+            const int tn0 = tip_state(a, hn.x, hn.z, p), tn1 = tip_state(a, hn.y, hn.w, p);
+            const DevPostOp op = pipe.obuf[k % 3];
+            const T* mk = pipe.mats(k);
+            V4<T> acc[CPL];
+            int cum = 0;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const T* mc = mk + c * pipe.matf + r0 * 4;
+                V4<T> v[CPL];
+                if (op.kind[c] == kTipStates) {
+                    const int col = tip_col((int8_t)ts[0][c]);
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j)
+                        v[j] = act[j] ? lds4(mc + col * cs + j * LPP * 4) : zero;
+                } else {
+                    V4<T> x[CPL];
+                    const int si = op.slot_in[c];
+                    if (si == kFromRegisters) {
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j) x[j] = prev[j];
+                        cum += prev_cum;
+                    } else if (si >= 0) {
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j) x[j] = slots[(si * CPL + j) * 32 + lane];
+                        cum += sexp[si * 32 + lane];
+                    } else {
+                        const T* b = (op.kind[c] == kTipPartials)
+                                         ? a.tipbuf[op.child[c]]
+                                         : a.pool + (size_t)op.child[c] * a.bstride;
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j) x[j] = act[j] ? ld4(b + off0 + j * offj) : zero;
+                        if (op.kind[c] == kInternal)
+                            cum += a.epool[(size_t)op.child[c] * a.Ppad + p];
+                    }
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j) {
+                        if (act[j]) {
+                            const T* col = mc + j * LPP * 4;
+                            const V4<T> c0 = lds4(col), c1 = lds4(col + cs), c2 = lds4(col + 2 * cs),
+                                        c3 = lds4(col + 3 * cs);
+                            const V4<T> xx = x[j];
+                            v[j].x = xx.x * c0.x + xx.y * c1.x + xx.z * c2.x + xx.w * c3.x;
+                            v[j].y = xx.x * c0.y + xx.y * c1.y + xx.z * c2.y + xx.w * c3.y;
+                            v[j].z = xx.x * c0.z + xx.y * c1.z + xx.z * c2.z + xx.w * c3.z;
+                            v[j].w = xx.x * c0.w + xx.y * c1.w + xx.z * c2.w + xx.w * c3.w;
+                        } else {
+                            v[j] = zero;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) acc[j] = (c == 0) ? v[j] : mul(acc[j], v[j]);
+            }
+#pragma unroll
+            for (int j = 0; j + 1 < kAhead; ++j) {
+                ts[j][0] = ts[j + 1][0];
+                ts[j][1] = ts[j + 1][1];
+            }
+            ts[kAhead - 1][0] = tn0;
+            ts[kAhead - 1][1] = tn1;
+            if (a.rescale) {
+                T m = vmax(acc[0]);
+#pragma unroll
+                for (int j = 1; j < CPL; ++j) m = fmax(m, vmax(acc[j]));
+#pragma unroll
+                for (int o = 1; o < LPP; o <<= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+                const int e = frexp_exp(m);
+                if (e != 0) {
+                    scale_by_pow2(acc, CPL, -e);
+                    cum += e;
+                }
+            }
+            if (op.store) {
+                T* d = a.pool + (size_t)op.dest * a.bstride + off0;
+#pragma unroll
+                for (int j = 0; j < CPL; ++j)
+                    if (act[j]) st4(d + j * offj, acc[j]);
+                if (r0 == 0) a.epool[(size_t)op.dest * a.Ppad + p] = cum;
+            }
+            if (op.slot_out >= 0) {
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) slots[(op.slot_out * CPL + j) * 32 + lane] = acc[j];
+                sexp[op.slot_out * 32 + lane] = cum;
+            }
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) prev[j] = acc[j];
+            prev_cum = cum;
+        }
+        cp_async_wait_all();
     }
-    contrib = warp_sum(contrib);
-    if (lane == 0) part[tile] = contrib;
+}
+
+// Sum over the LPP lanes of one pattern (every lane of the group gets it).
+template <int LPP, typename X>
+__device__ __forceinline__ X group_sum(X v) {
+#pragma unroll
+    for (int o = 1; o < LPP; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+// Sum over the patterns of a warp tile of a value that is equal on the LPP
+// lanes of each pattern.
+template <int LPP, typename X = double>
+__device__ __forceinline__ X tile_sum(X v) {
+#pragma unroll
+    for (int o = LPP; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// root log-likelihood: per-tile partial sums of w_p l_p
+// ---------------------------------------------------------------------------
+template <typename T, int LPP>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+k_root4(int kind, int root, NucArgs<T> a, const double* __restrict__ pi,
+        double* __restrict__ site, double* __restrict__ part, int* __restrict__ err) {
+    constexpr int TP = 32 / LPP;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = lane % LPP, pp = lane / LPP;
+    const bool ract = r < a.R;
+    const int nw = gridDim.x * kWarpsPerBlock;
+    for (int tile = blockIdx.x * kWarpsPerBlock + warp; tile < a.n_tiles; tile += nw) {
+        const int p = tile * TP + pp;
+        double Lr = 0.0;
+        int cum = 0;
+        if (kind == kTipStates) {
+            const int s = a.tips[(size_t)root * a.Ppad + p];
+            double v = (s >= 0 && s < 4) ? pi[s] : pi[0] + pi[1] + pi[2] + pi[3];
+            if (ract) Lr = (double)a.catw[r] * v;
+        } else {
+            if (ract) {
+                const T* b = (kind == kTipPartials) ? a.tipbuf[root]
+                                                    : a.pool + (size_t)root * a.bstride;
+                V4<T> x = ld4(b + ((size_t)r * a.Ppad + p) * 4);
+                Lr = (double)a.catw[r] * (pi[0] * (double)x.x + pi[1] * (double)x.y +
+                                          pi[2] * (double)x.z + pi[3] * (double)x.w);
+            }
+            if (kind == kInternal) cum = a.epool[(size_t)root * a.Ppad + p];
+        }
+        const double L = group_sum<LPP>(Lr);
+        const double l = log(L) + 0.69314718055994530942 * (double)cum;
+        double contrib = 0.0;
+        if (p < a.P) {
+            if (r == 0) {
+                if (!(L > 0.0) || !isfinite(l)) atomicOr(err, 1);
+                if (site) site[p] = l;
+            }
+            contrib = a.patw[p] * l;
+        }
+        contrib = tile_sum<LPP>(contrib);
+        if (lane == 0) part[tile] = contrib;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // fused pre-order pass + branch-length gradient
 // ---------------------------------------------------------------------------
-template <typename T, int RM>
+template <typename T, int LPP, int CPL, int NR>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_pre4(const DevPreOp* __restrict__ ops, int n_ops, PathArgs<T> a, const T* __restrict__ piw,
-       double* __restrict__ gpart, int n_tiles) {
+k_pre4(const DevPreOp* __restrict__ ops, int n_ops, NucArgs<T> a, const T* __restrict__ piw,
+       const T* __restrict__ Qw, double* __restrict__ gpart) {
+    constexpr int TP = 32 / LPP;
+    constexpr bool kFull = NR > 0 && LPP * CPL == NR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * kWarpsPerBlock + warp;
-    if (tile * kTile >= a.Ppad) return;
-    const int p = tile * kTile + lane;
-    const int R = a.R;
-    V4<T>* slots = reinterpret_cast<V4<T>*>(smem_raw) + (size_t)warp * a.n_slots * RM * 32;
+    const int r0 = lane % LPP, pp = lane / LPP;
+    const int R = NR > 0 ? NR : a.R;
+    const int cs = R * 4;  // matrix column stride (all categories of a column)
+    bool act[CPL];
+    T wr[CPL], wrr[CPL];
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+        act[j] = kFull || (r0 + j * LPP < R);
+        wr[j] = act[j] ? a.catw[r0 + j * LPP] : T(0);
+        wrr[j] = act[j] ? a.catw[r0 + j * LPP] * a.rates[r0 + j * LPP] : T(0);
+    }
+    // Q rows: an internal child's derivative term is rho q_c . (Q p_c), with
+    // q_c = P_c^T u_c before rescaling (dP/dt = rho Q P and Q, P commute), so
+    // only tip children need the dP columns
+    const V4<T> Q0 = ldg4(Qw), Q1 = ldg4(Qw + 4), Q2 = ldg4(Qw + 8), Q3 = ldg4(Qw + 12);
+    V4<T>* slots = reinterpret_cast<V4<T>*>(smem_raw) + (size_t)warp * a.n_slots * CPL * 32;
+    unsigned char* pipe_base = reinterpret_cast<unsigned char*>(
+        reinterpret_cast<V4<T>*>(smem_raw) + (size_t)kWarpsPerBlock * a.n_slots * CPL * 32);
+    WarpPipe<DevPreOp, T, 4> pipe;
+    pipe.obuf = reinterpret_cast<DevPreOp*>(pipe_base + (size_t)warp * pipe_bytes<DevPreOp, T, 4>(R));
+    pipe.mbuf = reinterpret_cast<T*>(pipe.obuf + 3);
+    pipe.matf = kColStride * 4 * R;
     const V4<T> piv = ldg4(piw);
-    const double wp = (p < a.P) ? a.patw[p] : 0.0;
-
-    for (int k = 0; k < n_ops; ++k) {
-        const DevPreOp op = ops[k];
-        V4<T> q[RM];
-        if (op.q_slot_in == -2) {
+    const V4<T> zero = {T(0), T(0), T(0), T(0)};
+    const int nw = gridDim.x * kWarpsPerBlock;
+    for (int tile = blockIdx.x * kWarpsPerBlock + warp; tile < a.n_tiles; tile += nw) {
+        const int p = tile * TP + pp;
+        const size_t off0 = ((size_t)r0 * a.Ppad + p) * 4;
+        const size_t offj = (size_t)LPP * a.Ppad * 4;
+        const T wpt = (p < a.P) ? (T)a.patw[p] : T(0);
+        // a child's post-order partial (memory, or tip partials), prefetched
+        auto child_x = [&](int child, int kind, V4<T>* x) {
+            if (kind == kTipStates || kind < 0) {
 #pragma unroll
-            for (int r = 0; r < RM; ++r) q[r] = piv;
-        } else if (op.q_slot_in >= 0) {
-            const V4<T>* s = slots + (size_t)op.q_slot_in * RM * 32;
+                for (int j = 0; j < CPL; ++j) x[j] = zero;
+                return;
+            }
+            const T* b = (kind == kTipPartials) ? a.tipbuf[child] : a.pool + (size_t)child * a.bstride;
 #pragma unroll
-            for (int r = 0; r < RM; ++r)
-                if (r < R) q[r] = s[r * 32 + lane];
-        } else {
-            const T* b = a.buf[op.q_buf_in];
+            for (int j = 0; j < CPL; ++j) x[j] = act[j] ? ld4(b + off0 + j * offj) : zero;
+        };
+        V4<T> prevq[CPL];  // the q output the next op reads from registers
 #pragma unroll
-            for (int r = 0; r < RM; ++r)
-                if (r < R) q[r] = ld4(b + ((size_t)r * a.Ppad + p) * 4);
+        for (int j = 0; j < CPL; ++j) prevq[j] = zero;
+        int ts[kAhead][2];
+#pragma unroll
+        for (int j = 0; j < kAhead; ++j) {
+            const int4 h = op_head(ops, j, n_ops);
+            ts[j][0] = tip_state(a, h.x, h.z, p);
+            ts[j][1] = tip_state(a, h.y, h.w, p);
         }
-        // v_c = P_c p_c and d_c = dP_c p_c for both children
-        V4<T> v[2][RM], d[2][RM];
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int ch = op.child[c];
-            const T* mc = a.mat + (size_t)op.mat[c] * a.mat_stride;
-            const T* dc = (op.dmat[c] >= 0) ? a.mat + (size_t)op.dmat[c] * a.mat_stride : nullptr;
-            const int8_t* ts = (ch < a.n_tips) ? a.tipst[ch] : nullptr;
-            if (ts != nullptr) {
-                const int col = tip_col(__ldg(ts + p));
-#pragma unroll
-                for (int r = 0; r < RM; ++r) {
-                    if (r < R) {
-                        v[c][r] = ldg4(mc + (r * kColStride + col) * 4);
-                        if (dc) d[c][r] = ldg4(dc + (r * kColStride + col) * 4);
-                    }
-                }
+        V4<T> xc[2][CPL];
+        {
+            const int4 h = op_head(ops, 0, n_ops);
+            child_x(h.x, h.z, xc[0]);
+            child_x(h.y, h.w, xc[1]);
+        }
+        __syncwarp();
+        pipe.issue_op(ops, 0, n_ops, lane);
+        pipe.issue_op(ops, 1, n_ops, lane);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncwarp();
+        {
+            const DevPreOp& o0 = pipe.obuf[0];
+            const int idx[4] = {o0.mat[0], o0.mat[1], o0.kind[0] != kInternal ? o0.dmat[0] : -1,
+                                o0.kind[1] != kInternal ? o0.dmat[1] : -1};
+            pipe.issue_mats(0, n_ops, idx, a.mat, a.mat_stride, lane);
+        }
+        cp_async_commit();
+        for (int k = 0; k < n_ops; ++k) {
+            cp_async_wait_all();
+            __syncwarp();
+            pipe.issue_op(ops, k + 2, n_ops, lane);
+            if (k + 1 < n_ops) {
+                const DevPreOp& o1 = pipe.obuf[(k + 1) % 3];
+                const int idx[4] = {o1.mat[0], o1.mat[1],
+                                    o1.kind[0] != kInternal ? o1.dmat[0] : -1,
+                                    o1.kind[1] != kInternal ? o1.dmat[1] : -1};
+                pipe.issue_mats(k + 1, n_ops, idx, a.mat, a.mat_stride, lane);
+            }
+            cp_async_commit();
+            const int4 hn = op_head(ops, k + kAhead, n_ops);
+            const int tn0 = tip_state(a, hn.x, hn.z, p), tn1 = tip_state(a, hn.y, hn.w, p);
+            V4<T> xn[2][CPL];
+            if (k + 1 < n_ops) {
+                const DevPreOp& o1 = pipe.obuf[(k + 1) % 3];
+                child_x(o1.child[0], o1.kind[0], xn[0]);
+                child_x(o1.child[1], o1.kind[1], xn[1]);
             } else {
-                const T* b = a.buf[ch];
+                child_x(0, -1, xn[0]);
+                child_x(0, -1, xn[1]);
+            }
+            const DevPreOp op = pipe.obuf[k % 3];
+            const T* mk = pipe.mats(k);
+            V4<T> q[CPL];
 #pragma unroll
-                for (int r = 0; r < RM; ++r) {
-                    if (r < R) {
-                        V4<T> x = ld4(b + ((size_t)r * a.Ppad + p) * 4);
-                        v[c][r] = matvec(mc + r * kColStride * 4, x);
-                        if (dc) d[c][r] = matvec(dc + r * kColStride * 4, x);
+            for (int j = 0; j < CPL; ++j) {
+                if (op.q_src == kFromRoot) q[j] = piv;
+                else if (op.q_src == kFromRegisters) q[j] = prevq[j];
+                else if (op.q_src >= 0) q[j] = slots[(op.q_src * CPL + j) * 32 + lane];
+                else q[j] = act[j] ? ld4(a.pool + (size_t)op.q_buf_in * a.bstride + off0 + j * offj)
+                                   : zero;
+            }
+            // v_c = P_c p_c for both children (a column for tips); smem
+            // matrices are [P_0, P_1, dP_0, dP_1], dP only for tip children
+            const int tcol[2] = {tip_col((int8_t)ts[0][0]), tip_col((int8_t)ts[0][1])};
+            V4<T> v[2][CPL];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const T* mc = mk + c * pipe.matf + r0 * 4;
+                if (op.kind[c] == kTipStates) {
+                    const int col = tcol[c];
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j)
+                        v[c][j] = act[j] ? lds4(mc + col * cs + j * LPP * 4) : zero;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j)
+                        v[c][j] = act[j] ? matvec(mc + j * LPP * 4, cs, xc[c][j]) : zero;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j + 1 < kAhead; ++j) {
+                ts[j][0] = ts[j + 1][0];
+                ts[j][1] = ts[j + 1][1];
+            }
+            ts[kAhead - 1][0] = tn0;
+            ts[kAhead - 1][1] = tn1;
+            // den: the pattern likelihood up to the scales of q and the children
+            T den_l = T(0);
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) den_l += wr[j] * dot(q[j], mul(v[0][j], v[1][j]));
+            const T den = group_sum<LPP>(den_l);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                V4<T> u[CPL];
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) u[j] = mul(q[j], v[1 - c][j]);
+                const bool tip = op.kind[c] != kInternal;
+                const T* mc = mk + c * pipe.matf + r0 * 4;
+                V4<T> qc[CPL];
+                if (!tip || op.need_q[c]) {
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j)
+                        qc[j] = act[j] ? matTvec(mc + j * LPP * 4, cs, u[j]) : zero;
+                }
+                if (op.edge[c] >= 0) {
+                    // numerator: tips u_c . (dP_c p_c) (a column of dP for tip
+                    // states, bit-identical to the product with a one-hot tip
+                    // partial); internal children rho q_c . (Q p_c). Per-pattern
+                    // ratio and the tile's sum
+                    // in working precision; FP64 (a slow unit on this part)
+                    // only once per tile and edge
+                    T num_l = T(0);
+                    if (tip) {
+                        const T* dc = mk + (2 + c) * pipe.matf + r0 * 4;
+                        const int col = tcol[c];
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j) {
+                            if (!act[j]) continue;
+                            const V4<T> dv = (op.kind[c] == kTipStates)
+                                                 ? lds4(dc + col * cs + j * LPP * 4)
+                                                 : matvec(dc + j * LPP * 4, cs, xc[c][j]);
+                            num_l += wr[j] * dot(u[j], dv);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j) {
+                            const V4<T> x = xc[c][j];
+                            const V4<T> Qx = {dot(Q0, x), dot(Q1, x), dot(Q2, x), dot(Q3, x)};
+                            num_l += wrr[j] * dot(qc[j], Qx);
+                        }
+                    }
+                    const T num = group_sum<LPP>(num_l);
+                    T g = wpt * (num / den);
+                    g = tile_sum<LPP, T>(g);
+                    if (lane == 0) gpart[(size_t)op.edge[c] * a.n_tiles + tile] = (double)g;
+                }
+                if (op.need_q[c]) {
+                    T m = T(0);
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j) m = fmax(m, vmax(qc[j]));
+#pragma unroll
+                    for (int o = 1; o < LPP; o <<= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+                    const int e = frexp_exp(m);
+                    if (e != 0) scale_by_pow2(qc, CPL, -e);
+                    if (op.q_slot_out[c] >= 0) {
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j)
+                            slots[(op.q_slot_out[c] * CPL + j) * 32 + lane] = qc[j];
+                    }
+                    if (op.q_buf_out[c] >= 0) {
+                        T* b = a.pool + (size_t)op.q_buf_out[c] * a.bstride + off0;
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j)
+                            if (act[j]) st4(b + j * offj, qc[j]);
+                    }
+                    if (op.q_reg == c) {
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j) prevq[j] = qc[j];
                     }
                 }
             }
-        }
-        // den = sum_r w_r q . (v_a o v_b): the pattern likelihood up to scale
-        T den = T(0);
 #pragma unroll
-        for (int r = 0; r < RM; ++r)
-            if (r < R) den += a.catw[r] * dot(q[r], mul(v[0][r], v[1][r]));
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            V4<T> u[RM];
-#pragma unroll
-            for (int r = 0; r < RM; ++r)
-                if (r < R) u[r] = mul(q[r], v[1 - c][r]);
-            if (op.edge[c] >= 0) {
-                T num = T(0);
-#pragma unroll
-                for (int r = 0; r < RM; ++r)
-                    if (r < R) num += a.catw[r] * dot(u[r], d[c][r]);
-                double g = (p < a.P) ? wp * ((double)num / (double)den) : 0.0;
-                g = warp_sum(g);
-                if (lane == 0) gpart[(size_t)op.edge[c] * n_tiles + tile] = g;
-            }
-            if (op.need_q[c]) {
-                const T* mc = a.mat + (size_t)op.mat[c] * a.mat_stride;
-                V4<T> qc[RM];
-                T m = T(0);
-#pragma unroll
-                for (int r = 0; r < RM; ++r) {
-                    if (r < R) {
-                        qc[r] = matTvec(mc + r * kColStride * 4, u[r]);
-                        m = fmax(m, vmax(qc[r]));
-                    }
-                }
-                const int e = frexp_exp(m);
-                if (e != 0) scale_by_pow2(qc, R < RM ? R : RM, -e);
-                if (op.q_slot_out[c] >= 0) {
-                    V4<T>* s = slots + (size_t)op.q_slot_out[c] * RM * 32;
-#pragma unroll
-                    for (int r = 0; r < RM; ++r)
-                        if (r < R) s[r * 32 + lane] = qc[r];
-                }
-                if (op.q_buf_out[c] >= 0) {
-                    T* b = a.buf[op.q_buf_out[c]];
-#pragma unroll
-                    for (int r = 0; r < RM; ++r)
-                        if (r < R) st4(b + ((size_t)r * a.Ppad + p) * 4, qc[r]);
-                }
+            for (int j = 0; j < CPL; ++j) {
+                xc[0][j] = xn[0][j];
+                xc[1][j] = xn[1][j];
             }
         }
+        cp_async_wait_all();
     }
 }
 
 // ---------------------------------------------------------------------------
 // edge derivatives from stored pre- and post-order partials
 // ---------------------------------------------------------------------------
-template <typename T, int RM>
+template <typename T, int LPP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_edge4(const DevEdge* __restrict__ edges, int n_edges, PathArgs<T> a, const T* __restrict__ Qw,
-        double* __restrict__ gpart, int n_tiles) {
+k_edge4(const DevEdge* __restrict__ edges, int n_edges, NucArgs<T> a, const T* __restrict__ Qw,
+        double* __restrict__ gpart) {
+    constexpr int TP = 32 / LPP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x * kWarpsPerBlock + warp;
-    if (tile * kTile >= a.Ppad) return;
-    const int p = tile * kTile + lane;
-    const int R = a.R;
-    // Q rows as V4
+    const int r = lane % LPP, pp = lane / LPP;
+    const bool ract = r < a.R;
+    const T wr = ract ? a.catw[r] : T(0);
+    const T rr = ract ? a.rates[r] : T(0);
     const V4<T> q0 = ldg4(Qw), q1 = ldg4(Qw + 4), q2 = ldg4(Qw + 8), q3 = ldg4(Qw + 12);
-    const double wp = (p < a.P) ? a.patw[p] : 0.0;
-    for (int k = 0; k < n_edges; ++k) {
-        const DevEdge e = edges[k];
-        const int8_t* ts = (e.post < a.n_tips) ? a.tipst[e.post] : nullptr;
-        const T* qb = a.buf[e.pre];
-        T num = T(0), den = T(0);
-        V4<T> onehot;
-        if (ts) {
-            int s = ts[p];
-            bool amb = !(s >= 0 && s < 4);
-            onehot = {T(amb || s == 0), T(amb || s == 1), T(amb || s == 2), T(amb || s == 3)};
-        }
-#pragma unroll
-        for (int r = 0; r < RM; ++r) {
-            if (r < R) {
-                V4<T> x = ts ? onehot : ld4(a.buf[e.post] + ((size_t)r * a.Ppad + p) * 4);
-                V4<T> qq = ld4(qb + ((size_t)r * a.Ppad + p) * 4);
-                V4<T> Qx = {dot(q0, x), dot(q1, x), dot(q2, x), dot(q3, x)};
-                num += a.catw[r] * a.rates[r] * dot(qq, Qx);
-                den += a.catw[r] * dot(qq, x);
+    const int nw = gridDim.x * kWarpsPerBlock;
+    for (int tile = blockIdx.x * kWarpsPerBlock + warp; tile < a.n_tiles; tile += nw) {
+        const int p = tile * TP + pp;
+        const size_t off = ((size_t)r * a.Ppad + p) * 4;
+        const T wpt = (p < a.P) ? (T)a.patw[p] : T(0);
+        for (int k = 0; k < n_edges; ++k) {
+            const DevEdge e = edges[k];
+            V4<T> x = {T(0), T(0), T(0), T(0)}, qq = {T(0), T(0), T(0), T(0)};
+            if (e.kind == kTipStates) {
+                const int s = a.tips[(size_t)e.post * a.Ppad + p];
+                const bool amb = !(s >= 0 && s < 4);
+                x = {T(amb || s == 0), T(amb || s == 1), T(amb || s == 2), T(amb || s == 3)};
+            } else if (ract) {
+                const T* b = (e.kind == kTipPartials) ? a.tipbuf[e.post]
+                                                      : a.pool + (size_t)e.post * a.bstride;
+                x = ld4(b + off);
             }
+            if (ract) qq = ld4(a.pool + (size_t)e.pre * a.bstride + off);
+            const V4<T> Qx = {dot(q0, x), dot(q1, x), dot(q2, x), dot(q3, x)};
+            const T num = group_sum<LPP>(wr * rr * dot(qq, Qx));
+            const T den = group_sum<LPP>(wr * dot(qq, x));
+            T g = wpt * (num / den);
+            g = tile_sum<LPP, T>(g);
+            if (lane == 0) gpart[(size_t)e.edge * a.n_tiles + tile] = (double)g;
         }
-        double g = (p < a.P) ? wp * ((double)num / (double)den) : 0.0;
-        g = warp_sum(g);
-        if (lane == 0) gpart[(size_t)e.edge * n_tiles + tile] = g;
     }
 }
 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+// Lanes per pattern of the root and edge-derivative kernels (one category
+// per lane).
+int nuc_lanes(const Instance* I) {
+    return I->R <= 1 ? 1 : I->R <= 2 ? 2 : I->R <= 4 ? 4 : 8;
+}
+
+// Lanes per pattern of the post- and pre-order kernels: 1 (all categories in
+// one lane) unless TL_NUC_LANES selects 1, 2, 4 or 8.
+int nuc_lanes_main(const Instance* I) {
+    static int env = -1;
+    if (env < 0) {
+        const char* s = getenv("TL_NUC_LANES");
+        env = s ? atoi(s) : 0;
+    }
+    int lpp = (env == 1 || env == 2 || env == 4 || env == 8) ? env : 1;
+    if (I->R > 4 && lpp == 1) lpp = 2;    // at most four categories per lane
+    return lpp;
+}
+
+int nuc_cpl(const Instance* I) {
+    const int lpp = nuc_lanes_main(I);
+    return (I->R + lpp - 1) / lpp;
+}
+
+int nuc_tiles_for(const Instance* I, int lpp) { return I->Ppad / (32 / lpp); }
+int nuc_tiles(const Instance* I) { return nuc_tiles_for(I, nuc_lanes(I)); }
+int nuc_tiles_main(const Instance* I) { return nuc_tiles_for(I, nuc_lanes_main(I)); }
+
+int nuc_smem_per_slot(const Instance* I) {
+    return 32 * (nuc_cpl(I) * 4 * I->elt + (int)sizeof(int));
+}
+
 template <typename T>
-static PathArgs<T> make_args(const Instance* I, int n_slots) {
-    PathArgs<T> a;
-    a.buf = reinterpret_cast<T* const*>(I->d_buf);
-    a.scale = I->d_scale;
-    a.tipst = I->d_tipst;
+static NucArgs<T> make_args(const Instance* I, int n_slots) {
+    NucArgs<T> a;
+    a.pool = reinterpret_cast<T*>(I->pool);
+    a.epool = I->scale_pool;
+    a.tips = I->tip_pool;
+    a.tipbuf = reinterpret_cast<T* const*>(I->d_buf);
     a.mat = reinterpret_cast<const T*>(I->d_matw);
     a.patw = I->d_patw;
-    a.n_tips = I->n_tips;
+    a.bstride = (size_t)I->R * I->Ppad * 4;
     a.P = I->P;
     a.Ppad = I->Ppad;
     a.R = I->R;
-    a.S = I->S;
-    a.Spad = I->Spad;
     a.n_slots = n_slots;
     a.rescale = I->rescale;
     a.mat_stride = (int)I->matw_stride;
+    a.n_tiles = nuc_tiles(I);  // launchers of the main kernels override
     for (int r = 0; r < kMaxCat; ++r) {
         a.catw[r] = (T)(r < I->R ? I->h_catw[r] : 0.0);
         a.rates[r] = (T)(r < I->R ? I->h_rates[r] : 0.0);
@@ -443,99 +748,120 @@ static PathArgs<T> make_args(const Instance* I, int n_slots) {
     return a;
 }
 
-int nuc_smem_per_slot(const Instance* I) {
-    const int RM = I->R <= 4 ? 4 : 8;
-    return RM * 32 * 4 * I->elt + 32 * (int)sizeof(int);
+// Persistent grid: as many blocks as fit at once, never more than the tiles.
+template <typename K>
+static int grid_for(const Instance* I, K kernel, size_t smem, int n_tiles) {
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kWarpsPerBlock * 32, smem);
+    const int need = (n_tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int fit = std::max(1, per_sm) * std::max(1, sms);
+    return std::max(1, std::min(need, fit));
 }
 
-static int n_blocks(const Instance* I) {
-    const int tiles = I->Ppad / kTile;
-    return (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
-}
+#define TL_NUC_DISPATCH(I, FN, ...)                                      \
+    do {                                                                 \
+        const int lpp_ = nuc_lanes(I);                                   \
+        if ((I)->prec == kF32) {                                         \
+            if (lpp_ == 1) FN<float, 1>(__VA_ARGS__);                    \
+            else if (lpp_ == 2) FN<float, 2>(__VA_ARGS__);               \
+            else if (lpp_ == 4) FN<float, 4>(__VA_ARGS__);               \
+            else FN<float, 8>(__VA_ARGS__);                              \
+        } else {                                                         \
+            if (lpp_ == 1) FN<double, 1>(__VA_ARGS__);                   \
+            else if (lpp_ == 2) FN<double, 2>(__VA_ARGS__);              \
+            else if (lpp_ == 4) FN<double, 4>(__VA_ARGS__);              \
+            else FN<double, 8>(__VA_ARGS__);                             \
+        }                                                                \
+    } while (0)
 
-template <typename T, int RM>
+// Four categories (the common case) get kernels specialised on the count
+// and on the lane layout; other counts use a runtime-R kernel.
+#define TL_MAIN_DISPATCH_T(T, I, FN, ...)                                   \
+    do {                                                                    \
+        const int lpp_ = nuc_lanes_main(I);                                 \
+        if ((I)->R == 4) {                                                  \
+            if (lpp_ == 1) FN<T, 1, 4, 4>(__VA_ARGS__);                     \
+            else if (lpp_ == 2) FN<T, 2, 2, 4>(__VA_ARGS__);                \
+            else FN<T, 4, 1, 4>(__VA_ARGS__);                               \
+        } else if ((I)->R < 4) {                                            \
+            FN<T, 4, 1, 0>(__VA_ARGS__);                                    \
+        } else {                                                            \
+            FN<T, 8, 1, 0>(__VA_ARGS__);                                    \
+        }                                                                   \
+    } while (0)
+#define TL_MAIN_DISPATCH(I, FN, ...)                                        \
+    do {                                                                    \
+        if ((I)->prec == kF32) TL_MAIN_DISPATCH_T(float, I, FN, __VA_ARGS__); \
+        else TL_MAIN_DISPATCH_T(double, I, FN, __VA_ARGS__);               \
+    } while (0)
+
+template <typename T, int LPP, int CPL, int NR>
 static void post4_t(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots) {
-    size_t smem = (size_t)kWarpsPerBlock * n_slots * (RM * 32 * sizeof(V4<T>) + 32 * sizeof(int));
-    cudaFuncSetAttribute(k_post4<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_post4<T, RM><<<n_blocks(I), kWarpsPerBlock * 32, smem, I->stream>>>(d_ops, n_ops,
-                                                                           make_args<T>(I, n_slots));
+    const size_t smem = (size_t)kWarpsPerBlock *
+                        (n_slots * nuc_smem_per_slot(I) + pipe_bytes<DevPostOp, T, 2>(I->R));
+    cudaFuncSetAttribute(k_post4<T, LPP, CPL, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    NucArgs<T> a = make_args<T>(I, n_slots);
+    a.n_tiles = nuc_tiles_for(I, LPP);
+    const int grid = grid_for(I, k_post4<T, LPP, CPL, NR>, smem, a.n_tiles);
+    k_post4<T, LPP, CPL, NR><<<grid, kWarpsPerBlock * 32, smem, I->stream>>>(d_ops, n_ops, a);
 }
 
 int launch_post4(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots) {
-    if (I->prec == kF32) {
-        if (I->R <= 4) post4_t<float, 4>(I, d_ops, n_ops, n_slots);
-        else post4_t<float, 8>(I, d_ops, n_ops, n_slots);
-    } else {
-        if (I->R <= 4) post4_t<double, 4>(I, d_ops, n_ops, n_slots);
-        else post4_t<double, 8>(I, d_ops, n_ops, n_slots);
-    }
+    TL_MAIN_DISPATCH(I, post4_t, I, d_ops, n_ops, n_slots);
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "post-order kernel");
 }
 
-int launch_root4(Instance* I, int root, int model, double* d_site, double* d_part, int n_tiles) {
-    (void)n_tiles;
-    const double* pi = I->models[model].pi;
-    if (I->prec == kF32) {
-        if (I->R <= 4)
-            k_root4<float, 4><<<n_blocks(I), kWarpsPerBlock * 32, 0, I->stream>>>(
-                root, make_args<float>(I, 0), pi, d_site, d_part, I->d_err + 1);
-        else
-            k_root4<float, 8><<<n_blocks(I), kWarpsPerBlock * 32, 0, I->stream>>>(
-                root, make_args<float>(I, 0), pi, d_site, d_part, I->d_err + 1);
-    } else {
-        if (I->R <= 4)
-            k_root4<double, 4><<<n_blocks(I), kWarpsPerBlock * 32, 0, I->stream>>>(
-                root, make_args<double>(I, 0), pi, d_site, d_part, I->d_err + 1);
-        else
-            k_root4<double, 8><<<n_blocks(I), kWarpsPerBlock * 32, 0, I->stream>>>(
-                root, make_args<double>(I, 0), pi, d_site, d_part, I->d_err + 1);
-    }
+template <typename T, int LPP>
+static void root4_t(Instance* I, int kind, int root, const double* pi, double* d_site,
+                    double* d_part) {
+    const int grid = grid_for(I, k_root4<T, LPP>, 0, nuc_tiles(I));
+    k_root4<T, LPP><<<grid, kWarpsPerBlock * 32, 0, I->stream>>>(
+        kind, root, make_args<T>(I, 0), pi, d_site, d_part, I->d_err + 1);
+}
+
+int launch_root4(Instance* I, int root_kind, int root, int model, double* d_site,
+                 double* d_part) {
+    TL_NUC_DISPATCH(I, root4_t, I, root_kind, root, I->models[model].pi, d_site, d_part);
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "root kernel");
 }
 
-template <typename T, int RM>
+template <typename T, int LPP, int CPL, int NR>
 static void pre4_t(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, const void* piw,
-                   double* d_gpart, int n_tiles) {
-    size_t smem = (size_t)kWarpsPerBlock * n_slots * RM * 32 * sizeof(V4<T>);
-    cudaFuncSetAttribute(k_pre4<T, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_pre4<T, RM><<<n_blocks(I), kWarpsPerBlock * 32, smem, I->stream>>>(
-        d_ops, n_ops, make_args<T>(I, n_slots), reinterpret_cast<const T*>(piw), d_gpart, n_tiles);
+                   const void* Qw, double* d_gpart) {
+    const size_t smem = (size_t)kWarpsPerBlock * ((size_t)n_slots * CPL * 32 * 4 * sizeof(T) +
+                                                  pipe_bytes<DevPreOp, T, 4>(I->R));
+    cudaFuncSetAttribute(k_pre4<T, LPP, CPL, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    NucArgs<T> a = make_args<T>(I, n_slots);
+    a.n_tiles = nuc_tiles_for(I, LPP);
+    const int grid = grid_for(I, k_pre4<T, LPP, CPL, NR>, smem, a.n_tiles);
+    k_pre4<T, LPP, CPL, NR><<<grid, kWarpsPerBlock * 32, smem, I->stream>>>(
+        d_ops, n_ops, a, reinterpret_cast<const T*>(piw), reinterpret_cast<const T*>(Qw), d_gpart);
 }
 
 int launch_pre4(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, int model,
-                double* d_gpart, int n_tiles) {
-    const void* piw = I->models[model].piw;
-    if (I->prec == kF32) {
-        if (I->R <= 4) pre4_t<float, 4>(I, d_ops, n_ops, n_slots, piw, d_gpart, n_tiles);
-        else pre4_t<float, 8>(I, d_ops, n_ops, n_slots, piw, d_gpart, n_tiles);
-    } else {
-        if (I->R <= 4) pre4_t<double, 4>(I, d_ops, n_ops, n_slots, piw, d_gpart, n_tiles);
-        else pre4_t<double, 8>(I, d_ops, n_ops, n_slots, piw, d_gpart, n_tiles);
-    }
+                double* d_gpart) {
+    TL_MAIN_DISPATCH(I, pre4_t, I, d_ops, n_ops, n_slots, I->models[model].piw,
+                     I->models[model].Qw, d_gpart);
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "pre-order kernel");
 }
 
-int launch_edge4(Instance* I, const DevEdge* d_edges, int n_edges, int model, double* d_gpart,
-                 int n_tiles) {
-    const void* Qw = I->models[model].Qw;
-    if (I->prec == kF32) {
-        if (I->R <= 4)
-            k_edge4<float, 4><<<n_blocks(I), kWarpsPerBlock * 32, 0, I->stream>>>(
-                d_edges, n_edges, make_args<float>(I, 0), (const float*)Qw, d_gpart, n_tiles);
-        else
-            k_edge4<float, 8><<<n_blocks(I), kWarpsPerBlock * 32, 0, I->stream>>>(
-                d_edges, n_edges, make_args<float>(I, 0), (const float*)Qw, d_gpart, n_tiles);
-    } else {
-        if (I->R <= 4)
-            k_edge4<double, 4><<<n_blocks(I), kWarpsPerBlock * 32, 0, I->stream>>>(
-                d_edges, n_edges, make_args<double>(I, 0), (const double*)Qw, d_gpart, n_tiles);
-        else
-            k_edge4<double, 8><<<n_blocks(I), kWarpsPerBlock * 32, 0, I->stream>>>(
-                d_edges, n_edges, make_args<double>(I, 0), (const double*)Qw, d_gpart, n_tiles);
-    }
+template <typename T, int LPP>
+static void edge4_t(Instance* I, const DevEdge* d_edges, int n_edges, const void* Qw,
+                    double* d_gpart) {
+    const int grid = grid_for(I, k_edge4<T, LPP>, 0, nuc_tiles(I));
+    k_edge4<T, LPP><<<grid, kWarpsPerBlock * 32, 0, I->stream>>>(
+        d_edges, n_edges, make_args<T>(I, 0), reinterpret_cast<const T*>(Qw), d_gpart);
+}
+
+int launch_edge4(Instance* I, const DevEdge* d_edges, int n_edges, int model, double* d_gpart) {
+    TL_NUC_DISPATCH(I, edge4_t, I, d_edges, n_edges, I->models[model].Qw, d_gpart);
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "edge-derivative kernel");
 }
