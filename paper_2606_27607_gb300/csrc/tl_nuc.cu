@@ -425,8 +425,11 @@ k_root4(int kind, int root, NucArgs<T> a, const double* __restrict__ pi,
 // ---------------------------------------------------------------------------
 // fused pre-order pass + branch-length gradient
 // ---------------------------------------------------------------------------
+#ifndef TL_PRE_MIN_BLOCKS
+#define TL_PRE_MIN_BLOCKS 1
+#endif
 template <typename T, int LPP, int CPL, int NR>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, TL_PRE_MIN_BLOCKS)
 k_pre4(const DevPreOp* __restrict__ ops, int n_ops, NucArgs<T> a, const T* __restrict__ piw,
        const T* __restrict__ Qw, double* __restrict__ gpart) {
     constexpr int TP = 32 / LPP;
