@@ -15,6 +15,17 @@ namespace tl {
 
 static thread_local std::string g_create_err;
 
+// Round an FP32 value to TF32 (10 explicit mantissa bits), nearest with ties
+// away from zero, as cvt.rna.tf32.f32 does on the device.
+float tf32_host(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u = (u + 0x1000u) & 0xffffe000u;
+    float y;
+    std::memcpy(&y, &u, 4);
+    return y;
+}
+
 int fail(Instance* I, int code, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -206,6 +217,26 @@ int ensure_out(Instance* I, size_t n) {
 }
 
 bool use_nuc(const Instance* I) { return I->S == 4 && (I->prec == kF32 || I->prec == kF64); }
+bool use_tc(const Instance* I) { return I->prec == kTF32; }
+
+// Device area `which` with at least `bytes` (contents not kept).
+void* area(Instance* I, int which, size_t bytes, int* rc) {
+    OpArea& A = extra(I).areas[which];
+    if (A.cap < bytes) {
+        if (A.d) {
+            cudaStreamSynchronize(I->stream);
+            cudaFree(A.d);
+            I->bytes -= A.cap;
+            A.d = nullptr;
+        }
+        const size_t cap = std::max<size_t>(bytes * 2, 4096);
+        if ((*rc = dev_alloc(I, &A.d, cap, "op list"))) return nullptr;
+        A.cap = cap;
+    }
+    A.last.clear();
+    *rc = TL_OK;
+    return A.d;
+}
 
 int max_slots(const Instance* I) {
     // keep the per-block on-chip slot area near 56 KB so four blocks
@@ -606,7 +637,8 @@ int tl_destroy(tl_instance* inst) {
     };
     fr(I->pool);
     fr(I->scale_pool);
-    for (void* p : I->tip_part) fr(p);
+    if (I->prec != kTF32)
+        for (void* p : I->tip_part) fr(p);
     fr(I->tip_pool);
     fr(I->d_buf);
     fr(I->d_scale);
@@ -626,6 +658,8 @@ int tl_destroy(tl_instance* inst) {
     }
     fr(I->d_red);
     fr(I->d_err);
+    fr(I->d_rowsum);
+    fr(I->tc_tip_pool);
     fr(I->d_tmp);
     if (I->host_extra) {
         Extra* X = reinterpret_cast<Extra*>(I->host_extra);
@@ -661,15 +695,18 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
                 : (precs == TL_PREC_TF32) ? kTF32 : kBF16X3;
     if (prec == kF32 && n_states != 4)
         return fail(nullptr, TL_ERR_UNSUPPORTED, "TL_PREC_F32 is built for 4 states");
-    if ((prec == kTF32 || prec == kBF16X3))
-        return fail(nullptr, TL_ERR_UNSUPPORTED, "tensor-core precisions are not built in this library");
+    if (prec == kBF16X3)
+        return fail(nullptr, TL_ERR_UNSUPPORTED, "TL_PREC_BF16X3 is not built in this library");
+    if (prec == kTF32 && (n_states < 33 || n_states > 64))
+        return fail(nullptr, TL_ERR_UNSUPPORTED, "TL_PREC_TF32 is built for 33..64 states");
     if ((flags & TL_SCALE_NONE) && prec != kF64)
         return fail(nullptr, TL_ERR_ARG, "TL_SCALE_NONE needs TL_PREC_F64");
 
     Instance* I = new Instance();
     I->n_tips = n_tips;
     I->P = n_patterns;
-    I->Ppad = ((n_patterns + kPadPatterns - 1) / kPadPatterns) * kPadPatterns;
+    const int pad = (prec == kTF32 || prec == kBF16X3) ? 128 : kPadPatterns;
+    I->Ppad = ((n_patterns + pad - 1) / pad) * pad;
     I->S = n_states;
     I->Spad = (n_states == 4) ? 4 : ((n_states + 3) / 4) * 4;
     if (prec == kTF32 || prec == kBF16X3) I->Spad = 64;
@@ -732,6 +769,7 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
     if ((rc = dev_alloc(I, &I->d_mat64, sizeof(double) * mat64 * n_matrices, "matrices")))
         return bail(rc);
     if (use_nuc(I)) I->matw_stride = (size_t)I->R * kColStride * 4;
+    else if (prec == kTF32) I->matw_stride = (size_t)2 * I->R * I->Spad * I->Spad;
     else I->matw_stride = (size_t)I->R * (I->Spad + 1) * I->Spad;
     if ((rc = dev_alloc(I, &I->d_matw, (size_t)I->elt * I->matw_stride * n_matrices, "matrix copies")))
         return bail(rc);
@@ -748,6 +786,12 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
             (rc = dev_alloc(I, &M.piw, (size_t)I->elt * I->Spad, "pi copy")) ||
             (rc = dev_alloc(I, &M.Qw, (size_t)I->elt * SS, "Q copy")))
             return bail(rc);
+    }
+    if (prec == kTF32) {
+        if ((rc = dev_alloc(I, &I->d_rowsum, sizeof(float) * (size_t)n_matrices * I->R * I->Spad,
+                            "row sums")))
+            return bail(rc);
+        if ((rc = tc_setup(I))) return bail(rc);
     }
     if ((rc = dev_alloc(I, &I->d_err, sizeof(int) * 4, "error flags"))) return bail(rc);
     cudaMemsetAsync(I->d_err, 0, sizeof(int) * 4, I->stream);
@@ -824,7 +868,15 @@ int tl_set_tip_partials(tl_instance* inst, int tip, const double* partials) {
             return fail(I, TL_ERR_NUMERIC, "tip partial %zu is negative or not finite", i);
     const size_t n = (size_t)I->R * I->Ppad * I->Spad;
     int rc;
-    if (!I->tip_part[tip]) {
+    if (I->prec == kTF32) {
+        // tensor-core instances keep tip partials in one pool the TMA map covers
+        if (!I->tc_tip_pool) {
+            if ((rc = dev_alloc(I, &I->tc_tip_pool, n * sizeof(float) * I->n_tips, "tip partials")))
+                return rc;
+            if ((rc = tc_set_tip_pool(I))) return rc;
+        }
+        I->tip_part[tip] = I->tc_tip_pool + n * tip;
+    } else if (!I->tip_part[tip]) {
         if ((rc = dev_alloc(I, &I->tip_part[tip], n * I->elt, "tip partials"))) return rc;
     }
     std::vector<char> h(n * I->elt);
@@ -834,6 +886,7 @@ int tl_set_tip_partials(tl_instance* inst, int tip, const double* partials) {
                 double v = (s >= I->S) ? 0.0 : (p < I->P ? partials[(size_t)p * I->S + s] : 1.0);
                 size_t off = ((size_t)r * I->Ppad + p) * I->Spad + s;
                 if (I->elt == 8) reinterpret_cast<double*>(h.data())[off] = v;
+                else if (I->prec == kTF32) reinterpret_cast<float*>(h.data())[off] = tf32_host((float)v);
                 else reinterpret_cast<float*>(h.data())[off] = (float)v;
             }
     cudaMemcpyAsync(I->tip_part[tip], h.data(), h.size(), cudaMemcpyHostToDevice, I->stream);
@@ -1110,7 +1163,14 @@ int tl_update_partials(tl_instance* inst, const tl_op* ops, int count) {
     if (count < 0 || (count > 0 && !ops)) return fail(I, TL_ERR_ARG, "bad op list");
     if (count == 0) return TL_OK;
     int rc;
-    if (use_nuc(I)) {
+    if (use_tc(I)) {
+        PostPlan plan;
+        if ((rc = plan_post(I, ops, count, &plan, true))) return rc;
+        const size_t bytes = (size_t)count * 32;
+        void* d = area(I, 0, bytes, &rc);
+        if (rc) return rc;
+        if ((rc = launch_post_tc(I, ops, count, d, bytes))) return rc;
+    } else if (use_nuc(I)) {
         PostPlan plan;
         if ((rc = plan_post(I, ops, count, &plan, false))) return rc;
         void* d_ops = nullptr;
@@ -1133,6 +1193,14 @@ static int root_common(Instance* I, int root, int model, double* d_site, double*
     if (model < 0 || model >= I->n_models || !I->models[model].ready)
         return fail(I, TL_ERR_STATE, "model %d not set", model);
     int rc;
+    if (use_tc(I)) {
+        if (root < I->n_tips) return fail(I, TL_ERR_UNSUPPORTED, "root must be an internal buffer");
+        const int parts = I->Ppad / 128;
+        if ((rc = ensure_scratch(I, parts))) return rc;
+        if ((rc = h2d(I, I->d_tmp, I->h_catw, sizeof(double) * I->R))) return rc;
+        if ((rc = launch_root_tc(I, root - I->n_tips, model, d_site, I->d_red, parts))) return rc;
+        return reduce_fixed(I, I->d_red, 1, parts, d_out);
+    }
     if (use_nuc(I)) {
         const int n_tiles = nuc_tiles(I);
         if ((rc = ensure_scratch(I, n_tiles))) return rc;
@@ -1179,6 +1247,7 @@ static int pre_common(Instance* I, const tl_pre_op* ops, int count, int model, i
     if (model < 0 || model >= I->n_models || !I->models[model].ready)
         return fail(I, TL_ERR_STATE, "model %d not set", model);
     if (n_grad < 0) return fail(I, TL_ERR_ARG, "n_grad < 0");
+    if (use_tc(I)) return fail(I, TL_ERR_UNSUPPORTED, "pre-order pass not built for TL_PREC_TF32");
     PrePlan plan;
     int rc = plan_pre(I, ops, count, n_grad, store_all, &plan);
     if (rc) return rc;
@@ -1266,6 +1335,7 @@ int tl_edge_derivatives(tl_instance* inst, const tl_edge* edges, int count, int 
         return fail(I, TL_ERR_ARG, "bad arguments");
     if (model < 0 || model >= I->n_models || !I->models[model].ready)
         return fail(I, TL_ERR_STATE, "model %d not set", model);
+    if (use_tc(I)) return fail(I, TL_ERR_UNSUPPORTED, "edge derivatives not built for TL_PREC_TF32");
     std::vector<int> row(std::max(n_grad, 1), -1), map;
     std::vector<tl_edge> e(edges, edges + count);
     for (int k = 0; k < count; ++k) {
@@ -1314,3 +1384,9 @@ int tl_edge_derivatives(tl_instance* inst, const tl_edge* edges, int count, int 
 }
 
 }  // extern "C"
+
+namespace tl {
+int upload_bytes(Instance* I, void* dst, const void* src, size_t bytes) {
+    return h2d(I, dst, src, bytes);
+}
+}  // namespace tl

@@ -2,6 +2,7 @@
 // state and the launchers each translation unit exports).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -140,6 +141,10 @@ struct Instance {
     double* d_tmp = nullptr;         // small staging (params, lengths)
     size_t tmp_cap = 0;
     void* host_extra = nullptr;      // host-side helper state (tl_api.cu)
+    // tensor-core (TF32) instances
+    float* d_rowsum = nullptr;       // [mat][R][64] row sums of the rounded P
+    float* tc_tip_pool = nullptr;    // [n_tips][R][Ppad][64] tip partials (lazy)
+    std::vector<unsigned char> tmaps;  // CUtensorMap x3: pool, tip pool, matrices
 
     size_t bytes = 0;
     unsigned long long launches = 0; // kernels this instance has launched
@@ -179,7 +184,16 @@ int launch_edge_generic(Instance* I, const tl_edge* h_edges, int n_edges, int mo
                         double* d_gpart, int n_parts);
 int generic_parts(const Instance* I);
 
+// tl_codon_tc.cu (tcgen05 codon path)
+int tc_tile();
+int tc_setup(Instance* I);
+int tc_set_tip_pool(Instance* I);
+int launch_post_tc(Instance* I, const tl_op* ops, int n, void* d_ops_area, size_t cap);
+int launch_root_tc(Instance* I, int root_pool, int model, double* d_site, double* d_part,
+                   int n_parts);
+
 // tl_api.cu helpers used by the other units
+int upload_bytes(Instance* I, void* dst, const void* src, size_t bytes);
 int fail(Instance* I, int code, const char* fmt, ...);
 int cuda_check(Instance* I, cudaError_t e, const char* what);
 int reduce_fixed(Instance* I, const double* d_in, int n_out, int n_in, double* d_out);

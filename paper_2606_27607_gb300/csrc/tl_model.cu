@@ -317,7 +317,7 @@ __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
                       const int* __restrict__ pidx, const int* __restrict__ dpidx,
                       const double* __restrict__ len, const double* __restrict__ rates,
                       double* __restrict__ mat64, T* __restrict__ matw, size_t matw_stride,
-                      int layout) {
+                      int layout, T* __restrict__ rowsum) {
     extern __shared__ double sm_tpm[];
     double* e = sm_tpm;              // [Spad]
     double* de = sm_tpm + 64;        // [Spad]
@@ -377,13 +377,22 @@ __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
                 w[idx] = v;
             }
         } else {
-            w += (size_t)r * (Spad + 1) * Spad;
-            for (int idx = t; idx < Spad * Spad; idx += nt) w[idx] = (T)round_tf32((float)Pm[idx]);
+            // tensor-core layout [2][R][64][64]: P row-major (the B operand)
+            // and P^T (tip lookups), both TF32-rounded; row sums of the
+            // rounded P summed in order (ambiguous tips)
+            T* wp = w + (size_t)r * Spad * Spad;
+            T* wt = w + ((size_t)R + r) * Spad * Spad;
+            for (int idx = t; idx < Spad * Spad; idx += nt) {
+                const int i = idx / Spad, j = idx % Spad;
+                const T v = (T)round_tf32((float)Pm[idx]);
+                wp[idx] = v;
+                wt[j * Spad + i] = v;
+            }
             __syncthreads();
             for (int i = t; i < Spad; i += nt) {
-                double v = 0.0;
-                for (int q = 0; q < S; ++q) v += (double)w[i * Spad + q];
-                w[Spad * Spad + i] = (T)v;
+                T v = wp[i * Spad];
+                for (int q = 1; q < S; ++q) v = v + wp[i * Spad + q];
+                rowsum[((size_t)slot * R + r) * Spad + i] = v;
             }
         }
         __syncthreads();
@@ -481,12 +490,14 @@ int launch_update_matrices(Instance* I, int m, const int* d_pidx, const int* d_d
         cudaFuncSetAttribute(k_tpm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
         k_tpm<double><<<grid, 256, smem, I->stream>>>(I->S, I->Spad, I->R, M.V, M.Vinv, M.lam,
                                                       d_pidx, d_dpidx, d_len, d_rates, I->d_mat64,
-                                                      (double*)I->d_matw, I->matw_stride, layout);
+                                                      (double*)I->d_matw, I->matw_stride, layout,
+                                                      nullptr);
     } else {
         cudaFuncSetAttribute(k_tpm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
         k_tpm<float><<<grid, 256, smem, I->stream>>>(I->S, I->Spad, I->R, M.V, M.Vinv, M.lam,
                                                      d_pidx, d_dpidx, d_len, d_rates, I->d_mat64,
-                                                     (float*)I->d_matw, I->matw_stride, layout);
+                                                     (float*)I->d_matw, I->matw_stride, layout,
+                                                     I->d_rowsum);
     }
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "update matrices");

@@ -1,0 +1,89 @@
+"""Codon (GY94, 61 states padded to 64) tensor-core path (tcgen05 kind::tf32)
+against the FP64 oracle. Reduced-precision tolerance: 1e-5 relative on
+logL. Per-pattern log-likelihoods: TF32 keeps 11 significant bits, so every
+stored partial and every entry of P carries a relative rounding error up to
+2^-11; a pattern accumulates about one such error per internal node, hence
+|l_p - l_p*| <= 2^-11 * (N - 1)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import model as om, pruning as op
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2606_27607_gb300 import build
+    build.build()
+
+
+def codon_workload(n_tips, n_patterns):
+    return synth.workload("gy94_128x20k", n_tips=n_tips, n_patterns=n_patterns)
+
+
+def run(w, prec, site=False, tips_as_partials=False):
+    from paper_2606_27607_gb300 import TreeLikelihood
+    tl = TreeLikelihood(w.tree.n_tips, w.n_patterns, 61, 4, prec)
+    try:
+        if tips_as_partials:
+            for t in range(w.tree.n_tips):
+                tl.inst.set_tip_partials(t, op.tip_partials(w.tips[t:t + 1], 61)[0])
+        else:
+            tl.set_tips(w.tips)
+        tl.set_model("gy94", w.params, w.freqs)
+        tl.set_rates(w.rates, w.cat_weights)
+        tl.set_pattern_weights(w.pattern_weights)
+        tl.set_tree(w.tree.children, w.tree.edge_len)
+        return tl.loglik(site=site)
+    finally:
+        tl.close()
+
+
+@pytest.mark.parametrize("n_tips,n_pat", [(2, 1), (5, 150), (12, 300), (40, 257)])
+def test_codon_tf32_matches_oracle(n_tips, n_pat):
+    w = codon_workload(n_tips, n_pat)
+    Q, pi, _ = om.build(w.model, w.params, w.freqs)
+    want_l, want_site = op.loglik(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights, w.tips)
+    logl, site = run(w, "tf32", site=True)
+    assert abs(logl - want_l) <= 1e-5 * abs(want_l), (logl, want_l)
+    assert np.max(np.abs(site - want_site)) <= 2.0 ** -11 * (n_tips - 1)
+
+
+def test_codon_tf32_tip_states_equal_one_hot_partials_bit_exact():
+    w = codon_workload(9, 200)
+    a = run(w, "tf32")
+    b = run(w, "tf32", tips_as_partials=True)
+    assert a == b
+
+
+def test_codon_tf32_ambiguous_tips():
+    w = codon_workload(7, 130)
+    rng = np.random.default_rng(3)
+    w.tips = w.tips.copy()
+    w.tips[rng.random(w.tips.shape) < 0.05] = 61
+    Q, pi, _ = om.build(w.model, w.params, w.freqs)
+    want_l, _ = op.loglik(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights, w.tips)
+    logl = run(w, "tf32")
+    assert abs(logl - want_l) <= 1e-5 * abs(want_l)
+
+
+@pytest.mark.slow
+def test_codon_128x20k_full_size_sampled():
+    w = synth.workload("gy94_128x20k")
+    logl, site = run(w, "tf32", site=True)
+    Q, pi, _ = om.build(w.model, w.params, w.freqs)
+    rng = np.random.default_rng(2)
+    idx = np.sort(rng.choice(w.n_patterns, 300, replace=False))
+    idx[-1] = w.n_patterns - 1
+    _, want_site = op.loglik_chunked(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights,
+                                     w.tips, patterns=idx)
+    assert np.max(np.abs(site[idx] - want_site)) <= 2.0 ** -11 * 127
+    assert abs(logl - np.sum(site)) <= 1e-9 * abs(logl)
+    # the FP64 generic GPU path (itself oracle-checked at small sizes) agrees
+    l64 = run(w, "f64")
+    assert abs(logl - l64) <= 1e-5 * abs(l64)
