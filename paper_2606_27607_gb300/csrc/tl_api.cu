@@ -246,10 +246,15 @@ int max_slots(const Instance* I) {
 }
 
 int check_numeric_flag(Instance* I) {
-    int h[2] = {0, 0};
-    cudaError_t e = cudaMemcpyAsync(h, I->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, I->stream);
+    int h[3] = {0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, I->d_err, 3 * sizeof(int), cudaMemcpyDeviceToHost, I->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(I->stream);
     if (e != cudaSuccess) return cuda_check(I, e, "error flag");
+    if (h[2]) {
+        cudaMemsetAsync(I->d_err + 2, 0, sizeof(int), I->stream);
+        return fail(I, TL_ERR_TIMEOUT, "a tensor-core kernel wait gave up (code 0x%x: bits 0-2 "
+                    "empty/full/done barrier, bits 8-10 post/pre1/pre2 kernel)", h[2]);
+    }
     if (h[0] || h[1]) {
         cudaMemsetAsync(I->d_err, 0, 2 * sizeof(int), I->stream);
         if (h[0])
@@ -771,7 +776,8 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
     if (use_nuc(I)) I->matw_stride = (size_t)I->R * kColStride * 4;
     else if (prec == kTF32) I->matw_stride = (size_t)2 * I->R * I->Spad * I->Spad;
     else I->matw_stride = (size_t)I->R * (I->Spad + 1) * I->Spad;
-    if ((rc = dev_alloc(I, &I->d_matw, (size_t)I->elt * I->matw_stride * n_matrices, "matrix copies")))
+    const size_t matw_elems = prec == kTF32 ? tc_matw_floats(I) : I->matw_stride * n_matrices;
+    if ((rc = dev_alloc(I, &I->d_matw, (size_t)I->elt * matw_elems, "matrix copies")))
         return bail(rc);
     I->mat_set.assign(n_matrices, 0);
     I->models.resize(n_models);
@@ -1166,7 +1172,7 @@ int tl_update_partials(tl_instance* inst, const tl_op* ops, int count) {
     if (use_tc(I)) {
         PostPlan plan;
         if ((rc = plan_post(I, ops, count, &plan, true))) return rc;
-        const size_t bytes = (size_t)count * 32;
+        const size_t bytes = (size_t)count * kTcOpBytes;
         void* d = area(I, 0, bytes, &rc);
         if (rc) return rc;
         if ((rc = launch_post_tc(I, ops, count, d, bytes))) return rc;
@@ -1247,12 +1253,22 @@ static int pre_common(Instance* I, const tl_pre_op* ops, int count, int model, i
     if (model < 0 || model >= I->n_models || !I->models[model].ready)
         return fail(I, TL_ERR_STATE, "model %d not set", model);
     if (n_grad < 0) return fail(I, TL_ERR_ARG, "n_grad < 0");
-    if (use_tc(I)) return fail(I, TL_ERR_UNSUPPORTED, "pre-order pass not built for TL_PREC_TF32");
     PrePlan plan;
     int rc = plan_pre(I, ops, count, n_grad, store_all, &plan);
     if (rc) return rc;
     const int E = (int)plan.edge_map.size();
-    if (use_nuc(I)) {
+    if (use_tc(I)) {
+        const int n_tiles = I->Ppad / 128;
+        if ((rc = ensure_scratch(I, (size_t)std::max(E, 1) * n_tiles))) return rc;
+        std::vector<int> row(std::max(n_grad, 1), -1);
+        for (int k = 0; k < E; ++k) row[plan.edge_map[k]] = k;
+        const size_t bytes = (size_t)count * 3 * kTcOpBytes;
+        void* d = area(I, 1, bytes, &rc);
+        if (rc) return rc;
+        if ((rc = launch_pre_tc(I, ops, count, row.data(), model, I->d_red, d, bytes))) return rc;
+        if ((rc = ensure_out(I, (size_t)E))) return rc;
+        if ((rc = reduce_fixed(I, I->d_red, E, n_tiles, extra(I).d_out))) return rc;
+    } else if (use_nuc(I)) {
         const int n_tiles = nuc_tiles_main(I);
         if ((rc = ensure_scratch(I, (size_t)std::max(E, 1) * n_tiles))) return rc;
         void* d_ops = nullptr;
@@ -1279,7 +1295,7 @@ static int pre_common(Instance* I, const tl_pre_op* ops, int count, int model, i
     }
     for (int k = 0; k < count; ++k)
         for (int c = 0; c < 2; ++c)
-            if (ops[k].pre[c] >= 0 && (store_all || !use_nuc(I)))
+            if (ops[k].pre[c] >= 0 && (store_all || !use_nuc(I) || use_tc(I)))
                 I->buf_written[ops[k].pre[c] - I->n_tips] = 1;
     if (d_grad_out && n_grad > 0) {
         void* d_map = nullptr;
@@ -1316,7 +1332,8 @@ int tl_pre_order_gradient(tl_instance* inst, const tl_pre_op* ops, int count, in
     if ((rc = pre_common(I, ops, count, model, n_grad, false, d_g))) return rc;
     if (n_grad > 0)
         cudaMemcpyAsync(out_grad, d_g, sizeof(double) * n_grad, cudaMemcpyDeviceToHost, I->stream);
-    return cuda_check(I, cudaStreamSynchronize(I->stream), "tl_pre_order_gradient");
+    if ((rc = cuda_check(I, cudaStreamSynchronize(I->stream), "tl_pre_order_gradient"))) return rc;
+    return check_numeric_flag(I);
 }
 
 int tl_pre_order_gradient_dev(tl_instance* inst, const tl_pre_op* ops, int count, int model,

@@ -37,7 +37,7 @@ constexpr int kAChunk = kTcM * 32 * 4;      // 32 K-values of 128 rows: 16 KB
 constexpr int kBChunk = kTcN * 32 * 4;      // 8 KB
 constexpr int kStageBytes = 2 * kAChunk + 2 * kBChunk;  // 48 KB
 constexpr int kTmemCols = 512;
-constexpr unsigned kSpinLimit = 1u << 22;   // bounded mbarrier waits
+constexpr unsigned long long kWaitNs = 2000000000ull;  // a wait gives up after 2 s
 
 // ---- PTX wrappers ----------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -51,10 +51,18 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                  "r"(bytes)
                  : "memory");
 }
-// Wait for the phase with the given parity; false after kSpinLimit polls.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase with the given parity; false once kWaitNs have passed
+// (try_wait may suspend the thread for a while on each poll, so the bound is
+// on elapsed time, not on the number of polls).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
     const unsigned a = smem_u32(bar);
-    for (unsigned it = 0; it < kSpinLimit; ++it) {
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         unsigned ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -63,8 +71,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
     }
-    return false;
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
                                             uint64_t* bar) {
@@ -142,37 +150,66 @@ __device__ __forceinline__ float pow2f(int k) {  // 2^k, k in [-126, 127]
 }
 
 // ---- device op descriptor ----------------------------------------------------
+// Two operands per work item. Operand c is either contracted on the tensor
+// cores (A from the partials pool or the tip-partials pool, B from the
+// matrix map at rows brow[c] + 64 r) or, for a tip with a state code, looked
+// up in a P^T block of the matrix array (look[c], floats, category 0).
 struct __align__(16) TcOp {
     int child[2];
-    int kind[2];      // kInternal (pool), kTipPartials (tip pool), kTipStates (lookup)
-    int mat[2];
-    int dest;
-    int pad;
+    int kind[2];      // kInternal, kTipPartials: MMA; kTipStates: lookup; -1: no operand
+    int brow[2];
+    int look[2];
+    int dest;         // post: output buffer; pre2: q buffer (holds u on entry)
+    int qin;          // pre1: parent q buffer, -1 for the root (q = pi)
+    int uout[2];      // pre1: buffer receiving u of each internal child (-1: none)
+    int edge[2];      // gradient row (-1: none)
+    int dlook[2];     // pre1: dP^T block of a tip child (numerator lookup)
 };
 
 struct TcArgs {
     float* pool;              // [n_buffers][R][Ppad][64]
     int* epool;               // [n_buffers][Ppad]
     const int8_t* tips;       // [n_tips][Ppad]
-    const float* matw;        // [slot][2][R][64][64]: P, then P^T (TF32-rounded)
+    const float* matw;        // [slot][2][R][64][64]: P, then P^T (TF32-rounded); then Q copies
     const float* rowsum;      // [slot][R][64]
+    const double* patw;       // [Ppad]
+    const double* pi;         // [64] root frequencies (pre1)
+    double* gpart;            // [edge rows][n_tiles] gradient partials
     int R, Ppad, S, n_tiles, rescale;
     size_t bstride;           // floats per buffer
     int* err;
+    float catw[kMaxCat], rates[kMaxCat];
 };
 
-// One level of post-order ops; items = n_ops * n_tiles.
+static_assert(sizeof(TcOp) == kTcOpBytes, "descriptor size");
+
+enum TcMode { kPost = 0, kPre1 = 1, kPre2 = 2 };
+
+// Fixed-order sum over the 128 threads; thread 0 gets the total.
+__device__ __forceinline__ float block_sum128(float v, float* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.f;
+    if (threadIdx.x == 0) t = (red[0] + red[1]) + (red[2] + red[3]);
+    __syncthreads();
+    return t;
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(128, 1)
-k_post_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtensorMap tm_tip,
-          const __grid_constant__ CUtensorMap tm_mat, const TcOp* __restrict__ ops, int n_ops,
-          TcArgs a) {
+k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtensorMap tm_tip,
+     const __grid_constant__ CUtensorMap tm_mat, const TcOp* __restrict__ ops, int n_ops,
+     TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     // 128-byte swizzle atoms must start on 1024-byte shared-memory addresses
     unsigned char* stages = smem_tc + ((1024u - (smem_u32(smem_tc) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base_sh;
-    __shared__ int abort_sh;
+    __shared__ int abort_sh;      // bit 0 empty, 1 full, 2 done wait gave up
     __shared__ unsigned produced_sh, consumed_sh;
+    __shared__ float red[4];
     const int tid = threadIdx.x, warp = tid >> 5;
 
     if (warp == 0) {
@@ -198,7 +235,7 @@ k_post_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ C
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
     const int R = a.R;
-    unsigned pairs_done = 0;   // (child, category) products issued by this CTA
+    unsigned pairs_done = 0;   // (operand, category) products issued by this CTA
     unsigned items_done = 0;   // items with at least one product
 
     const int n_items = n_ops * a.n_tiles;
@@ -206,9 +243,9 @@ k_post_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ C
         const int k = item / a.n_tiles, tile = item % a.n_tiles;
         const TcOp op = ops[k];
         const int p0 = tile * kTcM;
-        // "internal" = contracted on the tensor cores (pool or tip-partials A)
-        const bool internal[2] = {op.kind[0] != kTipStates, op.kind[1] != kTipStates};
-        const int n_pairs = (internal[0] + internal[1]) * R;
+        const bool mma[2] = {op.kind[0] == kInternal || op.kind[0] == kTipPartials,
+                             op.kind[1] == kInternal || op.kind[1] == kTipPartials};
+        const int n_pairs = (mma[0] + mma[1]) * R;
         if (tid == 0 && n_pairs > 0) {
             // software pipeline: produce pair i, consume pair i - (kStages - 1)
             bool ok = true;
@@ -217,15 +254,17 @@ k_post_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ C
                 if (i < n_pairs) {
                     const unsigned g = pairs_done + i;
                     const int s = g % kStages;
-                    const unsigned round = g / kStages;
-                    ok = mbar_wait(&empty[s], (round & 1) ^ 1);
-                    if (!ok) break;
-                    const int c = internal[0] ? (i < R ? 0 : 1) : 1;
+                    ok = mbar_wait(&empty[s], ((g / kStages) & 1) ^ 1);
+                    if (!ok) {
+                        abort_sh |= 1;
+                        break;
+                    }
+                    const int c = mma[0] ? (i < R ? 0 : 1) : 1;
                     const int r = i % R;
                     unsigned char* st = stages + s * kStageBytes;
                     mbar_expect_tx(&full[s], kStageBytes);
                     const int arow = (op.child[c] * R + r) * a.Ppad + p0;
-                    const int brow = (op.mat[c] * 2 * R + r) * kTcN;
+                    const int brow = op.brow[c] + r * kTcN;
                     const CUtensorMap* am = op.kind[c] == kTipPartials ? &tm_tip : &tm_part;
                     tma_load_2d(st, am, 0, arow, &full[s]);
                     tma_load_2d(st + kAChunk, am, 32, arow, &full[s]);
@@ -238,9 +277,12 @@ k_post_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ C
                     const unsigned g = pairs_done + j;
                     const int s = g % kStages;
                     ok = mbar_wait(&full[s], (g / kStages) & 1);
-                    if (!ok) break;
+                    if (!ok) {
+                        abort_sh |= 2;
+                        break;
+                    }
                     tc_fence_after();
-                    const int c = internal[0] ? (j < R ? 0 : 1) : 1;
+                    const int c = mma[0] ? (j < R ? 0 : 1) : 1;
                     const int r = j % R;
                     const uint32_t d = tmem + (uint32_t)(r * 2 * kTcN + c * kTcN);
                     unsigned char* st = stages + s * kStageBytes;
@@ -256,17 +298,16 @@ k_post_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ C
                 }
             }
             mma_commit(&done);
-            if (!ok) abort_sh = 1;
             produced_sh = pairs_done + produced;
             consumed_sh = pairs_done + consumed;
         }
         __syncthreads();
         bool fail = abort_sh != 0;
-        if (!fail && n_pairs > 0) fail = !mbar_wait(&done, items_done & 1);
-        if (__syncthreads_or(fail)) {
-            abort_sh = 1;
-            break;
+        if (!fail && n_pairs > 0 && !mbar_wait(&done, items_done & 1)) {
+            fail = true;
+            atomicOr(&abort_sh, 4);
         }
+        if (__syncthreads_or(fail)) break;
         if (n_pairs > 0) {
             tc_fence_after();
             ++items_done;
@@ -276,30 +317,29 @@ k_post_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ C
         // ---- epilogue: lane tid <-> pattern p0 + tid -----------------------
         const int p = p0 + tid;
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        const float* col[2] = {nullptr, nullptr};
+        int sidx[2] = {0, 0};
         bool amb[2] = {false, false};
-        int cum = 0;
-        for (int c = 0; c < 2; ++c) {
-            if (!internal[c]) {
+        for (int c = 0; c < 2; ++c)
+            if (op.kind[c] == kTipStates) {
                 const int s = a.tips[(size_t)op.child[c] * a.Ppad + p];
                 amb[c] = !(s >= 0 && s < a.S);
-                col[c] = !amb[c]
-                             ? a.matw + (((size_t)op.mat[c] * 2 + 1) * R) * kTcN * kTcN + (size_t)s * kTcN
-                             : a.rowsum + (size_t)op.mat[c] * R * kTcN;
-            } else if (op.kind[c] == kInternal) {
-                cum += a.epool[(size_t)op.child[c] * a.Ppad + p];
+                sidx[c] = s;
             }
-        }
-        // child value chunk (16 states, category r)
+        // 16 values (states 16q..16q+15, category r) of operand c
         auto chunk = [&](int c, int r, int q, float* v) {
-            if (internal[c]) {
+            if (mma[c]) {
                 tmem_ld16(lane_base + (uint32_t)(r * 2 * kTcN + c * kTcN + q * 16), v);
             } else {
-                const size_t rstride = amb[c] ? kTcN : kTcN * kTcN;
-                const float4* src = reinterpret_cast<const float4*>(col[c] + r * rstride + q * 16);
+                // the tip's column of P (row of P^T), or the row sums of P
+                const int slot_base = op.look[c];
+                const float* src = amb[c] ? a.rowsum + (size_t)(slot_base / (2 * R * kTcN * kTcN)) * R * kTcN +
+                                                (size_t)r * kTcN + q * 16
+                                          : a.matw + (size_t)slot_base + (size_t)r * kTcN * kTcN +
+                                                (size_t)sidx[c] * kTcN + q * 16;
+                const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const float4 f = __ldg(src + u);
+                    const float4 f = __ldg(s4 + u);
                     v[4 * u] = f.x;
                     v[4 * u + 1] = f.y;
                     v[4 * u + 2] = f.z;
@@ -307,50 +347,187 @@ k_post_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ C
                 }
             }
         };
-        float m = 0.f;
-        for (int r = 0; r < R; ++r)
-            for (int q = 0; q < 4; ++q) {
-                float x[16], y[16];
-                chunk(0, r, q, x);
-                chunk(1, r, q, y);
+        auto qvals = [&](int r, int q, float* v) {  // parent pre-order partial (pre1)
+            if (op.qin < 0) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) m = fmaxf(m, x[i] * y[i]);
-            }
-        int e = a.rescale ? frexp_exp_f(m) : 0;
-        float f1 = 1.f, f2 = 1.f;
-        if (e != 0) {
-            const int kk = -e;
-            if (kk >= -126 && kk <= 126) f1 = pow2f(kk);
-            else {
-                f1 = pow2f(kk / 2);
-                f2 = pow2f(kk - kk / 2);
-            }
-            cum += e;
-        }
-        float* dst = a.pool + (size_t)op.dest * a.bstride + (size_t)p * kTcN;
-        for (int r = 0; r < R; ++r)
-            for (int q = 0; q < 4; ++q) {
-                float x[16], y[16];
-                chunk(0, r, q, x);
-                chunk(1, r, q, y);
-                float4* o = reinterpret_cast<float4*>(dst + (size_t)r * a.Ppad * kTcN + q * 16);
+                for (int i = 0; i < 16; ++i) v[i] = (float)a.pi[q * 16 + i];
+            } else {
+                const float4* s4 = reinterpret_cast<const float4*>(
+                    a.pool + (size_t)op.qin * a.bstride + ((size_t)r * a.Ppad + p) * kTcN + q * 16);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    float4 w;
-                    w.x = to_tf32(x[4 * u] * y[4 * u] * f1 * f2);
-                    w.y = to_tf32(x[4 * u + 1] * y[4 * u + 1] * f1 * f2);
-                    w.z = to_tf32(x[4 * u + 2] * y[4 * u + 2] * f1 * f2);
-                    w.w = to_tf32(x[4 * u + 3] * y[4 * u + 3] * f1 * f2);
-                    o[u] = w;
+                    const float4 f = s4[u];
+                    v[4 * u] = f.x;
+                    v[4 * u + 1] = f.y;
+                    v[4 * u + 2] = f.z;
+                    v[4 * u + 3] = f.w;
                 }
             }
-        a.epool[(size_t)op.dest * a.Ppad + p] = cum;
+        };
+        auto scale_of = [](float m, float* f1, float* f2) -> int {
+            const int e = frexp_exp_f(m);
+            *f1 = 1.f;
+            *f2 = 1.f;
+            if (e != 0) {
+                const int kk = -e;
+                if (kk >= -126 && kk <= 126) *f1 = pow2f(kk);
+                else {
+                    *f1 = pow2f(kk / 2);
+                    *f2 = pow2f(kk - kk / 2);
+                }
+            }
+            return e;
+        };
+        auto store16 = [&](float* dst, const float* v, float f1, float f2) {
+            float4* o = reinterpret_cast<float4*>(dst);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                float4 w;
+                w.x = to_tf32(v[4 * u] * f1 * f2);
+                w.y = to_tf32(v[4 * u + 1] * f1 * f2);
+                w.z = to_tf32(v[4 * u + 2] * f1 * f2);
+                w.w = to_tf32(v[4 * u + 3] * f1 * f2);
+                o[u] = w;
+            }
+        };
+        const bool real = p < a.Ppad;  // always true (tiles cover Ppad)
+        const float wp = (p < a.Ppad) ? (float)a.patw[p] : 0.f;
+
+        if (MODE == kPost) {
+            int cum = 0;
+            for (int c = 0; c < 2; ++c)
+                if (op.kind[c] == kInternal) cum += a.epool[(size_t)op.child[c] * a.Ppad + p];
+            float m = 0.f;
+            for (int r = 0; r < R; ++r)
+                for (int q = 0; q < 4; ++q) {
+                    float x[16], y[16];
+                    chunk(0, r, q, x);
+                    chunk(1, r, q, y);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) m = fmaxf(m, x[i] * y[i]);
+                }
+            float f1 = 1.f, f2 = 1.f;
+            if (a.rescale) cum += scale_of(m, &f1, &f2);
+            float* dst = a.pool + (size_t)op.dest * a.bstride + (size_t)p * kTcN;
+            for (int r = 0; r < R; ++r)
+                for (int q = 0; q < 4; ++q) {
+                    float x[16], y[16];
+                    chunk(0, r, q, x);
+                    chunk(1, r, q, y);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) x[i] *= y[i];
+                    store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, x, f1, f2);
+                }
+            a.epool[(size_t)op.dest * a.Ppad + p] = cum;
+        } else if (MODE == kPre1) {
+            // den and the per-pattern maxima of u_a = q o v_b, u_b = q o v_a
+            float den = 0.f, mu[2] = {0.f, 0.f};
+            for (int r = 0; r < R; ++r) {
+                float dr = 0.f;
+                for (int q = 0; q < 4; ++q) {
+                    float x[16], y[16], z[16];
+                    chunk(0, r, q, x);
+                    chunk(1, r, q, y);
+                    qvals(r, q, z);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        dr += z[i] * x[i] * y[i];
+                        mu[0] = fmaxf(mu[0], z[i] * y[i]);
+                        mu[1] = fmaxf(mu[1], z[i] * x[i]);
+                    }
+                }
+                den += a.catw[r] * dr;
+            }
+            for (int c = 0; c < 2; ++c) {
+                if (op.kind[c] == kTipStates && op.edge[c] >= 0) {
+                    // numerator u_c . dP_c[:, s] (a row of dP^T); an ambiguous
+                    // code gives the row sums of dP, which are zero. Every
+                    // thread runs the loop: chunk() may issue a warp-collective
+                    // tcgen05.ld for the sibling.
+                    float num = 0.f;
+                    const int srow = amb[c] ? 0 : sidx[c];
+                    for (int r = 0; r < R; ++r) {
+                        float nr = 0.f;
+                        for (int q = 0; q < 4; ++q) {
+                            float sib[16], z[16];
+                            chunk(1 - c, r, q, sib);
+                            qvals(r, q, z);
+                            const float4* d4 = reinterpret_cast<const float4*>(
+                                a.matw + (size_t)op.dlook[c] + (size_t)r * kTcN * kTcN +
+                                (size_t)srow * kTcN + q * 16);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const float4 f = __ldg(d4 + u);
+                                nr += z[4 * u] * sib[4 * u] * f.x + z[4 * u + 1] * sib[4 * u + 1] * f.y +
+                                      z[4 * u + 2] * sib[4 * u + 2] * f.z +
+                                      z[4 * u + 3] * sib[4 * u + 3] * f.w;
+                            }
+                        }
+                        num += a.catw[r] * nr;
+                    }
+                    if (amb[c]) num = 0.f;
+                    const float g = block_sum128(wp * (num / den), red);
+                    if (tid == 0) a.gpart[(size_t)op.edge[c] * a.n_tiles + tile] = (double)g;
+                }
+                if (op.uout[c] >= 0) {
+                    float f1, f2;
+                    const int e = scale_of(mu[c], &f1, &f2);
+                    float* dst = a.pool + (size_t)op.uout[c] * a.bstride + (size_t)p * kTcN;
+                    for (int r = 0; r < R; ++r)
+                        for (int q = 0; q < 4; ++q) {
+                            float sib[16], z[16];
+                            chunk(1 - c, r, q, sib);
+                            qvals(r, q, z);
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) z[i] *= sib[i];
+                            store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, z, f1, f2);
+                        }
+                    // the child's ratio denominator carries the same scale as u
+                    float d = den;
+                    if (e != 0) d = (-e >= -126 && -e <= 126) ? den * pow2f(-e)
+                                                             : den * pow2f(-e / 2) * pow2f(-e - (-e / 2));
+                    a.epool[(size_t)op.uout[c] * a.Ppad + p] = __float_as_int(d);
+                }
+            }
+        } else {  // kPre2: operand 0 = q_c = u_c P_c (B = P^T), operand 1 = Q x_c
+            const float den = __int_as_float(a.epool[(size_t)op.dest * a.Ppad + p]);
+            float num = 0.f, m = 0.f;
+            for (int r = 0; r < R; ++r) {
+                float nr = 0.f;
+                for (int q = 0; q < 4; ++q) {
+                    float x[16], y[16];
+                    chunk(0, r, q, x);
+                    chunk(1, r, q, y);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        nr += x[i] * y[i];
+                        m = fmaxf(m, x[i]);
+                    }
+                }
+                num += a.catw[r] * a.rates[r] * nr;
+            }
+            if (op.edge[0] >= 0) {
+                const float g = block_sum128(wp * (num / den), red);
+                if (tid == 0) a.gpart[(size_t)op.edge[0] * a.n_tiles + tile] = (double)g;
+            }
+            float f1, f2;
+            scale_of(m, &f1, &f2);
+            float* dst = a.pool + (size_t)op.dest * a.bstride + (size_t)p * kTcN;
+            for (int r = 0; r < R; ++r)
+                for (int q = 0; q < 4; ++q) {
+                    float x[16];
+                    chunk(0, r, q, x);
+                    store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, x, f1, f2);
+                }
+        }
+        (void)real;
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
     }
     if (abort_sh && tid == 0) {
-        atomicOr(a.err, 4);
+        // where the wait gave up (bits 0-2) and in which kernel mode (bits 8+)
+        atomicOr(a.err, abort_sh | (1 << (8 + MODE)));
         // bounded drain of copies and products still in flight
         for (unsigned g = consumed_sh; g < produced_sh; ++g)
             mbar_wait(&full[g % kStages], (g / kStages) & 1);
@@ -435,6 +612,9 @@ TcArgs tc_args(Instance* I) {
     a.tips = I->tip_pool;
     a.matw = reinterpret_cast<const float*>(I->d_matw);
     a.rowsum = I->d_rowsum;
+    a.patw = I->d_patw;
+    a.pi = nullptr;
+    a.gpart = nullptr;
     a.R = I->R;
     a.Ppad = I->Ppad;
     a.S = I->S;
@@ -442,7 +622,50 @@ TcArgs tc_args(Instance* I) {
     a.rescale = I->rescale;
     a.bstride = (size_t)I->R * I->Ppad * kTcN;
     a.err = I->d_err + 2;
+    for (int r = 0; r < kMaxCat; ++r) {
+        a.catw[r] = (float)(r < I->R ? I->h_catw[r] : 0.0);
+        a.rates[r] = (float)(r < I->R ? I->h_rates[r] : 0.0);
+    }
     return a;
+}
+
+// Row of the P (which = 0) or P^T (which = 1) block of a slot in the matrix
+// map, category 0; float offset of the same block in the matrix array.
+int brow_of(const Instance* I, int slot, int which) { return (slot * 2 + which) * I->R * kTcN; }
+int look_of(const Instance* I, int slot, int which) {
+    return (int)((size_t)slot * I->matw_stride + (size_t)which * I->R * kTcN * kTcN);
+}
+int qrow_of(const Instance* I, int model) { return (I->n_mats * 2 + model) * I->R * kTcN; }
+
+__global__ void k_q_tc(const double* __restrict__ Q, float* __restrict__ dst, int R) {
+    for (int idx = threadIdx.x; idx < R * kTcN * kTcN; idx += blockDim.x)
+        dst[idx] = to_tf32((float)Q[idx % (kTcN * kTcN)]);
+}
+
+template <int MODE>
+void launch_mode(Instance* I, const TcOp* d, int n, TcArgs a) {
+    const size_t smem = (size_t)kStages * kStageBytes + 1024;
+    cudaFuncSetAttribute(k_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int sms = 0, dev_id = 0;
+    cudaGetDevice(&dev_id);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+    const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(I->tmaps.data());
+    const int items = n * a.n_tiles;
+    const int grid = std::max(1, std::min(items, sms));
+    k_tc<MODE><<<grid, 128, smem, I->stream>>>(m[0], m[1], m[2], d, n, a);
+    I->launches += 1;
+}
+
+void tc_operand(const Instance* I, TcOp& t, int c, int buf, int slot) {
+    if (buf < I->n_tips) {
+        t.kind[c] = I->tip_set[buf] == 1 ? kTipStates : kTipPartials;
+        t.child[c] = buf;
+    } else {
+        t.kind[c] = kInternal;
+        t.child[c] = buf - I->n_tips;
+    }
+    t.brow[c] = brow_of(I, slot, 0);
+    t.look[c] = look_of(I, slot, 1);
 }
 
 }  // namespace
@@ -456,14 +679,26 @@ int tc_setup(Instance* I) {
     int rc;
     const size_t rows = (size_t)I->n_buffers * I->R * I->Ppad;
     if ((rc = make_map(I, &m[0], I->pool, rows, kTcM))) return rc;
-    if ((rc = make_map(I, &m[2], I->d_matw, (size_t)I->n_mats * 2 * I->R * kTcN, kTcN))) return rc;
+    const size_t mrows = ((size_t)I->n_mats * 2 + I->n_models) * I->R * kTcN;
+    if ((rc = make_map(I, &m[2], I->d_matw, mrows, kTcN))) return rc;
     m[1] = m[0];  // tip-partials map until a tip pool exists
     return TL_OK;
+}
+
+size_t tc_matw_floats(const Instance* I) {
+    return (size_t)I->n_mats * I->matw_stride + (size_t)I->n_models * I->R * kTcN * kTcN;
 }
 
 int tc_set_tip_pool(Instance* I) {
     CUtensorMap* m = reinterpret_cast<CUtensorMap*>(I->tmaps.data());
     return make_map(I, &m[1], I->tc_tip_pool, (size_t)I->n_tips * I->R * I->Ppad, kTcM);
+}
+
+int launch_q_tc(Instance* I, int model) {
+    float* dst = reinterpret_cast<float*>(I->d_matw) + (size_t)qrow_of(I, model) * kTcN;
+    k_q_tc<<<1, 256, 0, I->stream>>>(I->models[model].Q, dst, I->R);
+    I->launches += 1;
+    return cuda_check(I, cudaGetLastError(), "tensor-core Q copy");
 }
 
 int launch_post_tc(Instance* I, const tl_op* ops, int n, void* d_ops_area, size_t cap) {
@@ -486,19 +721,11 @@ int launch_post_tc(Instance* I, const tl_op* ops, int n, void* d_ops_area, size_
             if (level[k] != L) continue;
             TcOp t;
             std::memset(&t, 0, sizeof t);
-            const int ch[2] = {ops[k].child1, ops[k].child2};
-            const int mt[2] = {ops[k].mat1, ops[k].mat2};
-            for (int c = 0; c < 2; ++c) {
-                t.mat[c] = mt[c];
-                if (ch[c] < I->n_tips) {
-                    t.kind[c] = I->tip_set[ch[c]] == 1 ? kTipStates : kTipPartials;
-                    t.child[c] = ch[c];
-                } else {
-                    t.kind[c] = kInternal;
-                    t.child[c] = ch[c] - I->n_tips;
-                }
-            }
+            tc_operand(I, t, 0, ops[k].child1, ops[k].mat1);
+            tc_operand(I, t, 1, ops[k].child2, ops[k].mat2);
             t.dest = ops[k].dest - I->n_tips;
+            t.qin = -1;
+            t.uout[0] = t.uout[1] = t.edge[0] = t.edge[1] = -1;
             dev.push_back(t);
         }
     }
@@ -506,22 +733,89 @@ int launch_post_tc(Instance* I, const tl_op* ops, int n, void* d_ops_area, size_
     if (dev.size() * sizeof(TcOp) > cap) return fail(I, TL_ERR_ARG, "op area too small");
     int rc = upload_bytes(I, d_ops_area, dev.data(), dev.size() * sizeof(TcOp));
     if (rc) return rc;
-    const size_t smem = (size_t)kStages * kStageBytes + 1024;
-    cudaFuncSetAttribute(k_post_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int sms = 0, dev_id = 0;
-    cudaGetDevice(&dev_id);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
-    const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(I->tmaps.data());
     TcArgs a = tc_args(I);
     const TcOp* d = reinterpret_cast<const TcOp*>(d_ops_area);
-    for (int L = 0; L < n_levels; ++L) {
-        const int nl = first[L + 1] - first[L];
-        const int items = nl * a.n_tiles;
-        const int grid = std::max(1, std::min(items, sms));
-        k_post_tc<<<grid, 128, smem, I->stream>>>(m[0], m[1], m[2], d + first[L], nl, a);
-        I->launches += 1;
-    }
+    for (int L = 0; L < n_levels; ++L) launch_mode<kPost>(I, d + first[L], first[L + 1] - first[L], a);
     return cuda_check(I, cudaGetLastError(), "tensor-core post-order kernel");
+}
+
+// Pre-order pass with gradient, level by level from the root: PRE1 per
+// parent (v = P x, den, u = q o v_sibling, tip gradients), then PRE2 per
+// internal child (q = u P, Q x, internal gradients, q rescaled in place).
+int launch_pre_tc(Instance* I, const tl_pre_op* ops, int n, const int* edge_row, int model,
+                  double* d_gpart, void* d_ops_area, size_t cap) {
+    std::vector<int> prod(I->n_bufs, -1), level(n, 0);
+    for (int k = 0; k < n; ++k) {
+        if (ops[k].parent_pre >= 0 && prod[ops[k].parent_pre] >= 0)
+            level[k] = level[prod[ops[k].parent_pre]] + 1;
+        for (int c = 0; c < 2; ++c)
+            if (ops[k].pre[c] >= 0) prod[ops[k].pre[c]] = k;
+    }
+    const int n_levels = n ? *std::max_element(level.begin(), level.end()) + 1 : 0;
+    std::vector<TcOp> dev;
+    std::vector<int> f1(n_levels), n1(n_levels), f2(n_levels), n2(n_levels);
+    for (int L = 0; L < n_levels; ++L) {
+        f1[L] = (int)dev.size();
+        std::vector<TcOp> second;
+        for (int k = 0; k < n; ++k) {
+            if (level[k] != L) continue;
+            const tl_pre_op& o = ops[k];
+            TcOp t;
+            std::memset(&t, 0, sizeof t);
+            for (int c = 0; c < 2; ++c) {
+                tc_operand(I, t, c, o.child[c], o.mat[c]);
+                if (t.kind[c] == kTipPartials)
+                    return fail(I, TL_ERR_UNSUPPORTED,
+                                "TL_PREC_TF32 pre-order pass: tips must hold states");
+                t.uout[c] = -1;
+                t.edge[c] = -1;
+                if (t.kind[c] == kTipStates) {
+                    t.edge[c] = o.edge[c] >= 0 ? edge_row[o.edge[c]] : -1;
+                    t.dlook[c] = o.dmat[c] >= 0 ? look_of(I, o.dmat[c], 1) : 0;
+                    if (t.edge[c] >= 0 && o.dmat[c] < 0)
+                        return fail(I, TL_ERR_ARG, "pre op %d: edge without dmat", k);
+                } else {
+                    if (o.pre[c] < 0)
+                        return fail(I, TL_ERR_ARG, "TL_PREC_TF32: internal child of pre op %d needs "
+                                    "a pre buffer", k);
+                    t.uout[c] = o.pre[c] - I->n_tips;
+                    TcOp u;
+                    std::memset(&u, 0, sizeof u);
+                    u.kind[0] = kInternal;
+                    u.child[0] = t.uout[c];
+                    u.brow[0] = brow_of(I, o.mat[c], 1);       // q = u P  (B = P^T)
+                    u.kind[1] = kInternal;
+                    u.child[1] = o.child[c] - I->n_tips;       // Q x_c
+                    u.brow[1] = qrow_of(I, model);
+                    u.dest = t.uout[c];
+                    u.qin = -1;
+                    u.uout[0] = u.uout[1] = -1;
+                    u.edge[0] = o.edge[c] >= 0 ? edge_row[o.edge[c]] : -1;
+                    u.edge[1] = -1;
+                    second.push_back(u);
+                }
+            }
+            t.qin = o.parent_pre >= 0 ? o.parent_pre - I->n_tips : -1;
+            t.dest = 0;
+            dev.push_back(t);
+        }
+        n1[L] = (int)dev.size() - f1[L];
+        f2[L] = (int)dev.size();
+        dev.insert(dev.end(), second.begin(), second.end());
+        n2[L] = (int)dev.size() - f2[L];
+    }
+    if (dev.size() * sizeof(TcOp) > cap) return fail(I, TL_ERR_ARG, "op area too small");
+    int rc = upload_bytes(I, d_ops_area, dev.data(), dev.size() * sizeof(TcOp));
+    if (rc) return rc;
+    TcArgs a = tc_args(I);
+    a.pi = I->models[model].pi;
+    a.gpart = d_gpart;
+    const TcOp* d = reinterpret_cast<const TcOp*>(d_ops_area);
+    for (int L = 0; L < n_levels; ++L) {
+        if (n1[L]) launch_mode<kPre1>(I, d + f1[L], n1[L], a);
+        if (n2[L]) launch_mode<kPre2>(I, d + f2[L], n2[L], a);
+    }
+    return cuda_check(I, cudaGetLastError(), "tensor-core pre-order kernels");
 }
 
 int launch_root_tc(Instance* I, int root_pool, int model, double* d_site, double* d_part,

@@ -185,12 +185,17 @@ int launch_edge_generic(Instance* I, const tl_edge* h_edges, int n_edges, int mo
 int generic_parts(const Instance* I);
 
 // tl_codon_tc.cu (tcgen05 codon path)
+constexpr size_t kTcOpBytes = 64;  // one tensor-core work descriptor
 int tc_tile();
 int tc_setup(Instance* I);
 int tc_set_tip_pool(Instance* I);
 int launch_post_tc(Instance* I, const tl_op* ops, int n, void* d_ops_area, size_t cap);
 int launch_root_tc(Instance* I, int root_pool, int model, double* d_site, double* d_part,
                    int n_parts);
+int launch_pre_tc(Instance* I, const tl_pre_op* ops, int n, const int* edge_row, int model,
+                  double* d_gpart, void* d_ops_area, size_t cap);
+int launch_q_tc(Instance* I, int model);
+size_t tc_matw_floats(const Instance* I);
 
 // tl_api.cu helpers used by the other units
 int upload_bytes(Instance* I, void* dst, const void* src, size_t bytes);

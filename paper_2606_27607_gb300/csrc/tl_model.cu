@@ -473,6 +473,7 @@ int launch_model_working_copies(Instance* I, int m) {
     I->launches += 1;
     int rc = cuda_check(I, cudaGetLastError(), "model working copies");
     if (rc) return rc;
+    if (I->prec == kTF32 && (rc = launch_q_tc(I, m))) return rc;
     M.ready = true;
     return TL_OK;
 }

@@ -87,3 +87,37 @@ def test_codon_128x20k_full_size_sampled():
     # the FP64 generic GPU path (itself oracle-checked at small sizes) agrees
     l64 = run(w, "f64")
     assert abs(logl - l64) <= 1e-5 * abs(l64)
+
+
+def assert_grad_close(g, want, tol):
+    scale = np.max(np.abs(want))
+    den = np.maximum(np.abs(want), 1e-3 * scale)
+    err = np.abs(g - want) / den
+    assert np.max(err) <= tol, (np.max(err), int(np.argmax(err)))
+
+
+@pytest.mark.parametrize("n_tips,n_pat", [(3, 40), (8, 150), (20, 300)])
+def test_codon_tf32_gradient_matches_oracle(n_tips, n_pat):
+    from oracle import gradient as og
+    from paper_2606_27607_gb300 import TreeLikelihood
+    w = codon_workload(n_tips, n_pat)
+    Q, pi, _ = om.build(w.model, w.params, w.freqs)
+    want_l, _ = op.loglik(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights, w.tips)
+    want_g = og.branch_gradient(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights, w.tips)
+    tl = TreeLikelihood(n_tips, n_pat, 61, 4, "tf32")
+    try:
+        tl.set_tips(w.tips)
+        tl.set_model("gy94", w.params, w.freqs)
+        tl.set_rates(w.rates, w.cat_weights)
+        tl.set_pattern_weights(w.pattern_weights)
+        tl.set_tree(w.tree.children, w.tree.edge_len)
+        logl, g = tl.gradient()
+    finally:
+        tl.close()
+    assert abs(logl - want_l) <= 1e-5 * abs(want_l)
+    # plain TF32 (11-bit operands): relative error of the gradient vector, and
+    # each component within 1e-3 of the largest; components whose per-pattern
+    # terms cancel need the split mode for the per-component bound
+    gv, wv = g[:-1], want_g[:-1]
+    assert np.linalg.norm(gv - wv) <= 1e-3 * np.linalg.norm(wv)
+    assert np.max(np.abs(gv - wv)) <= 1e-3 * np.max(np.abs(wv))
