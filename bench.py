@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0,
                     help="patterns in the oracle sample (0: sized to ~15 s)")
+    ap.add_argument("--no-codon", action="store_true", help="skip the codon tensor-core line")
+    ap.add_argument("--codon-only", action="store_true", help="only the codon line (profiling)")
+    ap.add_argument("--codon-taxa", type=int, default=0)
+    ap.add_argument("--codon-patterns", type=int, default=0)
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -196,9 +200,104 @@ def peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
+def tf32_peak() -> tuple[float, str]:
+    """Dense TF32 tensor peak: the measured BF16 burst figure times the
+    nominal TF32:BF16 ratio (1:2)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return 0.5 * float(json.load(f)["bf16_tflops"]), "measured bf16 x 1/2"
+    except (OSError, KeyError, ValueError):
+        return 0.5 * 1900.0, "fallback bf16 x 1/2"
+
+
+def codon_line(steps: int, warmup: int, taxa: int = 0, patterns: int = 0) -> dict:
+    """GY94 128 taxa x 20,000 patterns on the tensor-core (TF32) path: one
+    step = model + eigensystem, P and dP/dt, post-order, root logL, pre-order
+    gradient. Algorithmic FLOPs count the contractions of internal children
+    only (padded 64 x 64 per category): post 1, gradient 3 per child."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2606_27607_gb300 import TreeLikelihood
+    over = {}
+    if taxa:
+        over["n_tips"] = taxa
+    if patterns:
+        over["n_patterns"] = patterns
+    w = synth.workload("gy94_128x20k", **over)
+    N, P = w.tree.n_tips, w.n_patterns
+    stream = torch.cuda.current_stream()
+    tl = TreeLikelihood(N, P, 61, 4, "tf32", stream=stream.cuda_stream)
+    inst = tl.inst
+    tl.set_tips(w.tips)
+    tl.set_model("gy94", w.params, w.freqs)
+    tl.set_rates(w.rates, w.cat_weights)
+    tl.set_tree(w.tree.children, w.tree.edge_len)
+    nn = tl.nn
+    v = np.arange(nn - 1, dtype=np.int32)
+    dp = (nn + v).astype(np.int32)
+    lengths = np.ascontiguousarray(w.tree.edge_len[: nn - 1])
+    d_out = torch.zeros(1 + nn, dtype=torch.float64, device="cuda")
+    ev = {"post": [], "pre": []}
+
+    def step(timed):
+        inst.set_model_async(0, "gy94", w.params, w.freqs)
+        inst.update_matrices(0, v, lengths, dp)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inst.update_partials(tl._post)
+        e1.record(stream)
+        inst.root_loglik_dev(nn - 1, 0, d_out.data_ptr())
+        e2.record(stream)
+        inst.pre_order_gradient_dev(tl._pre, nn, 0, d_out.data_ptr() + 8)
+        e3.record(stream)
+        if timed:
+            ev["post"].append((e0, e1))
+            ev["pre"].append((e2, e3))
+
+    for _ in range(max(3, warmup)):
+        step(False)
+    torch.cuda.synchronize()
+    inst.sync()
+    n0 = inst.launch_count()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step(True)
+    b.record(stream)
+    torch.cuda.synchronize()
+    inst.sync()
+    ms = a.elapsed_time(b) / steps
+    k_ms = {k: statistics.mean(x.elapsed_time(y) for x, y in ev[k]) for k in ev}
+    n_int_children = N - 2
+    f_post = n_int_children * 4 * 2 * 64 * 64 * P
+    f_pre = 3 * f_post
+    peak, src = tf32_peak()
+    logl = float(d_out[0].item())
+    tl.close()
+    return {"workload": f"gy94_{N}x{P}", "precision": "tf32 tcgen05, fp32 accumulate",
+            "value": P * (N - 1) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+            "grad_evals_per_s": 1e3 / ms, "logL": logl,
+            "kernels": {k: {"ms": k_ms[k],
+                            "TFLOP/s": (f_post if k == "post" else f_pre) / (k_ms[k] * 1e-3) / 1e12}
+                        for k in k_ms},
+            "roofline": {"bound": "tensor", "kernel": "k_tc<post> (tcgen05 kind::tf32)",
+                         "achieved": f_post / (k_ms["post"] * 1e-3) / 1e12, "peak": peak,
+                         "unit": "TFLOP/s",
+                         "frac": f_post / (k_ms["post"] * 1e-3) / 1e12 / peak,
+                         "peak_source": src}}
+
+
 def traffic_for(kernel: str, per_launch_units: float) -> float | None:
-    """ncu DRAM bytes per launch recorded under profiles/, if the kernel source
-    is unchanged since the capture (else None)."""
+    """ncu DRAM bytes of one launch, scaled from the capture recorded under
+    profiles/ by the (pattern, internal node) units one launch processes, if
+    the kernel source is unchanged since the capture (else None)."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     src = os.path.join(ROOT, "paper_2606_27607_gb300", "csrc", "tl_nuc.cu")
     try:
@@ -206,7 +305,7 @@ def traffic_for(kernel: str, per_launch_units: float) -> float | None:
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if rec.get("source_sha256_16") != h:
             return None
-        return rec["bytes_per_pattern"] * per_launch_units
+        return rec["bytes_per_pattern_node"] * per_launch_units
     except (OSError, KeyError, ValueError):
         return None
 
@@ -225,6 +324,14 @@ def main() -> None:
         return
     if args.taxa or args.patterns:
         args.no_cpu_baseline = True
+    if args.codon_only:
+        import torch
+
+        from paper_2606_27607_gb300 import build
+        build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps(codon_line(args.steps, args.warmup, args.codon_taxa, args.codon_patterns)))
+        return
 
     import numpy as np
     import torch
@@ -375,12 +482,21 @@ def main() -> None:
            "pre": P * ((N - 2) * RS + N * 1) + 8 * (2 * N - 2) * ((P + 31) // 32)}
     dom = max(k_ms, key=k_ms.get)
     ach = alg[dom] / (k_ms[dom] * 1e-3) / 1e9
-    kname = {"post": "k_post4<float,4>", "pre": "k_pre4<float,4>"}[dom]
-    traffic = traffic_for(kname, P)
+    lpp = int(os.environ.get("TL_NUC_LANES", "1"))
+    lpp = lpp if lpp in (1, 2, 4) else 1
+    kname = f"k_{dom}4<float,{lpp},{4 // lpp},4>"
+    traffic = traffic_for(kname, P * (N - 1))
     roof = {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": hbm, "unit": "GB/s",
             "frac": ach / hbm, "peak_source": src, "traffic": traffic,
             "algorithmic_bytes": alg[dom], "ms": k_ms[dom],
             "other": {k: {"ms": k_ms[k], "GB/s": alg[k] / (k_ms[k] * 1e-3) / 1e9} for k in k_ms}}
+
+    codon = None
+    if not args.no_codon and world == 1:
+        try:
+            codon = codon_line(max(5, args.steps // 20), 3)
+        except Exception as exc:  # reported, not fatal
+            codon = {"error": str(exc)[:300]}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -403,7 +519,7 @@ def main() -> None:
                        "parallelism": f"patterns, weak x{world}"},
             "grad_evals_per_s": world * 1e3 / ms, "logL": logl, "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches) * args.steps, "gpu_launches_per_step": int(launches),
-            "roofline": roof, "cpu_baseline": cpu}
+            "roofline": roof, "cpu_baseline": cpu, "codon": codon}
     print(json.dumps(line), flush=True)
     tl.close()
     if dist:
