@@ -208,6 +208,21 @@ int tl_pre_order_gradient(tl_instance* inst, const tl_pre_op* ops, int count, in
                           double* out_grad, int n_grad);
 int tl_pre_order_gradient_dev(tl_instance* inst, const tl_pre_op* ops, int count, int model,
                               double* out_grad_dev, int n_grad);
+/* Substitution-parameter derivative matrices (Sec. "Discussion": exact
+ * gradients through the matrix exponential). For i < count and every
+ * category r, slot idx[i] receives dP_r(t_i)/dtheta_param, the Frechet
+ * derivative of exp(rho_r t_i Q) in the direction rho_r t_i dQ/dtheta_param,
+ * computed in the eigenbasis as V [(Vinv dQ V) o Phi] Vinv with
+ * Phi_jk = (e^{a_j} - e^{a_k}) / (a_j - a_k), a = rho_r t_i lambda. param
+ * indexes the model's dQ/dtheta (tl_get_model reports how many). */
+int tl_update_param_matrices(tl_instance* inst, int model, int param, const int* idx,
+                             const double* edge_len, int count);
+/* As tl_pre_order_gradient, but dmat_c may hold any derivative of P_c (for
+ * example from tl_update_param_matrices): slot edge[c] receives
+ *   sum_p w_p [sum_r w_r u_c^T dmat_c p_c] / [sum_r w_r u_c^T P_c p_c].
+ * Summing the slots of every edge gives dlogL/dtheta. */
+int tl_pre_order_derivative(tl_instance* inst, const tl_pre_op* ops, int count, int model,
+                            double* out, int n_out);
 /* Edge derivatives from materialised partials:
  *   g_c = sum_p w_p [sum_r w_r rho_r q_c^T Q p_c] / [sum_r w_r q_c^T p_c]. */
 int tl_edge_derivatives(tl_instance* inst, const tl_edge* edges, int count, int model,

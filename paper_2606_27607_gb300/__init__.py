@@ -13,7 +13,7 @@ from . import tree as _tree
 from ._lib import (EDGE_DTYPE, OP_DTYPE, PRE_OP_DTYPE, Instance, TreelikError,  # noqa: F401
                    load)
 
-__all__ = ["Instance", "TreeLikelihood", "TreelikError", "load"]
+__all__ = ["Instance", "TreeLikelihood", "TreelikError", "load", "LogLikelihood"]
 
 
 class TreeLikelihood:
@@ -87,3 +87,29 @@ class TreeLikelihood:
         logl = self.inst.root_loglik(self.nn - 1, 0)
         g = self.inst.pre_order_gradient(self._pre, self.nn, 0)
         return logl, g
+
+    def subst_gradient(self) -> np.ndarray:
+        """dlogL/dtheta for every parameter of the model (kappa for HKY, the
+        six exchangeabilities for GTR, kappa and omega for GY94), with the
+        post-order partials of the current tree. One pre-order pass per
+        parameter with dP/dtheta in the derivative slots; the next gradient()
+        recomputes dP/dt there."""
+        _, _, dq = self.inst.get_model(0)
+        v = np.arange(self.nn - 1, dtype=np.int32)
+        out = np.zeros(len(dq))
+        for k in range(len(dq)):
+            self.inst.update_param_matrices(0, k, self.nn + v, self.edge_len[: self.nn - 1])
+            out[k] = self.inst.pre_order_derivative(self._pre, self.nn, 0).sum()
+        return out
+
+    def value_and_grad(self):
+        """(logL, dlogL/dt per node, dlogL/dtheta) in one forward/backward."""
+        logl, g = self.gradient()
+        return logl, g, self.subst_gradient()
+
+
+def __getattr__(name):
+    if name == "LogLikelihood":
+        from .autograd import LogLikelihood
+        return LogLikelihood
+    raise AttributeError(name)

@@ -69,6 +69,8 @@ SIGNATURES = {
     "tl_set_model_async": [_VP, _I, _I, _VP, _I, _VP, _I],
     "tl_launch_count": [_VP, C.POINTER(C.c_ulonglong)],
     "tl_root_loglik_static": [_VP, _VP, _VP, _VP, _VP, _I, _I, _I, _VP, _VP],
+    "tl_update_param_matrices": [_VP, _I, _I, _VP, _VP, _I],
+    "tl_pre_order_derivative": [_VP, _VP, _I, _I, _VP, _I],
     "tl_sync": [_VP],
 }
 
@@ -250,6 +252,12 @@ class Instance:
         _check(load().tl_update_matrices(self.h, model, _ptr(pi_), _ptr(dp), _ptr(el), pi_.size),
                self.h)
 
+    def update_param_matrices(self, model: int, param: int, idx, edge_len) -> None:
+        i = _arr(idx, np.int32)
+        el = _arr(edge_len, np.float64)
+        _check(load().tl_update_param_matrices(self.h, model, param, _ptr(i), _ptr(el), i.size),
+               self.h)
+
     def get_matrix(self, mat: int) -> np.ndarray:
         out = np.zeros((self.n_categories, self.n_states, self.n_states))
         _check(load().tl_get_matrix(self.h, mat, _ptr(out)), self.h)
@@ -292,6 +300,13 @@ class Instance:
         a = _arr(ops, PRE_OP_DTYPE)
         _check(load().tl_pre_order_gradient_dev(self.h, _ptr(a), a.size, model,
                                                 C.c_void_p(out_ptr), n_grad), self.h)
+
+    def pre_order_derivative(self, ops: np.ndarray, n_out: int, model: int = 0) -> np.ndarray:
+        a = _arr(ops, PRE_OP_DTYPE)
+        g = np.zeros(n_out)
+        _check(load().tl_pre_order_derivative(self.h, _ptr(a), a.size, model, _ptr(g), n_out),
+               self.h)
+        return g
 
     def edge_derivatives(self, edges: np.ndarray, n_grad: int, model: int = 0) -> np.ndarray:
         a = _arr(edges, EDGE_DTYPE)

@@ -1,0 +1,40 @@
+"""torch.autograd.Function over the library: forward = post-order pass and
+root log-likelihood; backward = the pre-order pass (branch lengths) and one
+pre-order pass per substitution parameter with dP/dtheta (Sec. "Algorithmic
+advances": linear-time gradients; Sec. "Discussion": exact substitution
+gradients through the matrix exponential). All arithmetic runs in the
+library's kernels; this module moves tensors across the boundary."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+
+class LogLikelihood(torch.autograd.Function):
+    """logL(t, theta) for a TreeLikelihood whose tips, frequencies, rates and
+    topology are set. ``edge_len`` holds one length per non-root node;
+    ``params`` are the model parameters (kappa | six GTR exchangeabilities |
+    kappa, omega). Returns a 0-d float64 tensor."""
+
+    @staticmethod
+    def forward(ctx, edge_len: torch.Tensor, params: torch.Tensor, tl, kind: str, freqs):
+        t = edge_len.detach().cpu().double().numpy()
+        th = params.detach().cpu().double().numpy()
+        tl.set_model(kind, th, freqs)
+        full = np.zeros(tl.nn)
+        full[: tl.nn - 1] = t
+        tl.set_tree(tl.children, full)
+        logl = tl.loglik()
+        ctx.tl = tl
+        ctx.dev = edge_len.device
+        return torch.tensor(logl, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        tl = ctx.tl
+        _, g = tl.gradient()
+        gth = tl.subst_gradient()
+        s = float(grad_out)
+        gt = torch.from_numpy(s * g[: tl.nn - 1]).to(ctx.dev)
+        gp = torch.from_numpy(s * gth).to(ctx.dev)
+        return gt, gp, None, None, None

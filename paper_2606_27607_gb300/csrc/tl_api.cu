@@ -658,6 +658,7 @@ int tl_destroy(tl_instance* inst) {
         fr(M.Vinv);
         fr(M.lam);
         fr(M.dQ);
+        fr(M.G);
         fr(M.piw);
         fr(M.Qw);
     }
@@ -789,6 +790,7 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
             (rc = dev_alloc(I, &M.Vinv, sizeof(double) * SS, "Vinv")) ||
             (rc = dev_alloc(I, &M.lam, sizeof(double) * I->Spad, "lambda")) ||
             (rc = dev_alloc(I, &M.dQ, sizeof(double) * SS * kMaxDq, "dQ")) ||
+            (rc = dev_alloc(I, &M.G, sizeof(double) * SS * kMaxDq, "parameter basis")) ||
             (rc = dev_alloc(I, &M.piw, (size_t)I->elt * I->Spad, "pi copy")) ||
             (rc = dev_alloc(I, &M.Qw, (size_t)I->elt * SS, "Q copy")))
             return bail(rc);
@@ -1248,7 +1250,7 @@ int tl_root_loglik_dev(tl_instance* inst, int root, int model, double* out_logl_
 }
 
 static int pre_common(Instance* I, const tl_pre_op* ops, int count, int model, int n_grad,
-                      bool store_all, double* d_grad_out) {
+                      bool store_all, double* d_grad_out, int dgen = 0) {
     if (count < 0 || (count > 0 && !ops)) return fail(I, TL_ERR_ARG, "bad op list");
     if (model < 0 || model >= I->n_models || !I->models[model].ready)
         return fail(I, TL_ERR_STATE, "model %d not set", model);
@@ -1265,7 +1267,8 @@ static int pre_common(Instance* I, const tl_pre_op* ops, int count, int model, i
         const size_t bytes = (size_t)count * 3 * kTcOpBytes;
         void* d = area(I, 1, bytes, &rc);
         if (rc) return rc;
-        if ((rc = launch_pre_tc(I, ops, count, row.data(), model, I->d_red, d, bytes))) return rc;
+        if ((rc = launch_pre_tc(I, ops, count, row.data(), model, I->d_red, d, bytes, dgen)))
+            return rc;
         if ((rc = ensure_out(I, (size_t)E))) return rc;
         if ((rc = reduce_fixed(I, I->d_red, E, n_tiles, extra(I).d_out))) return rc;
     } else if (use_nuc(I)) {
@@ -1274,7 +1277,8 @@ static int pre_common(Instance* I, const tl_pre_op* ops, int count, int model, i
         void* d_ops = nullptr;
         if ((rc = upload(I, extra(I).areas[1], plan.dev.data(), sizeof(DevPreOp) * count, &d_ops)))
             return rc;
-        if ((rc = launch_pre4(I, (const DevPreOp*)d_ops, count, plan.n_slots, model, I->d_red)))
+        if ((rc = launch_pre4(I, (const DevPreOp*)d_ops, count, plan.n_slots, model, I->d_red,
+                              dgen)))
             return rc;
         if ((rc = ensure_out(I, (size_t)E))) return rc;
         if ((rc = reduce_fixed(I, I->d_red, E, n_tiles, extra(I).d_out))) return rc;
@@ -1334,6 +1338,54 @@ int tl_pre_order_gradient(tl_instance* inst, const tl_pre_op* ops, int count, in
         cudaMemcpyAsync(out_grad, d_g, sizeof(double) * n_grad, cudaMemcpyDeviceToHost, I->stream);
     if ((rc = cuda_check(I, cudaStreamSynchronize(I->stream), "tl_pre_order_gradient"))) return rc;
     return check_numeric_flag(I);
+}
+
+int tl_pre_order_derivative(tl_instance* inst, const tl_pre_op* ops, int count, int model,
+                            double* out, int n_out) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (!out && n_out > 0) return fail(I, TL_ERR_ARG, "out is null");
+    if (!use_nuc(I) && !use_tc(I))
+        return fail(I, TL_ERR_UNSUPPORTED, "general derivatives need the four-state or TF32 path");
+    int rc;
+    if ((rc = ensure_out(I, (size_t)2 * std::max(n_out, 1) + 16))) return rc;
+    double* d_g = extra(I).d_out + std::max(n_out, 1) + 8;
+    if ((rc = pre_common(I, ops, count, model, n_out, false, d_g, 1))) return rc;
+    if (n_out > 0)
+        cudaMemcpyAsync(out, d_g, sizeof(double) * n_out, cudaMemcpyDeviceToHost, I->stream);
+    if ((rc = cuda_check(I, cudaStreamSynchronize(I->stream), "tl_pre_order_derivative"))) return rc;
+    return check_numeric_flag(I);
+}
+
+int tl_update_param_matrices(tl_instance* inst, int model, int param, const int* idx,
+                             const double* edge_len, int count) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (model < 0 || model >= I->n_models || !I->models[model].ready)
+        return fail(I, TL_ERR_STATE, "model %d not set", model);
+    if (param < 0 || param >= I->models[model].n_dq)
+        return fail(I, TL_ERR_INDEX, "model %d has %d parameters", model, I->models[model].n_dq);
+    if (count < 0 || (count > 0 && (!idx || !edge_len))) return fail(I, TL_ERR_ARG, "bad arguments");
+    for (int i = 0; i < count; ++i) {
+        if (idx[i] < 0 || idx[i] >= I->n_mats) return fail(I, TL_ERR_INDEX, "idx[%d] out of range", i);
+        if (!std::isfinite(edge_len[i]) || edge_len[i] < 0)
+            return fail(I, TL_ERR_NUMERIC, "edge_len[%d] is negative or not finite", i);
+    }
+    if ((size_t)(I->R + count) > I->tmp_cap) {
+        cudaStreamSynchronize(I->stream);
+        cudaFree(I->d_tmp);
+        I->tmp_cap = I->R + count + 1024;
+        int rc = dev_alloc(I, &I->d_tmp, sizeof(double) * I->tmp_cap, "staging");
+        if (rc) return rc;
+    }
+    int rc = stage(I, I->h_rates, I->R, edge_len, count);
+    if (rc) return rc;
+    void* d_idx = nullptr;
+    if ((rc = upload(I, extra(I).areas[3], idx, sizeof(int) * count, &d_idx))) return rc;
+    if ((rc = launch_param_matrices(I, model, param, (const int*)d_idx, I->d_tmp + I->R, count)))
+        return rc;
+    for (int i = 0; i < count; ++i) I->mat_set[idx[i]] = 1;
+    return TL_OK;
 }
 
 int tl_pre_order_gradient_dev(tl_instance* inst, const tl_pre_op* ops, int count, int model,

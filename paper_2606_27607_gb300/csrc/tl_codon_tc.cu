@@ -176,6 +176,7 @@ struct TcArgs {
     const double* pi;         // [64] root frequencies (pre1)
     double* gpart;            // [edge rows][n_tiles] gradient partials
     int R, Ppad, S, n_tiles, rescale;
+    int dgen;                 // pre2: operand 1 is dP x for any derivative dP (not Q x)
     size_t bstride;           // floats per buffer
     int* err;
     float catw[kMaxCat], rates[kMaxCat];
@@ -490,7 +491,9 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                 }
             }
         } else {  // kPre2: operand 0 = q_c = u_c P_c (B = P^T), operand 1 = Q x_c
+                  // (or dP x_c for a general derivative, paired with u_c)
             const float den = __int_as_float(a.epool[(size_t)op.dest * a.Ppad + p]);
+            const float* ub = a.pool + (size_t)op.dest * a.bstride + (size_t)p * kTcN;
             float num = 0.f, m = 0.f;
             for (int r = 0; r < R; ++r) {
                 float nr = 0.f;
@@ -498,13 +501,23 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                     float x[16], y[16];
                     chunk(0, r, q, x);
                     chunk(1, r, q, y);
+                    if (a.dgen) {
+                        const float4* u4 =
+                            reinterpret_cast<const float4*>(ub + (size_t)r * a.Ppad * kTcN + q * 16);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        nr += x[i] * y[i];
-                        m = fmaxf(m, x[i]);
+                        for (int u = 0; u < 4; ++u) {
+                            const float4 f = u4[u];
+                            nr += f.x * y[4 * u] + f.y * y[4 * u + 1] + f.z * y[4 * u + 2] +
+                                  f.w * y[4 * u + 3];
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) nr += x[i] * y[i];
                     }
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) m = fmaxf(m, x[i]);
                 }
-                num += a.catw[r] * a.rates[r] * nr;
+                num += a.catw[r] * (a.dgen ? 1.f : a.rates[r]) * nr;
             }
             if (op.edge[0] >= 0) {
                 const float g = block_sum128(wp * (num / den), red);
@@ -615,6 +628,7 @@ TcArgs tc_args(Instance* I) {
     a.patw = I->d_patw;
     a.pi = nullptr;
     a.gpart = nullptr;
+    a.dgen = 0;
     a.R = I->R;
     a.Ppad = I->Ppad;
     a.S = I->S;
@@ -743,7 +757,7 @@ int launch_post_tc(Instance* I, const tl_op* ops, int n, void* d_ops_area, size_
 // parent (v = P x, den, u = q o v_sibling, tip gradients), then PRE2 per
 // internal child (q = u P, Q x, internal gradients, q rescaled in place).
 int launch_pre_tc(Instance* I, const tl_pre_op* ops, int n, const int* edge_row, int model,
-                  double* d_gpart, void* d_ops_area, size_t cap) {
+                  double* d_gpart, void* d_ops_area, size_t cap, int dgen) {
     std::vector<int> prod(I->n_bufs, -1), level(n, 0);
     for (int k = 0; k < n; ++k) {
         if (ops[k].parent_pre >= 0 && prod[ops[k].parent_pre] >= 0)
@@ -785,8 +799,11 @@ int launch_pre_tc(Instance* I, const tl_pre_op* ops, int n, const int* edge_row,
                     u.child[0] = t.uout[c];
                     u.brow[0] = brow_of(I, o.mat[c], 1);       // q = u P  (B = P^T)
                     u.kind[1] = kInternal;
-                    u.child[1] = o.child[c] - I->n_tips;       // Q x_c
-                    u.brow[1] = qrow_of(I, model);
+                    u.child[1] = o.child[c] - I->n_tips;       // Q x_c, or dP x_c
+                    u.brow[1] = dgen ? brow_of(I, o.dmat[c], 0) : qrow_of(I, model);
+                    if (dgen && o.dmat[c] < 0 && o.edge[c] >= 0)
+                        return fail(I, TL_ERR_ARG, "pre op %d: edge without dmat", k);
+                    if (dgen && o.dmat[c] < 0) u.brow[1] = qrow_of(I, model);
                     u.dest = t.uout[c];
                     u.qin = -1;
                     u.uout[0] = u.uout[1] = -1;
@@ -810,6 +827,7 @@ int launch_pre_tc(Instance* I, const tl_pre_op* ops, int n, const int* edge_row,
     TcArgs a = tc_args(I);
     a.pi = I->models[model].pi;
     a.gpart = d_gpart;
+    a.dgen = dgen;
     const TcOp* d = reinterpret_cast<const TcOp*>(d_ops_area);
     for (int L = 0; L < n_levels; ++L) {
         if (n1[L]) launch_mode<kPre1>(I, d + f1[L], n1[L], a);

@@ -80,6 +80,7 @@ struct NucArgs {
     const double* patw;             // [Ppad] pattern weights (0 on padding)
     size_t bstride;
     int P, Ppad, R, n_slots, rescale, mat_stride, n_tiles;
+    int dgen;                       // pre-order: dmat is any derivative of P (no Q shortcut)
     T catw[kMaxCat];
     T rates[kMaxCat];
 };
@@ -91,6 +92,7 @@ struct ModelDev {
     double* Vinv = nullptr;   // [Spad][Spad]
     double* lam = nullptr;    // [Spad]
     double* dQ = nullptr;     // [kMaxDq][Spad][Spad]
+    double* G = nullptr;      // [kMaxDq][Spad][Spad]: Vinv dQ V
     void* piw = nullptr;      // pi in working precision [Spad]
     void* Qw = nullptr;       // Q in working precision [Spad][Spad]
     int n_dq = 0;
@@ -160,6 +162,8 @@ int launch_q_from_eigen(Instance* I, int m);  // V, Vinv, lambda already in the 
 int launch_model_working_copies(Instance* I, int m);
 int launch_update_matrices(Instance* I, int m, const int* d_pidx, const int* d_dpidx,
                            const double* d_len, int count);
+int launch_param_matrices(Instance* I, int m, int param, const int* d_idx, const double* d_len,
+                          int count);
 
 // tl_nuc.cu (four-state pattern-tile kernels, T = float or double)
 int nuc_lanes(const Instance* I);            // lanes per pattern (root, edge kernels)
@@ -171,7 +175,7 @@ int launch_post4(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots);
 int launch_root4(Instance* I, int root_kind, int root, int model, double* d_site,
                  double* d_part);
 int launch_pre4(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, int model,
-                double* d_gpart);
+                double* d_gpart, int dgen);
 int launch_edge4(Instance* I, const DevEdge* d_edges, int n_edges, int model, double* d_gpart);
 
 // tl_generic.cu (FP64, any S)
@@ -193,7 +197,7 @@ int launch_post_tc(Instance* I, const tl_op* ops, int n, void* d_ops_area, size_
 int launch_root_tc(Instance* I, int root_pool, int model, double* d_site, double* d_part,
                    int n_parts);
 int launch_pre_tc(Instance* I, const tl_pre_op* ops, int n, const int* edge_row, int model,
-                  double* d_gpart, void* d_ops_area, size_t cap);
+                  double* d_gpart, void* d_ops_area, size_t cap, int dgen);
 int launch_q_tc(Instance* I, int model);
 size_t tc_matw_floats(const Instance* I);
 

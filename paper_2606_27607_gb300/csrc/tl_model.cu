@@ -307,6 +307,64 @@ __global__ void k_model_working(int S, int Spad, const double* __restrict__ Q,
     (void)tf32;
 }
 
+// Write one category of one matrix slot (Pm, FP64 [Spad][Spad] in shared
+// memory) into the working layout of the instance.
+template <typename T>
+__device__ void write_layout(const double* Pm, int slot, int r, int S, int Spad, int R,
+                             T* __restrict__ matw, size_t matw_stride, int layout,
+                             T* __restrict__ rowsum) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    T* w = matw + (size_t)slot * matw_stride;
+    if (layout == 0) {
+        // [5 columns][R][4]: column j of every category contiguous; the
+        // row-sum column (ambiguous tips) is summed in T in column order,
+        // exactly as a product with an all-ones partial rounds
+        for (int idx = t; idx < kColStride * 4; idx += nt) {
+            int j = idx / 4, i = idx % 4;
+            T v;
+            if (j < 4) {
+                v = (T)Pm[i * Spad + j];
+            } else {
+                v = (T)Pm[i * Spad];
+                for (int q = 1; q < S; ++q) v = v + (T)Pm[i * Spad + q];
+            }
+            w[((size_t)j * R + r) * 4 + i] = v;
+        }
+    } else if (layout == 1) {
+        w += (size_t)r * (Spad + 1) * Spad;
+        for (int idx = t; idx < (Spad + 1) * Spad; idx += nt) {
+            int j = idx / Spad, i = idx % Spad;
+            T v;
+            if (j < Spad) {
+                v = (T)Pm[i * Spad + j];
+            } else {
+                v = (T)Pm[i * Spad];
+                for (int q = 1; q < S; ++q) v = v + (T)Pm[i * Spad + q];
+            }
+            w[idx] = v;
+        }
+    } else {
+        // tensor-core layout [2][R][64][64]: P row-major (the B operand)
+        // and P^T (tip lookups), both TF32-rounded; row sums of the
+        // rounded P summed in order (ambiguous tips)
+        T* wp = w + (size_t)r * Spad * Spad;
+        T* wt = w + ((size_t)R + r) * Spad * Spad;
+        for (int idx = t; idx < Spad * Spad; idx += nt) {
+            const int i = idx / Spad, j = idx % Spad;
+            const T v = (T)round_tf32((float)Pm[idx]);
+            wp[idx] = v;
+            wt[j * Spad + i] = v;
+        }
+        __syncthreads();
+        for (int i = t; i < Spad; i += nt) {
+            T v = wp[i * Spad];
+            for (int q = 1; q < S; ++q) v = v + wp[i * Spad + q];
+            rowsum[((size_t)slot * R + r) * Spad + i] = v;
+        }
+    }
+
+}
+
 // P and dP/dt for `count` edges; grid (count, R).
 //  layout 0: four-state column layout [R][5][4] of T: column j of P, then row sums
 //  layout 1: FP64 transposed layout [R][Spad+1][Spad]: W[j][i] = P[i][j], row Spad = row sums
@@ -347,54 +405,7 @@ __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
             Pm[idx] = acc;
         }
         __syncthreads();
-        T* w = matw + (size_t)slot * matw_stride;
-        if (layout == 0) {
-            // [5 columns][R][4]: column j of every category contiguous; the
-            // row-sum column (ambiguous tips) is summed in T in column order,
-            // exactly as a product with an all-ones partial rounds
-            for (int idx = t; idx < kColStride * 4; idx += nt) {
-                int j = idx / 4, i = idx % 4;
-                T v;
-                if (j < 4) {
-                    v = (T)Pm[i * Spad + j];
-                } else {
-                    v = (T)Pm[i * Spad];
-                    for (int q = 1; q < S; ++q) v = v + (T)Pm[i * Spad + q];
-                }
-                w[((size_t)j * R + r) * 4 + i] = v;
-            }
-        } else if (layout == 1) {
-            w += (size_t)r * (Spad + 1) * Spad;
-            for (int idx = t; idx < (Spad + 1) * Spad; idx += nt) {
-                int j = idx / Spad, i = idx % Spad;
-                T v;
-                if (j < Spad) {
-                    v = (T)Pm[i * Spad + j];
-                } else {
-                    v = (T)Pm[i * Spad];
-                    for (int q = 1; q < S; ++q) v = v + (T)Pm[i * Spad + q];
-                }
-                w[idx] = v;
-            }
-        } else {
-            // tensor-core layout [2][R][64][64]: P row-major (the B operand)
-            // and P^T (tip lookups), both TF32-rounded; row sums of the
-            // rounded P summed in order (ambiguous tips)
-            T* wp = w + (size_t)r * Spad * Spad;
-            T* wt = w + ((size_t)R + r) * Spad * Spad;
-            for (int idx = t; idx < Spad * Spad; idx += nt) {
-                const int i = idx / Spad, j = idx % Spad;
-                const T v = (T)round_tf32((float)Pm[idx]);
-                wp[idx] = v;
-                wt[j * Spad + i] = v;
-            }
-            __syncthreads();
-            for (int i = t; i < Spad; i += nt) {
-                T v = wp[i * Spad];
-                for (int q = 1; q < S; ++q) v = v + wp[i * Spad + q];
-                rowsum[((size_t)slot * R + r) * Spad + i] = v;
-            }
-        }
+        write_layout(Pm, slot, r, S, Spad, R, matw, matw_stride, layout, rowsum);
         __syncthreads();
     }
 }
@@ -453,6 +464,8 @@ int launch_eigen_from_q(Instance* I, int m, bool check) {
     return launch_model_working_copies(I, m);
 }
 
+int launch_param_basis(Instance* I, int m);
+
 int launch_q_from_eigen(Instance* I, int m) {
     ModelDev& M = I->models[m];
     k_q_from_eigen<<<1, 256, 0, I->stream>>>(I->S, I->Spad, M.V, M.Vinv, M.lam, M.Q);
@@ -474,6 +487,7 @@ int launch_model_working_copies(Instance* I, int m) {
     int rc = cuda_check(I, cudaGetLastError(), "model working copies");
     if (rc) return rc;
     if (I->prec == kTF32 && (rc = launch_q_tc(I, m))) return rc;
+    if ((rc = launch_param_basis(I, m))) return rc;
     M.ready = true;
     return TL_OK;
 }
@@ -502,6 +516,111 @@ int launch_update_matrices(Instance* I, int m, const int* d_pidx, const int* d_d
     }
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "update matrices");
+}
+
+
+// G_k = Vinv dQ_k V for every parameter derivative of a model. One block per k.
+__global__ void k_param_basis(int S, int Spad, const double* __restrict__ V,
+                              const double* __restrict__ Vinv, const double* __restrict__ dQ,
+                              double* __restrict__ G) {
+    const int k = blockIdx.x;
+    const double* D = dQ + (size_t)k * Spad * Spad;
+    double* out = G + (size_t)k * Spad * Spad;
+    for (int idx = threadIdx.x; idx < Spad * Spad; idx += blockDim.x) {
+        const int i = idx / Spad, j = idx % Spad;
+        double acc = 0.0;
+        if (i < S && j < S)
+            for (int a = 0; a < S; ++a) {
+                double va = 0.0;
+                for (int b2 = 0; b2 < S; ++b2) va += D[a * Spad + b2] * V[b2 * Spad + j];
+                acc += Vinv[i * Spad + a] * va;
+            }
+        out[idx] = acc;
+    }
+}
+
+// dP_r(t)/dtheta = V [G o Phi] Vinv with Phi_ij = rho t (e^{a_i} - e^{a_j}) / (a_i - a_j),
+// a = rho t lambda (the Frechet derivative of the matrix exponential in the
+// eigenbasis, Daleckii-Krein); grid (count, R).
+template <typename T>
+__global__ void k_param_tpm(int S, int Spad, int R, const double* __restrict__ V,
+                            const double* __restrict__ Vinv, const double* __restrict__ lam,
+                            const double* __restrict__ G, const int* __restrict__ idx_out,
+                            const double* __restrict__ len, const double* __restrict__ rates,
+                            double* __restrict__ mat64, T* __restrict__ matw, size_t matw_stride,
+                            int layout, T* __restrict__ rowsum) {
+    extern __shared__ double sm_ptpm[];
+    double* X = sm_ptpm;                         // [Spad*Spad]
+    double* Pm = sm_ptpm + (size_t)Spad * Spad;  // [Spad*Spad]
+    __shared__ double a[64], ea[64];
+    const int b = blockIdx.x, r = blockIdx.y;
+    const int t = threadIdx.x, nt = blockDim.x;
+    const double rt = rates[r] * len[b];
+    const int slot = idx_out[b];
+    for (int k = t; k < Spad; k += nt) {
+        a[k] = (k < S) ? lam[k] * rt : 0.0;
+        ea[k] = (k < S) ? exp(a[k]) : 0.0;
+    }
+    __syncthreads();
+    for (int idx = t; idx < Spad * Spad; idx += nt) {
+        const int i = idx / Spad, j = idx % Spad;
+        double phi = 0.0;
+        if (i < S && j < S) {
+            const double d = a[i] - a[j];
+            // (e^{a_i} - e^{a_j}) / (a_i - a_j) = e^{a_j} expm1(d) / d, -> e^{a_i} as d -> 0
+            phi = (fabs(d) < 1e-12) ? ea[i] : ea[j] * expm1(d) / d;
+        }
+        X[idx] = rt * G[idx] * phi;
+    }
+    __syncthreads();
+    // Pm = V X Vinv (via a row of V X at a time)
+    for (int idx = t; idx < Spad * Spad; idx += nt) {
+        const int i = idx / Spad, j = idx % Spad;
+        double acc = 0.0;
+        if (i < S && j < S)
+            for (int k = 0; k < S; ++k) {
+                double vx = 0.0;
+                for (int l = 0; l < S; ++l) vx += V[i * Spad + l] * X[l * Spad + k];
+                acc += vx * Vinv[k * Spad + j];
+            }
+        Pm[idx] = acc;
+        mat64[((size_t)slot * R + r) * Spad * Spad + idx] = acc;
+    }
+    __syncthreads();
+    write_layout(Pm, slot, r, S, Spad, R, matw, matw_stride, layout, rowsum);
+}
+
+int launch_param_basis(Instance* I, int m) {
+    ModelDev& M = I->models[m];
+    if (M.n_dq == 0) return TL_OK;
+    k_param_basis<<<M.n_dq, 256, 0, I->stream>>>(I->S, I->Spad, M.V, M.Vinv, M.dQ, M.G);
+    I->launches += 1;
+    return cuda_check(I, cudaGetLastError(), "parameter basis");
+}
+
+int launch_param_matrices(Instance* I, int m, int param, const int* d_idx, const double* d_len,
+                          int count) {
+    if (count <= 0) return TL_OK;
+    ModelDev& M = I->models[m];
+    const double* d_rates = I->d_tmp;
+    dim3 grid(count, I->R);
+    const size_t smem = 2 * (size_t)I->Spad * I->Spad * sizeof(double);
+    const int layout = (I->S == 4 && (I->prec == kF32 || I->prec == kF64)) ? 0
+                       : (I->prec == kF64 ? 1 : 2);
+    const double* G = M.G + (size_t)param * I->Spad * I->Spad;
+    if (I->prec == kF64) {
+        cudaFuncSetAttribute(k_param_tpm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_param_tpm<double><<<grid, 256, smem, I->stream>>>(
+            I->S, I->Spad, I->R, M.V, M.Vinv, M.lam, G, d_idx, d_len, d_rates, I->d_mat64,
+            (double*)I->d_matw, I->matw_stride, layout, nullptr);
+    } else {
+        cudaFuncSetAttribute(k_param_tpm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_param_tpm<float><<<grid, 256, smem, I->stream>>>(
+            I->S, I->Spad, I->R, M.V, M.Vinv, M.lam, G, d_idx, d_len, d_rates, I->d_mat64,
+            (float*)I->d_matw, I->matw_stride, layout, I->d_rowsum);
+    }
+    I->launches += 1;
+    return cuda_check(I, cudaGetLastError(), "parameter derivative matrices");
 }
 
 }  // namespace tl

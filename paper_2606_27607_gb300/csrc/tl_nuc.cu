@@ -501,8 +501,9 @@ k_pre4(const DevPreOp* __restrict__ ops, int n_ops, NucArgs<T> a, const T* __res
         __syncwarp();
         {
             const DevPreOp& o0 = pipe.obuf[0];
-            const int idx[4] = {o0.mat[0], o0.mat[1], o0.kind[0] != kInternal ? o0.dmat[0] : -1,
-                                o0.kind[1] != kInternal ? o0.dmat[1] : -1};
+            const int idx[4] = {o0.mat[0], o0.mat[1],
+                                (o0.kind[0] != kInternal || a.dgen) ? o0.dmat[0] : -1,
+                                (o0.kind[1] != kInternal || a.dgen) ? o0.dmat[1] : -1};
             pipe.issue_mats(0, n_ops, idx, a.mat, a.mat_stride, lane);
         }
         cp_async_commit();
@@ -513,8 +514,8 @@ k_pre4(const DevPreOp* __restrict__ ops, int n_ops, NucArgs<T> a, const T* __res
             if (k + 1 < n_ops) {
                 const DevPreOp& o1 = pipe.obuf[(k + 1) % 3];
                 const int idx[4] = {o1.mat[0], o1.mat[1],
-                                    o1.kind[0] != kInternal ? o1.dmat[0] : -1,
-                                    o1.kind[1] != kInternal ? o1.dmat[1] : -1};
+                                    (o1.kind[0] != kInternal || a.dgen) ? o1.dmat[0] : -1,
+                                    (o1.kind[1] != kInternal || a.dgen) ? o1.dmat[1] : -1};
                 pipe.issue_mats(k + 1, n_ops, idx, a.mat, a.mat_stride, lane);
             }
             cp_async_commit();
@@ -591,7 +592,7 @@ k_pre4(const DevPreOp* __restrict__ ops, int n_ops, NucArgs<T> a, const T* __res
                     // in working precision; FP64 (a slow unit on this part)
                     // only once per tile and edge
                     T num_l = T(0);
-                    if (tip) {
+                    if (tip || a.dgen) {
                         const T* dc = mk + (2 + c) * pipe.matf + r0 * 4;
                         const int col = tcol[c];
 #pragma unroll
@@ -744,6 +745,7 @@ static NucArgs<T> make_args(const Instance* I, int n_slots) {
     a.rescale = I->rescale;
     a.mat_stride = (int)I->matw_stride;
     a.n_tiles = nuc_tiles(I);  // launchers of the main kernels override
+    a.dgen = 0;
     for (int r = 0; r < kMaxCat; ++r) {
         a.catw[r] = (T)(r < I->R ? I->h_catw[r] : 0.0);
         a.rates[r] = (T)(r < I->R ? I->h_rates[r] : 0.0);
@@ -835,22 +837,23 @@ int launch_root4(Instance* I, int root_kind, int root, int model, double* d_site
 
 template <typename T, int LPP, int CPL, int NR>
 static void pre4_t(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, const void* piw,
-                   const void* Qw, double* d_gpart) {
+                   const void* Qw, double* d_gpart, int dgen) {
     const size_t smem = (size_t)kWarpsPerBlock * ((size_t)n_slots * CPL * 32 * 4 * sizeof(T) +
                                                   pipe_bytes<DevPreOp, T, 4>(I->R));
     cudaFuncSetAttribute(k_pre4<T, LPP, CPL, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     NucArgs<T> a = make_args<T>(I, n_slots);
     a.n_tiles = nuc_tiles_for(I, LPP);
+    a.dgen = dgen;
     const int grid = grid_for(I, k_pre4<T, LPP, CPL, NR>, smem, a.n_tiles);
     k_pre4<T, LPP, CPL, NR><<<grid, kWarpsPerBlock * 32, smem, I->stream>>>(
         d_ops, n_ops, a, reinterpret_cast<const T*>(piw), reinterpret_cast<const T*>(Qw), d_gpart);
 }
 
 int launch_pre4(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, int model,
-                double* d_gpart) {
+                double* d_gpart, int dgen) {
     TL_MAIN_DISPATCH(I, pre4_t, I, d_ops, n_ops, n_slots, I->models[model].piw,
-                     I->models[model].Qw, d_gpart);
+                     I->models[model].Qw, d_gpart, dgen);
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "pre-order kernel");
 }
