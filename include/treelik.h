@@ -267,6 +267,46 @@ int tl_launch_count(const tl_instance* inst, unsigned long long* out);
 /* Wait for the instance's stream and report any pending device error. */
 int tl_sync(tl_instance* inst);
 
+/* ---- batched evaluation of several instances ------------------------------
+ * Patterns are conditionally independent given the tree and so are separate
+ * trees: the per-pattern updates of many instances (different trees, taxa
+ * and pattern counts) are one data-parallel launch (Sec. "Benchmarks on
+ * NVIDIA and AMD GPUs" splits one alignment across devices by the same
+ * independence). These calls take n four-state instances (S = 4, FP32 or
+ * FP64, all of one precision and category count, each at most once) and do
+ * for all of them what the single-instance call does for one, with one
+ * kernel launch per pass instead of one per instance. Each instance's
+ * results are bit-identical to its single-instance call and do not depend on
+ * the other instances in the batch.
+ *
+ * Streams: the batched work runs on the batch's stream, after the work
+ * already queued on each instance's stream; each instance's stream then
+ * waits for the batched work (events; no host synchronisation).
+ * Errors: the batch's status and tl_batch_last_error; an error in instance
+ * k's arguments names k and launches nothing. Output pointers are device
+ * memory. */
+typedef struct tl_batch tl_batch;
+
+int tl_batch_create(void* cuda_stream, tl_batch** out);
+int tl_batch_destroy(tl_batch* b);
+int tl_batch_last_error(const tl_batch* b, char* buf, size_t len);
+/* Kernels launched by the batch (not counted by the instances). */
+int tl_batch_launch_count(const tl_batch* b, unsigned long long* out);
+
+/* tl_update_partials for each instance k with ops[k][0 .. counts[k]). */
+int tl_batch_update_partials(tl_batch* b, tl_instance* const* insts, const tl_op* const* ops,
+                             const int* counts, int n);
+/* tl_root_loglik_dev for each instance: out_logl_dev[k] (device, n doubles)
+ * receives logL of instance k at buffer roots[k] under model models[k]. */
+int tl_batch_root_loglik_dev(tl_batch* b, tl_instance* const* insts, const int* roots,
+                             const int* models, int n, double* out_logl_dev);
+/* tl_pre_order_gradient_dev for each instance: out_grad_dev[k] (device,
+ * n_grad[k] doubles) receives instance k's branch-length gradient. */
+int tl_batch_pre_order_gradient_dev(tl_batch* b, tl_instance* const* insts,
+                                    const tl_pre_op* const* ops, const int* counts,
+                                    const int* models, double* const* out_grad_dev,
+                                    const int* n_grad, int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,13 @@ SIGNATURES = {
     "tl_update_param_matrices": [_VP, _I, _I, _VP, _VP, _I],
     "tl_pre_order_derivative": [_VP, _VP, _I, _I, _VP, _I],
     "tl_sync": [_VP],
+    "tl_batch_create": [_VP, C.POINTER(_VP)],
+    "tl_batch_destroy": [_VP],
+    "tl_batch_last_error": [_VP, C.c_char_p, C.c_size_t],
+    "tl_batch_launch_count": [_VP, C.POINTER(C.c_ulonglong)],
+    "tl_batch_update_partials": [_VP, _VP, _VP, _VP, _I],
+    "tl_batch_root_loglik_dev": [_VP, _VP, _VP, _VP, _I, _VP],
+    "tl_batch_pre_order_gradient_dev": [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _I],
 }
 
 _lib = None
@@ -314,3 +321,72 @@ class Instance:
         _check(load().tl_edge_derivatives(self.h, _ptr(a), a.size, model, _ptr(g), n_grad),
                self.h)
         return g
+
+
+def _batch_check(rc: int, handle) -> None:
+    if rc != TL_OK:
+        buf = C.create_string_buffer(1024)
+        load().tl_batch_last_error(handle, buf, 1024)
+        raise TreelikError(rc, buf.value.decode(errors="replace"))
+
+
+class Batch:
+    """A batch context (tl_batch_*): the calls below evaluate several
+    four-state instances with one launch per pass, on ``stream``."""
+
+    def __init__(self, stream: int | None = None):
+        h = C.c_void_p()
+        _check(load().tl_batch_create(C.c_void_p(stream or 0), C.byref(h)), None)
+        self.h = h
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            load().tl_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        n = C.c_ulonglong()
+        _batch_check(load().tl_batch_launch_count(self.h, C.byref(n)), self.h)
+        return int(n.value)
+
+    @staticmethod
+    def _handles(insts) -> C.Array:
+        return (C.c_void_p * max(len(insts), 1))(*[i.h for i in insts])
+
+    @staticmethod
+    def _lists(lists, dtype):
+        arrs = [_arr(a, dtype) for a in lists]
+        ptrs = (C.c_void_p * max(len(arrs), 1))(*[a.ctypes.data for a in arrs])
+        counts = np.array([a.size for a in arrs], dtype=np.int32)
+        return arrs, ptrs, counts
+
+    def update_partials(self, insts, ops) -> None:
+        """ops[k]: instance k's post-order op list (OP_DTYPE)."""
+        arrs, ptrs, counts = self._lists(ops, OP_DTYPE)
+        _batch_check(load().tl_batch_update_partials(self.h, self._handles(insts), ptrs,
+                                                     _ptr(counts), len(insts)), self.h)
+
+    def root_loglik_dev(self, insts, roots, models, out_ptr: int) -> None:
+        """out_ptr: device array of len(insts) doubles."""
+        r = _arr(roots, np.int32)
+        m = _arr(models, np.int32)
+        _batch_check(load().tl_batch_root_loglik_dev(self.h, self._handles(insts), _ptr(r),
+                                                     _ptr(m), len(insts), C.c_void_p(out_ptr)),
+                     self.h)
+
+    def pre_order_gradient_dev(self, insts, ops, models, out_ptrs, n_grad) -> None:
+        """ops[k]: instance k's pre-order op list; out_ptrs[k]: device array
+        of n_grad[k] doubles."""
+        arrs, ptrs, counts = self._lists(ops, PRE_OP_DTYPE)
+        m = _arr(models, np.int32)
+        ng = _arr(n_grad, np.int32)
+        outs = (C.c_void_p * max(len(out_ptrs), 1))(*[int(x) for x in out_ptrs])
+        _batch_check(load().tl_batch_pre_order_gradient_dev(
+            self.h, self._handles(insts), ptrs, _ptr(counts), _ptr(m), outs, _ptr(ng),
+            len(insts)), self.h)

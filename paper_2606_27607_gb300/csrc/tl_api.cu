@@ -43,19 +43,46 @@ int cuda_check(Instance* I, cudaError_t e, const char* what) {
                 cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
-// Sum each of n_out rows of n_in doubles in a fixed order (deterministic).
-__global__ void k_reduce_rows(const double* __restrict__ in, int n_in, double* __restrict__ out) {
-    __shared__ double s[256];
-    const int row = blockIdx.x;
+// Fixed-order sum of n doubles by one warp: lane l adds in[l], in[l + 32],
+// ... in order, then a butterfly over the lanes (every lane gets the sum).
+// Single and batched reductions both use it, so their results are identical.
+__device__ __forceinline__ double warp_row_sum(const double* __restrict__ in, int n) {
+    const int lane = threadIdx.x & 31;
     double acc = 0.0;
-    for (int j = threadIdx.x; j < n_in; j += blockDim.x) acc += in[(size_t)row * n_in + j];
-    s[threadIdx.x] = acc;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
-        __syncthreads();
+    for (int j = lane; j < n; j += 32) acc += in[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
+constexpr int kRedWarps = 8;  // rows per block of the reductions
+
+// Sum each of n_out rows of n_in doubles in a fixed order (deterministic).
+__global__ void k_reduce_rows(const double* __restrict__ in, int n_in, int n_out,
+                              double* __restrict__ out) {
+    const int row = blockIdx.x * kRedWarps + (threadIdx.x >> 5);
+    if (row >= n_out) return;
+    const double v = warp_row_sum(in + (size_t)row * n_in, n_in);
+    if ((threadIdx.x & 31) == 0) out[row] = v;
+}
+
+// Batched form over RedJob descriptors: global row -> job by binary search
+// over row_begin; jobs[j] owns rows [row_begin[j], row_begin[j + 1]).
+__global__ void k_reduce_batch(const RedJob* __restrict__ jobs, const int* __restrict__ row_begin,
+                               int n_jobs, int total) {
+    const int row = blockIdx.x * kRedWarps + (threadIdx.x >> 5);
+    if (row >= total) return;
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (row_begin[mid] <= row) lo = mid;
+        else hi = mid - 1;
     }
-    if (threadIdx.x == 0) out[row] = s[0];
+    const RedJob J = jobs[lo];
+    const int g = row - row_begin[lo];
+    const int src = J.inv ? J.inv[g] : g;
+    const double v = src >= 0 ? warp_row_sum(J.in + (size_t)src * J.n_in, J.n_in) : 0.0;
+    if ((threadIdx.x & 31) == 0) J.out[g] = v;
 }
 
 // out[map[k]] = in[k] for k < n; out has n_out entries, the rest zeroed.
@@ -70,7 +97,8 @@ __global__ void k_scatter(const double* __restrict__ in, const int* __restrict__
 
 int reduce_fixed(Instance* I, const double* d_in, int n_out, int n_in, double* d_out) {
     if (n_out <= 0) return TL_OK;
-    k_reduce_rows<<<n_out, 256, 0, I->stream>>>(d_in, n_in, d_out);
+    k_reduce_rows<<<(n_out + kRedWarps - 1) / kRedWarps, kRedWarps * 32, 0, I->stream>>>(
+        d_in, n_in, n_out, d_out);
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "reduction");
 }
@@ -164,7 +192,8 @@ int upload(Instance* I, OpArea& A, const void* src, size_t bytes, void** dptr) {
 struct Extra {
     PinnedSlot ring[kRing];
     int ring_next = 0;
-    OpArea areas[5];
+    OpArea areas[6];
+    cudaEvent_t order_ev = nullptr;  // orders this stream against a batch stream
     std::vector<void*> gen_q;     // generic path: scratch pre-order buffers
     double* d_out = nullptr;      // small result area
     size_t out_cap = 0;
@@ -674,6 +703,7 @@ int tl_destroy(tl_instance* inst) {
             if (s.ev) cudaEventDestroy(s.ev);
         }
         for (auto& A : X->areas) fr(A.d);
+        if (X->order_ev) cudaEventDestroy(X->order_ev);
         for (void* p : X->gen_q) fr(p);
         fr(X->d_out);
         delete X;
@@ -1452,10 +1482,333 @@ int tl_edge_derivatives(tl_instance* inst, const tl_edge* edges, int count, int 
     return TL_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// batched four-state calls
+// ---------------------------------------------------------------------------
+namespace {
+
+Batch* as_batch(tl_batch* b) { return reinterpret_cast<Batch*>(b); }
+
+// Instances of a batched call: four-state FP32 or FP64, all of one precision
+// and category count, on the batch's device, each at most once.
+int batch_instances(Batch* B, tl_instance* const* insts, int n, std::vector<Instance*>* out) {
+    if (n < 0 || (n > 0 && !insts)) return batch_fail(B, TL_ERR_ARG, "bad instance list");
+    out->assign(n, nullptr);
+    for (int k = 0; k < n; ++k) {
+        Instance* I = reinterpret_cast<Instance*>(insts[k]);
+        if (!I) return batch_fail(B, TL_ERR_ARG, "instance %d is null", k);
+        if (!use_nuc(I))
+            return batch_fail(B, TL_ERR_UNSUPPORTED,
+                              "instance %d: batched calls take four-state FP32/FP64 instances", k);
+        if (I->device != B->device)
+            return batch_fail(B, TL_ERR_ARG, "instance %d is on device %d, the batch on %d", k,
+                              I->device, B->device);
+        if (k > 0 && (I->prec != (*out)[0]->prec || I->R != (*out)[0]->R))
+            return batch_fail(B, TL_ERR_UNSUPPORTED,
+                              "instance %d: precision or category count differs from instance 0", k);
+        (*out)[k] = I;
+    }
+    std::vector<Instance*> sorted(*out);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end())
+        return batch_fail(B, TL_ERR_ARG, "an instance appears twice in one batch");
+    return TL_OK;
+}
+
+// An instance-level failure (validation, planning) reported on the batch.
+int batch_from(Batch* B, Instance* I, int k, int rc) {
+    return batch_fail(B, rc, "instance %d: %s", k, I->err.c_str());
+}
+
+// Batch stream after each instance stream's queued work (uploads, matrices).
+int batch_order_before(Batch* B, const std::vector<Instance*>& I) {
+    for (Instance* x : I) {
+        if (x->stream == B->stream) continue;
+        Extra& X = extra(x);
+        cudaError_t e = cudaSuccess;
+        if (!X.order_ev) e = cudaEventCreateWithFlags(&X.order_ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(X.order_ev, x->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(B->stream, X.order_ev, 0);
+        if (e != cudaSuccess) return batch_cuda(B, e, "ordering before the batch");
+    }
+    return TL_OK;
+}
+
+// Each instance stream after the batched work (its buffers and scratch were
+// in use on the batch stream).
+int batch_order_after(Batch* B, const std::vector<Instance*>& I) {
+    bool any = false;
+    for (Instance* x : I) any = any || x->stream != B->stream;
+    if (!any) return TL_OK;
+    cudaError_t e = cudaSuccess;
+    if (!B->done) e = cudaEventCreateWithFlags(&B->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(B->done, B->stream);
+    for (Instance* x : I)
+        if (e == cudaSuccess && x->stream != B->stream) e = cudaStreamWaitEvent(x->stream, B->done, 0);
+    return batch_cuda(B, e, "ordering after the batch");
+}
+
+// One launch of fixed-order row sums for all jobs (area `which`).
+int batch_reduce(Batch* B, int which, const std::vector<RedJob>& jobs) {
+    const int n = (int)jobs.size();
+    if (n == 0) return TL_OK;
+    std::vector<int> begin(n + 1, 0);
+    for (int k = 0; k < n; ++k) begin[k + 1] = begin[k] + jobs[k].n_out;
+    const int total = begin[n];
+    if (total == 0) return TL_OK;
+    const size_t hdr = (((size_t)(n + 1) * sizeof(int) + 15) / 16) * 16;
+    std::vector<unsigned char> buf(hdr + sizeof(RedJob) * n, 0);
+    std::memcpy(buf.data(), begin.data(), sizeof(int) * (n + 1));
+    std::memcpy(buf.data() + hdr, jobs.data(), sizeof(RedJob) * n);
+    void* d = nullptr;
+    int rc = batch_upload(B, which, buf.data(), buf.size(), &d);
+    if (rc) return rc;
+    const int* d_begin = static_cast<const int*>(d);
+    const RedJob* d_jobs = reinterpret_cast<const RedJob*>(static_cast<unsigned char*>(d) + hdr);
+    k_reduce_batch<<<(total + kRedWarps - 1) / kRedWarps, kRedWarps * 32, 0, B->stream>>>(
+        d_jobs, d_begin, n, total);
+    B->launches += 1;
+    return batch_cuda(B, cudaGetLastError(), "batched reduction");
+}
+
+}  // namespace
+
+int tl_batch_create(void* stream, tl_batch** out) {
+    if (!out) return fail(nullptr, TL_ERR_ARG, "out is null");
+    *out = nullptr;
+    Batch* B = new Batch();
+    B->stream = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&B->device);
+    if (e != cudaSuccess) {
+        delete B;
+        return cuda_check(nullptr, e, "tl_batch_create");
+    }
+    *out = reinterpret_cast<tl_batch*>(B);
+    return TL_OK;
+}
+
+int tl_batch_destroy(tl_batch* b) {
+    if (!b) return TL_ERR_ARG;
+    Batch* B = as_batch(b);
+    cudaStreamSynchronize(B->stream);
+    for (auto& A : B->areas)
+        if (A.d) cudaFree(A.d);
+    for (auto& s : B->ring) {
+        if (s.h) cudaFreeHost(s.h);
+        if (s.ev) cudaEventDestroy(s.ev);
+    }
+    if (B->done) cudaEventDestroy(B->done);
+    delete B;
+    return TL_OK;
+}
+
+int tl_batch_last_error(const tl_batch* b, char* buf, size_t len) {
+    if (!buf || len == 0) return TL_ERR_ARG;
+    const std::string& s = b ? reinterpret_cast<const Batch*>(b)->err : g_create_err;
+    size_t n = std::min(len - 1, s.size());
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+    return TL_OK;
+}
+
+int tl_batch_launch_count(const tl_batch* b, unsigned long long* out) {
+    if (!b || !out) return TL_ERR_ARG;
+    *out = reinterpret_cast<const Batch*>(b)->launches;
+    return TL_OK;
+}
+
+int tl_batch_update_partials(tl_batch* b, tl_instance* const* insts, const tl_op* const* ops,
+                             const int* counts, int n) {
+    if (!b) return fail(nullptr, TL_ERR_ARG, "null batch");
+    Batch* B = as_batch(b);
+    std::vector<Instance*> I;
+    int rc = batch_instances(B, insts, n, &I);
+    if (rc) return rc;
+    if (n > 0 && !counts) return batch_fail(B, TL_ERR_ARG, "counts is null");
+    std::vector<const DevPostOp*> d_ops(n, nullptr);
+    std::vector<int> n_ops(n, 0), n_slots(n, 0);
+    for (int k = 0; k < n; ++k) {
+        if (counts[k] < 0 || (counts[k] > 0 && (!ops || !ops[k])))
+            return batch_fail(B, TL_ERR_ARG, "instance %d: bad op list", k);
+        if (counts[k] == 0) continue;
+        PostPlan plan;
+        if ((rc = plan_post(I[k], ops[k], counts[k], &plan, false))) return batch_from(B, I[k], k, rc);
+        void* d = nullptr;
+        if ((rc = upload(I[k], extra(I[k]).areas[0], plan.dev.data(),
+                         sizeof(DevPostOp) * counts[k], &d)))
+            return batch_from(B, I[k], k, rc);
+        d_ops[k] = static_cast<const DevPostOp*>(d);
+        n_ops[k] = counts[k];
+        n_slots[k] = plan.n_slots;
+    }
+    if ((rc = batch_order_before(B, I))) return rc;
+    if ((rc = nuc_batch_post(B, I.data(), d_ops.data(), n_ops.data(), n_slots.data(), n))) return rc;
+    if ((rc = batch_order_after(B, I))) return rc;
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < counts[k]; ++j) I[k]->buf_written[ops[k][j].dest - I[k]->n_tips] = 1;
+    return TL_OK;
+}
+
+int tl_batch_root_loglik_dev(tl_batch* b, tl_instance* const* insts, const int* roots,
+                             const int* models, int n, double* out_logl_dev) {
+    if (!b) return fail(nullptr, TL_ERR_ARG, "null batch");
+    Batch* B = as_batch(b);
+    std::vector<Instance*> I;
+    int rc = batch_instances(B, insts, n, &I);
+    if (rc) return rc;
+    if (n == 0) return TL_OK;
+    if (!roots || !models || !out_logl_dev) return batch_fail(B, TL_ERR_ARG, "null argument");
+    std::vector<int> kind(n), idx(n);
+    std::vector<double*> part(n);
+    std::vector<RedJob> red(n);
+    for (int k = 0; k < n; ++k) {
+        Instance* x = I[k];
+        const int root = roots[k], model = models[k];
+        if (root < 0 || root >= x->n_bufs)
+            return batch_fail(B, TL_ERR_INDEX, "instance %d: root %d out of range", k, root);
+        if (root >= x->n_tips ? !x->buf_written[root - x->n_tips] : !x->tip_set[root])
+            return batch_fail(B, TL_ERR_STATE, "instance %d: root buffer %d holds no data", k, root);
+        if (model < 0 || model >= x->n_models || !x->models[model].ready)
+            return batch_fail(B, TL_ERR_STATE, "instance %d: model %d not set", k, model);
+        const int n_tiles = nuc_tiles(x);
+        if ((rc = ensure_scratch(x, n_tiles))) return batch_from(B, x, k, rc);
+        kind[k] = kInternal;
+        idx[k] = root - x->n_tips;
+        if (root < x->n_tips) {
+            kind[k] = x->tip_set[root] == 1 ? kTipStates : kTipPartials;
+            idx[k] = root;
+        }
+        part[k] = x->d_red;
+        red[k] = RedJob{x->d_red, nullptr, out_logl_dev + k, n_tiles, 1};
+    }
+    if ((rc = batch_order_before(B, I))) return rc;
+    if ((rc = nuc_batch_root(B, I.data(), kind.data(), idx.data(), models, n, part.data())))
+        return rc;
+    if ((rc = batch_reduce(B, 3, red))) return rc;
+    return batch_order_after(B, I);
+}
+
+int tl_batch_pre_order_gradient_dev(tl_batch* b, tl_instance* const* insts,
+                                    const tl_pre_op* const* ops, const int* counts,
+                                    const int* models, double* const* out_grad_dev,
+                                    const int* n_grad, int n) {
+    if (!b) return fail(nullptr, TL_ERR_ARG, "null batch");
+    Batch* B = as_batch(b);
+    std::vector<Instance*> I;
+    int rc = batch_instances(B, insts, n, &I);
+    if (rc) return rc;
+    if (n == 0) return TL_OK;
+    if (!counts || !models || !out_grad_dev || !n_grad)
+        return batch_fail(B, TL_ERR_ARG, "null argument");
+    std::vector<const DevPreOp*> d_ops(n, nullptr);
+    std::vector<int> n_ops(n, 0), n_slots(n, 0);
+    std::vector<double*> gpart(n);
+    std::vector<RedJob> red;
+    for (int k = 0; k < n; ++k) {
+        Instance* x = I[k];
+        if (counts[k] < 0 || (counts[k] > 0 && (!ops || !ops[k])))
+            return batch_fail(B, TL_ERR_ARG, "instance %d: bad op list", k);
+        if (models[k] < 0 || models[k] >= x->n_models || !x->models[models[k]].ready)
+            return batch_fail(B, TL_ERR_STATE, "instance %d: model %d not set", k, models[k]);
+        if (n_grad[k] < 0) return batch_fail(B, TL_ERR_ARG, "instance %d: n_grad < 0", k);
+        if (n_grad[k] > 0 && !out_grad_dev[k])
+            return batch_fail(B, TL_ERR_ARG, "instance %d: output is null", k);
+        PrePlan plan;
+        if ((rc = plan_pre(x, ops ? ops[k] : nullptr, counts[k], n_grad[k], false, &plan)))
+            return batch_from(B, x, k, rc);
+        const int E = (int)plan.edge_map.size();
+        const int n_tiles = nuc_tiles_main(x);
+        if ((rc = ensure_scratch(x, (size_t)std::max(E, 1) * n_tiles))) return batch_from(B, x, k, rc);
+        void* d = nullptr;
+        if (counts[k] > 0 &&
+            (rc = upload(x, extra(x).areas[1], plan.dev.data(), sizeof(DevPreOp) * counts[k], &d)))
+            return batch_from(B, x, k, rc);
+        d_ops[k] = static_cast<const DevPreOp*>(d);
+        n_ops[k] = counts[k];
+        n_slots[k] = plan.n_slots;
+        gpart[k] = x->d_red;
+        if (n_grad[k] > 0) {
+            // out[g] = row inv[g] of the gradient partials, 0 for slots no op names
+            std::vector<int> inv(n_grad[k], -1);
+            for (int e = 0; e < E; ++e) inv[plan.edge_map[e]] = e;
+            void* d_inv = nullptr;
+            if ((rc = upload(x, extra(x).areas[5], inv.data(), sizeof(int) * inv.size(), &d_inv)))
+                return batch_from(B, x, k, rc);
+            red.push_back(RedJob{x->d_red, static_cast<const int*>(d_inv), out_grad_dev[k], n_tiles,
+                                 n_grad[k]});
+        }
+    }
+    if ((rc = batch_order_before(B, I))) return rc;
+    if ((rc = nuc_batch_pre(B, I.data(), d_ops.data(), n_ops.data(), n_slots.data(), models,
+                            gpart.data(), n)))
+        return rc;
+    if ((rc = batch_reduce(B, 4, red))) return rc;
+    return batch_order_after(B, I);
+}
+
 }  // extern "C"
 
 namespace tl {
 int upload_bytes(Instance* I, void* dst, const void* src, size_t bytes) {
     return h2d(I, dst, src, bytes);
+}
+
+int batch_fail(Batch* B, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (B) B->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+int batch_cuda(Batch* B, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return TL_OK;
+    return batch_fail(B, e == cudaErrorMemoryAllocation ? TL_ERR_OOM : TL_ERR_CUDA, "%s: %s (%s)",
+                      what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+int batch_upload(Batch* B, int which, const void* src, size_t bytes, void** dptr) {
+    Batch::Area& A = B->areas[which];
+    cudaError_t e = cudaSuccess;
+    if (A.cap < bytes) {
+        if (A.d) {
+            cudaStreamSynchronize(B->stream);
+            cudaFree(A.d);
+            A.d = nullptr;
+            A.cap = 0;
+        }
+        const size_t cap = std::max<size_t>(bytes * 2, 4096);
+        e = cudaMalloc(&A.d, cap);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            A.d = nullptr;
+            return batch_cuda(B, e, "batch table");
+        }
+        A.cap = cap;
+    }
+    Batch::Slot& s = B->ring[B->ring_next];
+    B->ring_next = (B->ring_next + 1) % Batch::kSlots;
+    if (s.ev) e = cudaEventSynchronize(s.ev);
+    else e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return batch_cuda(B, e, "staging event");
+    if (s.cap < bytes) {
+        if (s.h) cudaFreeHost(s.h);
+        s.cap = std::max<size_t>(bytes, 64 * 1024);
+        e = cudaHostAlloc(&s.h, s.cap, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            s.h = nullptr;
+            s.cap = 0;
+            return batch_cuda(B, e, "pinned staging");
+        }
+    }
+    std::memcpy(s.h, src, bytes);
+    e = cudaMemcpyAsync(A.d, s.h, bytes, cudaMemcpyHostToDevice, B->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s.ev, B->stream);
+    *dptr = A.d;
+    return batch_cuda(B, e, "batch table copy");
 }
 }  // namespace tl

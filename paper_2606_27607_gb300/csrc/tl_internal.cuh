@@ -85,6 +85,44 @@ struct NucArgs {
     T rates[kMaxCat];
 };
 
+// One instance's share of a batched four-state launch: its kernel
+// arguments, op list and outputs, and the first tile of the launch's global
+// tile range that belongs to it (tiles are handed out in global order).
+template <typename T>
+struct __align__(16) BatchJob {
+    NucArgs<T> a;         // a.n_tiles: this job's tiles
+    const void* ops;      // DevPostOp or DevPreOp list
+    const T* piw;         // pre-order: pi and Q of the job's model (working precision)
+    const T* Qw;
+    double* gpart;        // pre-order: [edge][a.n_tiles] gradient partials
+    const double* pi;     // root: pi (FP64)
+    double* part;         // root: [a.n_tiles] partial sums
+    int* err;             // root: the instance's numeric-error flag
+    int n_ops;
+    int root_kind, root;  // root: the buffer and its kind
+    int pad;
+};
+
+// The job table of a batched launch: jobs[j] owns global tiles
+// [tile_begin[j], tile_begin[j + 1]); warps claim tiles from *counter.
+template <typename T>
+struct BatchRef {
+    const BatchJob<T>* jobs;
+    const int* tile_begin;
+    int* counter;
+    int n_jobs;
+};
+
+// One job of a batched fixed-order reduction: out[g] = sum of the n_in
+// doubles of row inv[g] of `in` (row g when inv is null; 0 when inv[g] < 0),
+// for g < n_out.
+struct __align__(16) RedJob {
+    const double* in;
+    const int* inv;
+    double* out;
+    int n_in, n_out;
+};
+
 struct ModelDev {
     double* Q = nullptr;      // [Spad][Spad]
     double* pi = nullptr;     // [Spad]
@@ -153,6 +191,34 @@ struct Instance {
     std::string err;
 };
 
+// A batch context: a stream, device areas for job tables and a pinned
+// staging ring, shared by the batched calls (tl_api.cu).
+struct Batch {
+    struct Area {
+        void* d = nullptr;
+        size_t cap = 0;
+    };
+    struct Slot {
+        void* h = nullptr;
+        size_t cap = 0;
+        cudaEvent_t ev = nullptr;
+    };
+    static constexpr int kAreas = 8, kSlots = 8;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    Area areas[kAreas];
+    Slot ring[kSlots];
+    int ring_next = 0;
+    cudaEvent_t done = nullptr;  // instance streams wait on this after a batched call
+    unsigned long long launches = 0;
+    std::string err;
+};
+// Copy bytes to device area `which` of the batch (grown as needed) through
+// the pinned ring, on the batch stream; *dptr receives the area.
+int batch_upload(Batch* B, int which, const void* src, size_t bytes, void** dptr);
+int batch_fail(Batch* B, int code, const char* fmt, ...);
+int batch_cuda(Batch* B, cudaError_t e, const char* what);
+
 // ---- launchers (one translation unit each) --------------------------------
 // tl_model.cu
 int launch_build_model(Instance* I, int m, int kind, const double* d_params, int n_params,
@@ -177,6 +243,16 @@ int launch_root4(Instance* I, int root_kind, int root, int model, double* d_site
 int launch_pre4(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, int model,
                 double* d_gpart, int dgen);
 int launch_edge4(Instance* I, const DevEdge* d_edges, int n_edges, int model, double* d_gpart);
+
+// batched four-state launches over several instances of one precision and
+// category count (tl_batch.cu builds the job tables)
+struct Batch;
+int nuc_batch_post(Batch* B, Instance* const* I, const DevPostOp* const* d_ops, const int* n_ops,
+                   const int* n_slots, int n);
+int nuc_batch_root(Batch* B, Instance* const* I, const int* kind, const int* root,
+                   const int* model, int n, double* const* d_part);
+int nuc_batch_pre(Batch* B, Instance* const* I, const DevPreOp* const* d_ops, const int* n_ops,
+                  const int* n_slots, const int* model, double* const* d_gpart, int n);
 
 // tl_generic.cu (FP64, any S)
 int launch_post_generic(Instance* I, const tl_op* h_ops, int n_ops);

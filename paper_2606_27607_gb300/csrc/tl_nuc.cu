@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <cstring>
+#include <vector>
 
 #include "tl_internal.cuh"
 
@@ -132,6 +134,48 @@ __device__ __forceinline__ double warp_sum(double v) {
 __device__ __forceinline__ int tip_col(int8_t s) { return (s >= 0 && s < 4) ? (int)s : 4; }
 
 // ---------------------------------------------------------------------------
+// batched launches: one launch walks the op lists of several instances.
+// Warps claim global tiles from a counter (largest jobs first, so the long
+// walks start in the first wave), find the owning job by binary search and
+// stage its arguments in a warp-private shared-memory copy. A job's tiles
+// are computed exactly as in its own launch, so results do not depend on
+// what else is in the batch.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ bool batch_claim(const BatchRef<T>& br, int total, BatchJob<T>* stage,
+                                            int& cur, int& tile, int lane) {
+    int g = 0;
+    if (lane == 0) g = atomicAdd(br.counter, 1);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= total) return false;
+    int lo = 0, hi = br.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(br.tile_begin + mid) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    if (lo != cur) {
+        __syncwarp();  // every lane is done with the previous job's copy
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(br.jobs + lo);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(stage);
+        for (int i = lane; i < (int)(sizeof(BatchJob<T>) / 8); i += 32) dst[i] = __ldg(src + i);
+        __syncwarp();
+        cur = lo;
+    }
+    tile = g - __ldg(br.tile_begin + lo);
+    return true;
+}
+
+// The arguments a tile is computed with: the kernel parameter, or the
+// staged job.
+template <bool BATCH, typename T>
+__device__ __forceinline__ const NucArgs<T>& pick_args(const NucArgs<T>& param,
+                                                       const BatchJob<T>* stage) {
+    if constexpr (BATCH) return stage->a;
+    else return param;
+}
+
+// ---------------------------------------------------------------------------
 // post-order
 // ---------------------------------------------------------------------------
 // Loads that feed op k are issued while op k-kAhead..k-1 compute: tip states
@@ -209,35 +253,51 @@ __host__ __device__ constexpr size_t pipe_bytes(int R) {
 // warp tile has 32 / LPP patterns. Fewer lanes per pattern amortise the
 // per-op work (op fetch, addressing, control) over more patterns; more lanes
 // lower the registers each lane needs.
-template <typename T, int LPP, int CPL, int NR>
+// BATCH: `a_` gives the shared-memory layout (the largest slot count of the
+// jobs, their common R) and the total tile count; each tile's arguments and
+// ops come from its job in `br`.
+template <typename T, int LPP, int CPL, int NR, bool BATCH>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_post4(const DevPostOp* __restrict__ ops, int n_ops, NucArgs<T> a) {
+k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ NucArgs<T> a_,
+        const BatchRef<T> br) {
     constexpr int TP = 32 / LPP;
     // NR > 0: the category count is a compile-time constant
     constexpr bool kFull = NR > 0 && LPP * CPL == NR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = lane % LPP, pp = lane / LPP;
-    const int R = NR > 0 ? NR : a.R;
+    const int R = NR > 0 ? NR : a_.R;
     const int cs = R * 4;  // matrix column stride (all categories of a column)
     bool act[CPL];
 #pragma unroll
     for (int j = 0; j < CPL; ++j) act[j] = kFull || (r0 + j * LPP < R);
-    V4<T>* slots = reinterpret_cast<V4<T>*>(smem_raw) + (size_t)warp * a.n_slots * CPL * 32;
+    V4<T>* slots = reinterpret_cast<V4<T>*>(smem_raw) + (size_t)warp * a_.n_slots * CPL * 32;
     int* sexp = reinterpret_cast<int*>(reinterpret_cast<V4<T>*>(smem_raw) +
-                                       (size_t)kWarpsPerBlock * a.n_slots * CPL * 32) +
-                warp * a.n_slots * 32;
+                                       (size_t)kWarpsPerBlock * a_.n_slots * CPL * 32) +
+                warp * a_.n_slots * 32;
     unsigned char* pipe_base = reinterpret_cast<unsigned char*>(
         reinterpret_cast<int*>(reinterpret_cast<V4<T>*>(smem_raw) +
-                               (size_t)kWarpsPerBlock * a.n_slots * CPL * 32) +
-        kWarpsPerBlock * a.n_slots * 32);
+                               (size_t)kWarpsPerBlock * a_.n_slots * CPL * 32) +
+        kWarpsPerBlock * a_.n_slots * 32);
     WarpPipe<DevPostOp, T, 2> pipe;
     pipe.obuf = reinterpret_cast<DevPostOp*>(pipe_base + (size_t)warp * pipe_bytes<DevPostOp, T, 2>(R));
     pipe.mbuf = reinterpret_cast<T*>(pipe.obuf + 3);
     pipe.matf = kColStride * 4 * R;
+    BatchJob<T>* stage = reinterpret_cast<BatchJob<T>*>(
+        pipe_base + (size_t)kWarpsPerBlock * pipe_bytes<DevPostOp, T, 2>(R)) + warp;
+    const NucArgs<T>& a = pick_args<BATCH>(a_, stage);
     const V4<T> zero = {T(0), T(0), T(0), T(0)};
     const int nw = gridDim.x * kWarpsPerBlock;
-    for (int tile = blockIdx.x * kWarpsPerBlock + warp; tile < a.n_tiles; tile += nw) {
+    const DevPostOp* ops = ops_;
+    int n_ops = n_ops_;
+    int cur = -1;
+    for (int next = blockIdx.x * kWarpsPerBlock + warp; BATCH || next < a_.n_tiles; next += nw) {
+        int tile = next;
+        if constexpr (BATCH) {
+            if (!batch_claim(br, a_.n_tiles, stage, cur, tile, lane)) break;
+            ops = static_cast<const DevPostOp*>(stage->ops);
+            n_ops = stage->n_ops;
+        }
         const int p = tile * TP + pp;
         const size_t off0 = ((size_t)r0 * a.Ppad + p) * 4;       // category r0
         const size_t offj = (size_t)LPP * a.Ppad * 4;            // next category of this lane
@@ -380,16 +440,35 @@ __device__ __forceinline__ X tile_sum(X v) {
 // ---------------------------------------------------------------------------
 // root log-likelihood: per-tile partial sums of w_p l_p
 // ---------------------------------------------------------------------------
-template <typename T, int LPP>
+template <typename T, int LPP, bool BATCH>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-k_root4(int kind, int root, NucArgs<T> a, const double* __restrict__ pi,
-        double* __restrict__ site, double* __restrict__ part, int* __restrict__ err) {
+k_root4(int kind_, int root_, const __grid_constant__ NucArgs<T> a_, const double* __restrict__ pi_,
+        double* __restrict__ site_, double* __restrict__ part_, int* __restrict__ err_,
+        const BatchRef<T> br) {
     constexpr int TP = 32 / LPP;
+    __shared__ BatchJob<T> stages[BATCH ? kWarpsPerBlock : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = lane % LPP, pp = lane / LPP;
-    const bool ract = r < a.R;
+    BatchJob<T>* stage = stages + (BATCH ? warp : 0);
+    const NucArgs<T>& a = pick_args<BATCH>(a_, stage);
+    const bool ract = r < a_.R;
     const int nw = gridDim.x * kWarpsPerBlock;
-    for (int tile = blockIdx.x * kWarpsPerBlock + warp; tile < a.n_tiles; tile += nw) {
+    int kind = kind_, root = root_;
+    const double* pi = pi_;
+    double *site = site_, *part = part_;
+    int* err = err_;
+    int cur = -1;
+    for (int next = blockIdx.x * kWarpsPerBlock + warp; BATCH || next < a_.n_tiles; next += nw) {
+        int tile = next;
+        if constexpr (BATCH) {
+            if (!batch_claim(br, a_.n_tiles, stage, cur, tile, lane)) break;
+            kind = stage->root_kind;
+            root = stage->root;
+            pi = stage->pi;
+            site = nullptr;
+            part = stage->part;
+            err = stage->err;
+        }
         const int p = tile * TP + pp;
         double Lr = 0.0;
         int cum = 0;
@@ -428,40 +507,64 @@ k_root4(int kind, int root, NucArgs<T> a, const double* __restrict__ pi,
 #ifndef TL_PRE_MIN_BLOCKS
 #define TL_PRE_MIN_BLOCKS 1
 #endif
-template <typename T, int LPP, int CPL, int NR>
+template <typename T, int LPP, int CPL, int NR, bool BATCH>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, TL_PRE_MIN_BLOCKS)
-k_pre4(const DevPreOp* __restrict__ ops, int n_ops, NucArgs<T> a, const T* __restrict__ piw,
-       const T* __restrict__ Qw, double* __restrict__ gpart) {
+k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ NucArgs<T> a_,
+       const T* __restrict__ piw_, const T* __restrict__ Qw_, double* __restrict__ gpart_,
+       const BatchRef<T> br) {
     constexpr int TP = 32 / LPP;
     constexpr bool kFull = NR > 0 && LPP * CPL == NR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = lane % LPP, pp = lane / LPP;
-    const int R = NR > 0 ? NR : a.R;
+    const int R = NR > 0 ? NR : a_.R;
     const int cs = R * 4;  // matrix column stride (all categories of a column)
-    bool act[CPL];
-    T wr[CPL], wrr[CPL];
-#pragma unroll
-    for (int j = 0; j < CPL; ++j) {
-        act[j] = kFull || (r0 + j * LPP < R);
-        wr[j] = act[j] ? a.catw[r0 + j * LPP] : T(0);
-        wrr[j] = act[j] ? a.catw[r0 + j * LPP] * a.rates[r0 + j * LPP] : T(0);
-    }
-    // Q rows: an internal child's derivative term is rho q_c . (Q p_c), with
-    // q_c = P_c^T u_c before rescaling (dP/dt = rho Q P and Q, P commute), so
-    // only tip children need the dP columns
-    const V4<T> Q0 = ldg4(Qw), Q1 = ldg4(Qw + 4), Q2 = ldg4(Qw + 8), Q3 = ldg4(Qw + 12);
-    V4<T>* slots = reinterpret_cast<V4<T>*>(smem_raw) + (size_t)warp * a.n_slots * CPL * 32;
+    V4<T>* slots = reinterpret_cast<V4<T>*>(smem_raw) + (size_t)warp * a_.n_slots * CPL * 32;
     unsigned char* pipe_base = reinterpret_cast<unsigned char*>(
-        reinterpret_cast<V4<T>*>(smem_raw) + (size_t)kWarpsPerBlock * a.n_slots * CPL * 32);
+        reinterpret_cast<V4<T>*>(smem_raw) + (size_t)kWarpsPerBlock * a_.n_slots * CPL * 32);
     WarpPipe<DevPreOp, T, 4> pipe;
     pipe.obuf = reinterpret_cast<DevPreOp*>(pipe_base + (size_t)warp * pipe_bytes<DevPreOp, T, 4>(R));
     pipe.mbuf = reinterpret_cast<T*>(pipe.obuf + 3);
     pipe.matf = kColStride * 4 * R;
-    const V4<T> piv = ldg4(piw);
+    BatchJob<T>* stage = reinterpret_cast<BatchJob<T>*>(
+        pipe_base + (size_t)kWarpsPerBlock * pipe_bytes<DevPreOp, T, 4>(R)) + warp;
+    const NucArgs<T>& a = pick_args<BATCH>(a_, stage);
+    bool act[CPL];
+    T wr[CPL], wrr[CPL];
+    // Q rows: an internal child's derivative term is rho q_c . (Q p_c), with
+    // q_c = P_c^T u_c before rescaling (dP/dt = rho Q P and Q, P commute), so
+    // only tip children need the dP columns
+    V4<T> Q0, Q1, Q2, Q3, piv;
+    auto job_constants = [&](const NucArgs<T>& aj, const T* piw, const T* Qw) {
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            act[j] = kFull || (r0 + j * LPP < R);
+            wr[j] = act[j] ? aj.catw[r0 + j * LPP] : T(0);
+            wrr[j] = act[j] ? aj.catw[r0 + j * LPP] * aj.rates[r0 + j * LPP] : T(0);
+        }
+        Q0 = ldg4(Qw);
+        Q1 = ldg4(Qw + 4);
+        Q2 = ldg4(Qw + 8);
+        Q3 = ldg4(Qw + 12);
+        piv = ldg4(piw);
+    };
+    if constexpr (!BATCH) job_constants(a_, piw_, Qw_);
     const V4<T> zero = {T(0), T(0), T(0), T(0)};
     const int nw = gridDim.x * kWarpsPerBlock;
-    for (int tile = blockIdx.x * kWarpsPerBlock + warp; tile < a.n_tiles; tile += nw) {
+    const DevPreOp* ops = ops_;
+    int n_ops = n_ops_;
+    double* gpart = gpart_;
+    int cur = -1;
+    for (int next = blockIdx.x * kWarpsPerBlock + warp; BATCH || next < a_.n_tiles; next += nw) {
+        int tile = next;
+        if constexpr (BATCH) {
+            const int was = cur;
+            if (!batch_claim(br, a_.n_tiles, stage, cur, tile, lane)) break;
+            ops = static_cast<const DevPreOp*>(stage->ops);
+            n_ops = stage->n_ops;
+            gpart = stage->gpart;
+            if (cur != was) job_constants(stage->a, stage->piw, stage->Qw);
+        }
         const int p = tile * TP + pp;
         const size_t off0 = ((size_t)r0 * a.Ppad + p) * 4;
         const size_t offj = (size_t)LPP * a.Ppad * 4;
@@ -806,12 +909,13 @@ template <typename T, int LPP, int CPL, int NR>
 static void post4_t(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots) {
     const size_t smem = (size_t)kWarpsPerBlock *
                         (n_slots * nuc_smem_per_slot(I) + pipe_bytes<DevPostOp, T, 2>(I->R));
-    cudaFuncSetAttribute(k_post4<T, LPP, CPL, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    cudaFuncSetAttribute(k_post4<T, LPP, CPL, NR, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     NucArgs<T> a = make_args<T>(I, n_slots);
     a.n_tiles = nuc_tiles_for(I, LPP);
-    const int grid = grid_for(I, k_post4<T, LPP, CPL, NR>, smem, a.n_tiles);
-    k_post4<T, LPP, CPL, NR><<<grid, kWarpsPerBlock * 32, smem, I->stream>>>(d_ops, n_ops, a);
+    const int grid = grid_for(I, k_post4<T, LPP, CPL, NR, false>, smem, a.n_tiles);
+    k_post4<T, LPP, CPL, NR, false><<<grid, kWarpsPerBlock * 32, smem, I->stream>>>(
+        d_ops, n_ops, a, BatchRef<T>{});
 }
 
 int launch_post4(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots) {
@@ -823,9 +927,9 @@ int launch_post4(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots) {
 template <typename T, int LPP>
 static void root4_t(Instance* I, int kind, int root, const double* pi, double* d_site,
                     double* d_part) {
-    const int grid = grid_for(I, k_root4<T, LPP>, 0, nuc_tiles(I));
-    k_root4<T, LPP><<<grid, kWarpsPerBlock * 32, 0, I->stream>>>(
-        kind, root, make_args<T>(I, 0), pi, d_site, d_part, I->d_err + 1);
+    const int grid = grid_for(I, k_root4<T, LPP, false>, 0, nuc_tiles(I));
+    k_root4<T, LPP, false><<<grid, kWarpsPerBlock * 32, 0, I->stream>>>(
+        kind, root, make_args<T>(I, 0), pi, d_site, d_part, I->d_err + 1, BatchRef<T>{});
 }
 
 int launch_root4(Instance* I, int root_kind, int root, int model, double* d_site,
@@ -840,14 +944,15 @@ static void pre4_t(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, c
                    const void* Qw, double* d_gpart, int dgen) {
     const size_t smem = (size_t)kWarpsPerBlock * ((size_t)n_slots * CPL * 32 * 4 * sizeof(T) +
                                                   pipe_bytes<DevPreOp, T, 4>(I->R));
-    cudaFuncSetAttribute(k_pre4<T, LPP, CPL, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    cudaFuncSetAttribute(k_pre4<T, LPP, CPL, NR, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     NucArgs<T> a = make_args<T>(I, n_slots);
     a.n_tiles = nuc_tiles_for(I, LPP);
     a.dgen = dgen;
-    const int grid = grid_for(I, k_pre4<T, LPP, CPL, NR>, smem, a.n_tiles);
-    k_pre4<T, LPP, CPL, NR><<<grid, kWarpsPerBlock * 32, smem, I->stream>>>(
-        d_ops, n_ops, a, reinterpret_cast<const T*>(piw), reinterpret_cast<const T*>(Qw), d_gpart);
+    const int grid = grid_for(I, k_pre4<T, LPP, CPL, NR, false>, smem, a.n_tiles);
+    k_pre4<T, LPP, CPL, NR, false><<<grid, kWarpsPerBlock * 32, smem, I->stream>>>(
+        d_ops, n_ops, a, reinterpret_cast<const T*>(piw), reinterpret_cast<const T*>(Qw), d_gpart,
+        BatchRef<T>{});
 }
 
 int launch_pre4(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, int model,
@@ -870,6 +975,193 @@ int launch_edge4(Instance* I, const DevEdge* d_edges, int n_edges, int model, do
     TL_NUC_DISPATCH(I, edge4_t, I, d_edges, n_edges, I->models[model].Qw, d_gpart);
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "edge-derivative kernel");
+}
+
+
+// ---------------------------------------------------------------------------
+// batched launchers: one job table upload and one launch for n instances of
+// one precision and category count
+// ---------------------------------------------------------------------------
+// Table layout in the batch area: [counter, pad x3][tile_begin: n + 1 ints,
+// padded to 16 bytes][jobs].
+template <typename T>
+static int upload_table(Batch* B, int which, const std::vector<BatchJob<T>>& jobs,
+                        const std::vector<int>& begin, BatchRef<T>* br) {
+    const int n = (int)jobs.size();
+    const size_t hdr = 16 + (((size_t)(n + 1) * sizeof(int) + 15) / 16) * 16;
+    std::vector<unsigned char> buf(hdr + (size_t)n * sizeof(BatchJob<T>), 0);
+    std::memcpy(buf.data() + 16, begin.data(), sizeof(int) * (n + 1));
+    std::memcpy(buf.data() + hdr, jobs.data(), sizeof(BatchJob<T>) * n);
+    void* d = nullptr;
+    int rc = batch_upload(B, which, buf.data(), buf.size(), &d);
+    if (rc) return rc;
+    unsigned char* base = static_cast<unsigned char*>(d);
+    br->counter = reinterpret_cast<int*>(base);
+    br->tile_begin = reinterpret_cast<const int*>(base + 16);
+    br->jobs = reinterpret_cast<const BatchJob<T>*>(base + hdr);
+    br->n_jobs = n;
+    return TL_OK;
+}
+
+// Jobs in order of decreasing op count (stable), so the longest tile walks
+// are claimed first; jobs without ops or tiles are left out.
+static std::vector<int> by_work(const int* n_ops, int n) {
+    std::vector<int> order;
+    for (int k = 0; k < n; ++k)
+        if (n_ops[k] > 0) order.push_back(k);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return n_ops[x] > n_ops[y]; });
+    return order;
+}
+
+template <typename T, int LPP, int CPL, int NR>
+static int post4_batch_t(Batch* B, Instance* const* I, const DevPostOp* const* d_ops,
+                         const int* n_ops, const int* n_slots, int n) {
+    const std::vector<int> order = by_work(n_ops, n);
+    if (order.empty()) return TL_OK;
+    std::vector<BatchJob<T>> jobs;
+    std::vector<int> begin(1, 0);
+    int max_slots = 0;
+    long long total = 0;
+    for (int k : order) {
+        BatchJob<T> j{};
+        j.a = make_args<T>(I[k], n_slots[k]);
+        j.a.n_tiles = nuc_tiles_for(I[k], LPP);
+        j.ops = d_ops[k];
+        j.n_ops = n_ops[k];
+        jobs.push_back(j);
+        total += j.a.n_tiles;
+        if (total > (1LL << 30)) return batch_fail(B, TL_ERR_UNSUPPORTED, "batch too large");
+        begin.push_back((int)total);
+        max_slots = std::max(max_slots, n_slots[k]);
+    }
+    BatchRef<T> br;
+    int rc = upload_table(B, 0, jobs, begin, &br);
+    if (rc) return rc;
+    Instance* I0 = I[order[0]];
+    const size_t smem = (size_t)kWarpsPerBlock *
+                        (max_slots * nuc_smem_per_slot(I0) + pipe_bytes<DevPostOp, T, 2>(I0->R) +
+                         sizeof(BatchJob<T>));
+    cudaFuncSetAttribute(k_post4<T, LPP, CPL, NR, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    NucArgs<T> layout = make_args<T>(I0, max_slots);
+    layout.n_tiles = (int)total;
+    const int grid = grid_for(I0, k_post4<T, LPP, CPL, NR, true>, smem, (int)total);
+    k_post4<T, LPP, CPL, NR, true><<<grid, kWarpsPerBlock * 32, smem, B->stream>>>(
+        nullptr, 0, layout, br);
+    B->launches += 1;
+    return batch_cuda(B, cudaGetLastError(), "batched post-order kernel");
+}
+
+#define TL_BATCH_DISPATCH(I0, FN, ...)                                          \
+    do {                                                                        \
+        if ((I0)->prec == kF32) TL_MAIN_DISPATCH_T(float, I0, return FN, __VA_ARGS__); \
+        else TL_MAIN_DISPATCH_T(double, I0, return FN, __VA_ARGS__);           \
+    } while (0)
+
+int nuc_batch_post(Batch* B, Instance* const* I, const DevPostOp* const* d_ops, const int* n_ops,
+                   const int* n_slots, int n) {
+    if (n <= 0) return TL_OK;
+    TL_BATCH_DISPATCH(I[0], post4_batch_t, B, I, d_ops, n_ops, n_slots, n);
+    return TL_OK;
+}
+
+template <typename T, int LPP>
+static int root4_batch_t(Batch* B, Instance* const* I, const int* kind, const int* root,
+                         const int* model, int n, double* const* d_part) {
+    std::vector<BatchJob<T>> jobs;
+    std::vector<int> begin(1, 0);
+    long long total = 0;
+    for (int k = 0; k < n; ++k) {
+        BatchJob<T> j{};
+        j.a = make_args<T>(I[k], 0);
+        j.a.n_tiles = nuc_tiles_for(I[k], LPP);
+        j.root_kind = kind[k];
+        j.root = root[k];
+        j.pi = I[k]->models[model[k]].pi;
+        j.part = d_part[k];
+        j.err = I[k]->d_err + 1;
+        jobs.push_back(j);
+        total += j.a.n_tiles;
+        if (total > (1LL << 30)) return batch_fail(B, TL_ERR_UNSUPPORTED, "batch too large");
+        begin.push_back((int)total);
+    }
+    BatchRef<T> br;
+    int rc = upload_table(B, 1, jobs, begin, &br);
+    if (rc) return rc;
+    NucArgs<T> layout = make_args<T>(I[0], 0);
+    layout.n_tiles = (int)total;
+    const int grid = grid_for(I[0], k_root4<T, LPP, true>, 0, (int)total);
+    k_root4<T, LPP, true><<<grid, kWarpsPerBlock * 32, 0, B->stream>>>(
+        0, 0, layout, nullptr, nullptr, nullptr, nullptr, br);
+    B->launches += 1;
+    return batch_cuda(B, cudaGetLastError(), "batched root kernel");
+}
+
+int nuc_batch_root(Batch* B, Instance* const* I, const int* kind, const int* root,
+                   const int* model, int n, double* const* d_part) {
+    if (n <= 0) return TL_OK;
+    const int lpp = nuc_lanes(I[0]);
+    if (I[0]->prec == kF32) {
+        if (lpp == 1) return root4_batch_t<float, 1>(B, I, kind, root, model, n, d_part);
+        if (lpp == 2) return root4_batch_t<float, 2>(B, I, kind, root, model, n, d_part);
+        if (lpp == 4) return root4_batch_t<float, 4>(B, I, kind, root, model, n, d_part);
+        return root4_batch_t<float, 8>(B, I, kind, root, model, n, d_part);
+    }
+    if (lpp == 1) return root4_batch_t<double, 1>(B, I, kind, root, model, n, d_part);
+    if (lpp == 2) return root4_batch_t<double, 2>(B, I, kind, root, model, n, d_part);
+    if (lpp == 4) return root4_batch_t<double, 4>(B, I, kind, root, model, n, d_part);
+    return root4_batch_t<double, 8>(B, I, kind, root, model, n, d_part);
+}
+
+template <typename T, int LPP, int CPL, int NR>
+static int pre4_batch_t(Batch* B, Instance* const* I, const DevPreOp* const* d_ops,
+                        const int* n_ops, const int* n_slots, const int* model,
+                        double* const* d_gpart, int n) {
+    const std::vector<int> order = by_work(n_ops, n);
+    if (order.empty()) return TL_OK;
+    std::vector<BatchJob<T>> jobs;
+    std::vector<int> begin(1, 0);
+    int max_slots = 0;
+    long long total = 0;
+    for (int k : order) {
+        BatchJob<T> j{};
+        j.a = make_args<T>(I[k], n_slots[k]);
+        j.a.n_tiles = nuc_tiles_for(I[k], LPP);
+        j.ops = d_ops[k];
+        j.n_ops = n_ops[k];
+        j.piw = reinterpret_cast<const T*>(I[k]->models[model[k]].piw);
+        j.Qw = reinterpret_cast<const T*>(I[k]->models[model[k]].Qw);
+        j.gpart = d_gpart[k];
+        jobs.push_back(j);
+        total += j.a.n_tiles;
+        if (total > (1LL << 30)) return batch_fail(B, TL_ERR_UNSUPPORTED, "batch too large");
+        begin.push_back((int)total);
+        max_slots = std::max(max_slots, n_slots[k]);
+    }
+    BatchRef<T> br;
+    int rc = upload_table(B, 2, jobs, begin, &br);
+    if (rc) return rc;
+    Instance* I0 = I[order[0]];
+    const size_t smem = (size_t)kWarpsPerBlock *
+                        ((size_t)max_slots * CPL * 32 * 4 * sizeof(T) +
+                         pipe_bytes<DevPreOp, T, 4>(I0->R) + sizeof(BatchJob<T>));
+    cudaFuncSetAttribute(k_pre4<T, LPP, CPL, NR, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    NucArgs<T> layout = make_args<T>(I0, max_slots);
+    layout.n_tiles = (int)total;
+    const int grid = grid_for(I0, k_pre4<T, LPP, CPL, NR, true>, smem, (int)total);
+    k_pre4<T, LPP, CPL, NR, true><<<grid, kWarpsPerBlock * 32, smem, B->stream>>>(
+        nullptr, 0, layout, nullptr, nullptr, nullptr, br);
+    B->launches += 1;
+    return batch_cuda(B, cudaGetLastError(), "batched pre-order kernel");
+}
+
+int nuc_batch_pre(Batch* B, Instance* const* I, const DevPreOp* const* d_ops, const int* n_ops,
+                  const int* n_slots, const int* model, double* const* d_gpart, int n) {
+    if (n <= 0) return TL_OK;
+    TL_BATCH_DISPATCH(I[0], pre4_batch_t, B, I, d_ops, n_ops, n_slots, model, d_gpart, n);
+    return TL_OK;
 }
 
 }  // namespace tl
