@@ -52,6 +52,14 @@ def parse():
     ap.add_argument("--codon-taxa", type=int, default=0)
     ap.add_argument("--codon-patterns", type=int, default=0)
     ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--serving", action="store_true",
+                    help="continuous-batching serving run instead of the step benchmark")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--chains", type=int, default=128)
+    ap.add_argument("--loads", default="0.5,0.8,1.2",
+                    help="offered loads as fractions of the measured capacity")
+    ap.add_argument("--baseline-seconds", type=float, default=60.0,
+                    help="time budget of the one-at-a-time FP64 baseline")
     return ap.parse_args()
 
 
@@ -314,8 +322,130 @@ def traffic_for(kernel: str, per_launch_units: float) -> float | None:
 # the GPU arm
 # ---------------------------------------------------------------------------
 
+# ---------------------------------------------------------------------------
+# serving: continuous batching over many chains
+# ---------------------------------------------------------------------------
+
+def _pct(x, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(x), q)) if len(x) else None
+
+
+def serving_line(args) -> dict:
+    """Poisson arrivals from many chains (taxa 16-1,024 and patterns
+    100-200,000 log-uniform, 30% GY94 codon, half with gradients) through
+    the continuous-batching server: capacity from a closed-loop pass, then
+    p50/p99 latency at each offered load; next to the same requests served
+    one at a time in FP64 (no batching) within a time budget."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2606_27607_gb300 import TreeLikelihood, build
+    from paper_2606_27607_gb300.serve import Server, run_open_loop
+    build.build()
+    torch.cuda.set_device(0)
+    t0 = time.perf_counter()
+    chains, reqs, gaps = synth.serving_stream(args.requests, args.chains)
+    t_gen = time.perf_counter() - t0
+    work = [(chains[r.chain].tree.n_tips - 1) * chains[r.chain].n_patterns for r in reqs]
+    server = Server()
+    for w in chains:
+        server.add_chain(w)
+    resident = server.preload()
+    clocks = Clocks(not args.no_clocks, device_id_for_smi())
+
+    def summarise(futs, span, offered=None):
+        ok = [i for i, f in enumerate(futs) if f.exception() is None]
+        lat = [futs[i].result().latency for i in ok]
+        gsz = [futs[i].result().group_size for i in ok]
+        return {"offered_req_per_s": offered, "completed": len(ok),
+                "rejected": len(futs) - len(ok), "seconds": span,
+                "req_per_s": len(ok) / span,
+                "pattern_node_per_s": sum(work[i] for i in ok) / span,
+                "p50_s": _pct(lat, 50), "p99_s": _pct(lat, 99), "max_s": max(lat) if lat else None,
+                "mean_group": float(np.mean(gsz)) if gsz else None}
+
+    # warm-up (first launches, pinned staging), then capacity: every request
+    # present at time 0
+    warm = [server.submit(r) for r in reqs[:32]]
+    server.drain()
+    del warm
+    t1 = time.perf_counter()
+    futs, span = run_open_loop(server, reqs, np.zeros(len(reqs)))
+    cap = summarise(futs, span)
+    capacity = cap["req_per_s"]
+    loads = []
+    for f in [float(x) for x in args.loads.split(",") if x]:
+        arrivals = np.cumsum(gaps) / (f * capacity)
+        futs, span = run_open_loop(server, reqs, arrivals)
+        loads.append(dict(load=f, **summarise(futs, span, f * capacity)))
+    t_serve = time.perf_counter() - t1
+    clk = clocks.stop()
+    stats = dict(server.stats)
+    budget_gb = server.budget / 1e9
+    n_codon = sum(chains[r.chain].n_states == 61 for r in reqs)
+    server.close()
+    del server
+    torch.cuda.empty_cache()
+
+    # one request at a time, FP64, no batching (codon through the FP64
+    # generic path), in arrival order until the time budget is spent
+    base_lat, base_work = [], 0
+    cache: dict = {}
+    tb = time.perf_counter()
+    for r in reqs:
+        if time.perf_counter() - tb > args.baseline_seconds:
+            break
+        w = chains[r.chain]
+        tl = cache.get(r.chain)
+        if tl is None:
+            for k in list(cache):
+                cache.pop(k).close()
+            torch.cuda.empty_cache()
+            try:
+                tl = TreeLikelihood(w.tree.n_tips, w.n_patterns, w.n_states, 4, "f64")
+            except Exception:
+                continue
+            tl.inst.set_tip_states_all(w.tips)
+            tl.set_rates(w.rates, w.cat_weights)
+            tl.set_pattern_weights(w.pattern_weights)
+            tl.set_model(w.model, w.params, w.freqs)
+            cache[r.chain] = tl
+        ts = time.perf_counter()
+        tl.set_model(w.model, r.params, w.freqs)
+        tl.set_tree(w.tree.children, r.edge_len)
+        if r.gradient:
+            tl.gradient()
+        else:
+            tl.loglik()
+        base_lat.append(time.perf_counter() - ts)
+        base_work += (w.tree.n_tips - 1) * w.n_patterns
+    for tl in cache.values():
+        tl.close()
+    t_base = sum(base_lat)
+    baseline = {"kind": "fp64 one request at a time, no batching", "requests": len(base_lat),
+                "req_per_s": len(base_lat) / t_base if t_base else None,
+                "pattern_node_per_s": base_work / t_base if t_base else None,
+                "p50_service_s": _pct(base_lat, 50), "p99_service_s": _pct(base_lat, 99)}
+    return {"metric": "serving requests/s and p50/p99 latency (s) at offered load",
+            "value": capacity, "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f32 (4-state), tf32 (codon)", "data": "synthetic",
+            "config": {"workload": "serving", "requests": len(reqs), "chains": len(chains),
+                       "codon_requests": int(n_codon),
+                       "gradient_requests": int(sum(r.gradient for r in reqs)),
+                       "taxa": [16, 1024], "patterns": [100, 200000],
+                       "resident_at_start": resident, "memory_budget_gb": budget_gb},
+            "capacity": cap, "loads": loads, "server_stats": stats,
+            "baseline_fp64_one_at_a_time": baseline, "clocks": clk,
+            "generate_s": t_gen, "serve_s": t_serve}
+
+
 def main() -> None:
     args = parse()
+    if args.serving:
+        print(json.dumps(serving_line(args)), flush=True)
+        return
     if args.cpu_worker:
         cpu_worker(args.workload, args.cpu_sample, max(1, args.steps))
         return

@@ -150,7 +150,7 @@ def gamma_rates(alpha: float, ncat: int = 4) -> np.ndarray:
 
 
 def _f81_down(tree: Tree, n_sites: int, n_states: int, cats: np.ndarray,
-              rates: np.ndarray, beta: float, draw, rng) -> np.ndarray:
+              rates: np.ndarray, beta: float, draw, rng, sparse: bool = False) -> np.ndarray:
     states = np.empty((tree.n_nodes, n_sites), dtype=np.int64)
     states[tree.root] = draw(n_sites)
     # walk parents before children: internal labels are post-order, so a
@@ -160,13 +160,20 @@ def _f81_down(tree: Tree, n_sites: int, n_states: int, cats: np.ndarray,
         for c in (a, b):
             keep = np.exp(-beta * rates[cats] * tree.edge_len[c])
             u = rng.random(n_sites)
-            new = draw(n_sites)
-            states[c] = np.where(u < keep, states[node], new)
+            if sparse:
+                # the same process, drawing new states only where a jump happens
+                states[c] = states[node]
+                jump = np.nonzero(u >= keep)[0]
+                states[c, jump] = draw(jump.size)
+            else:
+                new = draw(n_sites)
+                states[c] = np.where(u < keep, states[node], new)
     return states[: tree.n_tips]
 
 
 def simulate_nucleotide(tree: Tree, pi: np.ndarray, rates: np.ndarray,
-                        n_sites: int, rng: np.random.Generator) -> np.ndarray:
+                        n_sites: int, rng: np.random.Generator,
+                        sparse: bool = False) -> np.ndarray:
     """int8 [n_tips, n_sites] nucleotide states (0..3 = A,C,G,T)."""
     pi = np.asarray(pi, dtype=float)
     beta = 1.0 / (1.0 - float(np.sum(pi * pi)))
@@ -176,11 +183,11 @@ def simulate_nucleotide(tree: Tree, pi: np.ndarray, rates: np.ndarray,
         return rng.choice(4, size=n, p=pi)
 
     return _f81_down(tree, n_sites, 4, cats, np.asarray(rates), beta, draw,
-                     rng).astype(np.int8)
+                     rng, sparse).astype(np.int8)
 
 
 def simulate_codon(tree: Tree, f3x4: np.ndarray, rates: np.ndarray,
-                   n_sites: int, rng: np.random.Generator) -> np.ndarray:
+                   n_sites: int, rng: np.random.Generator, sparse: bool = False) -> np.ndarray:
     """int8 [n_tips, n_sites] sense-codon states (0..60, ACGT-lexicographic
     with TAA, TAG, TGA removed). ``f3x4`` is [3, 4] per-position nucleotide
     frequencies; a stationary draw takes one nucleotide per position and is
@@ -211,7 +218,7 @@ def simulate_codon(tree: Tree, f3x4: np.ndarray, rates: np.ndarray,
     beta = 1.0 / (1.0 - float(np.sum(w * w)))
     cats = rng.integers(len(rates), size=n_sites)
     return _f81_down(tree, n_sites, 61, cats, np.asarray(rates), beta, draw,
-                     rng).astype(np.int8)
+                     rng, sparse).astype(np.int8)
 
 
 @dataclass
@@ -288,3 +295,90 @@ def workload(name: str, **override) -> Workload:
     kw = dict(CONFIGS[name])
     kw.update(override)
     return make_workload(name=name, **kw)
+
+
+# ---------------------------------------------------------------------------
+# serving stream: requests from many MCMC chains
+# ---------------------------------------------------------------------------
+SERVING_CONFIG = 4
+
+
+@dataclass
+class ServingRequest:
+    """One likelihood (or likelihood + gradient) request of a chain: a tree
+    proposal (new branch lengths on the chain's topology) and the chain's
+    current substitution-model parameters, so a request alone fixes its
+    result."""
+
+    chain: int
+    edge_len: np.ndarray
+    params: np.ndarray
+    gradient: bool
+
+
+def _loguniform_int(rng, lo: int, hi: int) -> int:
+    return int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi))))))
+
+
+def _chunked(sim, tree, freqs, rates, n_sites, rng, chunk=16384) -> np.ndarray:
+    """Simulate in site chunks so memory stays O(nodes x chunk)."""
+    parts = [sim(tree, freqs, rates, min(chunk, n_sites - s), rng, sparse=True)
+             for s in range(0, n_sites, chunk)]
+    return np.concatenate(parts, axis=1)
+
+
+def serving_stream(n_requests: int = 2000, n_chains: int = 128, *, taxa=(16, 1024),
+                   patterns=(100, 200_000), codon_frac: float = 0.3, grad_frac: float = 0.5,
+                   param_move_frac: float = 0.2, alpha: float = 0.5):
+    """(chains, requests, gaps) of the serving workload.
+
+    Chains draw taxa and pattern counts log-uniformly in the given ranges;
+    a chain is GY94 codon with probability ``codon_frac``, otherwise HKY or
+    GTR with equal probability. Every request picks a chain uniformly, keeps
+    its topology and multiplies each branch length by a log-normal factor
+    (sd 0.1); with probability ``param_move_frac`` the chain's model
+    parameters take a log-normal step (sd 0.1) first; with probability
+    ``grad_frac`` it asks for the gradient as well. ``gaps`` are unit-mean exponential inter-arrival times
+    (a Poisson process, scaled to the offered load by the caller)."""
+    root = np.random.SeedSequence(ROOT_SEED).spawn(SERVING_CONFIG + 1)[SERVING_CONFIG]
+    s_chain, s_req = root.spawn(2)
+    rq = np.random.Generator(np.random.PCG64(s_req))
+    chains = []
+    for c, ss in enumerate(s_chain.spawn(n_chains)):
+        rng = np.random.Generator(np.random.PCG64(ss))
+        n_tips = max(2, _loguniform_int(rng, *taxa))
+        n_pat = max(1, _loguniform_int(rng, *patterns))
+        u = rng.random()
+        model = "gy94" if u < codon_frac else ("hky" if u < codon_frac + (1 - codon_frac) / 2
+                                               else "gtr")
+        tree = yule_tree(n_tips, rng)
+        rates = gamma_rates(alpha, 4)
+        if model == "hky":
+            freqs = rng.dirichlet(np.ones(4))
+            params = np.array([2.0])
+            tips = _chunked(simulate_nucleotide, tree, freqs, rates, n_pat, rng)
+            S = 4
+        elif model == "gtr":
+            params = rng.dirichlet(np.ones(6)) * 6.0
+            freqs = rng.dirichlet(np.ones(4))
+            tips = _chunked(simulate_nucleotide, tree, freqs, rates, n_pat, rng)
+            S = 4
+        else:
+            params = np.array([2.0, 0.3])
+            freqs = np.stack([rng.dirichlet(np.ones(4)) for _ in range(3)])
+            tips = _chunked(simulate_codon, tree, freqs, rates, n_pat, rng)
+            S = 61
+        chains.append(Workload(f"chain{c}", tree, model, params, freqs, alpha, rates,
+                               np.full(4, 0.25), np.ones(n_pat), tips, S))
+    requests = []
+    current = [np.asarray(w.params, dtype=float).copy() for w in chains]
+    for _ in range(n_requests):
+        c = int(rq.integers(n_chains))
+        w = chains[c]
+        el = w.tree.edge_len * np.exp(rq.normal(0.0, 0.1, size=w.tree.edge_len.size))
+        el[w.tree.root] = 0.0
+        if rq.random() < param_move_frac:
+            current[c] = current[c] * np.exp(rq.normal(0.0, 0.1, size=current[c].size))
+        requests.append(ServingRequest(c, el, current[c].copy(), bool(rq.random() < grad_frac)))
+    gaps = rq.exponential(1.0, size=n_requests)
+    return chains, requests, gaps
