@@ -64,6 +64,15 @@ extern "C" {
 #define TL_PREC_BF16X3 0x8u   /* S in 33..64: tcgen05 kind::f16 with a BF16
                                  hi/lo split, three products per contraction   */
 #define TL_SCALE_NONE  0x100u /* no per-pattern rescaling (FP64 only)          */
+#define TL_SPLIT_MATRICES 0x200u /* with TL_PREC_TF32: every transition matrix
+                                 (and Q, dP) is the exact FP32 sum of two TF32
+                                 terms, hi + lo, and each contraction is two
+                                 tensor-core products (x.P_hi + x.P_lo). The
+                                 stored partials are TF32 values already, so
+                                 a split of them would add nothing; the split
+                                 removes the matrix rounding, the one error
+                                 shared by all patterns (it would not average
+                                 out over the pattern sum). */
 
 /* ---- model kinds for tl_set_model -------------------------------------- */
 #define TL_MODEL_HKY   1  /* S=4.  params: kappa.  freqs: pi[4]                */

@@ -22,8 +22,10 @@ ERRORS = {-1: "TL_ERR_ARG", -2: "TL_ERR_INDEX", -3: "TL_ERR_ORDER", -4: "TL_ERR_
           -8: "TL_ERR_UNSUPPORTED", -9: "TL_ERR_STATE"}
 TL_PREC_F64, TL_PREC_F32, TL_PREC_TF32, TL_PREC_BF16X3 = 0x1, 0x2, 0x4, 0x8
 TL_SCALE_NONE = 0x100
+TL_SPLIT_MATRICES = 0x200
 TL_MODEL_HKY, TL_MODEL_GTR, TL_MODEL_GY94, TL_MODEL_REV = 1, 2, 3, 4
 PRECISIONS = {"f64": TL_PREC_F64, "f32": TL_PREC_F32, "tf32": TL_PREC_TF32,
+              "tf32x2": TL_PREC_TF32 | TL_SPLIT_MATRICES,
               "bf16x3": TL_PREC_BF16X3}
 MODELS = {"hky": TL_MODEL_HKY, "gtr": TL_MODEL_GTR, "gy94": TL_MODEL_GY94, "rev": TL_MODEL_REV}
 

@@ -737,6 +737,8 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
         return fail(nullptr, TL_ERR_UNSUPPORTED, "TL_PREC_TF32 is built for 33..64 states");
     if ((flags & TL_SCALE_NONE) && prec != kF64)
         return fail(nullptr, TL_ERR_ARG, "TL_SCALE_NONE needs TL_PREC_F64");
+    if ((flags & TL_SPLIT_MATRICES) && prec != kTF32)
+        return fail(nullptr, TL_ERR_ARG, "TL_SPLIT_MATRICES needs TL_PREC_TF32");
 
     Instance* I = new Instance();
     I->n_tips = n_tips;
@@ -755,6 +757,7 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
     I->prec = prec;
     I->elt = (prec == kF64) ? 8 : 4;
     I->rescale = (flags & TL_SCALE_NONE) ? 0 : 1;
+    I->split = (flags & TL_SPLIT_MATRICES) ? 1 : 0;
     I->stream = reinterpret_cast<cudaStream_t>(stream);
     I->h_catw = new double[kMaxCat];
     I->h_rates = new double[kMaxCat];
@@ -805,7 +808,8 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
     if ((rc = dev_alloc(I, &I->d_mat64, sizeof(double) * mat64 * n_matrices, "matrices")))
         return bail(rc);
     if (use_nuc(I)) I->matw_stride = (size_t)I->R * kColStride * 4;
-    else if (prec == kTF32) I->matw_stride = (size_t)2 * I->R * I->Spad * I->Spad;
+    else if (prec == kTF32)
+        I->matw_stride = (size_t)(I->split ? 4 : 2) * I->R * I->Spad * I->Spad;
     else I->matw_stride = (size_t)I->R * (I->Spad + 1) * I->Spad;
     const size_t matw_elems = prec == kTF32 ? tc_matw_floats(I) : I->matw_stride * n_matrices;
     if ((rc = dev_alloc(I, &I->d_matw, (size_t)I->elt * matw_elems, "matrix copies")))

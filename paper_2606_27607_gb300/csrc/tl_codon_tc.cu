@@ -32,10 +32,16 @@ namespace {
 
 constexpr int kTcM = 128;                   // patterns per tile (TMEM lanes)
 constexpr int kTcN = 64;                    // padded states
-constexpr int kStages = 4;
+constexpr int kStages = 4;                  // most pipeline stages (barrier arrays)
 constexpr int kAChunk = kTcM * 32 * 4;      // 32 K-values of 128 rows: 16 KB
 constexpr int kBChunk = kTcN * 32 * 4;      // 8 KB
-constexpr int kStageBytes = 2 * kAChunk + 2 * kBChunk;  // 48 KB
+// Stage: A (2 x 16 KB) and B (2 x 8 KB) = 48 KB, four stages; with split
+// matrices a stage also holds B_lo (64 KB), so three fit.
+template <bool SPLIT>
+struct TcPipe {
+    static constexpr int stages = SPLIT ? 3 : 4;
+    static constexpr int bytes = 2 * kAChunk + (SPLIT ? 4 : 2) * kBChunk;
+};
 constexpr int kTmemCols = 512;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // a wait gives up after 2 s
 
@@ -198,11 +204,17 @@ __device__ __forceinline__ float block_sum128(float v, float* red) {
     return t;
 }
 
-template <int MODE>
+// SPLIT: B = B_hi + B_lo, the lo rows 2 R 64 rows after the hi rows of the
+// same block (lookups: 2 R 64 64 floats after), and each k-step issues the
+// hi and the lo product into the same accumulator.
+template <int MODE, bool SPLIT>
 __global__ void __launch_bounds__(128, 1)
 k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtensorMap tm_tip,
      const __grid_constant__ CUtensorMap tm_mat, const TcOp* __restrict__ ops, int n_ops,
      TcArgs a) {
+    constexpr int kSt = TcPipe<SPLIT>::stages;
+    constexpr int kStB = TcPipe<SPLIT>::bytes;
+    const size_t kLoFloats = (size_t)2 * a.R * kTcN * kTcN;  // hi block -> lo block
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     // 128-byte swizzle atoms must start on 1024-byte shared-memory addresses
     unsigned char* stages = smem_tc + ((1024u - (smem_u32(smem_tc) & 1023u)) & 1023u);
@@ -222,7 +234,7 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < kSt; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -251,19 +263,19 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
             // software pipeline: produce pair i, consume pair i - (kStages - 1)
             bool ok = true;
             int produced = 0, consumed = 0;
-            for (int i = 0; ok && i < n_pairs + kStages - 1; ++i) {
+            for (int i = 0; ok && i < n_pairs + kSt - 1; ++i) {
                 if (i < n_pairs) {
                     const unsigned g = pairs_done + i;
-                    const int s = g % kStages;
-                    ok = mbar_wait(&empty[s], ((g / kStages) & 1) ^ 1);
+                    const int s = g % kSt;
+                    ok = mbar_wait(&empty[s], ((g / kSt) & 1) ^ 1);
                     if (!ok) {
                         abort_sh |= 1;
                         break;
                     }
                     const int c = mma[0] ? (i < R ? 0 : 1) : 1;
                     const int r = i % R;
-                    unsigned char* st = stages + s * kStageBytes;
-                    mbar_expect_tx(&full[s], kStageBytes);
+                    unsigned char* st = stages + s * kStB;
+                    mbar_expect_tx(&full[s], kStB);
                     const int arow = (op.child[c] * R + r) * a.Ppad + p0;
                     const int brow = op.brow[c] + r * kTcN;
                     const CUtensorMap* am = op.kind[c] == kTipPartials ? &tm_tip : &tm_part;
@@ -271,13 +283,18 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                     tma_load_2d(st + kAChunk, am, 32, arow, &full[s]);
                     tma_load_2d(st + 2 * kAChunk, &tm_mat, 0, brow, &full[s]);
                     tma_load_2d(st + 2 * kAChunk + kBChunk, &tm_mat, 32, brow, &full[s]);
+                    if (SPLIT) {
+                        const int lrow = brow + 2 * R * kTcN;
+                        tma_load_2d(st + 2 * kAChunk + 2 * kBChunk, &tm_mat, 0, lrow, &full[s]);
+                        tma_load_2d(st + 2 * kAChunk + 3 * kBChunk, &tm_mat, 32, lrow, &full[s]);
+                    }
                     ++produced;
                 }
-                const int j = i - (kStages - 1);
+                const int j = i - (kSt - 1);
                 if (j >= 0) {
                     const unsigned g = pairs_done + j;
-                    const int s = g % kStages;
-                    ok = mbar_wait(&full[s], (g / kStages) & 1);
+                    const int s = g % kSt;
+                    ok = mbar_wait(&full[s], (g / kSt) & 1);
                     if (!ok) {
                         abort_sh |= 2;
                         break;
@@ -286,13 +303,18 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                     const int c = mma[0] ? (j < R ? 0 : 1) : 1;
                     const int r = j % R;
                     const uint32_t d = tmem + (uint32_t)(r * 2 * kTcN + c * kTcN);
-                    unsigned char* st = stages + s * kStageBytes;
+                    unsigned char* st = stages + s * kStB;
 #pragma unroll
                     for (int ks = 0; ks < 8; ++ks) {
                         const int chunk = ks >> 2, kin = (ks & 3) * 32;
                         const uint64_t ad = sw128_desc(st + chunk * kAChunk + kin);
                         const uint64_t bd = sw128_desc(st + 2 * kAChunk + chunk * kBChunk + kin);
                         mma_tf32(d, ad, bd, ks > 0 ? 1u : 0u);
+                        if (SPLIT) {
+                            const uint64_t bl =
+                                sw128_desc(st + 2 * kAChunk + (2 + chunk) * kBChunk + kin);
+                            mma_tf32(d, ad, bl, 1u);
+                        }
                     }
                     mma_commit(&empty[s]);
                     ++consumed;
@@ -333,7 +355,7 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
             } else {
                 // the tip's column of P (row of P^T), or the row sums of P
                 const int slot_base = op.look[c];
-                const float* src = amb[c] ? a.rowsum + (size_t)(slot_base / (2 * R * kTcN * kTcN)) * R * kTcN +
+                const float* src = amb[c] ? a.rowsum + (size_t)(slot_base / ((SPLIT ? 4 : 2) * R * kTcN * kTcN)) * R * kTcN +
                                                 (size_t)r * kTcN + q * 16
                                           : a.matw + (size_t)slot_base + (size_t)r * kTcN * kTcN +
                                                 (size_t)sidx[c] * kTcN + q * 16;
@@ -345,6 +367,17 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                     v[4 * u + 1] = f.y;
                     v[4 * u + 2] = f.z;
                     v[4 * u + 3] = f.w;
+                }
+                if (SPLIT && !amb[c]) {  // + the lo term (row sums already hold hi + lo)
+                    const float4* l4 = reinterpret_cast<const float4*>(src + kLoFloats);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 f = __ldg(l4 + u);
+                        v[4 * u] += f.x;
+                        v[4 * u + 1] += f.y;
+                        v[4 * u + 2] += f.z;
+                        v[4 * u + 3] += f.w;
+                    }
                 }
             }
         };
@@ -458,7 +491,14 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                                 (size_t)srow * kTcN + q * 16);
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
-                                const float4 f = __ldg(d4 + u);
+                                float4 f = __ldg(d4 + u);
+                                if (SPLIT) {
+                                    const float4 l = __ldg(d4 + u + kLoFloats / 4);
+                                    f.x += l.x;
+                                    f.y += l.y;
+                                    f.z += l.z;
+                                    f.w += l.w;
+                                }
                                 nr += z[4 * u] * sib[4 * u] * f.x + z[4 * u + 1] * sib[4 * u + 1] * f.y +
                                       z[4 * u + 2] * sib[4 * u + 2] * f.z +
                                       z[4 * u + 3] * sib[4 * u + 3] * f.w;
@@ -543,7 +583,7 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
         atomicOr(a.err, abort_sh | (1 << (8 + MODE)));
         // bounded drain of copies and products still in flight
         for (unsigned g = consumed_sh; g < produced_sh; ++g)
-            mbar_wait(&full[g % kStages], (g / kStages) & 1);
+            mbar_wait(&full[g % kSt], (g / kSt) & 1);
         mbar_wait(&done, items_done & 1);
     }
     // no MMA may still write TMEM when it is released
@@ -645,29 +685,53 @@ TcArgs tc_args(Instance* I) {
 
 // Row of the P (which = 0) or P^T (which = 1) block of a slot in the matrix
 // map, category 0; float offset of the same block in the matrix array.
-int brow_of(const Instance* I, int slot, int which) { return (slot * 2 + which) * I->R * kTcN; }
+// A slot holds 2 blocks of R 64 x 64 floats (P, P^T), 4 with split matrices
+// (P_hi, P_hi^T, P_lo, P_lo^T); a model's Q copy 1 block, or 4 (Q_hi, -,
+// Q_lo, -) so that lo is always two blocks after hi.
+int blocks_per_slot(const Instance* I) { return I->split ? 4 : 2; }
+int blocks_per_q(const Instance* I) { return I->split ? 4 : 1; }
+int brow_of(const Instance* I, int slot, int which) {
+    return (slot * blocks_per_slot(I) + which) * I->R * kTcN;
+}
 int look_of(const Instance* I, int slot, int which) {
     return (int)((size_t)slot * I->matw_stride + (size_t)which * I->R * kTcN * kTcN);
 }
-int qrow_of(const Instance* I, int model) { return (I->n_mats * 2 + model) * I->R * kTcN; }
-
-__global__ void k_q_tc(const double* __restrict__ Q, float* __restrict__ dst, int R) {
-    for (int idx = threadIdx.x; idx < R * kTcN * kTcN; idx += blockDim.x)
-        dst[idx] = to_tf32((float)Q[idx % (kTcN * kTcN)]);
+int qrow_of(const Instance* I, int model) {
+    return (I->n_mats * blocks_per_slot(I) + model * blocks_per_q(I)) * I->R * kTcN;
 }
 
-template <int MODE>
-void launch_mode(Instance* I, const TcOp* d, int n, TcArgs a) {
-    const size_t smem = (size_t)kStages * kStageBytes + 1024;
-    cudaFuncSetAttribute(k_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+// Q in TF32 for every category block; with split matrices also the lo
+// term (the TF32 truncation of fl32(Q) - Q_hi) two blocks later.
+__global__ void k_q_tc(const double* __restrict__ Q, float* __restrict__ dst, int R, int split) {
+    for (int idx = threadIdx.x; idx < R * kTcN * kTcN; idx += blockDim.x) {
+        const float f = (float)Q[idx % (kTcN * kTcN)];
+        const float hi = to_tf32(f);
+        dst[idx] = hi;
+        if (split)
+            dst[idx + (size_t)2 * R * kTcN * kTcN] =
+                __uint_as_float(__float_as_uint(f - hi) & 0xffffe000u);
+    }
+}
+
+template <int MODE, bool SPLIT>
+void launch_mode_t(Instance* I, const TcOp* d, int n, TcArgs a) {
+    const size_t smem = (size_t)TcPipe<SPLIT>::stages * TcPipe<SPLIT>::bytes + 1024;
+    cudaFuncSetAttribute(k_tc<MODE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     int sms = 0, dev_id = 0;
     cudaGetDevice(&dev_id);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
     const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(I->tmaps.data());
     const int items = n * a.n_tiles;
     const int grid = std::max(1, std::min(items, sms));
-    k_tc<MODE><<<grid, 128, smem, I->stream>>>(m[0], m[1], m[2], d, n, a);
+    k_tc<MODE, SPLIT><<<grid, 128, smem, I->stream>>>(m[0], m[1], m[2], d, n, a);
     I->launches += 1;
+}
+
+template <int MODE>
+void launch_mode(Instance* I, const TcOp* d, int n, TcArgs a) {
+    if (I->split) launch_mode_t<MODE, true>(I, d, n, a);
+    else launch_mode_t<MODE, false>(I, d, n, a);
 }
 
 void tc_operand(const Instance* I, TcOp& t, int c, int buf, int slot) {
@@ -693,14 +757,16 @@ int tc_setup(Instance* I) {
     int rc;
     const size_t rows = (size_t)I->n_buffers * I->R * I->Ppad;
     if ((rc = make_map(I, &m[0], I->pool, rows, kTcM))) return rc;
-    const size_t mrows = ((size_t)I->n_mats * 2 + I->n_models) * I->R * kTcN;
+    const size_t mrows =
+        ((size_t)I->n_mats * blocks_per_slot(I) + (size_t)I->n_models * blocks_per_q(I)) * I->R * kTcN;
     if ((rc = make_map(I, &m[2], I->d_matw, mrows, kTcN))) return rc;
     m[1] = m[0];  // tip-partials map until a tip pool exists
     return TL_OK;
 }
 
 size_t tc_matw_floats(const Instance* I) {
-    return (size_t)I->n_mats * I->matw_stride + (size_t)I->n_models * I->R * kTcN * kTcN;
+    return (size_t)I->n_mats * I->matw_stride +
+           (size_t)I->n_models * blocks_per_q(I) * I->R * kTcN * kTcN;
 }
 
 int tc_set_tip_pool(Instance* I) {
@@ -710,7 +776,7 @@ int tc_set_tip_pool(Instance* I) {
 
 int launch_q_tc(Instance* I, int model) {
     float* dst = reinterpret_cast<float*>(I->d_matw) + (size_t)qrow_of(I, model) * kTcN;
-    k_q_tc<<<1, 256, 0, I->stream>>>(I->models[model].Q, dst, I->R);
+    k_q_tc<<<1, 256, 0, I->stream>>>(I->models[model].Q, dst, I->R, I->split);
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "tensor-core Q copy");
 }

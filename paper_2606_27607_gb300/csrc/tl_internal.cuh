@@ -145,6 +145,7 @@ struct Instance {
     Prec prec = kF64;
     int elt = 8;      // bytes per stored partial element
     int rescale = 1;
+    int split = 0;    // TF32: matrices as hi + lo (TL_SPLIT_MATRICES)
     cudaStream_t stream = nullptr;
     int device = 0;
     int smem_optin = 0;

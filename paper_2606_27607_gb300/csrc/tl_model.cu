@@ -292,6 +292,10 @@ __device__ __forceinline__ float round_tf32(float x) {
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
 }
+// The TF32 value of x with the low 13 mantissa bits cleared (toward zero).
+__device__ __forceinline__ float trunc_tf32(float x) {
+    return __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+}
 
 // Working-precision copies of pi and Q.
 template <typename T>
@@ -343,7 +347,7 @@ __device__ void write_layout(const double* Pm, int slot, int r, int S, int Spad,
             }
             w[idx] = v;
         }
-    } else {
+    } else if (layout == 2) {
         // tensor-core layout [2][R][64][64]: P row-major (the B operand)
         // and P^T (tip lookups), both TF32-rounded; row sums of the
         // rounded P summed in order (ambiguous tips)
@@ -361,6 +365,34 @@ __device__ void write_layout(const double* Pm, int slot, int r, int S, int Spad,
             for (int q = 1; q < S; ++q) v = v + wp[i * Spad + q];
             rowsum[((size_t)slot * R + r) * Spad + i] = v;
         }
+    } else {
+        // split tensor-core layout [4][R][64][64]: P_hi, P_hi^T, P_lo,
+        // P_lo^T with P_hi = TF32(P) (nearest) and P_lo = the TF32
+        // truncation of fl32(P) - P_hi. P_hi + P_lo is then exact in FP32
+        // (its bits lie within those of fl32(P), or of P_hi when it rounded
+        // up to the next binade), so a product with a one-hot partial, hi
+        // term then lo term, gives the same FP32 value as adding the two
+        // looked-up entries. Row sums of P_hi + P_lo in order.
+        T* wp = w + (size_t)r * Spad * Spad;
+        T* wt = w + ((size_t)R + r) * Spad * Spad;
+        T* lp = w + ((size_t)2 * R + r) * Spad * Spad;
+        T* lt = w + ((size_t)3 * R + r) * Spad * Spad;
+        for (int idx = t; idx < Spad * Spad; idx += nt) {
+            const int i = idx / Spad, j = idx % Spad;
+            const float f = (float)Pm[idx];
+            const float hi = round_tf32(f);
+            const float lo = trunc_tf32(f - hi);
+            wp[idx] = (T)hi;
+            wt[j * Spad + i] = (T)hi;
+            lp[idx] = (T)lo;
+            lt[j * Spad + i] = (T)lo;
+        }
+        __syncthreads();
+        for (int i = t; i < Spad; i += nt) {
+            T v = wp[i * Spad] + lp[i * Spad];
+            for (int q = 1; q < S; ++q) v = v + (wp[i * Spad + q] + lp[i * Spad + q]);
+            rowsum[((size_t)slot * R + r) * Spad + i] = v;
+        }
     }
 
 }
@@ -369,6 +401,7 @@ __device__ void write_layout(const double* Pm, int slot, int r, int S, int Spad,
 //  layout 0: four-state column layout [R][5][4] of T: column j of P, then row sums
 //  layout 1: FP64 transposed layout [R][Spad+1][Spad]: W[j][i] = P[i][j], row Spad = row sums
 //  layout 2: TF32 row-major [R][Spad][Spad] floats (rounded) + row sums [R][Spad]
+//  layout 3: layout 2 as hi and lo TF32 terms (TL_SPLIT_MATRICES)
 template <typename T>
 __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
                       const double* __restrict__ Vinv, const double* __restrict__ lam,
@@ -500,7 +533,7 @@ int launch_update_matrices(Instance* I, int m, const int* d_pidx, const int* d_d
     dim3 grid(count, I->R);
     size_t smem = (128 + (size_t)I->Spad * I->Spad) * sizeof(double);
     int layout = (I->S == 4 && (I->prec == kF32 || I->prec == kF64)) ? 0
-                 : (I->prec == kF64 ? 1 : 2);
+                 : (I->prec == kF64 ? 1 : (I->split ? 3 : 2));
     if (I->prec == kF64) {
         cudaFuncSetAttribute(k_tpm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
         k_tpm<double><<<grid, 256, smem, I->stream>>>(I->S, I->Spad, I->R, M.V, M.Vinv, M.lam,
@@ -606,7 +639,7 @@ int launch_param_matrices(Instance* I, int m, int param, const int* d_idx, const
     dim3 grid(count, I->R);
     const size_t smem = 2 * (size_t)I->Spad * I->Spad * sizeof(double);
     const int layout = (I->S == 4 && (I->prec == kF32 || I->prec == kF64)) ? 0
-                       : (I->prec == kF64 ? 1 : 2);
+                       : (I->prec == kF64 ? 1 : (I->split ? 3 : 2));
     const double* G = M.G + (size_t)param * I->Spad * I->Spad;
     if (I->prec == kF64) {
         cudaFuncSetAttribute(k_param_tpm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

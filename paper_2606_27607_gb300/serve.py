@@ -53,7 +53,8 @@ def footprint(n_tips: int, n_patterns: int, n_states: int, precision: str) -> in
     elt = 8 if precision == "f64" else 4
     nb = 2 * (N - 1)
     partials = nb * R * ppad * spad * elt + nb * ppad * 4
-    mats = 2 * (2 * N - 1) * R * spad * spad * (8 + 2 * elt)
+    copies = 4 if precision == "tf32x2" else 2   # working copies per matrix slot
+    mats = 2 * (2 * N - 1) * R * spad * spad * (8 + copies * elt)
     return int(1.02 * (partials + mats + N * ppad)) + (1 << 20)
 
 
@@ -105,7 +106,7 @@ class Server:
 
     def __init__(self, memory_budget: int | None = None, max_batch: int = 512,
                  codon_streams: int = 2, nuc_precision: str = "f32",
-                 codon_precision: str = "tf32"):
+                 codon_precision: str = "tf32x2"):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", torch.cuda.current_device())
