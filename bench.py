@@ -614,6 +614,9 @@ def main() -> None:
     ach = alg[dom] / (k_ms[dom] * 1e-3) / 1e9
     lpp = int(os.environ.get("TL_NUC_LANES", "1"))
     lpp = lpp if lpp in (1, 2, 4) else 1
+    if dom == "pre":
+        lpp = max(lpp, int(os.environ.get("TL_PRE_LANES", "0") or 0))
+        lpp = lpp if lpp in (1, 2, 4) else 1
     kname = f"k_{dom}4<float,{lpp},{4 // lpp},4>"
     traffic = traffic_for(kname, P * (N - 1))
     roof = {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": hbm, "unit": "GB/s",

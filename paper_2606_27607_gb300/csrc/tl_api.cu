@@ -1306,7 +1306,7 @@ static int pre_common(Instance* I, const tl_pre_op* ops, int count, int model, i
         if ((rc = ensure_out(I, (size_t)E))) return rc;
         if ((rc = reduce_fixed(I, I->d_red, E, n_tiles, extra(I).d_out))) return rc;
     } else if (use_nuc(I)) {
-        const int n_tiles = nuc_tiles_main(I);
+        const int n_tiles = nuc_tiles_pre(I);
         if ((rc = ensure_scratch(I, (size_t)std::max(E, 1) * n_tiles))) return rc;
         void* d_ops = nullptr;
         if ((rc = upload(I, extra(I).areas[1], plan.dev.data(), sizeof(DevPreOp) * count, &d_ops)))
@@ -1722,7 +1722,7 @@ int tl_batch_pre_order_gradient_dev(tl_batch* b, tl_instance* const* insts,
         if ((rc = plan_pre(x, ops ? ops[k] : nullptr, counts[k], n_grad[k], false, &plan)))
             return batch_from(B, x, k, rc);
         const int E = (int)plan.edge_map.size();
-        const int n_tiles = nuc_tiles_main(x);
+        const int n_tiles = nuc_tiles_pre(x);
         if ((rc = ensure_scratch(x, (size_t)std::max(E, 1) * n_tiles))) return batch_from(B, x, k, rc);
         void* d = nullptr;
         if (counts[k] > 0 &&

@@ -236,7 +236,9 @@ int launch_param_matrices(Instance* I, int m, int param, const int* d_idx, const
 int nuc_lanes(const Instance* I);            // lanes per pattern (root, edge kernels)
 int nuc_tiles(const Instance* I);            // their tiles
 int nuc_lanes_main(const Instance* I);       // lanes per pattern (post, pre kernels)
-int nuc_tiles_main(const Instance* I);       // their tiles (= gradient partial columns)
+int nuc_tiles_main(const Instance* I);       // their tiles
+int nuc_lanes_pre(const Instance* I);        // lanes per pattern (pre-order kernel)
+int nuc_tiles_pre(const Instance* I);        // its tiles (= gradient partial columns)
 int nuc_smem_per_slot(const Instance* I);    // bytes per slot per warp
 int launch_post4(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots);
 int launch_root4(Instance* I, int root_kind, int root, int model, double* d_site,

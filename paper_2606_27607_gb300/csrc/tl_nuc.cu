@@ -70,6 +70,41 @@ __device__ __forceinline__ T vmax(V4<T> a) {
     return fmax(fmax(a.x, a.y), fmax(a.z, a.w));
 }
 
+// ---- packed FP32 pairs (fma/mul/add .f32x2 of sm_100 and later): two
+// lanes of a V4<float> per instruction, each rounded exactly as the scalar
+// instruction would, so a packed chain gives the scalar chain's bits.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 r, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ V4<float> mul(V4<float> a, V4<float> b) {
+    V4<float> r;
+    upk2(mul2(pk2(a.x, a.y), pk2(b.x, b.y)), r.x, r.y);
+    upk2(mul2(pk2(a.z, a.w), pk2(b.z, b.w)), r.z, r.w);
+    return r;
+}
+// (a.x b.x + a.z b.z) + (a.y b.y + a.w b.w)
+__device__ __forceinline__ float dot(V4<float> a, V4<float> b) {
+    float lo, hi;
+    upk2(fma2(pk2(a.z, a.w), pk2(b.z, b.w), mul2(pk2(a.x, a.y), pk2(b.x, b.y))), lo, hi);
+    return lo + hi;
+}
+
 // P x with P given by its columns c0..c3 (column j at col + j * cs):
 // x0 c0 + x1 c1 + x2 c2 + x3 c3.
 template <typename T>
@@ -87,6 +122,25 @@ template <typename T>
 __device__ __forceinline__ V4<T> matTvec(const T* col, int cs, V4<T> u) {
     V4<T> c0 = ld4(col), c1 = ld4(col + cs), c2 = ld4(col + 2 * cs), c3 = ld4(col + 3 * cs);
     return {dot(c0, u), dot(c1, u), dot(c2, u), dot(c3, u)};
+}
+// The FP32 matvec as packed pairs, in the scalar chain's order (same bits).
+__device__ __forceinline__ V4<float> matvec_cols(V4<float> c0, V4<float> c1, V4<float> c2,
+                                                 V4<float> c3, V4<float> x) {
+    const f32x2 sx = pk2(x.x, x.x), sy = pk2(x.y, x.y), sz = pk2(x.z, x.z), sw = pk2(x.w, x.w);
+    f32x2 a = mul2(sx, pk2(c0.x, c0.y)), b = mul2(sx, pk2(c0.z, c0.w));
+    a = fma2(sy, pk2(c1.x, c1.y), a);
+    b = fma2(sy, pk2(c1.z, c1.w), b);
+    a = fma2(sz, pk2(c2.x, c2.y), a);
+    b = fma2(sz, pk2(c2.z, c2.w), b);
+    a = fma2(sw, pk2(c3.x, c3.y), a);
+    b = fma2(sw, pk2(c3.z, c3.w), b);
+    V4<float> r;
+    upk2(a, r.x, r.y);
+    upk2(b, r.z, r.w);
+    return r;
+}
+__device__ __forceinline__ V4<float> matvec(const float* col, int cs, V4<float> x) {
+    return matvec_cols(ld4(col), ld4(col + cs), ld4(col + 2 * cs), ld4(col + 3 * cs), x);
 }
 
 // frexp exponent e of m >= 0 (m = f 2^e, f in [0.5, 1)); 0 for m == 0.
@@ -227,14 +281,23 @@ struct WarpPipe {
             cp_async16(reinterpret_cast<char*>(obuf + j % 3) + lane * 16,
                        reinterpret_cast<const char*>(ops + j) + lane * 16);
     }
+    // idx: the NMAT matrix slots (-1: none). A lane's chunks are lane,
+    // lane + 32, ...; the slot is picked by selects, not by indexing, so idx
+    // stays in registers when it is a local array.
     __device__ __forceinline__ void issue_mats(int j, int n, const int* idx, const T* mat,
                                                int mat_stride, int lane) {
         if (j >= n) return;
         T* dst = mbuf + (j & 1) * NMAT * matf;
         const int per = matf * (int)sizeof(T) / 16;
+        int slots[NMAT];
+#pragma unroll
+        for (int m = 0; m < NMAT; ++m) slots[m] = idx[m];
         for (int q = lane; q < NMAT * per; q += 32) {
             const int m = q / per, c = q % per;
-            const int slot = idx[m];
+            int slot = slots[0];
+#pragma unroll
+            for (int i = 1; i < NMAT; ++i)
+                if (m == i) slot = slots[i];
             if (slot >= 0)
                 cp_async16(reinterpret_cast<char*>(dst + m * matf) + c * 16,
                            reinterpret_cast<const char*>(mat + (size_t)slot * mat_stride) + c * 16);
@@ -366,14 +429,7 @@ k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ 
 #pragma unroll
                     for (int j = 0; j < CPL; ++j) {
                         if (act[j]) {
-                            const T* col = mc + j * LPP * 4;
-                            const V4<T> c0 = lds4(col), c1 = lds4(col + cs), c2 = lds4(col + 2 * cs),
-                                        c3 = lds4(col + 3 * cs);
-                            const V4<T> xx = x[j];
-                            v[j].x = xx.x * c0.x + xx.y * c1.x + xx.z * c2.x + xx.w * c3.x;
-                            v[j].y = xx.x * c0.y + xx.y * c1.y + xx.z * c2.y + xx.w * c3.y;
-                            v[j].z = xx.x * c0.z + xx.y * c1.z + xx.z * c2.z + xx.w * c3.z;
-                            v[j].w = xx.x * c0.w + xx.y * c1.w + xx.z * c2.w + xx.w * c3.w;
+                            v[j] = matvec(mc + j * LPP * 4, cs, x[j]);
                         } else {
                             v[j] = zero;
                         }
@@ -504,11 +560,17 @@ k_root4(int kind_, int root_, const __grid_constant__ NucArgs<T> a_, const doubl
 // ---------------------------------------------------------------------------
 // fused pre-order pass + branch-length gradient
 // ---------------------------------------------------------------------------
-#ifndef TL_PRE_MIN_BLOCKS
-#define TL_PRE_MIN_BLOCKS 1
-#endif
+// Minimum resident blocks per SM the pre-order kernel is compiled for, by
+// lane layout: one lane per pattern holds four categories of state and
+// needs the full register file of a thread (two blocks, eight warps per
+// SM); two and four lanes per pattern fit three and four blocks without
+// spilling.
+template <int LPP>
+struct PreMinBlocks {
+    static constexpr int value = LPP == 1 ? 1 : (LPP == 2 ? 3 : 4);
+};
 template <typename T, int LPP, int CPL, int NR, bool BATCH>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, TL_PRE_MIN_BLOCKS)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, PreMinBlocks<LPP>::value)
 k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ NucArgs<T> a_,
        const T* __restrict__ piw_, const T* __restrict__ Qw_, double* __restrict__ gpart_,
        const BatchRef<T> br) {
@@ -528,6 +590,13 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
     pipe.matf = kColStride * 4 * R;
     BatchJob<T>* stage = reinterpret_cast<BatchJob<T>*>(
         pipe_base + (size_t)kWarpsPerBlock * pipe_bytes<DevPreOp, T, 4>(R)) + warp;
+    // gradient terms of up to 32 edges, [edge][lane] (row stride 33), summed
+    // over the lanes 32 edges at a time: one store per edge and lane
+    // instead of a five-step shuffle reduction per edge
+    T* gbuf = reinterpret_cast<T*>(reinterpret_cast<BatchJob<T>*>(
+                  pipe_base + (size_t)kWarpsPerBlock * pipe_bytes<DevPreOp, T, 4>(R)) +
+              kWarpsPerBlock) +
+              (size_t)warp * 32 * 33;
     const NucArgs<T>& a = pick_args<BATCH>(a_, stage);
     bool act[CPL];
     T wr[CPL], wrr[CPL];
@@ -569,6 +638,17 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
         const size_t off0 = ((size_t)r0 * a.Ppad + p) * 4;
         const size_t offj = (size_t)LPP * a.Ppad * 4;
         const T wpt = (p < a.P) ? (T)a.patw[p] : T(0);
+        int nbuf = 0, my_edge = 0;  // buffered edges; lane e holds edge e's row
+        auto flush_edges = [&]() {
+            __syncwarp();
+            if (lane < nbuf) {
+                T acc = T(0);
+                for (int i = 0; i < 32; ++i) acc += gbuf[lane * 33 + i];
+                gpart[(size_t)my_edge * a.n_tiles + tile] = (double)acc;
+            }
+            __syncwarp();
+            nbuf = 0;
+        };
         // a child's post-order partial (memory, or tip partials), prefetched
         auto child_x = [&](int child, int kind, V4<T>* x) {
             if (kind == kTipStates || kind < 0) {
@@ -674,6 +754,7 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
 #pragma unroll
             for (int j = 0; j < CPL; ++j) den_l += wr[j] * dot(q[j], mul(v[0][j], v[1][j]));
             const T den = group_sum<LPP>(den_l);
+            const T wden = wpt / den;  // both children's ratios share it
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 V4<T> u[CPL];
@@ -715,9 +796,10 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
                         }
                     }
                     const T num = group_sum<LPP>(num_l);
-                    T g = wpt * (num / den);
-                    g = tile_sum<LPP, T>(g);
-                    if (lane == 0) gpart[(size_t)op.edge[c] * a.n_tiles + tile] = (double)g;
+                    // one value per pattern (the first of its LPP lanes)
+                    gbuf[nbuf * 33 + lane] = (r0 == 0) ? num * wden : T(0);
+                    if (lane == nbuf) my_edge = op.edge[c];
+                    if (++nbuf == 32) flush_edges();
                 }
                 if (op.need_q[c]) {
                     T m = T(0);
@@ -750,6 +832,7 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
                 xc[1][j] = xn[1][j];
             }
         }
+        if (nbuf > 0) flush_edges();
         cp_async_wait_all();
     }
 }
@@ -818,6 +901,19 @@ int nuc_lanes_main(const Instance* I) {
     return lpp;
 }
 
+// Lanes per pattern of the pre-order kernel: TL_PRE_LANES (1, 2, 4 or 8,
+// at least the post-order kernel's), else the post-order kernel's.
+int nuc_lanes_pre(const Instance* I) {
+    static int env = -1;
+    if (env < 0) {
+        const char* s = getenv("TL_PRE_LANES");
+        env = s ? atoi(s) : 0;
+    }
+    const int main = nuc_lanes_main(I);
+    const int lpp = (env == 1 || env == 2 || env == 4 || env == 8) ? env : main;
+    return std::max(lpp, main);
+}
+
 int nuc_cpl(const Instance* I) {
     const int lpp = nuc_lanes_main(I);
     return (I->R + lpp - 1) / lpp;
@@ -826,6 +922,7 @@ int nuc_cpl(const Instance* I) {
 int nuc_tiles_for(const Instance* I, int lpp) { return I->Ppad / (32 / lpp); }
 int nuc_tiles(const Instance* I) { return nuc_tiles_for(I, nuc_lanes(I)); }
 int nuc_tiles_main(const Instance* I) { return nuc_tiles_for(I, nuc_lanes_main(I)); }
+int nuc_tiles_pre(const Instance* I) { return nuc_tiles_for(I, nuc_lanes_pre(I)); }
 
 int nuc_smem_per_slot(const Instance* I) {
     return 32 * (nuc_cpl(I) * 4 * I->elt + (int)sizeof(int));
@@ -899,6 +996,20 @@ static int grid_for(const Instance* I, K kernel, size_t smem, int n_tiles) {
             FN<T, 8, 1, 0>(__VA_ARGS__);                                    \
         }                                                                   \
     } while (0)
+// The same over the pre-order kernel's lane layouts.
+#define TL_PRE_DISPATCH_T(T, I, FN, ...)                                    \
+    do {                                                                    \
+        const int lpp_ = nuc_lanes_pre(I);                                  \
+        if ((I)->R == 4) {                                                  \
+            if (lpp_ == 1) FN<T, 1, 4, 4>(__VA_ARGS__);                     \
+            else if (lpp_ == 2) FN<T, 2, 2, 4>(__VA_ARGS__);                \
+            else FN<T, 4, 1, 4>(__VA_ARGS__);                               \
+        } else if ((I)->R < 4) {                                            \
+            FN<T, 4, 1, 0>(__VA_ARGS__);                                    \
+        } else {                                                            \
+            FN<T, 8, 1, 0>(__VA_ARGS__);                                    \
+        }                                                                   \
+    } while (0)
 #define TL_MAIN_DISPATCH(I, FN, ...)                                        \
     do {                                                                    \
         if ((I)->prec == kF32) TL_MAIN_DISPATCH_T(float, I, FN, __VA_ARGS__); \
@@ -943,7 +1054,8 @@ template <typename T, int LPP, int CPL, int NR>
 static void pre4_t(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, const void* piw,
                    const void* Qw, double* d_gpart, int dgen) {
     const size_t smem = (size_t)kWarpsPerBlock * ((size_t)n_slots * CPL * 32 * 4 * sizeof(T) +
-                                                  pipe_bytes<DevPreOp, T, 4>(I->R));
+                                                  pipe_bytes<DevPreOp, T, 4>(I->R) +
+                                                  sizeof(BatchJob<T>) + 32 * 33 * sizeof(T));
     cudaFuncSetAttribute(k_pre4<T, LPP, CPL, NR, false>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     NucArgs<T> a = make_args<T>(I, n_slots);
@@ -957,8 +1069,12 @@ static void pre4_t(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, c
 
 int launch_pre4(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, int model,
                 double* d_gpart, int dgen) {
-    TL_MAIN_DISPATCH(I, pre4_t, I, d_ops, n_ops, n_slots, I->models[model].piw,
-                     I->models[model].Qw, d_gpart, dgen);
+    if (I->prec == kF32)
+        TL_PRE_DISPATCH_T(float, I, pre4_t, I, d_ops, n_ops, n_slots, I->models[model].piw,
+                          I->models[model].Qw, d_gpart, dgen);
+    else
+        TL_PRE_DISPATCH_T(double, I, pre4_t, I, d_ops, n_ops, n_slots, I->models[model].piw,
+                          I->models[model].Qw, d_gpart, dgen);
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "pre-order kernel");
 }
@@ -1145,7 +1261,8 @@ static int pre4_batch_t(Batch* B, Instance* const* I, const DevPreOp* const* d_o
     Instance* I0 = I[order[0]];
     const size_t smem = (size_t)kWarpsPerBlock *
                         ((size_t)max_slots * CPL * 32 * 4 * sizeof(T) +
-                         pipe_bytes<DevPreOp, T, 4>(I0->R) + sizeof(BatchJob<T>));
+                         pipe_bytes<DevPreOp, T, 4>(I0->R) + sizeof(BatchJob<T>) +
+                         32 * 33 * sizeof(T));
     cudaFuncSetAttribute(k_pre4<T, LPP, CPL, NR, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     NucArgs<T> layout = make_args<T>(I0, max_slots);
@@ -1160,7 +1277,12 @@ static int pre4_batch_t(Batch* B, Instance* const* I, const DevPreOp* const* d_o
 int nuc_batch_pre(Batch* B, Instance* const* I, const DevPreOp* const* d_ops, const int* n_ops,
                   const int* n_slots, const int* model, double* const* d_gpart, int n) {
     if (n <= 0) return TL_OK;
-    TL_BATCH_DISPATCH(I[0], pre4_batch_t, B, I, d_ops, n_ops, n_slots, model, d_gpart, n);
+    if (I[0]->prec == kF32)
+        TL_PRE_DISPATCH_T(float, I[0], return pre4_batch_t, B, I, d_ops, n_ops, n_slots, model,
+                          d_gpart, n);
+    else
+        TL_PRE_DISPATCH_T(double, I[0], return pre4_batch_t, B, I, d_ops, n_ops, n_slots, model,
+                          d_gpart, n);
     return TL_OK;
 }
 
