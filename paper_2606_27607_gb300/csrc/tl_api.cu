@@ -412,7 +412,7 @@ int plan_post(Instance* I, const tl_op* ops, int n, PostPlan* plan, bool dry) {
             int pk = local(k, c);
             if (pk >= 0 && consumers[pk] == 1) sole_consumer[pk] = k;
         }
-    const int cap = max_slots(I);
+    const int cap = max_slots(I) / (use_nuc(I) ? nuc_post_ppl(I) : 1);
     std::vector<int> slot_of(n, -1), remaining(n, 0);
     for (int k = 0; k < n; ++k) remaining[k] = consumers[k];
     std::vector<int> free_slots;

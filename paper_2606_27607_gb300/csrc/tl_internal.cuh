@@ -18,7 +18,7 @@ constexpr int kMaxCat = 8;
 constexpr int kMaxStates = 64;
 constexpr int kMaxDq = 8;      // dQ/dtheta matrices kept per model
 constexpr int kColStride = 5;  // four-state matrices: 4 columns + row sums
-constexpr int kPadPatterns = 32;  // patterns are padded to a multiple of this
+constexpr int kPadPatterns = 64;  // patterns are padded to a multiple of this
 
 enum Prec { kF64 = 0, kF32 = 1, kTF32 = 2, kBF16X3 = 3 };
 
@@ -239,7 +239,8 @@ int nuc_lanes_main(const Instance* I);       // lanes per pattern (post, pre ker
 int nuc_tiles_main(const Instance* I);       // their tiles
 int nuc_lanes_pre(const Instance* I);        // lanes per pattern (pre-order kernel)
 int nuc_tiles_pre(const Instance* I);        // its tiles (= gradient partial columns)
-int nuc_smem_per_slot(const Instance* I);    // bytes per slot per warp
+int nuc_smem_per_slot(const Instance* I);    // bytes per slot per warp and pattern per lane
+int nuc_post_ppl(const Instance* I);         // patterns per lane (post-order kernel)
 int launch_post4(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots);
 int launch_root4(Instance* I, int root_kind, int root, int model, double* d_site,
                  double* d_part);

@@ -123,6 +123,15 @@ __device__ __forceinline__ V4<T> matTvec(const T* col, int cs, V4<T> u) {
     V4<T> c0 = ld4(col), c1 = ld4(col + cs), c2 = ld4(col + 2 * cs), c3 = ld4(col + 3 * cs);
     return {dot(c0, u), dot(c1, u), dot(c2, u), dot(c3, u)};
 }
+template <typename T>
+__device__ __forceinline__ V4<T> matvec_cols(V4<T> c0, V4<T> c1, V4<T> c2, V4<T> c3, V4<T> x) {
+    V4<T> r;
+    r.x = x.x * c0.x + x.y * c1.x + x.z * c2.x + x.w * c3.x;
+    r.y = x.x * c0.y + x.y * c1.y + x.z * c2.y + x.w * c3.y;
+    r.z = x.x * c0.z + x.y * c1.z + x.z * c2.z + x.w * c3.z;
+    r.w = x.x * c0.w + x.y * c1.w + x.z * c2.w + x.w * c3.w;
+    return r;
+}
 // The FP32 matvec as packed pairs, in the scalar chain's order (same bits).
 __device__ __forceinline__ V4<float> matvec_cols(V4<float> c0, V4<float> c1, V4<float> c2,
                                                  V4<float> c3, V4<float> x) {
@@ -319,13 +328,19 @@ __host__ __device__ constexpr size_t pipe_bytes(int R) {
 // BATCH: `a_` gives the shared-memory layout (the largest slot count of the
 // jobs, their common R) and the total tile count; each tile's arguments and
 // ops come from its job in `br`.
-template <typename T, int LPP, int CPL, int NR, bool BATCH>
+// PPL: patterns per lane. A warp tile is PPL sub-tiles of 32 / LPP
+// consecutive patterns; a lane computes the same categories of one pattern
+// in each, so the per-op work that does not depend on the pattern (op and
+// matrix fetches, matrix columns from shared memory, control) is shared by
+// PPL patterns.
+template <typename T, int LPP, int CPL, int NR, bool BATCH, int PPL>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ NucArgs<T> a_,
         const BatchRef<T> br) {
     constexpr int TP = 32 / LPP;
     // NR > 0: the category count is a compile-time constant
     constexpr bool kFull = NR > 0 && LPP * CPL == NR;
+    constexpr int SL = PPL * CPL;  // V4 values per lane in one slot
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r0 = lane % LPP, pp = lane / LPP;
@@ -334,14 +349,14 @@ k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ 
     bool act[CPL];
 #pragma unroll
     for (int j = 0; j < CPL; ++j) act[j] = kFull || (r0 + j * LPP < R);
-    V4<T>* slots = reinterpret_cast<V4<T>*>(smem_raw) + (size_t)warp * a_.n_slots * CPL * 32;
+    V4<T>* slots = reinterpret_cast<V4<T>*>(smem_raw) + (size_t)warp * a_.n_slots * SL * 32;
     int* sexp = reinterpret_cast<int*>(reinterpret_cast<V4<T>*>(smem_raw) +
-                                       (size_t)kWarpsPerBlock * a_.n_slots * CPL * 32) +
-                warp * a_.n_slots * 32;
+                                       (size_t)kWarpsPerBlock * a_.n_slots * SL * 32) +
+                warp * a_.n_slots * PPL * 32;
     unsigned char* pipe_base = reinterpret_cast<unsigned char*>(
         reinterpret_cast<int*>(reinterpret_cast<V4<T>*>(smem_raw) +
-                               (size_t)kWarpsPerBlock * a_.n_slots * CPL * 32) +
-        kWarpsPerBlock * a_.n_slots * 32);
+                               (size_t)kWarpsPerBlock * a_.n_slots * SL * 32) +
+        kWarpsPerBlock * a_.n_slots * PPL * 32);
     WarpPipe<DevPostOp, T, 2> pipe;
     pipe.obuf = reinterpret_cast<DevPostOp*>(pipe_base + (size_t)warp * pipe_bytes<DevPostOp, T, 2>(R));
     pipe.mbuf = reinterpret_cast<T*>(pipe.obuf + 3);
@@ -361,19 +376,31 @@ k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ 
             ops = static_cast<const DevPostOp*>(stage->ops);
             n_ops = stage->n_ops;
         }
-        const int p = tile * TP + pp;
-        const size_t off0 = ((size_t)r0 * a.Ppad + p) * 4;       // category r0
-        const size_t offj = (size_t)LPP * a.Ppad * 4;            // next category of this lane
-        V4<T> prev[CPL];
+        int p[PPL];
+        size_t off0[PPL];
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) prev[j] = zero;
-        int prev_cum = 0;
-        int ts[kAhead][2];
+        for (int i = 0; i < PPL; ++i) {
+            p[i] = (tile * PPL + i) * TP + pp;
+            off0[i] = ((size_t)r0 * a.Ppad + p[i]) * 4;  // category r0
+        }
+        const size_t offj = (size_t)LPP * a.Ppad * 4;    // next category of this lane
+        V4<T> prev[PPL][CPL];
+        int prev_cum[PPL];
 #pragma unroll
-        for (int j = 0; j < kAhead; ++j) {
-            const int4 h = op_head(ops, j, n_ops);
-            ts[j][0] = tip_state(a, h.x, h.z, p);
-            ts[j][1] = tip_state(a, h.y, h.w, p);
+        for (int i = 0; i < PPL; ++i) {
+            prev_cum[i] = 0;
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) prev[i][j] = zero;
+        }
+        int ts[kAhead][2][PPL];
+#pragma unroll
+        for (int k = 0; k < kAhead; ++k) {
+            const int4 h = op_head(ops, k, n_ops);
+#pragma unroll
+            for (int i = 0; i < PPL; ++i) {
+                ts[k][0][i] = tip_state(a, h.x, h.z, p[i]);
+                ts[k][1][i] = tip_state(a, h.y, h.w, p[i]);
+            }
         }
         // pipeline prologue: descriptors 0 and 1, then matrices of op 0
         __syncwarp();
@@ -392,86 +419,124 @@ k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ 
                 pipe.issue_mats(k + 1, n_ops, pipe.obuf[(k + 1) % 3].mat, a.mat, a.mat_stride, lane);
             cp_async_commit();
             const int4 hn = op_head(ops, k + kAhead, n_ops);
-            const int tn0 = tip_state(a, hn.x, hn.z, p), tn1 = tip_state(a, hn.y, hn.w, p);
+            int tn[2][PPL];
+#pragma unroll
+            for (int i = 0; i < PPL; ++i) {
+                tn[0][i] = tip_state(a, hn.x, hn.z, p[i]);
+                tn[1][i] = tip_state(a, hn.y, hn.w, p[i]);
+            }
             const DevPostOp op = pipe.obuf[k % 3];
             const T* mk = pipe.mats(k);
-            V4<T> acc[CPL];
-            int cum = 0;
+            V4<T> acc[PPL][CPL];
+            int cum[PPL];
+#pragma unroll
+            for (int i = 0; i < PPL; ++i) cum[i] = 0;
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
                 const T* mc = mk + c * pipe.matf + r0 * 4;
-                V4<T> v[CPL];
+                V4<T> v[PPL][CPL];
                 if (op.kind[c] == kTipStates) {
-                    const int col = tip_col((int8_t)ts[0][c]);
 #pragma unroll
-                    for (int j = 0; j < CPL; ++j)
-                        v[j] = act[j] ? lds4(mc + col * cs + j * LPP * 4) : zero;
+                    for (int i = 0; i < PPL; ++i) {
+                        const int col = tip_col((int8_t)ts[0][c][i]);
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j)
+                            v[i][j] = act[j] ? lds4(mc + col * cs + j * LPP * 4) : zero;
+                    }
                 } else {
-                    V4<T> x[CPL];
+                    V4<T> x[PPL][CPL];
                     const int si = op.slot_in[c];
                     if (si == kFromRegisters) {
 #pragma unroll
-                        for (int j = 0; j < CPL; ++j) x[j] = prev[j];
-                        cum += prev_cum;
+                        for (int i = 0; i < PPL; ++i) {
+#pragma unroll
+                            for (int j = 0; j < CPL; ++j) x[i][j] = prev[i][j];
+                            cum[i] += prev_cum[i];
+                        }
                     } else if (si >= 0) {
 #pragma unroll
-                        for (int j = 0; j < CPL; ++j) x[j] = slots[(si * CPL + j) * 32 + lane];
-                        cum += sexp[si * 32 + lane];
+                        for (int i = 0; i < PPL; ++i) {
+#pragma unroll
+                            for (int j = 0; j < CPL; ++j)
+                                x[i][j] = slots[((si * PPL + i) * CPL + j) * 32 + lane];
+                            cum[i] += sexp[(si * PPL + i) * 32 + lane];
+                        }
                     } else {
                         const T* b = (op.kind[c] == kTipPartials)
                                          ? a.tipbuf[op.child[c]]
                                          : a.pool + (size_t)op.child[c] * a.bstride;
 #pragma unroll
-                        for (int j = 0; j < CPL; ++j) x[j] = act[j] ? ld4(b + off0 + j * offj) : zero;
-                        if (op.kind[c] == kInternal)
-                            cum += a.epool[(size_t)op.child[c] * a.Ppad + p];
+                        for (int i = 0; i < PPL; ++i) {
+#pragma unroll
+                            for (int j = 0; j < CPL; ++j)
+                                x[i][j] = act[j] ? ld4(b + off0[i] + j * offj) : zero;
+                            if (op.kind[c] == kInternal)
+                                cum[i] += a.epool[(size_t)op.child[c] * a.Ppad + p[i]];
+                        }
                     }
 #pragma unroll
                     for (int j = 0; j < CPL; ++j) {
                         if (act[j]) {
-                            v[j] = matvec(mc + j * LPP * 4, cs, x[j]);
+                            // the columns once for all PPL patterns
+                            const T* col = mc + j * LPP * 4;
+                            const V4<T> c0 = lds4(col), c1 = lds4(col + cs), c2 = lds4(col + 2 * cs),
+                                        c3 = lds4(col + 3 * cs);
+#pragma unroll
+                            for (int i = 0; i < PPL; ++i) v[i][j] = matvec_cols(c0, c1, c2, c3, x[i][j]);
                         } else {
-                            v[j] = zero;
+#pragma unroll
+                            for (int i = 0; i < PPL; ++i) v[i][j] = zero;
                         }
                     }
                 }
 #pragma unroll
-                for (int j = 0; j < CPL; ++j) acc[j] = (c == 0) ? v[j] : mul(acc[j], v[j]);
+                for (int i = 0; i < PPL; ++i)
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j) acc[i][j] = (c == 0) ? v[i][j] : mul(acc[i][j], v[i][j]);
             }
 #pragma unroll
-            for (int j = 0; j + 1 < kAhead; ++j) {
-                ts[j][0] = ts[j + 1][0];
-                ts[j][1] = ts[j + 1][1];
-            }
-            ts[kAhead - 1][0] = tn0;
-            ts[kAhead - 1][1] = tn1;
-            if (a.rescale) {
-                T m = vmax(acc[0]);
+            for (int k2 = 0; k2 + 1 < kAhead; ++k2)
 #pragma unroll
-                for (int j = 1; j < CPL; ++j) m = fmax(m, vmax(acc[j]));
-#pragma unroll
-                for (int o = 1; o < LPP; o <<= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-                const int e = frexp_exp(m);
-                if (e != 0) {
-                    scale_by_pow2(acc, CPL, -e);
-                    cum += e;
+                for (int i = 0; i < PPL; ++i) {
+                    ts[k2][0][i] = ts[k2 + 1][0][i];
+                    ts[k2][1][i] = ts[k2 + 1][1][i];
                 }
-            }
-            if (op.store) {
-                T* d = a.pool + (size_t)op.dest * a.bstride + off0;
 #pragma unroll
-                for (int j = 0; j < CPL; ++j)
-                    if (act[j]) st4(d + j * offj, acc[j]);
-                if (r0 == 0) a.epool[(size_t)op.dest * a.Ppad + p] = cum;
-            }
-            if (op.slot_out >= 0) {
-#pragma unroll
-                for (int j = 0; j < CPL; ++j) slots[(op.slot_out * CPL + j) * 32 + lane] = acc[j];
-                sexp[op.slot_out * 32 + lane] = cum;
+            for (int i = 0; i < PPL; ++i) {
+                ts[kAhead - 1][0][i] = tn[0][i];
+                ts[kAhead - 1][1][i] = tn[1][i];
             }
 #pragma unroll
-            for (int j = 0; j < CPL; ++j) prev[j] = acc[j];
-            prev_cum = cum;
+            for (int i = 0; i < PPL; ++i) {
+                if (a.rescale) {
+                    T m = vmax(acc[i][0]);
+#pragma unroll
+                    for (int j = 1; j < CPL; ++j) m = fmax(m, vmax(acc[i][j]));
+#pragma unroll
+                    for (int o = 1; o < LPP; o <<= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+                    const int e = frexp_exp(m);
+                    if (e != 0) {
+                        scale_by_pow2(acc[i], CPL, -e);
+                        cum[i] += e;
+                    }
+                }
+                if (op.store) {
+                    T* d = a.pool + (size_t)op.dest * a.bstride + off0[i];
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j)
+                        if (act[j]) st4(d + j * offj, acc[i][j]);
+                    if (r0 == 0) a.epool[(size_t)op.dest * a.Ppad + p[i]] = cum[i];
+                }
+                if (op.slot_out >= 0) {
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j)
+                        slots[((op.slot_out * PPL + i) * CPL + j) * 32 + lane] = acc[i][j];
+                    sexp[(op.slot_out * PPL + i) * 32 + lane] = cum[i];
+                }
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) prev[i][j] = acc[i][j];
+                prev_cum[i] = cum[i];
+            }
         }
         cp_async_wait_all();
     }
@@ -924,6 +989,17 @@ int nuc_tiles(const Instance* I) { return nuc_tiles_for(I, nuc_lanes(I)); }
 int nuc_tiles_main(const Instance* I) { return nuc_tiles_for(I, nuc_lanes_main(I)); }
 int nuc_tiles_pre(const Instance* I) { return nuc_tiles_for(I, nuc_lanes_pre(I)); }
 
+// Patterns per lane of the post-order kernel: 2 (TL_POST_PPL=1 for one)
+// with one lane per pattern and four categories, else 1.
+int nuc_post_ppl(const Instance* I) {
+    static int env = -1;
+    if (env < 0) {
+        const char* s = getenv("TL_POST_PPL");
+        env = s ? atoi(s) : 2;
+    }
+    return (env == 2 && nuc_lanes_main(I) == 1 && I->R == 4) ? 2 : 1;
+}
+
 int nuc_smem_per_slot(const Instance* I) {
     return 32 * (nuc_cpl(I) * 4 * I->elt + (int)sizeof(int));
 }
@@ -1016,17 +1092,25 @@ static int grid_for(const Instance* I, K kernel, size_t smem, int n_tiles) {
         else TL_MAIN_DISPATCH_T(double, I, FN, __VA_ARGS__);               \
     } while (0)
 
-template <typename T, int LPP, int CPL, int NR>
-static void post4_t(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots) {
+template <typename T, int LPP, int CPL, int NR, int PPL>
+static void post4_tp(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots) {
     const size_t smem = (size_t)kWarpsPerBlock *
-                        (n_slots * nuc_smem_per_slot(I) + pipe_bytes<DevPostOp, T, 2>(I->R));
-    cudaFuncSetAttribute(k_post4<T, LPP, CPL, NR, false>,
+                        (n_slots * nuc_smem_per_slot(I) * PPL + pipe_bytes<DevPostOp, T, 2>(I->R));
+    cudaFuncSetAttribute(k_post4<T, LPP, CPL, NR, false, PPL>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     NucArgs<T> a = make_args<T>(I, n_slots);
-    a.n_tiles = nuc_tiles_for(I, LPP);
-    const int grid = grid_for(I, k_post4<T, LPP, CPL, NR, false>, smem, a.n_tiles);
-    k_post4<T, LPP, CPL, NR, false><<<grid, kWarpsPerBlock * 32, smem, I->stream>>>(
+    a.n_tiles = nuc_tiles_for(I, LPP) / PPL;
+    const int grid = grid_for(I, k_post4<T, LPP, CPL, NR, false, PPL>, smem, a.n_tiles);
+    k_post4<T, LPP, CPL, NR, false, PPL><<<grid, kWarpsPerBlock * 32, smem, I->stream>>>(
         d_ops, n_ops, a, BatchRef<T>{});
+}
+
+template <typename T, int LPP, int CPL, int NR>
+static void post4_t(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots) {
+    if constexpr (LPP == 1 && NR == 4) {
+        if (nuc_post_ppl(I) == 2) return post4_tp<T, LPP, CPL, NR, 2>(I, d_ops, n_ops, n_slots);
+    }
+    post4_tp<T, LPP, CPL, NR, 1>(I, d_ops, n_ops, n_slots);
 }
 
 int launch_post4(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots) {
@@ -1130,9 +1214,9 @@ static std::vector<int> by_work(const int* n_ops, int n) {
     return order;
 }
 
-template <typename T, int LPP, int CPL, int NR>
-static int post4_batch_t(Batch* B, Instance* const* I, const DevPostOp* const* d_ops,
-                         const int* n_ops, const int* n_slots, int n) {
+template <typename T, int LPP, int CPL, int NR, int PPL>
+static int post4_batch_tp(Batch* B, Instance* const* I, const DevPostOp* const* d_ops,
+                          const int* n_ops, const int* n_slots, int n) {
     const std::vector<int> order = by_work(n_ops, n);
     if (order.empty()) return TL_OK;
     std::vector<BatchJob<T>> jobs;
@@ -1142,7 +1226,7 @@ static int post4_batch_t(Batch* B, Instance* const* I, const DevPostOp* const* d
     for (int k : order) {
         BatchJob<T> j{};
         j.a = make_args<T>(I[k], n_slots[k]);
-        j.a.n_tiles = nuc_tiles_for(I[k], LPP);
+        j.a.n_tiles = nuc_tiles_for(I[k], LPP) / PPL;
         j.ops = d_ops[k];
         j.n_ops = n_ops[k];
         jobs.push_back(j);
@@ -1156,17 +1240,27 @@ static int post4_batch_t(Batch* B, Instance* const* I, const DevPostOp* const* d
     if (rc) return rc;
     Instance* I0 = I[order[0]];
     const size_t smem = (size_t)kWarpsPerBlock *
-                        (max_slots * nuc_smem_per_slot(I0) + pipe_bytes<DevPostOp, T, 2>(I0->R) +
-                         sizeof(BatchJob<T>));
-    cudaFuncSetAttribute(k_post4<T, LPP, CPL, NR, true>,
+                        (max_slots * nuc_smem_per_slot(I0) * PPL +
+                         pipe_bytes<DevPostOp, T, 2>(I0->R) + sizeof(BatchJob<T>));
+    cudaFuncSetAttribute(k_post4<T, LPP, CPL, NR, true, PPL>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     NucArgs<T> layout = make_args<T>(I0, max_slots);
     layout.n_tiles = (int)total;
-    const int grid = grid_for(I0, k_post4<T, LPP, CPL, NR, true>, smem, (int)total);
-    k_post4<T, LPP, CPL, NR, true><<<grid, kWarpsPerBlock * 32, smem, B->stream>>>(
+    const int grid = grid_for(I0, k_post4<T, LPP, CPL, NR, true, PPL>, smem, (int)total);
+    k_post4<T, LPP, CPL, NR, true, PPL><<<grid, kWarpsPerBlock * 32, smem, B->stream>>>(
         nullptr, 0, layout, br);
     B->launches += 1;
     return batch_cuda(B, cudaGetLastError(), "batched post-order kernel");
+}
+
+template <typename T, int LPP, int CPL, int NR>
+static int post4_batch_t(Batch* B, Instance* const* I, const DevPostOp* const* d_ops,
+                         const int* n_ops, const int* n_slots, int n) {
+    if constexpr (LPP == 1 && NR == 4) {
+        if (nuc_post_ppl(I[0]) == 2)
+            return post4_batch_tp<T, LPP, CPL, NR, 2>(B, I, d_ops, n_ops, n_slots, n);
+    }
+    return post4_batch_tp<T, LPP, CPL, NR, 1>(B, I, d_ops, n_ops, n_slots, n);
 }
 
 #define TL_BATCH_DISPATCH(I0, FN, ...)                                          \
