@@ -824,7 +824,7 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
             (rc = dev_alloc(I, &M.Vinv, sizeof(double) * SS, "Vinv")) ||
             (rc = dev_alloc(I, &M.lam, sizeof(double) * I->Spad, "lambda")) ||
             (rc = dev_alloc(I, &M.dQ, sizeof(double) * SS * kMaxDq, "dQ")) ||
-            (rc = dev_alloc(I, &M.G, sizeof(double) * SS * kMaxDq, "parameter basis")) ||
+            (rc = dev_alloc(I, &M.G, sizeof(double) * SS * kMaxDq * 2, "parameter basis")) ||
             (rc = dev_alloc(I, &M.piw, (size_t)I->elt * I->Spad, "pi copy")) ||
             (rc = dev_alloc(I, &M.Qw, (size_t)I->elt * SS, "Q copy")))
             return bail(rc);

@@ -130,11 +130,12 @@ struct ModelDev {
     double* Vinv = nullptr;   // [Spad][Spad]
     double* lam = nullptr;    // [Spad]
     double* dQ = nullptr;     // [kMaxDq][Spad][Spad]
-    double* G = nullptr;      // [kMaxDq][Spad][Spad]: Vinv dQ V
+    double* G = nullptr;      // [kMaxDq][Spad][Spad]: Vinv dQ V, then as much scratch
     void* piw = nullptr;      // pi in working precision [Spad]
     void* Qw = nullptr;       // Q in working precision [Spad][Spad]
     int n_dq = 0;
     bool ready = false;
+    bool basis_ready = false;  // G computed for the current V, Vinv, dQ
 };
 
 struct Instance {

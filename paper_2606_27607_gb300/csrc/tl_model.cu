@@ -151,67 +151,42 @@ __global__ void k_build_model(int kind, int S, int Spad, const double* __restric
     }
 }
 
-// Jacobi eigensystem of the symmetrised reversible Q. One block; A and U in
-// shared memory ([64][65] doubles each).
-__global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
-                        const double* __restrict__ pi, double* __restrict__ V,
-                        double* __restrict__ Vinv, double* __restrict__ lam,
-                        int* __restrict__ err) {
-    extern __shared__ double sm[];
-    constexpr int LD = 65;
-    double* A = sm;
-    double* U = sm + 64 * LD;
-    __shared__ double s_sq[64];
-    __shared__ double s_c[32], s_s[32];
-    __shared__ int s_p[32], s_q[32];
-    __shared__ double s_red[256];
-    __shared__ int s_done, s_conv;
+// One block-wide sweep set of cyclic Jacobi in tournament order on the
+// symmetric n x n matrix A (leading dimension LD), accumulating the
+// rotations into the columns of U. Each round rotates m / 2 disjoint pairs
+// at once. Stops after `settle` sweeps have ended with off(A)^2 <= done_tol *
+// diag(A)^2, or after max_sweeps; returns (to every thread) whether off(A)^2
+// <= conv_tol * diag(A)^2 at the end.
+template <typename T>
+__device__ bool jacobi_sweeps(T* A, T* U, int n, int LD, int max_sweeps, double done_tol,
+                              double conv_tol, int settle, T* s_c, T* s_s, int* s_p, int* s_q,
+                              double* s_red, int* s_flag) {
     const int t = threadIdx.x, nt = blockDim.x;
-    const int n = S;
     const int m = (n + 1) & ~1;  // players in the tournament (one dummy if n odd)
-
-    for (int i = t; i < n; i += nt) {
-        double p = pi[i];
-        s_sq[i] = sqrt(p);
-        if (!(p > 0.0)) err[0] = 2;
-    }
-    __syncthreads();
-    for (int idx = t; idx < n * n; idx += nt) {
-        int i = idx / n, j = idx % n;
-        // symmetrise: (D^1/2 Q D^-1/2 + transpose) / 2
-        double a = s_sq[i] * Q[i * Spad + j] / s_sq[j];
-        double b = s_sq[j] * Q[j * Spad + i] / s_sq[i];
-        A[i * LD + j] = 0.5 * (a + b);
-        U[i * LD + j] = (i == j) ? 1.0 : 0.0;
-    }
-    if (t == 0) {
-        s_done = 0;
-        s_conv = 0;
-    }
-    __syncthreads();
-
-    for (int sweep = 0; sweep < 40; ++sweep) {
+    int done = 0;
+    bool conv = false;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int round = 0; round < m - 1; ++round) {
             if (t < m / 2) {
                 int a = t, b = m - 1 - t;
                 int pa = (a == 0) ? 0 : ((a - 1 + round) % (m - 1)) + 1;
                 int pb = (b == 0) ? 0 : ((b - 1 + round) % (m - 1)) + 1;
                 int p = min(pa, pb), q = max(pa, pb);
-                double c = 1.0, s = 0.0;
+                T c = T(1), sn = T(0);
                 if (q < n) {
-                    double apq = A[p * LD + q];
-                    if (fabs(apq) > 1e-300) {
-                        double theta = (A[q * LD + q] - A[p * LD + p]) / (2.0 * apq);
-                        double tt = 1.0 / (fabs(theta) + sqrt(theta * theta + 1.0));
+                    T apq = A[p * LD + q];
+                    if (fabs((double)apq) > 1e-300) {
+                        T theta = (A[q * LD + q] - A[p * LD + p]) / (T(2) * apq);
+                        T tt = T(1) / (fabs(theta) + sqrt(theta * theta + T(1)));
                         if (theta < 0) tt = -tt;
-                        c = 1.0 / sqrt(tt * tt + 1.0);
-                        s = tt * c;
+                        c = T(1) / sqrt(tt * tt + T(1));
+                        sn = tt * c;
                     }
                 } else {
                     p = q = -1;
                 }
                 s_c[t] = c;
-                s_s[t] = s;
+                s_s[t] = sn;
                 s_p[t] = p;
                 s_q[t] = q;
             }
@@ -220,25 +195,25 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
             for (int idx = t; idx < (m / 2) * n; idx += nt) {
                 int k = idx / n, j = idx % n;
                 int p = s_p[k], q = s_q[k];
-                if (p < 0 || s_s[k] == 0.0) continue;
-                double c = s_c[k], s = s_s[k];
-                double ap = A[p * LD + j], aq = A[q * LD + j];
-                A[p * LD + j] = c * ap - s * aq;
-                A[q * LD + j] = s * ap + c * aq;
+                if (p < 0 || s_s[k] == T(0)) continue;
+                T c = s_c[k], sn = s_s[k];
+                T ap = A[p * LD + j], aq = A[q * LD + j];
+                A[p * LD + j] = c * ap - sn * aq;
+                A[q * LD + j] = sn * ap + c * aq;
             }
             __syncthreads();
             // columns: A <- A J, U <- U J
             for (int idx = t; idx < (m / 2) * n; idx += nt) {
                 int k = idx / n, i = idx % n;
                 int p = s_p[k], q = s_q[k];
-                if (p < 0 || s_s[k] == 0.0) continue;
-                double c = s_c[k], s = s_s[k];
-                double ap = A[i * LD + p], aq = A[i * LD + q];
-                A[i * LD + p] = c * ap - s * aq;
-                A[i * LD + q] = s * ap + c * aq;
-                double up = U[i * LD + p], uq = U[i * LD + q];
-                U[i * LD + p] = c * up - s * uq;
-                U[i * LD + q] = s * up + c * uq;
+                if (p < 0 || s_s[k] == T(0)) continue;
+                T c = s_c[k], sn = s_s[k];
+                T ap = A[i * LD + p], aq = A[i * LD + q];
+                A[i * LD + p] = c * ap - sn * aq;
+                A[i * LD + q] = sn * ap + c * aq;
+                T up = U[i * LD + p], uq = U[i * LD + q];
+                U[i * LD + p] = c * up - sn * uq;
+                U[i * LD + q] = sn * up + c * uq;
             }
             __syncthreads();
         }
@@ -246,7 +221,7 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
         double off = 0, dg = 0;
         for (int idx = t; idx < n * n; idx += nt) {
             int i = idx / n, j = idx % n;
-            double a = A[i * LD + j];
+            double a = (double)A[i * LD + j];
             if (i == j) dg += a * a;
             else off += a * a;
         }
@@ -264,16 +239,115 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
             if (t < w) s_red[t] += s_red[t + w];
             __syncthreads();
         }
-        // stop one sweep after the off-diagonal norm falls below 1e-15 of the
-        // diagonal norm (a rotation sweep then leaves it at rounding level)
         if (t == 0) {
-            if (offs <= 1e-30 * s_red[0]) s_done += 1;
-            s_conv = offs <= 1e-24 * s_red[0];
+            s_flag[0] = offs <= done_tol * s_red[0];
+            s_flag[1] = offs <= conv_tol * s_red[0];
         }
         __syncthreads();
-        if (s_done >= 2) break;
+        done += s_flag[0];
+        conv = s_flag[1];
+        __syncthreads();
+        if (done >= settle) break;
     }
-    if (t == 0 && !s_conv) err[0] = 3;
+    return conv;
+}
+
+// C = A^T B (transA) or A B for n x n blocks in shared memory (leading
+// dimension LD), FP64.
+__device__ void smem_gemm64(const double* A, const double* B, double* C, int n, int LD,
+                            bool transA) {
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx % n;
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k)
+            acc += (transA ? A[k * LD + i] : A[i * LD + k]) * B[k * LD + j];
+        C[i * LD + j] = acc;
+    }
+    __syncthreads();
+}
+
+// Eigensystem of the reversible Q through the symmetric form
+// A = D^1/2 Q D^-1/2 (D = diag(pi)), A = U diag(lambda) U^T, so
+// V = D^-1/2 U and Vinv = U^T D^1/2. One block, in two precisions: cyclic
+// Jacobi in FP32 brings A near diagonal at FP32 cost (FP64 issue is far
+// slower on this part); the FP32 rotations U32 are then made orthogonal to
+// FP64 accuracy by two Newton-Schulz steps U <- U (3 I - U^T U) / 2, A is
+// transformed to U^T A U in FP64, and FP64 Jacobi sweeps (accumulated onto
+// U) finish it, converging quadratically from the FP32 starting point.
+__global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
+                        const double* __restrict__ pi, double* __restrict__ V,
+                        double* __restrict__ Vinv, double* __restrict__ lam,
+                        int* __restrict__ err) {
+    extern __shared__ double sm[];
+    constexpr int LD = 65;
+    double* A = sm;                   // [64][LD] FP64
+    double* U = A + 64 * LD;          // [64][LD]
+    double* T1 = U + 64 * LD;         // [64][LD] scratch
+    double* T2 = T1 + 64 * LD;        // [64][LD] scratch
+    float* A32 = reinterpret_cast<float*>(T2 + 64 * LD);   // [64][LD]
+    float* U32 = A32 + 64 * LD;                            // [64][LD]
+    __shared__ double s_sq[64];
+    __shared__ double s_c[32], s_s[32];
+    __shared__ float s_cf[32], s_sf[32];
+    __shared__ int s_p[32], s_q[32];
+    __shared__ double s_red[256];
+    __shared__ int s_flag[2];
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int n = S;
+
+    for (int i = t; i < n; i += nt) {
+        double p = pi[i];
+        s_sq[i] = sqrt(p);
+        if (!(p > 0.0)) err[0] = 2;
+    }
+    __syncthreads();
+    for (int idx = t; idx < n * n; idx += nt) {
+        int i = idx / n, j = idx % n;
+        // symmetrise: (D^1/2 Q D^-1/2 + transpose) / 2
+        double a = s_sq[i] * Q[i * Spad + j] / s_sq[j];
+        double b = s_sq[j] * Q[j * Spad + i] / s_sq[i];
+        const double v = 0.5 * (a + b);
+        A[i * LD + j] = v;
+        A32[i * LD + j] = (float)v;
+        U32[i * LD + j] = (i == j) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    // FP32: until off(A)^2 <= 1e-12 diag(A)^2 (about FP32 rounding), 20 sweeps at most
+    jacobi_sweeps<float>(A32, U32, n, LD, 20, 1e-12, 1e-12, 1, s_cf, s_sf, s_p, s_q, s_red,
+                         s_flag);
+    // FP64 orthonormalisation of the FP32 rotations
+    for (int idx = t; idx < n * n; idx += nt) {
+        const int i = idx / n, j = idx % n;
+        U[i * LD + j] = (double)U32[i * LD + j];
+    }
+    __syncthreads();
+    for (int it = 0; it < 2; ++it) {
+        smem_gemm64(U, U, T1, n, LD, true);          // T1 = U^T U
+        for (int idx = t; idx < n * n; idx += nt) {
+            const int i = idx / n, j = idx % n;
+            T1[i * LD + j] = 0.5 * ((i == j ? 3.0 : 0.0) - T1[i * LD + j]);
+        }
+        __syncthreads();
+        smem_gemm64(U, T1, T2, n, LD, false);        // T2 = U (3 I - U^T U) / 2
+        for (int idx = t; idx < n * n; idx += nt) {
+            const int i = idx / n, j = idx % n;
+            U[i * LD + j] = T2[i * LD + j];
+        }
+        __syncthreads();
+    }
+    // A <- U^T A U in FP64, symmetrised
+    smem_gemm64(A, U, T1, n, LD, false);             // T1 = A U
+    smem_gemm64(U, T1, T2, n, LD, true);             // T2 = U^T A U
+    for (int idx = t; idx < n * n; idx += nt) {
+        const int i = idx / n, j = idx % n;
+        A[i * LD + j] = 0.5 * (T2[i * LD + j] + T2[j * LD + i]);
+    }
+    __syncthreads();
+    // FP64: stop one sweep after off(A)^2 <= 1e-30 diag(A)^2 (a rotation
+    // sweep then leaves it at rounding level); fail above 1e-24
+    const bool conv = jacobi_sweeps<double>(A, U, n, LD, 40, 1e-30, 1e-24, 2, s_c, s_s, s_p, s_q,
+                                            s_red, s_flag);
+    if (t == 0 && !conv) err[0] = 3;
     for (int idx = t; idx < Spad * Spad; idx += nt) {
         int i = idx / Spad, k = idx % Spad;
         double v = 0, vi = 0;
@@ -413,6 +487,8 @@ __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
     double* e = sm_tpm;              // [Spad]
     double* de = sm_tpm + 64;        // [Spad]
     double* Pm = sm_tpm + 128;       // [Spad*Spad] this matrix (for working copies)
+    double* Vi = Pm + Spad * Spad;   // [Spad*Spad] Vinv
+    double* W = Vi + Spad * Spad;    // [Spad*Spad] V diag(e) of the current pass
     const int b = blockIdx.x, r = blockIdx.y;
     const int t = threadIdx.x, nt = blockDim.x;
     const double rt = rates[r] * len[b];
@@ -422,17 +498,22 @@ __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
         e[k] = (k < S) ? expm1(lam[k] * rt) : 0.0;
         de[k] = (k < S) ? rates[r] * lam[k] * exp(lam[k] * rt) : 0.0;
     }
+    for (int idx = t; idx < Spad * Spad; idx += nt) Vi[idx] = Vinv[idx];
     __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
         const int slot = (pass == 0) ? pidx[b] : (dpidx ? dpidx[b] : -1);
         if (slot < 0) continue;
         const double* ev = (pass == 0) ? e : de;
+        // W = V diag(ev), rounded as the product V_ik ev_k was before each
+        // term's fused multiply-add
+        for (int idx = t; idx < Spad * Spad; idx += nt) W[idx] = V[idx] * ev[idx % Spad];
+        __syncthreads();
         double* out = mat64 + ((size_t)slot * R + r) * Spad * Spad;
         for (int idx = t; idx < Spad * Spad; idx += nt) {
             int i = idx / Spad, j = idx % Spad;
             double acc = 0.0;
             if (i < S && j < S)
-                for (int k = 0; k < S; ++k) acc += V[i * Spad + k] * ev[k] * Vinv[k * Spad + j];
+                for (int k = 0; k < S; ++k) acc += W[i * Spad + k] * Vi[k * Spad + j];
             if (pass == 0 && i == j && i < S) acc += 1.0;
             out[idx] = acc;
             Pm[idx] = acc;
@@ -487,7 +568,7 @@ int launch_build_model(Instance* I, int m, int kind, const double* d_params, int
 
 int launch_eigen_from_q(Instance* I, int m, bool check) {
     ModelDev& M = I->models[m];
-    const size_t smem = 2 * 64 * 65 * sizeof(double);
+    const size_t smem = 4 * 64 * 65 * sizeof(double) + 2 * 64 * 65 * sizeof(float);
     cudaFuncSetAttribute(k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_eigen<<<1, 256, smem, I->stream>>>(I->S, I->Spad, M.Q, M.pi, M.V, M.Vinv, M.lam, I->d_err);
     I->launches += 1;
@@ -520,7 +601,7 @@ int launch_model_working_copies(Instance* I, int m) {
     int rc = cuda_check(I, cudaGetLastError(), "model working copies");
     if (rc) return rc;
     if (I->prec == kTF32 && (rc = launch_q_tc(I, m))) return rc;
-    if ((rc = launch_param_basis(I, m))) return rc;
+    M.basis_ready = false;  // computed by the first parameter-derivative request
     M.ready = true;
     return TL_OK;
 }
@@ -531,17 +612,17 @@ int launch_update_matrices(Instance* I, int m, const int* d_pidx, const int* d_d
     ModelDev& M = I->models[m];
     const double* d_rates = I->d_tmp;  // rates staged by the caller at d_tmp[0..R)
     dim3 grid(count, I->R);
-    size_t smem = (128 + (size_t)I->Spad * I->Spad) * sizeof(double);
+    size_t smem = (128 + 3 * (size_t)I->Spad * I->Spad) * sizeof(double);
     int layout = (I->S == 4 && (I->prec == kF32 || I->prec == kF64)) ? 0
                  : (I->prec == kF64 ? 1 : (I->split ? 3 : 2));
     if (I->prec == kF64) {
-        cudaFuncSetAttribute(k_tpm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        cudaFuncSetAttribute(k_tpm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_tpm<double><<<grid, 256, smem, I->stream>>>(I->S, I->Spad, I->R, M.V, M.Vinv, M.lam,
                                                       d_pidx, d_dpidx, d_len, d_rates, I->d_mat64,
                                                       (double*)I->d_matw, I->matw_stride, layout,
                                                       nullptr);
     } else {
-        cudaFuncSetAttribute(k_tpm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        cudaFuncSetAttribute(k_tpm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_tpm<float><<<grid, 256, smem, I->stream>>>(I->S, I->Spad, I->R, M.V, M.Vinv, M.lam,
                                                      d_pidx, d_dpidx, d_len, d_rates, I->d_mat64,
                                                      (float*)I->d_matw, I->matw_stride, layout,
@@ -553,23 +634,33 @@ int launch_update_matrices(Instance* I, int m, const int* d_pidx, const int* d_d
 
 
 // G_k = Vinv dQ_k V for every parameter derivative of a model. One block per k.
-__global__ void k_param_basis(int S, int Spad, const double* __restrict__ V,
+// Two products of S^3 each, rows split over blockIdx.y: phase 0 writes
+// W_k = dQ_k V into G, phase 1 overwrites G row by row with Vinv W_k (each
+// block keeps W_k in shared memory, so rows of G can be written in place).
+constexpr int kBasisRowBlocks = 8;
+__global__ void k_param_basis(int S, int Spad, int phase, const double* __restrict__ V,
                               const double* __restrict__ Vinv, const double* __restrict__ dQ,
-                              double* __restrict__ G) {
+                              double* __restrict__ G, double* __restrict__ Wtmp) {
+    extern __shared__ double sm_basis[];
     const int k = blockIdx.x;
-    const double* D = dQ + (size_t)k * Spad * Spad;
-    double* out = G + (size_t)k * Spad * Spad;
-    for (int idx = threadIdx.x; idx < Spad * Spad; idx += blockDim.x) {
-        const int i = idx / Spad, j = idx % Spad;
+    const int rows = (S + kBasisRowBlocks - 1) / kBasisRowBlocks;
+    const int r0 = blockIdx.y * rows, r1 = min(S, r0 + rows);
+    const size_t SS = (size_t)Spad * Spad;
+    const double* L = phase == 0 ? dQ + k * SS : Vinv;   // left factor
+    const double* Rt = phase == 0 ? V : Wtmp + k * SS;   // right factor
+    double* out = phase == 0 ? Wtmp + k * SS : G + k * SS;
+    double* Rs = sm_basis;  // the right factor, [S][Spad]
+    for (int idx = threadIdx.x; idx < S * Spad; idx += blockDim.x) Rs[idx] = Rt[idx];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < (r1 - r0) * Spad; idx += blockDim.x) {
+        const int i = r0 + idx / Spad, j = idx % Spad;
         double acc = 0.0;
-        if (i < S && j < S)
-            for (int a = 0; a < S; ++a) {
-                double va = 0.0;
-                for (int b2 = 0; b2 < S; ++b2) va += D[a * Spad + b2] * V[b2 * Spad + j];
-                acc += Vinv[i * Spad + a] * va;
-            }
-        out[idx] = acc;
+        if (j < S)
+            for (int a = 0; a < S; ++a) acc += L[i * Spad + a] * Rs[a * Spad + j];
+        out[i * Spad + j] = acc;
     }
+    if (blockIdx.y == 0)
+        for (int idx = S * Spad + threadIdx.x; idx < Spad * Spad; idx += blockDim.x) out[idx] = 0.0;
 }
 
 // dP_r(t)/dtheta = V [G o Phi] Vinv with Phi_ij = rho t (e^{a_i} - e^{a_j}) / (a_i - a_j),
@@ -606,16 +697,21 @@ __global__ void k_param_tpm(int S, int Spad, int R, const double* __restrict__ V
         X[idx] = rt * G[idx] * phi;
     }
     __syncthreads();
-    // Pm = V X Vinv (via a row of V X at a time)
+    // Pm = (V X) Vinv: Y = V X first (in Pm's place), then Y Vinv
+    double* Y = X + 2 * (size_t)Spad * Spad;     // [Spad*Spad]
+    for (int idx = t; idx < Spad * Spad; idx += nt) {
+        const int i = idx / Spad, k = idx % Spad;
+        double vx = 0.0;
+        if (i < S && k < S)
+            for (int l = 0; l < S; ++l) vx += V[i * Spad + l] * X[l * Spad + k];
+        Y[idx] = vx;
+    }
+    __syncthreads();
     for (int idx = t; idx < Spad * Spad; idx += nt) {
         const int i = idx / Spad, j = idx % Spad;
         double acc = 0.0;
         if (i < S && j < S)
-            for (int k = 0; k < S; ++k) {
-                double vx = 0.0;
-                for (int l = 0; l < S; ++l) vx += V[i * Spad + l] * X[l * Spad + k];
-                acc += vx * Vinv[k * Spad + j];
-            }
+            for (int k = 0; k < S; ++k) acc += Y[i * Spad + k] * Vinv[k * Spad + j];
         Pm[idx] = acc;
         mat64[((size_t)slot * R + r) * Spad * Spad + idx] = acc;
     }
@@ -623,21 +719,35 @@ __global__ void k_param_tpm(int S, int Spad, int R, const double* __restrict__ V
     write_layout(Pm, slot, r, S, Spad, R, matw, matw_stride, layout, rowsum);
 }
 
+// G_k = Vinv dQ_k V, computed on first use after a model change (only the
+// substitution-parameter derivatives need it). W_k = dQ_k V goes to the
+// second half of the basis allocation ([2][kMaxDq][Spad][Spad]).
 int launch_param_basis(Instance* I, int m) {
     ModelDev& M = I->models[m];
-    if (M.n_dq == 0) return TL_OK;
-    k_param_basis<<<M.n_dq, 256, 0, I->stream>>>(I->S, I->Spad, M.V, M.Vinv, M.dQ, M.G);
-    I->launches += 1;
-    return cuda_check(I, cudaGetLastError(), "parameter basis");
+    if (M.n_dq == 0 || M.basis_ready) return TL_OK;
+    const size_t SS = (size_t)I->Spad * I->Spad;
+    const size_t smem = (size_t)I->S * I->Spad * sizeof(double);
+    cudaFuncSetAttribute(k_param_basis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(M.n_dq, kBasisRowBlocks);
+    double* W = M.G + SS * kMaxDq;
+    for (int phase = 0; phase < 2; ++phase)
+        k_param_basis<<<grid, 256, smem, I->stream>>>(I->S, I->Spad, phase, M.V, M.Vinv, M.dQ,
+                                                      M.G, W);
+    I->launches += 2;
+    int rc = cuda_check(I, cudaGetLastError(), "parameter basis");
+    if (!rc) M.basis_ready = true;
+    return rc;
 }
 
 int launch_param_matrices(Instance* I, int m, int param, const int* d_idx, const double* d_len,
                           int count) {
     if (count <= 0) return TL_OK;
     ModelDev& M = I->models[m];
+    int rc = launch_param_basis(I, m);
+    if (rc) return rc;
     const double* d_rates = I->d_tmp;
     dim3 grid(count, I->R);
-    const size_t smem = 2 * (size_t)I->Spad * I->Spad * sizeof(double);
+    const size_t smem = 3 * (size_t)I->Spad * I->Spad * sizeof(double);
     const int layout = (I->S == 4 && (I->prec == kF32 || I->prec == kF64)) ? 0
                        : (I->prec == kF64 ? 1 : (I->split ? 3 : 2));
     const double* G = M.G + (size_t)param * I->Spad * I->Spad;
