@@ -124,19 +124,24 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
 }
-// 16 consecutive 32-bit TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
+// 64 consecutive 32-bit TMEM columns of this thread's lane: one load, one
+// wait (the epilogue's latency is in these round trips, not in bandwidth).
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
+    uint32_t r[64];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15}, [%16];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st64(uint32_t taddr, const float* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64};\n"
+        ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31])), "r"(__float_as_uint(v[32])), "r"(__float_as_uint(v[33])), "r"(__float_as_uint(v[34])), "r"(__float_as_uint(v[35])), "r"(__float_as_uint(v[36])), "r"(__float_as_uint(v[37])), "r"(__float_as_uint(v[38])), "r"(__float_as_uint(v[39])), "r"(__float_as_uint(v[40])), "r"(__float_as_uint(v[41])), "r"(__float_as_uint(v[42])), "r"(__float_as_uint(v[43])), "r"(__float_as_uint(v[44])), "r"(__float_as_uint(v[45])), "r"(__float_as_uint(v[46])), "r"(__float_as_uint(v[47])), "r"(__float_as_uint(v[48])), "r"(__float_as_uint(v[49])), "r"(__float_as_uint(v[50])), "r"(__float_as_uint(v[51])), "r"(__float_as_uint(v[52])), "r"(__float_as_uint(v[53])), "r"(__float_as_uint(v[54])), "r"(__float_as_uint(v[55])), "r"(__float_as_uint(v[56])), "r"(__float_as_uint(v[57])), "r"(__float_as_uint(v[58])), "r"(__float_as_uint(v[59])), "r"(__float_as_uint(v[60])), "r"(__float_as_uint(v[61])), "r"(__float_as_uint(v[62])), "r"(__float_as_uint(v[63]))
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
 }
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;
@@ -252,6 +257,35 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
     unsigned items_done = 0;   // items with at least one product
 
     const int n_items = n_ops * a.n_tiles;
+    // thread 0: pairs loaded and pairs multiplied so far (both absolute)
+    unsigned produced_c = 0, consumed_c = 0;
+    // Load pair i of an item (operand c, category r) into stage g % kSt once
+    // the products that last read it are done; false if that wait gave up.
+    auto produce = [&](const TcOp& o, int q0, int i, unsigned g) -> bool {
+        const int s = g % kSt;
+        if (!mbar_wait(&empty[s], ((g / kSt) & 1) ^ 1)) {
+            abort_sh |= 1;
+            return false;
+        }
+        const bool m0 = o.kind[0] == kInternal || o.kind[0] == kTipPartials;
+        const int c = m0 ? (i < R ? 0 : 1) : 1;
+        const int r = i % R;
+        unsigned char* st = stages + s * kStB;
+        mbar_expect_tx(&full[s], kStB);
+        const int arow = (o.child[c] * R + r) * a.Ppad + q0;
+        const int brow = o.brow[c] + r * kTcN;
+        const CUtensorMap* am = o.kind[c] == kTipPartials ? &tm_tip : &tm_part;
+        tma_load_2d(st, am, 0, arow, &full[s]);
+        tma_load_2d(st + kAChunk, am, 32, arow, &full[s]);
+        tma_load_2d(st + 2 * kAChunk, &tm_mat, 0, brow, &full[s]);
+        tma_load_2d(st + 2 * kAChunk + kBChunk, &tm_mat, 32, brow, &full[s]);
+        if (SPLIT) {
+            const int lrow = brow + 2 * R * kTcN;
+            tma_load_2d(st + 2 * kAChunk + 2 * kBChunk, &tm_mat, 0, lrow, &full[s]);
+            tma_load_2d(st + 2 * kAChunk + 3 * kBChunk, &tm_mat, 32, lrow, &full[s]);
+        }
+        return true;
+    };
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int k = item / a.n_tiles, tile = item % a.n_tiles;
         const TcOp op = ops[k];
@@ -259,70 +293,63 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
         const bool mma[2] = {op.kind[0] == kInternal || op.kind[0] == kTipPartials,
                              op.kind[1] == kInternal || op.kind[1] == kTipPartials};
         const int n_pairs = (mma[0] + mma[1]) * R;
-        if (tid == 0 && n_pairs > 0) {
-            // software pipeline: produce pair i, consume pair i - (kStages - 1)
+        if (tid == 0) {
+            // Pairs are numbered across the CTA's items: pair g uses stage
+            // g % kSt. Up to kSt pairs are loaded ahead of the products; the
+            // first pairs of the next item are loaded before this item's
+            // epilogue, so their copies overlap it.
             bool ok = true;
-            int produced = 0, consumed = 0;
-            for (int i = 0; ok && i < n_pairs + kSt - 1; ++i) {
-                if (i < n_pairs) {
-                    const unsigned g = pairs_done + i;
-                    const int s = g % kSt;
-                    ok = mbar_wait(&empty[s], ((g / kSt) & 1) ^ 1);
-                    if (!ok) {
-                        abort_sh |= 1;
-                        break;
-                    }
-                    const int c = mma[0] ? (i < R ? 0 : 1) : 1;
-                    const int r = i % R;
-                    unsigned char* st = stages + s * kStB;
-                    mbar_expect_tx(&full[s], kStB);
-                    const int arow = (op.child[c] * R + r) * a.Ppad + p0;
-                    const int brow = op.brow[c] + r * kTcN;
-                    const CUtensorMap* am = op.kind[c] == kTipPartials ? &tm_tip : &tm_part;
-                    tma_load_2d(st, am, 0, arow, &full[s]);
-                    tma_load_2d(st + kAChunk, am, 32, arow, &full[s]);
-                    tma_load_2d(st + 2 * kAChunk, &tm_mat, 0, brow, &full[s]);
-                    tma_load_2d(st + 2 * kAChunk + kBChunk, &tm_mat, 32, brow, &full[s]);
-                    if (SPLIT) {
-                        const int lrow = brow + 2 * R * kTcN;
-                        tma_load_2d(st + 2 * kAChunk + 2 * kBChunk, &tm_mat, 0, lrow, &full[s]);
-                        tma_load_2d(st + 2 * kAChunk + 3 * kBChunk, &tm_mat, 32, lrow, &full[s]);
-                    }
-                    ++produced;
+            while (ok && n_pairs > 0 && consumed_c < pairs_done + n_pairs) {
+                while (ok && produced_c < pairs_done + n_pairs && produced_c < consumed_c + kSt) {
+                    ok = produce(op, p0, (int)(produced_c - pairs_done), produced_c);
+                    produced_c += ok;
                 }
-                const int j = i - (kSt - 1);
-                if (j >= 0) {
-                    const unsigned g = pairs_done + j;
-                    const int s = g % kSt;
-                    ok = mbar_wait(&full[s], (g / kSt) & 1);
-                    if (!ok) {
-                        abort_sh |= 2;
-                        break;
-                    }
-                    tc_fence_after();
-                    const int c = mma[0] ? (j < R ? 0 : 1) : 1;
-                    const int r = j % R;
-                    const uint32_t d = tmem + (uint32_t)(r * 2 * kTcN + c * kTcN);
-                    unsigned char* st = stages + s * kStB;
+                if (!ok) break;
+                const unsigned g = consumed_c;
+                const int s = g % kSt;
+                ok = mbar_wait(&full[s], (g / kSt) & 1);
+                if (!ok) {
+                    abort_sh |= 2;
+                    break;
+                }
+                tc_fence_after();
+                const int j = (int)(g - pairs_done);
+                const int c = mma[0] ? (j < R ? 0 : 1) : 1;
+                const int r = j % R;
+                const uint32_t d = tmem + (uint32_t)(r * 2 * kTcN + c * kTcN);
+                unsigned char* st = stages + s * kStB;
 #pragma unroll
-                    for (int ks = 0; ks < 8; ++ks) {
-                        const int chunk = ks >> 2, kin = (ks & 3) * 32;
-                        const uint64_t ad = sw128_desc(st + chunk * kAChunk + kin);
-                        const uint64_t bd = sw128_desc(st + 2 * kAChunk + chunk * kBChunk + kin);
-                        mma_tf32(d, ad, bd, ks > 0 ? 1u : 0u);
-                        if (SPLIT) {
-                            const uint64_t bl =
-                                sw128_desc(st + 2 * kAChunk + (2 + chunk) * kBChunk + kin);
-                            mma_tf32(d, ad, bl, 1u);
-                        }
+                for (int ks = 0; ks < 8; ++ks) {
+                    const int chunk = ks >> 2, kin = (ks & 3) * 32;
+                    const uint64_t ad = sw128_desc(st + chunk * kAChunk + kin);
+                    const uint64_t bd = sw128_desc(st + 2 * kAChunk + chunk * kBChunk + kin);
+                    mma_tf32(d, ad, bd, ks > 0 ? 1u : 0u);
+                    if (SPLIT) {
+                        const uint64_t bl =
+                            sw128_desc(st + 2 * kAChunk + (2 + chunk) * kBChunk + kin);
+                        mma_tf32(d, ad, bl, 1u);
                     }
-                    mma_commit(&empty[s]);
-                    ++consumed;
+                }
+                mma_commit(&empty[s]);
+                ++consumed_c;
+            }
+            if (n_pairs > 0) mma_commit(&done);
+            // the next item's first pairs
+            const int nxt = item + gridDim.x;
+            if (ok && nxt < n_items) {
+                const TcOp opn = ops[nxt / a.n_tiles];
+                const int p0n = (nxt % a.n_tiles) * kTcM;
+                const bool mn0 = opn.kind[0] == kInternal || opn.kind[0] == kTipPartials;
+                const bool mn1 = opn.kind[1] == kInternal || opn.kind[1] == kTipPartials;
+                const unsigned base = pairs_done + n_pairs;
+                const unsigned pn = (unsigned)((mn0 + mn1) * R);
+                while (ok && produced_c < base + pn && produced_c < base + kSt) {
+                    ok = produce(opn, p0n, (int)(produced_c - base), produced_c);
+                    produced_c += ok;
                 }
             }
-            mma_commit(&done);
-            produced_sh = pairs_done + produced;
-            consumed_sh = pairs_done + consumed;
+            produced_sh = produced_c;
+            consumed_sh = consumed_c;
         }
         __syncthreads();
         bool fail = abort_sh != 0;
@@ -348,53 +375,58 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                 amb[c] = !(s >= 0 && s < a.S);
                 sidx[c] = s;
             }
-        // 16 values (states 16q..16q+15, category r) of operand c
-        auto chunk = [&](int c, int r, int q, float* v) {
+        // all 64 values (category r) of operand c: its accumulator columns,
+        // or the tip's P^T row (+ the lo row with split matrices), or the row
+        // sums of P for an ambiguous code; the row loads are issued together
+        auto operand64 = [&](int c, int r, float* v) {
             if (mma[c]) {
-                tmem_ld16(lane_base + (uint32_t)(r * 2 * kTcN + c * kTcN + q * 16), v);
-            } else {
-                // the tip's column of P (row of P^T), or the row sums of P
-                const int slot_base = op.look[c];
-                const float* src = amb[c] ? a.rowsum + (size_t)(slot_base / ((SPLIT ? 4 : 2) * R * kTcN * kTcN)) * R * kTcN +
-                                                (size_t)r * kTcN + q * 16
-                                          : a.matw + (size_t)slot_base + (size_t)r * kTcN * kTcN +
-                                                (size_t)sidx[c] * kTcN + q * 16;
-                const float4* s4 = reinterpret_cast<const float4*>(src);
+                tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN + c * kTcN), v);
+                return;
+            }
+            const int slot_base = op.look[c];
+            const float* src =
+                amb[c] ? a.rowsum + (size_t)(slot_base / ((SPLIT ? 4 : 2) * R * kTcN * kTcN)) * R * kTcN +
+                             (size_t)r * kTcN
+                       : a.matw + (size_t)slot_base + (size_t)r * kTcN * kTcN + (size_t)sidx[c] * kTcN;
+            const float4* s4 = reinterpret_cast<const float4*>(src);
+            float4 f[16];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float4 f = __ldg(s4 + u);
-                    v[4 * u] = f.x;
-                    v[4 * u + 1] = f.y;
-                    v[4 * u + 2] = f.z;
-                    v[4 * u + 3] = f.w;
-                }
-                if (SPLIT && !amb[c]) {  // + the lo term (row sums already hold hi + lo)
-                    const float4* l4 = reinterpret_cast<const float4*>(src + kLoFloats);
+            for (int u = 0; u < 16; ++u) f[u] = __ldg(s4 + u);
+            if (SPLIT && !amb[c]) {
+                const float4* l4 = reinterpret_cast<const float4*>(src + kLoFloats);
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const float4 f = __ldg(l4 + u);
-                        v[4 * u] += f.x;
-                        v[4 * u + 1] += f.y;
-                        v[4 * u + 2] += f.z;
-                        v[4 * u + 3] += f.w;
-                    }
+                for (int u = 0; u < 16; ++u) {
+                    const float4 l = __ldg(l4 + u);
+                    f[u].x += l.x;
+                    f[u].y += l.y;
+                    f[u].z += l.z;
+                    f[u].w += l.w;
                 }
             }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                v[4 * u] = f[u].x;
+                v[4 * u + 1] = f[u].y;
+                v[4 * u + 2] = f[u].z;
+                v[4 * u + 3] = f[u].w;
+            }
         };
-        auto qvals = [&](int r, int q, float* v) {  // parent pre-order partial (pre1)
+        auto qvals64 = [&](int r, float* v) {  // parent pre-order partial (pre1), category r
             if (op.qin < 0) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = (float)a.pi[q * 16 + i];
+                for (int i = 0; i < 64; ++i) v[i] = (float)a.pi[i];
             } else {
                 const float4* s4 = reinterpret_cast<const float4*>(
-                    a.pool + (size_t)op.qin * a.bstride + ((size_t)r * a.Ppad + p) * kTcN + q * 16);
+                    a.pool + (size_t)op.qin * a.bstride + ((size_t)r * a.Ppad + p) * kTcN);
+                float4 f[16];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float4 f = s4[u];
-                    v[4 * u] = f.x;
-                    v[4 * u + 1] = f.y;
-                    v[4 * u + 2] = f.z;
-                    v[4 * u + 3] = f.w;
+                for (int u = 0; u < 16; ++u) f[u] = s4[u];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    v[4 * u] = f[u].x;
+                    v[4 * u + 1] = f[u].y;
+                    v[4 * u + 2] = f[u].z;
+                    v[4 * u + 3] = f[u].w;
                 }
             }
         };
@@ -431,104 +463,117 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
             int cum = 0;
             for (int c = 0; c < 2; ++c)
                 if (op.kind[c] == kInternal) cum += a.epool[(size_t)op.child[c] * a.Ppad + p];
+            // pass 1: the products of all categories and their maximum; each
+            // category's products replace operand 0's accumulator in TMEM
             float m = 0.f;
-            for (int r = 0; r < R; ++r)
-                for (int q = 0; q < 4; ++q) {
-                    float x[16], y[16];
-                    chunk(0, r, q, x);
-                    chunk(1, r, q, y);
+            for (int r = 0; r < R; ++r) {
+                float x[64], y[64];
+                operand64(0, r, x);
+                operand64(1, r, y);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) m = fmaxf(m, x[i] * y[i]);
+                for (int i = 0; i < 64; ++i) {
+                    x[i] *= y[i];
+                    m = fmaxf(m, x[i]);
                 }
+                tmem_st64(lane_base + (uint32_t)(r * 2 * kTcN), x);
+            }
             float f1 = 1.f, f2 = 1.f;
             if (a.rescale) cum += scale_of(m, &f1, &f2);
+            // pass 2: rescale, round to TF32, store
             float* dst = a.pool + (size_t)op.dest * a.bstride + (size_t)p * kTcN;
-            for (int r = 0; r < R; ++r)
-                for (int q = 0; q < 4; ++q) {
-                    float x[16], y[16];
-                    chunk(0, r, q, x);
-                    chunk(1, r, q, y);
+            for (int r = 0; r < R; ++r) {
+                float z[64];
+                tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN), z);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) x[i] *= y[i];
-                    store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, x, f1, f2);
-                }
+                for (int q = 0; q < 4; ++q)
+                    store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, z + 16 * q, f1, f2);
+            }
             a.epool[(size_t)op.dest * a.Ppad + p] = cum;
         } else if (MODE == kPre1) {
-            // den and the per-pattern maxima of u_a = q o v_b, u_b = q o v_a
-            float den = 0.f, mu[2] = {0.f, 0.f};
+            // pass 1 over categories: den, the maxima of u_a = q o v_b and
+            // u_b = q o v_a, tip numerators u_c . dP_c[:, s]; u of internal
+            // children replaces their accumulators in TMEM
+            float den = 0.f, mu[2] = {0.f, 0.f}, num[2] = {0.f, 0.f};
+            const bool tipg[2] = {op.kind[0] == kTipStates && op.edge[0] >= 0,
+                                  op.kind[1] == kTipStates && op.edge[1] >= 0};
             for (int r = 0; r < R; ++r) {
+                float x[64], y[64];
+                operand64(0, r, x);
+                operand64(1, r, y);
                 float dr = 0.f;
-                for (int q = 0; q < 4; ++q) {
-                    float x[16], y[16], z[16];
-                    chunk(0, r, q, x);
-                    chunk(1, r, q, y);
-                    qvals(r, q, z);
+                {
+                    float z[64];
+                    qvals64(r, z);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        dr += z[i] * x[i] * y[i];
-                        mu[0] = fmaxf(mu[0], z[i] * y[i]);
-                        mu[1] = fmaxf(mu[1], z[i] * x[i]);
+                    for (int i = 0; i < 64; ++i) {
+                        const float va = x[i], vb = y[i];
+                        dr += z[i] * va * vb;
+                        x[i] = z[i] * vb;  // u_a
+                        y[i] = z[i] * va;  // u_b
+                        mu[0] = fmaxf(mu[0], x[i]);
+                        mu[1] = fmaxf(mu[1], y[i]);
                     }
                 }
                 den += a.catw[r] * dr;
-            }
-            for (int c = 0; c < 2; ++c) {
-                if (op.kind[c] == kTipStates && op.edge[c] >= 0) {
-                    // numerator u_c . dP_c[:, s] (a row of dP^T); an ambiguous
-                    // code gives the row sums of dP, which are zero. Every
-                    // thread runs the loop: chunk() may issue a warp-collective
-                    // tcgen05.ld for the sibling.
-                    float num = 0.f;
+                for (int c = 0; c < 2; ++c) {
+                    if (!tipg[c]) continue;
+                    // u_c . (a row of dP^T); an ambiguous code gives the row
+                    // sums of dP, which are zero
                     const int srow = amb[c] ? 0 : sidx[c];
-                    for (int r = 0; r < R; ++r) {
-                        float nr = 0.f;
-                        for (int q = 0; q < 4; ++q) {
-                            float sib[16], z[16];
-                            chunk(1 - c, r, q, sib);
-                            qvals(r, q, z);
-                            const float4* d4 = reinterpret_cast<const float4*>(
-                                a.matw + (size_t)op.dlook[c] + (size_t)r * kTcN * kTcN +
-                                (size_t)srow * kTcN + q * 16);
+                    const float4* d4 = reinterpret_cast<const float4*>(
+                        a.matw + (size_t)op.dlook[c] + (size_t)r * kTcN * kTcN + (size_t)srow * kTcN);
+                    const float* uc = c == 0 ? x : y;
+                    float nr = 0.f;
+#pragma unroll
+                    for (int g4 = 0; g4 < 4; ++g4) {
+                        float4 f[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) f[u] = __ldg(d4 + 4 * g4 + u);
+                        if (SPLIT) {
 #pragma unroll
                             for (int u = 0; u < 4; ++u) {
-                                float4 f = __ldg(d4 + u);
-                                if (SPLIT) {
-                                    const float4 l = __ldg(d4 + u + kLoFloats / 4);
-                                    f.x += l.x;
-                                    f.y += l.y;
-                                    f.z += l.z;
-                                    f.w += l.w;
-                                }
-                                nr += z[4 * u] * sib[4 * u] * f.x + z[4 * u + 1] * sib[4 * u + 1] * f.y +
-                                      z[4 * u + 2] * sib[4 * u + 2] * f.z +
-                                      z[4 * u + 3] * sib[4 * u + 3] * f.w;
+                                const float4 l = __ldg(d4 + 4 * g4 + u + kLoFloats / 4);
+                                f[u].x += l.x;
+                                f[u].y += l.y;
+                                f[u].z += l.z;
+                                f[u].w += l.w;
                             }
                         }
-                        num += a.catw[r] * nr;
-                    }
-                    if (amb[c]) num = 0.f;
-                    const float g = block_sum128(wp * (num / den), red);
-                    if (tid == 0) a.gpart[(size_t)op.edge[c] * a.n_tiles + tile] = (double)g;
-                }
-                if (op.uout[c] >= 0) {
-                    float f1, f2;
-                    const int e = scale_of(mu[c], &f1, &f2);
-                    float* dst = a.pool + (size_t)op.uout[c] * a.bstride + (size_t)p * kTcN;
-                    for (int r = 0; r < R; ++r)
-                        for (int q = 0; q < 4; ++q) {
-                            float sib[16], z[16];
-                            chunk(1 - c, r, q, sib);
-                            qvals(r, q, z);
 #pragma unroll
-                            for (int i = 0; i < 16; ++i) z[i] *= sib[i];
-                            store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, z, f1, f2);
+                        for (int u = 0; u < 4; ++u) {
+                            const int b = 16 * g4 + 4 * u;
+                            nr += uc[b] * f[u].x + uc[b + 1] * f[u].y + uc[b + 2] * f[u].z +
+                                  uc[b + 3] * f[u].w;
                         }
-                    // the child's ratio denominator carries the same scale as u
-                    float d = den;
-                    if (e != 0) d = (-e >= -126 && -e <= 126) ? den * pow2f(-e)
-                                                             : den * pow2f(-e / 2) * pow2f(-e - (-e / 2));
-                    a.epool[(size_t)op.uout[c] * a.Ppad + p] = __float_as_int(d);
+                    }
+                    num[c] += a.catw[r] * nr;
                 }
+                if (op.uout[0] >= 0) tmem_st64(lane_base + (uint32_t)(r * 2 * kTcN), x);
+                if (op.uout[1] >= 0) tmem_st64(lane_base + (uint32_t)(r * 2 * kTcN + kTcN), y);
+            }
+            for (int c = 0; c < 2; ++c) {
+                if (!tipg[c]) continue;
+                const float g = block_sum128(wp * ((amb[c] ? 0.f : num[c]) / den), red);
+                if (tid == 0) a.gpart[(size_t)op.edge[c] * a.n_tiles + tile] = (double)g;
+            }
+            // pass 2: each internal child's u, rescaled, to its pre buffer;
+            // its ratio denominator carries the same scale as u
+            for (int c = 0; c < 2; ++c) {
+                if (op.uout[c] < 0) continue;
+                float f1, f2;
+                const int e = scale_of(mu[c], &f1, &f2);
+                float* dst = a.pool + (size_t)op.uout[c] * a.bstride + (size_t)p * kTcN;
+                for (int r = 0; r < R; ++r) {
+                    float u[64];
+                    tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN + c * kTcN), u);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, u + 16 * q, f1, f2);
+                }
+                float d = den;
+                if (e != 0) d = (-e >= -126 && -e <= 126) ? den * pow2f(-e)
+                                                         : den * pow2f(-e / 2) * pow2f(-e - (-e / 2));
+                a.epool[(size_t)op.uout[c] * a.Ppad + p] = __float_as_int(d);
             }
         } else {  // kPre2: operand 0 = q_c = u_c P_c (B = P^T), operand 1 = Q x_c
                   // (or dP x_c for a general derivative, paired with u_c)
@@ -536,27 +581,25 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
             const float* ub = a.pool + (size_t)op.dest * a.bstride + (size_t)p * kTcN;
             float num = 0.f, m = 0.f;
             for (int r = 0; r < R; ++r) {
+                float x[64], y[64];
+                tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN), x);
+                tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN + kTcN), y);
                 float nr = 0.f;
-                for (int q = 0; q < 4; ++q) {
-                    float x[16], y[16];
-                    chunk(0, r, q, x);
-                    chunk(1, r, q, y);
-                    if (a.dgen) {
-                        const float4* u4 =
-                            reinterpret_cast<const float4*>(ub + (size_t)r * a.Ppad * kTcN + q * 16);
+                if (a.dgen) {
+                    const float4* u4 = reinterpret_cast<const float4*>(ub + (size_t)r * a.Ppad * kTcN);
+                    float4 f[16];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const float4 f = u4[u];
-                            nr += f.x * y[4 * u] + f.y * y[4 * u + 1] + f.z * y[4 * u + 2] +
-                                  f.w * y[4 * u + 3];
-                        }
-                    } else {
+                    for (int u = 0; u < 16; ++u) f[u] = u4[u];
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) nr += x[i] * y[i];
-                    }
+                    for (int u = 0; u < 16; ++u)
+                        nr += f[u].x * y[4 * u] + f[u].y * y[4 * u + 1] + f[u].z * y[4 * u + 2] +
+                              f[u].w * y[4 * u + 3];
+                } else {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) m = fmaxf(m, x[i]);
+                    for (int i = 0; i < 64; ++i) nr += x[i] * y[i];
                 }
+#pragma unroll
+                for (int i = 0; i < 64; ++i) m = fmaxf(m, x[i]);
                 num += a.catw[r] * (a.dgen ? 1.f : a.rates[r]) * nr;
             }
             if (op.edge[0] >= 0) {
@@ -566,12 +609,13 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
             float f1, f2;
             scale_of(m, &f1, &f2);
             float* dst = a.pool + (size_t)op.dest * a.bstride + (size_t)p * kTcN;
-            for (int r = 0; r < R; ++r)
-                for (int q = 0; q < 4; ++q) {
-                    float x[16];
-                    chunk(0, r, q, x);
-                    store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, x, f1, f2);
-                }
+            for (int r = 0; r < R; ++r) {
+                float x[64];
+                tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN), x);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, x + 16 * q, f1, f2);
+            }
         }
         (void)real;
         tc_fence_before();
