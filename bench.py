@@ -219,11 +219,16 @@ def tf32_peak() -> tuple[float, str]:
         return 0.5 * 1900.0, "fallback bf16 x 1/2"
 
 
-def codon_line(steps: int, warmup: int, taxa: int = 0, patterns: int = 0) -> dict:
-    """GY94 128 taxa x 20,000 patterns on the tensor-core (TF32) path: one
-    step = model + eigensystem, P and dP/dt, post-order, root logL, pre-order
-    gradient. Algorithmic FLOPs count the contractions of internal children
-    only (padded 64 x 64 per category): post 1, gradient 3 per child."""
+def codon_line(steps: int, warmup: int, taxa: int = 0, patterns: int = 0,
+               prec: str = "tf32") -> dict:
+    """GY94 128 taxa x 20,000 patterns on the tensor-core path (TF32, or
+    "tf32x2": matrices split into two TF32 terms): one step = model +
+    eigensystem, P and dP/dt, post-order, root logL, pre-order gradient.
+    Algorithmic FLOPs count the contractions of internal children only
+    (padded 64 x 64 per category): post 1, gradient 3 per child (twice that
+    with split matrices). Algorithmic bytes of the post-order pass: each
+    internal child's partials read once, every internal node's partials and
+    exponents written once, tip states read once."""
     import numpy as np
     import torch
 
@@ -237,7 +242,7 @@ def codon_line(steps: int, warmup: int, taxa: int = 0, patterns: int = 0) -> dic
     w = synth.workload("gy94_128x20k", **over)
     N, P = w.tree.n_tips, w.n_patterns
     stream = torch.cuda.current_stream()
-    tl = TreeLikelihood(N, P, 61, 4, "tf32", stream=stream.cuda_stream)
+    tl = TreeLikelihood(N, P, 61, 4, prec, stream=stream.cuda_stream)
     inst = tl.inst
     tl.set_tips(w.tips)
     tl.set_model("gy94", w.params, w.freqs)
@@ -284,17 +289,26 @@ def codon_line(steps: int, warmup: int, taxa: int = 0, patterns: int = 0) -> dic
     ms = a.elapsed_time(b) / steps
     k_ms = {k: statistics.mean(x.elapsed_time(y) for x, y in ev[k]) for k in ev}
     n_int_children = N - 2
-    f_post = n_int_children * 4 * 2 * 64 * 64 * P
+    mult = 2 if prec == "tf32x2" else 1
+    f_post = mult * n_int_children * 4 * 2 * 64 * 64 * P
     f_pre = 3 * f_post
     peak, src = tf32_peak()
+    hbm, hsrc = peaks()
+    ppad = (P + 127) // 128 * 128
+    b_post = ppad * (n_int_children * 4 * 256 + (N - 1) * (4 * 256 + 4) + N)
     logl = float(d_out[0].item())
     tl.close()
-    return {"workload": f"gy94_{N}x{P}", "precision": "tf32 tcgen05, fp32 accumulate",
+    return {"workload": f"gy94_{N}x{P}",
+            "precision": (f"{prec} tcgen05" + (" (P = P_hi + P_lo, two products)"
+                                               if prec == "tf32x2" else "") + ", fp32 accumulate"),
             "value": P * (N - 1) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
             "grad_evals_per_s": 1e3 / ms, "logL": logl,
             "kernels": {k: {"ms": k_ms[k],
                             "TFLOP/s": (f_post if k == "post" else f_pre) / (k_ms[k] * 1e-3) / 1e12}
                         for k in k_ms},
+            "hbm": {"kernel": "k_tc<post>", "algorithmic_bytes": b_post,
+                    "achieved": b_post / (k_ms["post"] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": b_post / (k_ms["post"] * 1e-3) / 1e9 / hbm, "peak_source": hsrc},
             "roofline": {"bound": "tensor", "kernel": "k_tc<post> (tcgen05 kind::tf32)",
                          "achieved": f_post / (k_ms["post"] * 1e-3) / 1e12, "peak": peak,
                          "unit": "TFLOP/s",
@@ -430,7 +444,7 @@ def serving_line(args) -> dict:
                 "p50_service_s": _pct(base_lat, 50), "p99_service_s": _pct(base_lat, 99)}
     return {"metric": "serving requests/s and p50/p99 latency (s) at offered load",
             "value": capacity, "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
-            "dtype": "f32 (4-state), tf32 (codon)", "data": "synthetic",
+            "dtype": "f32 (4-state), tf32x2 (codon)", "data": "synthetic",
             "config": {"workload": "serving", "requests": len(reqs), "chains": len(chains),
                        "codon_requests": int(n_codon),
                        "gradient_requests": int(sum(r.gradient for r in reqs)),
@@ -460,7 +474,8 @@ def main() -> None:
         from paper_2606_27607_gb300 import build
         build.build()
         torch.cuda.set_device(0)
-        print(json.dumps(codon_line(args.steps, args.warmup, args.codon_taxa, args.codon_patterns)))
+        print(json.dumps(codon_line(args.steps, args.warmup, args.codon_taxa, args.codon_patterns,
+                                    os.environ.get("TL_CODON_PREC", "tf32"))))
         return
 
     import numpy as np
@@ -624,10 +639,11 @@ def main() -> None:
             "algorithmic_bytes": alg[dom], "ms": k_ms[dom],
             "other": {k: {"ms": k_ms[k], "GB/s": alg[k] / (k_ms[k] * 1e-3) / 1e9} for k in k_ms}}
 
-    codon = None
+    codon = codon_split = None
     if not args.no_codon and world == 1:
         try:
             codon = codon_line(max(5, args.steps // 20), 3)
+            codon_split = codon_line(max(5, args.steps // 20), 3, prec="tf32x2")
         except Exception as exc:  # reported, not fatal
             codon = {"error": str(exc)[:300]}
 
@@ -652,7 +668,7 @@ def main() -> None:
                        "parallelism": f"patterns, weak x{world}"},
             "grad_evals_per_s": world * 1e3 / ms, "logL": logl, "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches) * args.steps, "gpu_launches_per_step": int(launches),
-            "roofline": roof, "cpu_baseline": cpu, "codon": codon}
+            "roofline": roof, "cpu_baseline": cpu, "codon": codon, "codon_split": codon_split}
     print(json.dumps(line), flush=True)
     tl.close()
     if dist:
