@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "tl_internal.cuh"
 
@@ -112,25 +113,60 @@ using namespace tl;
 // ---------------------------------------------------------------------------
 namespace {
 
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// instance's stream) from the device's default pool, which is told to keep
+// freed memory: creating and destroying instances (a server admitting and
+// evicting them) then reuses memory without synchronising the device.
+void keep_pool_memory(int dev) {
+    static std::mutex mu;
+    static std::vector<int> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done.push_back(dev);
+}
+
 template <typename P>
 int dev_alloc(Instance* I, P** p, size_t bytes, const char* what) {
+    keep_pool_memory(I->device);
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    cudaError_t e = cudaMallocAsync(&q, bytes ? bytes : 16, I->stream);
+    if (e == cudaErrorMemoryAllocation) {
+        // the pool may hold freed blocks too small or too scattered for this
+        // request: let every pending free complete, return unused memory to
+        // the device and try once more
+        cudaGetLastError();
+        cudaDeviceSynchronize();
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, I->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+        e = cudaMallocAsync(&q, bytes ? bytes : 16, I->stream);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(I, TL_ERR_OOM, "cudaMalloc(%zu bytes) for %s failed: %s", bytes, what,
-                    cudaGetErrorString(e));
+        return fail(I, TL_ERR_OOM, "device allocation of %zu bytes for %s failed: %s", bytes,
+                    what, cudaGetErrorString(e));
     }
     I->bytes += bytes;
     *p = reinterpret_cast<P*>(q);
     return TL_OK;
 }
 
+// Stream-ordered free: work already queued on the instance's stream finishes
+// with the memory first; batched calls make each instance's stream wait for
+// them, so their uses are covered too.
+void dev_free(Instance* I, void* p) {
+    if (p) cudaFreeAsync(p, I->stream);
+}
+
 int ensure_scratch(Instance* I, size_t doubles) {
     if (I->red_cap >= doubles) return TL_OK;
     if (I->d_red) {
-        cudaStreamSynchronize(I->stream);
-        cudaFree(I->d_red);
+        dev_free(I, I->d_red);
         I->bytes -= I->red_cap * sizeof(double);
         I->d_red = nullptr;
         I->red_cap = 0;
@@ -152,6 +188,34 @@ struct PinnedSlot {
 };
 constexpr int kRing = 8;
 
+// Page-locked staging buffers outlive their instances: a destroyed
+// instance's ring slots (buffer and event) go to a process-wide list that
+// new instances draw from, so admission and eviction do not pay for
+// page-locked allocations. A slot's event guards its reuse as before.
+std::mutex g_pinned_mu;
+std::vector<PinnedSlot> g_pinned;
+constexpr size_t kPinnedKeep = 4096;
+
+void take_pinned(PinnedSlot* s) {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    if (g_pinned.empty()) return;
+    *s = g_pinned.back();
+    g_pinned.pop_back();
+}
+
+void give_pinned(PinnedSlot& s) {
+    if (!s.h && !s.ev) return;
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    if (g_pinned.size() < kPinnedKeep && s.h) {
+        g_pinned.push_back(s);
+    } else {
+        if (s.ev) cudaEventSynchronize(s.ev);
+        if (s.h) cudaFreeHost(s.h);
+        if (s.ev) cudaEventDestroy(s.ev);
+    }
+    s = PinnedSlot();
+}
+
 // Upload bytes to op area `which` unless identical to the last upload.
 struct OpArea {
     void* d = nullptr;
@@ -172,8 +236,7 @@ int upload(Instance* I, OpArea& A, const void* src, size_t bytes, void** dptr) {
     }
     if (A.cap < bytes) {
         if (A.d) {
-            cudaStreamSynchronize(I->stream);
-            cudaFree(A.d);
+            dev_free(I, A.d);
             I->bytes -= A.cap;
         }
         size_t cap = std::max<size_t>(bytes * 2, 4096);
@@ -210,6 +273,7 @@ int h2d(Instance* I, void* dst, const void* src, size_t bytes) {
     Extra& X = extra(I);
     PinnedSlot& s = X.ring[X.ring_next];
     X.ring_next = (X.ring_next + 1) % kRing;
+    if (!s.h && !s.ev) take_pinned(&s);  // a slot (and its event) from the shared list
     cudaError_t e = cudaSuccess;
     if (s.ev) e = cudaEventSynchronize(s.ev);
     else e = cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming);
@@ -234,8 +298,7 @@ int ensure_out(Instance* I, size_t n) {
     Extra& X = extra(I);
     if (X.out_cap >= n) return TL_OK;
     if (X.d_out) {
-        cudaStreamSynchronize(I->stream);
-        cudaFree(X.d_out);
+        dev_free(I, X.d_out);
         I->bytes -= X.out_cap * sizeof(double);
     }
     size_t cap = std::max<size_t>(n, 4096);
@@ -253,8 +316,7 @@ void* area(Instance* I, int which, size_t bytes, int* rc) {
     OpArea& A = extra(I).areas[which];
     if (A.cap < bytes) {
         if (A.d) {
-            cudaStreamSynchronize(I->stream);
-            cudaFree(A.d);
+            dev_free(I, A.d);
             I->bytes -= A.cap;
             A.d = nullptr;
         }
@@ -665,10 +727,9 @@ int tl_device_bytes(const tl_instance* inst, size_t* out) {
 int tl_destroy(tl_instance* inst) {
     if (!inst) return TL_ERR_ARG;
     Instance* I = reinterpret_cast<Instance*>(inst);
-    cudaStreamSynchronize(I->stream);
-    auto fr = [](void* p) {
-        if (p) cudaFree(p);
-    };
+    // nothing waits here: every free is ordered after the work queued on the
+    // instance's stream, and the staging buffers go back to the shared list
+    auto fr = [I](void* p) { dev_free(I, p); };
     fr(I->pool);
     fr(I->scale_pool);
     if (I->prec != kTF32)
@@ -698,10 +759,7 @@ int tl_destroy(tl_instance* inst) {
     fr(I->d_tmp);
     if (I->host_extra) {
         Extra* X = reinterpret_cast<Extra*>(I->host_extra);
-        for (auto& s : X->ring) {
-            if (s.h) cudaFreeHost(s.h);
-            if (s.ev) cudaEventDestroy(s.ev);
-        }
+        for (auto& s : X->ring) give_pinned(s);
         for (auto& A : X->areas) fr(A.d);
         if (X->order_ev) cudaEventDestroy(X->order_ev);
         for (void* p : X->gen_q) fr(p);
@@ -794,15 +852,16 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
         I->h_buf[n_tips + b] = (char*)I->pool + nbuf_elems * I->elt * b;
         I->h_scale[n_tips + b] = I->scale_pool + (size_t)I->Ppad * b;
     }
-    cudaMemcpyAsync(I->d_buf, I->h_buf.data(), sizeof(void*) * I->n_bufs, cudaMemcpyHostToDevice, I->stream);
-    cudaMemcpyAsync(I->d_scale, I->h_scale.data(), sizeof(int*) * I->n_bufs, cudaMemcpyHostToDevice, I->stream);
-    cudaMemcpyAsync(I->d_tipst, I->h_tipst.data(), sizeof(int8_t*) * n_tips, cudaMemcpyHostToDevice, I->stream);
+    // staged through the page-locked ring: nothing here waits for the stream
+    if ((rc = h2d(I, I->d_buf, I->h_buf.data(), sizeof(void*) * I->n_bufs)) ||
+        (rc = h2d(I, I->d_scale, I->h_scale.data(), sizeof(int*) * I->n_bufs)) ||
+        (rc = h2d(I, I->d_tipst, I->h_tipst.data(), sizeof(int8_t*) * n_tips)))
+        return bail(rc);
     if ((rc = dev_alloc(I, &I->d_patw, sizeof(double) * I->Ppad, "pattern weights"))) return bail(rc);
     {
         std::vector<double> w(I->Ppad, 0.0);
         for (int p = 0; p < n_patterns; ++p) w[p] = 1.0;
-        cudaMemcpyAsync(I->d_patw, w.data(), sizeof(double) * I->Ppad, cudaMemcpyHostToDevice, I->stream);
-        cudaStreamSynchronize(I->stream);
+        if ((rc = h2d(I, I->d_patw, w.data(), sizeof(double) * I->Ppad))) return bail(rc);
     }
     const size_t mat64 = (size_t)I->R * I->Spad * I->Spad;
     if ((rc = dev_alloc(I, &I->d_mat64, sizeof(double) * mat64 * n_matrices, "matrices")))
@@ -839,7 +898,7 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
     cudaMemsetAsync(I->d_err, 0, sizeof(int) * 4, I->stream);
     I->tmp_cap = 4096;
     if ((rc = dev_alloc(I, &I->d_tmp, sizeof(double) * I->tmp_cap, "staging"))) return bail(rc);
-    cudaError_t e = cudaStreamSynchronize(I->stream);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return bail(cuda_check(I, e, "tl_create"));
     *out = reinterpret_cast<tl_instance*>(I);
     return TL_OK;
@@ -1009,8 +1068,7 @@ static int set_model(tl_instance* inst, int model, int kind, const double* param
         if (!std::isfinite(freqs[i]) || freqs[i] <= 0)
             return fail(I, TL_ERR_NUMERIC, "frequency %d is not positive and finite", i);
     if (n_params + n_freqs > (int)I->tmp_cap) {
-        cudaStreamSynchronize(I->stream);
-        cudaFree(I->d_tmp);
+        dev_free(I, I->d_tmp);
         I->tmp_cap = n_params + n_freqs + 1024;
         int rc = dev_alloc(I, &I->d_tmp, sizeof(double) * I->tmp_cap, "staging");
         if (rc) return rc;
@@ -1128,8 +1186,7 @@ int tl_update_matrices(tl_instance* inst, int model, const int* p_idx, const int
     }
     // staging: rates [R] | lengths [count] in d_tmp; indices in d_ops area 3
     if ((size_t)(I->R + count) > I->tmp_cap) {
-        cudaStreamSynchronize(I->stream);
-        cudaFree(I->d_tmp);
+        dev_free(I, I->d_tmp);
         I->tmp_cap = I->R + count + 1024;
         int rc = dev_alloc(I, &I->d_tmp, sizeof(double) * I->tmp_cap, "staging");
         if (rc) return rc;
@@ -1406,8 +1463,7 @@ int tl_update_param_matrices(tl_instance* inst, int model, int param, const int*
             return fail(I, TL_ERR_NUMERIC, "edge_len[%d] is negative or not finite", i);
     }
     if ((size_t)(I->R + count) > I->tmp_cap) {
-        cudaStreamSynchronize(I->stream);
-        cudaFree(I->d_tmp);
+        dev_free(I, I->d_tmp);
         I->tmp_cap = I->R + count + 1024;
         int rc = dev_alloc(I, &I->d_tmp, sizeof(double) * I->tmp_cap, "staging");
         if (rc) return rc;

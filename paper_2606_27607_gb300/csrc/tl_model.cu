@@ -155,16 +155,20 @@ __global__ void k_build_model(int kind, int S, int Spad, const double* __restric
 // symmetric n x n matrix A (leading dimension LD), accumulating the
 // rotations into the columns of U. Each round rotates m / 2 disjoint pairs
 // at once. Stops after `settle` sweeps have ended with off(A)^2 <= done_tol *
-// diag(A)^2, or after max_sweeps; returns (to every thread) whether off(A)^2
-// <= conv_tol * diag(A)^2 at the end.
+// diag(A)^2, once a sweep near the diagonal (off(A)^2 <= 1e-8 diag(A)^2)
+// leaves off(A)^2 above stall * its previous value (stall > 0: the rounding
+// floor of T is reached), or after max_sweeps;
+// returns (to every thread) whether off(A)^2 <= conv_tol * diag(A)^2 at the
+// end.
 template <typename T>
 __device__ bool jacobi_sweeps(T* A, T* U, int n, int LD, int max_sweeps, double done_tol,
-                              double conv_tol, int settle, T* s_c, T* s_s, int* s_p, int* s_q,
-                              double* s_red, int* s_flag) {
+                              double conv_tol, int settle, double stall, T* s_c, T* s_s,
+                              int* s_p, int* s_q, double* s_red, int* s_flag) {
     const int t = threadIdx.x, nt = blockDim.x;
     const int m = (n + 1) & ~1;  // players in the tournament (one dummy if n odd)
     int done = 0;
     bool conv = false;
+    double prev = -1.0;  // off(A)^2 after the previous sweep (thread 0)
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int round = 0; round < m - 1; ++round) {
             if (t < m / 2) {
@@ -242,12 +246,17 @@ __device__ bool jacobi_sweeps(T* A, T* U, int n, int LD, int max_sweeps, double 
         if (t == 0) {
             s_flag[0] = offs <= done_tol * s_red[0];
             s_flag[1] = offs <= conv_tol * s_red[0];
+            // stalled: within 1e-8 of the diagonal and no longer shrinking fast
+            s_flag[2] = stall > 0.0 && prev >= 0.0 && offs > stall * prev &&
+                        offs <= 1e-8 * s_red[0];
+            prev = offs;
         }
         __syncthreads();
         done += s_flag[0];
         conv = s_flag[1];
+        const bool stalled = s_flag[2];
         __syncthreads();
-        if (done >= settle) break;
+        if (done >= settle || stalled) break;
     }
     return conv;
 }
@@ -291,7 +300,7 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
     __shared__ float s_cf[32], s_sf[32];
     __shared__ int s_p[32], s_q[32];
     __shared__ double s_red[256];
-    __shared__ int s_flag[2];
+    __shared__ int s_flag[3];
     const int t = threadIdx.x, nt = blockDim.x;
     const int n = S;
 
@@ -313,7 +322,7 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
     }
     __syncthreads();
     // FP32: until off(A)^2 <= 1e-12 diag(A)^2 (about FP32 rounding), 20 sweeps at most
-    jacobi_sweeps<float>(A32, U32, n, LD, 20, 1e-12, 1e-12, 1, s_cf, s_sf, s_p, s_q, s_red,
+    jacobi_sweeps<float>(A32, U32, n, LD, 20, 1e-12, 1e-12, 1, 0.1, s_cf, s_sf, s_p, s_q, s_red,
                          s_flag);
     // FP64 orthonormalisation of the FP32 rotations
     for (int idx = t; idx < n * n; idx += nt) {
@@ -345,8 +354,8 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
     __syncthreads();
     // FP64: stop one sweep after off(A)^2 <= 1e-30 diag(A)^2 (a rotation
     // sweep then leaves it at rounding level); fail above 1e-24
-    const bool conv = jacobi_sweeps<double>(A, U, n, LD, 40, 1e-30, 1e-24, 2, s_c, s_s, s_p, s_q,
-                                            s_red, s_flag);
+    const bool conv = jacobi_sweeps<double>(A, U, n, LD, 40, 1e-30, 1e-24, 2, 0.0, s_c, s_s, s_p,
+                                            s_q, s_red, s_flag);
     if (t == 0 && !conv) err[0] = 3;
     for (int idx = t; idx < Spad * Spad; idx += nt) {
         int i = idx / Spad, k = idx % Spad;

@@ -12,15 +12,16 @@ step:
    to the requests' futures and release their chains;
 2. admission: queued requests are taken in arrival order, at most one per
    chain (a chain's buffers hold one evaluation at a time). A chain without
-   a device instance is admitted only when its partials memory fits the
-   budget, evicting idle chains least recently used first; once a request
-   is blocked on memory, no other chain is newly admitted ahead of it. A
-   chain that could never fit is rejected;
+   a device instance is admitted when its partials memory fits the budget,
+   or, once its request has waited a while, by evicting idle chains least
+   recently used first; once a request is blocked on memory, no other
+   chain is newly admitted ahead of it. A chain that could never fit is
+   rejected;
 3. launch: per request the model (when it changed) and the transition
    matrices; then every four-state request of the step goes through the
    batched calls (one launch per pass for all of them), and codon requests
-   through their tensor-core passes on side streams, so both kinds run on
-   the GPU at once. Each group's results come back with one device-to-host
+   through their tensor-core passes on their chains' streams, so both
+   kinds run on the GPU at once. Each group's results come back with one device-to-host
    copy.
 
 The loop never waits for the GPU: a step is queued while earlier ones run,
@@ -102,11 +103,13 @@ class Server:
     ``memory_budget`` bounds the chains' instance bytes (default 80% of the
     device memory free at start). Four-state chains run in ``nuc_precision``
     (FP32 or FP64) through the batched calls; codon chains in
-    ``codon_precision`` on ``codon_streams`` side streams."""
+    ``codon_precision``, each on its own stream. A request whose chain is
+    not resident evicts idle chains once it has waited ``evict_after``
+    seconds (free memory is taken at once)."""
 
     def __init__(self, memory_budget: int | None = None, max_batch: int = 512,
-                 codon_streams: int = 2, nuc_precision: str = "f32",
-                 codon_precision: str = "tf32x2"):
+                 nuc_precision: str = "f32", codon_precision: str = "tf32x2",
+                 evict_after: float = 0.0):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", torch.cuda.current_device())
@@ -115,9 +118,9 @@ class Server:
         self.budget = int(memory_budget)
         self.used = 0
         self.max_batch = max_batch
+        self.evict_after = evict_after
         self.nuc_precision, self.codon_precision = nuc_precision, codon_precision
         self.stream = torch.cuda.Stream()
-        self.cstreams = [torch.cuda.Stream() for _ in range(max(1, codon_streams))]
         self.batch = Batch(self.stream.cuda_stream)
         self.chains: list[_Chain] = []
         self.queue: collections.deque[_Pending] = collections.deque()
@@ -129,8 +132,11 @@ class Server:
     def add_chain(self, data) -> int:
         prec = self.nuc_precision if data.n_states == 4 else self.codon_precision
         c = _Chain(data, prec)
-        c.stream = (self.stream if data.n_states == 4
-                    else self.cstreams[len(self.chains) % len(self.cstreams)])
+        # every chain has its own stream: its uploads, matrices and (codon)
+        # passes queue there, so admitting a chain never waits for other
+        # chains' work; batched launches order themselves after each
+        # chain's stream and each chain's stream after them (events)
+        c.stream = self.torch.cuda.Stream()
         self.chains.append(c)
         return len(self.chains) - 1
 
@@ -144,7 +150,7 @@ class Server:
         tl = TreeLikelihood(d.tree.n_tips, d.n_patterns, d.n_states, R_CATEGORIES, c.precision,
                             stream=c.stream.cuda_stream)
         tl.inst.set_tip_states_all(d.tips)
-        tl.set_model(d.model, d.params, d.freqs)
+        tl.inst.set_model_async(0, d.model, d.params, d.freqs)
         tl.set_rates(d.rates, d.cat_weights)
         tl.set_pattern_weights(d.pattern_weights)
         tl.set_tree(d.tree.children, d.tree.edge_len)
@@ -152,6 +158,29 @@ class Server:
         c.bytes = max(tl.inst.device_bytes(), self.need(k))
         self.used += c.bytes
         self.stats["admitted"] += 1
+
+    def _try_create(self, p: _Pending):
+        """Create p's chain; on a device allocation failure evict every idle
+        chain and retry once. True when created, False to wait, None when the
+        request was failed (nothing else is resident to make room)."""
+        from ._lib import TreelikError
+        try:
+            self._create(p.chain)
+            return True
+        except TreelikError:
+            idle = [k for k, c in enumerate(self.chains) if c.tl is not None and not c.busy]
+            for k in idle:
+                self._evict(k)
+            try:
+                self._create(p.chain)
+                return True
+            except TreelikError as exc:
+                if any(c.tl is not None for c in self.chains):
+                    return False
+                self.chains[p.chain].queued -= 1
+                self.stats["rejected"] += 1
+                p.future.set_exception(MemoryError(str(exc)))
+                return None
 
     def _evict(self, k: int) -> None:
         c = self.chains[k]
@@ -228,15 +257,24 @@ class Server:
     def _admit(self) -> list[_Pending]:
         picked, seen, rest = [], set(), collections.deque()
         blocked = False
+        now = time.perf_counter()
         while self.queue:
             p = self.queue.popleft()
             c = self.chains[p.chain]
             ok = len(picked) < self.max_batch and not c.busy and p.chain not in seen
             if ok and c.tl is None:
-                ok = not blocked and self._make_room(self.need(p.chain))
+                # a new chain takes free memory at once, but evicts others only
+                # once its request has waited evict_after seconds, so that
+                # resident chains keep their places while their requests flow
+                need = self.need(p.chain)
+                ok = not blocked and (self.used + need <= self.budget or
+                                      (now - p.arrival >= self.evict_after and
+                                       self._make_room(need)))
                 if ok:
-                    self._create(p.chain)
-                else:
+                    ok = self._try_create(p)
+                    if ok is None:      # cannot be created even on an empty device
+                        continue
+                if not ok:
                     blocked = True   # keep memory for the oldest blocked chain
             if ok:
                 picked.append(p)
@@ -314,13 +352,10 @@ class Server:
         nuc = [p for p in picked if self.chains[p.chain].data.n_states == 4]
         if nuc:
             self._launch_nuc(nuc)
-        by_stream = collections.defaultdict(list)
         for p in picked:
             c = self.chains[p.chain]
             if c.data.n_states != 4:
-                by_stream[id(c.stream)].append((c.stream, p))
-        for lst in by_stream.values():
-            self._launch_codon([p for _, p in lst], lst[0][0])
+                self._launch_codon([p], c.stream)
         self.stats["steps"] += 1
         return True
 
