@@ -60,6 +60,9 @@ def parse():
                     help="offered loads as fractions of the measured capacity")
     ap.add_argument("--baseline-seconds", type=float, default=60.0,
                     help="time budget of the one-at-a-time FP64 baseline")
+    ap.add_argument("--autograd", action="store_true",
+                    help="forward + backward through the autograd Function (GTR 1,024 x 50,000 "
+                         "and GY94 64 x 5,000) in each precision against FP64")
     return ap.parse_args()
 
 
@@ -455,8 +458,65 @@ def serving_line(args) -> dict:
             "generate_s": t_gen, "serve_s": t_serve}
 
 
+def autograd_line(args) -> dict:
+    """logL and its gradient (every branch length and the substitution
+    parameters) through the torch.autograd Function, one forward + backward
+    per evaluation (host-synchronous: the loss comes back as a number), on
+    GTR+G4 1,024 taxa x 50,000 patterns (FP32, FP64) and GY94 64 taxa x 5,000
+    patterns (TF32, split TF32, FP64 generic). Latency per evaluation, and
+    the error of each precision against the FP64 GPU path."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2606_27607_gb300 import LogLikelihood, TreeLikelihood, build
+    build.build()
+    torch.cuda.set_device(0)
+    out = {}
+    for name, precs, S in (("gtr_1024x50k", ("f64", "f32"), 4),
+                           ("gy94_64x5k", ("f64", "tf32", "tf32x2"), 61)):
+        w = synth.workload(name)
+        res, ref = {}, None
+        for prec in precs:
+            tl = TreeLikelihood(w.tree.n_tips, w.n_patterns, S, 4, prec)
+            tl.set_tips(w.tips)
+            tl.set_model(w.model, w.params, w.freqs)
+            tl.set_rates(w.rates, w.cat_weights)
+            tl.set_pattern_weights(w.pattern_weights)
+            tl.set_tree(w.tree.children, w.tree.edge_len)
+            lat = []
+            n_it = max(3, min(args.steps, 20))
+            for it in range(3 + n_it):
+                t = torch.tensor(w.tree.edge_len[:-1], dtype=torch.float64, requires_grad=True)
+                th = torch.tensor(w.params, dtype=torch.float64, requires_grad=True)
+                t0 = time.perf_counter()
+                y = LogLikelihood.apply(t, th, tl, w.model, w.freqs)
+                y.backward()
+                gt, gk = t.grad.numpy().copy(), th.grad.numpy().copy()
+                if it >= 3:
+                    lat.append(time.perf_counter() - t0)
+            tl.close()
+            r = {"evals_per_s": len(lat) / sum(lat), "p50_ms": 1e3 * _pct(lat, 50),
+                 "p99_ms": 1e3 * _pct(lat, 99), "logL": float(y.detach())}
+            if prec == "f64":
+                ref = (float(y.detach()), gt, gk)
+            else:
+                r["rel_err_logL"] = abs(float(y.detach()) - ref[0]) / abs(ref[0])
+                r["rel_err_grad_t"] = float(np.linalg.norm(gt - ref[1]) / np.linalg.norm(ref[1]))
+                r["rel_err_grad_theta"] = float(np.max(np.abs(gk - ref[2])) /
+                                                np.max(np.abs(ref[2])))
+            res[prec] = r
+        out[name] = res
+    return {"metric": "autograd forward+backward evaluations/s and latency", "unit": "evals/s",
+            "n_gpus": 1, "data": "synthetic", "config": {"workload": "autograd"},
+            "results": out}
+
+
 def main() -> None:
     args = parse()
+    if args.autograd:
+        print(json.dumps(autograd_line(args)), flush=True)
+        return
     if args.serving:
         print(json.dumps(serving_line(args)), flush=True)
         return
@@ -639,13 +699,60 @@ def main() -> None:
             "algorithmic_bytes": alg[dom], "ms": k_ms[dom],
             "other": {k: {"ms": k_ms[k], "GB/s": alg[k] / (k_ms[k] * 1e-3) / 1e9} for k in k_ms}}
 
-    codon = codon_split = None
+    codon = codon_split = codon64 = fp64 = None
     if not args.no_codon and world == 1:
         try:
             codon = codon_line(max(5, args.steps // 20), 3)
             codon_split = codon_line(max(5, args.steps // 20), 3, prec="tf32x2")
         except Exception as exc:  # reported, not fatal
             codon = {"error": str(exc)[:300]}
+        try:
+            c64 = codon_line(3, 1, prec="f64")
+            codon64 = {"ms_per_step": c64["ms_per_step"], "value": c64["value"],
+                       "logL": c64["logL"], "path": "FP64 generic kernels, one tree at a time",
+                       "speedup_tf32": c64["ms_per_step"] / codon["ms_per_step"],
+                       "rel_err_logL_tf32": abs(codon["logL"] - c64["logL"]) / abs(c64["logL"]),
+                       "rel_err_logL_tf32x2":
+                           abs(codon_split["logL"] - c64["logL"]) / abs(c64["logL"])}
+        except Exception as exc:  # reported, not fatal
+            codon64 = {"error": str(exc)[:300]}
+    if world == 1 and not args.taxa and not args.patterns:
+        # the same step on the FP64 four-state kernels (the plain FP64 path)
+        tl64 = TreeLikelihood(N, P, S, R, "f64", stream=stream.cuda_stream)
+        tl64.set_tips(w.tips)
+        tl64.set_model(w.model, w.params, w.freqs)
+        tl64.set_rates(w.rates, w.cat_weights)
+        tl64.set_pattern_weights(w.pattern_weights)
+        tl64.set_tree(w.tree.children, w.tree.edge_len)
+        d64 = torch.zeros(1 + nn, dtype=torch.float64, device="cuda")
+        i64 = tl64.inst
+
+        def step64():
+            i64.set_model_async(0, w.model, w.params, w.freqs)
+            i64.update_matrices(0, v, lengths, dp)
+            i64.update_partials(tl64._post)
+            i64.root_loglik_dev(nn - 1, 0, d64.data_ptr())
+            i64.pre_order_gradient_dev(tl64._pre, nn, 0, d64.data_ptr() + 8)
+
+        for _ in range(3):
+            step64()
+        torch.cuda.synchronize()
+        a64, b64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k64 = max(3, args.steps // 20)
+        a64.record(stream)
+        for _ in range(k64):
+            step64()
+        b64.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a64.elapsed_time(b64) / k64
+        l64 = float(d64[0].item())
+        g32 = d_out[1:].cpu().numpy()
+        g64 = d64[1:].cpu().numpy()
+        fp64 = {"ms_per_step": ms64, "value": P * (N - 1) / (ms64 * 1e-3), "logL": l64,
+                "path": "FP64 four-state kernels, one tree at a time",
+                "speedup_fp32": ms64 / ms, "rel_err_logL_fp32": abs(logl - l64) / abs(l64),
+                "rel_err_grad_fp32": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64))}
+        tl64.close()
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -668,7 +775,8 @@ def main() -> None:
                        "parallelism": f"patterns, weak x{world}"},
             "grad_evals_per_s": world * 1e3 / ms, "logL": logl, "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches) * args.steps, "gpu_launches_per_step": int(launches),
-            "roofline": roof, "cpu_baseline": cpu, "codon": codon, "codon_split": codon_split}
+            "roofline": roof, "cpu_baseline": cpu, "fp64": fp64, "codon": codon,
+            "codon_split": codon_split, "codon_fp64": codon64}
     print(json.dumps(line), flush=True)
     tl.close()
     if dist:

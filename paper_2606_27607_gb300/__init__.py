@@ -50,8 +50,11 @@ class TreeLikelihood:
         for t in range(self.N):
             self.inst.set_tip_states(t, tips[t])
 
+    N_PARAMS = {"hky": 1, "gtr": 6, "gy94": 2}
+
     def set_model(self, kind: str, params, freqs) -> None:
         self.inst.set_model(0, kind, params, freqs)
+        self.kind = kind
 
     def set_rates(self, rates, weights=None) -> None:
         self.inst.set_category_rates(rates)
@@ -75,10 +78,18 @@ class TreeLikelihood:
         dp = (self.nn + v).astype(np.int32) if derivatives else None
         self.inst.update_matrices(0, v, self.edge_len[: self.nn - 1], dp)
 
-    def loglik(self, site: bool = False):
-        self.update_matrices(False)
+    def loglik(self, site: bool = False, derivatives: bool = False):
+        """logL (and per-pattern values); ``derivatives`` also fills the
+        dP/dt slots so that branch_gradient() can follow without a second
+        post-order pass."""
+        self.update_matrices(derivatives)
         self.inst.update_partials(self._post)
         return self.inst.root_loglik(self.nn - 1, 0, site)
+
+    def branch_gradient(self) -> np.ndarray:
+        """dlogL/dt for every node (root entry 0) from the post-order
+        partials and dP/dt of the last loglik(derivatives=True)."""
+        return self.inst.pre_order_gradient(self._pre, self.nn, 0)
 
     def gradient(self):
         """(logL, dlogL/dt for every node, root entry 0)."""
@@ -94,10 +105,12 @@ class TreeLikelihood:
         post-order partials of the current tree. One pre-order pass per
         parameter with dP/dtheta in the derivative slots; the next gradient()
         recomputes dP/dt there."""
-        _, _, dq = self.inst.get_model(0)
+        n = self.N_PARAMS.get(getattr(self, "kind", None))
+        if n is None:
+            n = len(self.inst.get_model(0)[2])
         v = np.arange(self.nn - 1, dtype=np.int32)
-        out = np.zeros(len(dq))
-        for k in range(len(dq)):
+        out = np.zeros(n)
+        for k in range(n):
             self.inst.update_param_matrices(0, k, self.nn + v, self.edge_len[: self.nn - 1])
             out[k] = self.inst.pre_order_derivative(self._pre, self.nn, 0).sum()
         return out

@@ -24,7 +24,7 @@ class LogLikelihood(torch.autograd.Function):
         full = np.zeros(tl.nn)
         full[: tl.nn - 1] = t
         tl.set_tree(tl.children, full)
-        logl = tl.loglik()
+        logl = tl.loglik(derivatives=True)
         ctx.tl = tl
         ctx.dev = edge_len.device
         return torch.tensor(logl, dtype=torch.float64)
@@ -32,7 +32,9 @@ class LogLikelihood(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         tl = ctx.tl
-        _, g = tl.gradient()
+        # the forward pass left the post-order partials and dP/dt in place:
+        # one pre-order pass for the branch lengths, then one per parameter
+        g = tl.branch_gradient()
         gth = tl.subst_gradient()
         s = float(grad_out)
         gt = torch.from_numpy(s * g[: tl.nn - 1]).to(ctx.dev)

@@ -1436,8 +1436,8 @@ int tl_pre_order_derivative(tl_instance* inst, const tl_pre_op* ops, int count, 
     CHECK_INST(inst);
     Instance* I = reinterpret_cast<Instance*>(inst);
     if (!out && n_out > 0) return fail(I, TL_ERR_ARG, "out is null");
-    if (!use_nuc(I) && !use_tc(I))
-        return fail(I, TL_ERR_UNSUPPORTED, "general derivatives need the four-state or TF32 path");
+    // the FP64 generic path always forms u . (dmat p) from the stored
+    // derivative matrix, so it needs no switch for general derivatives
     int rc;
     if ((rc = ensure_out(I, (size_t)2 * std::max(n_out, 1) + 16))) return rc;
     double* d_g = extra(I).d_out + std::max(n_out, 1) + 8;

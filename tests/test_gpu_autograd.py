@@ -63,6 +63,22 @@ def test_codon_subst_gradient_tf32():
     assert np.linalg.norm(got - want) <= 1e-3 * np.linalg.norm(want), (got, want)
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("tf32x2", 1e-3)])
+def test_codon_subst_gradient_matches_oracle(prec, tol):
+    """dlogL/dkappa and dlogL/domega for GY94 on the FP64 generic path and on
+    the split-TF32 tensor-core path."""
+    w = synth.workload("gy94_64x5k", n_tips=6, n_patterns=120)
+    Q, pi, dQ = om.build(w.model, w.params, w.freqs)
+    want = og.subst_gradient(w.tree, Q, dQ, pi, w.rates, w.cat_weights, w.pattern_weights, w.tips)
+    tl = make(w, prec, 61)
+    try:
+        tl.loglik()
+        got = tl.subst_gradient()
+    finally:
+        tl.close()
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want)), (got, want)
+
+
 def test_autograd_function_matches_oracle_and_finite_differences():
     import torch
 
