@@ -352,9 +352,9 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
         A[i * LD + j] = 0.5 * (T2[i * LD + j] + T2[j * LD + i]);
     }
     __syncthreads();
-    // FP64: stop one sweep after off(A)^2 <= 1e-30 diag(A)^2 (a rotation
-    // sweep then leaves it at rounding level); fail above 1e-24
-    const bool conv = jacobi_sweeps<double>(A, U, n, LD, 40, 1e-30, 1e-24, 2, 0.0, s_c, s_s, s_p,
+    // FP64: stop once off(A)^2 <= 1e-28 diag(A)^2 (off-diagonal at 1e-14 of
+    // the diagonal; from the FP32 start one or two sweeps); fail above 1e-24
+    const bool conv = jacobi_sweeps<double>(A, U, n, LD, 40, 1e-28, 1e-24, 1, 0.0, s_c, s_s, s_p,
                                             s_q, s_red, s_flag);
     if (t == 0 && !conv) err[0] = 3;
     for (int idx = t; idx < Spad * Spad; idx += nt) {
