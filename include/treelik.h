@@ -122,7 +122,8 @@ typedef struct {
 } tl_edge;
 
 /* Create an instance. n_states: 1..64 (TL_PREC_F32: 4; TF32/BF16X3: 33..64,
- * stored padded to 64). n_categories: 1..8. n_buffers: internal partials
+ * stored padded to 64). n_categories: 1..8 (TL_PREC_TF32: 1..4; more
+ * returns TL_ERR_UNSUPPORTED). n_buffers: internal partials
  * buffers. n_matrices: transition-matrix slots (each holds all categories).
  * n_models: model slots (Q, pi, eigensystem, dQ/dtheta). stream: a
  * cudaStream_t or NULL. Exactly one TL_PREC_* flag must be set. */

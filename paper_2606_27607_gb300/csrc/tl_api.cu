@@ -793,6 +793,10 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
         return fail(nullptr, TL_ERR_UNSUPPORTED, "TL_PREC_BF16X3 is not built in this library");
     if (prec == kTF32 && (n_states < 33 || n_states > 64))
         return fail(nullptr, TL_ERR_UNSUPPORTED, "TL_PREC_TF32 is built for 33..64 states");
+    // the tensor-core kernels hold both children's products of every
+    // category in the 512 TMEM columns (2 x R x 64)
+    if (prec == kTF32 && n_categories > 4)
+        return fail(nullptr, TL_ERR_UNSUPPORTED, "TL_PREC_TF32 is built for at most 4 categories");
     if ((flags & TL_SCALE_NONE) && prec != kF64)
         return fail(nullptr, TL_ERR_ARG, "TL_SCALE_NONE needs TL_PREC_F64");
     if ((flags & TL_SPLIT_MATRICES) && prec != kTF32)

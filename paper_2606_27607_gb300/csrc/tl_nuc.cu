@@ -953,21 +953,25 @@ int nuc_lanes(const Instance* I) {
     return I->R <= 1 ? 1 : I->R <= 2 ? 2 : I->R <= 4 ? 4 : 8;
 }
 
-// Lanes per pattern of the post- and pre-order kernels: 1 (all categories in
-// one lane) unless TL_NUC_LANES selects 1, 2, 4 or 8.
+// Lanes per pattern of the post- and pre-order kernels, as their dispatch
+// instantiates them: with four categories 1 (all categories in one lane)
+// unless TL_NUC_LANES selects 2 or 4; fewer categories use four lanes (one
+// category each), more use eight. Tile counts (and so the columns of the
+// gradient partials) follow from it.
 int nuc_lanes_main(const Instance* I) {
     static int env = -1;
     if (env < 0) {
         const char* s = getenv("TL_NUC_LANES");
         env = s ? atoi(s) : 0;
     }
-    int lpp = (env == 1 || env == 2 || env == 4 || env == 8) ? env : 1;
-    if (I->R > 4 && lpp == 1) lpp = 2;    // at most four categories per lane
-    return lpp;
+    if (I->R < 4) return 4;
+    if (I->R > 4) return 8;
+    return (env == 1 || env == 2 || env == 4) ? env : 1;
 }
 
-// Lanes per pattern of the pre-order kernel: TL_PRE_LANES (1, 2, 4 or 8,
-// at least the post-order kernel's), else the post-order kernel's.
+// Lanes per pattern of the pre-order kernel: with four categories
+// TL_PRE_LANES (1, 2 or 4, at least the post-order kernel's), else the
+// post-order kernel's.
 int nuc_lanes_pre(const Instance* I) {
     static int env = -1;
     if (env < 0) {
@@ -975,7 +979,8 @@ int nuc_lanes_pre(const Instance* I) {
         env = s ? atoi(s) : 0;
     }
     const int main = nuc_lanes_main(I);
-    const int lpp = (env == 1 || env == 2 || env == 4 || env == 8) ? env : main;
+    if (I->R != 4) return main;
+    const int lpp = (env == 1 || env == 2 || env == 4) ? env : main;
     return std::max(lpp, main);
 }
 

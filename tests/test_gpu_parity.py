@@ -37,7 +37,8 @@ def oracle_run(w, grad=True):
 
 def gpu_run(w, prec, grad=True, site=False, tl_kwargs=None):
     from paper_2606_27607_gb300 import TreeLikelihood
-    tl = TreeLikelihood(w.tree.n_tips, w.n_patterns, w.n_states, 4, prec, **(tl_kwargs or {}))
+    tl = TreeLikelihood(w.tree.n_tips, w.n_patterns, w.n_states, len(w.rates), prec,
+                        **(tl_kwargs or {}))
     try:
         tl.set_tips(w.tips)
         tl.set_model(w.model, w.params, w.freqs)
@@ -340,3 +341,24 @@ def test_errors_are_reported():
         inst.update_partials(np.array([(2, 0, 0, 1, 1)], dtype=tree.OP_DTYPE))
         with pytest.raises(TreelikError, match="TL_ERR_NUMERIC"):
             inst.root_loglik(2)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("ncat", [1, 3, 6, 8])
+def test_category_counts_match_oracle(prec, ncat):
+    """Other category counts than four take the runtime-R kernels (one lane
+    per category for R < 4, eight lanes for R > 4) and the root/edge layouts
+    with LPP = 1, 4 or 8: logL and every branch derivative against the
+    oracle with the counts' own Gamma rates and unequal weights."""
+    import synth
+    w = synth.workload("gtr_512x100k", n_tips=23, n_patterns=517)
+    rates = synth.gamma_rates(0.7, ncat)
+    catw = np.linspace(1.0, 2.0, ncat)
+    catw = catw / catw.sum()
+    rates = rates / np.sum(rates * catw)
+    w.rates, w.cat_weights = rates, catw
+    want_l, _, want_g = oracle_run(w)
+    logl, _, g = gpu_run(w, prec)
+    tol_l, tol_g = (1e-11, 1e-10) if prec == "f64" else (1e-5, 1e-3)
+    assert abs(logl - want_l) <= tol_l * abs(want_l), (logl, want_l)
+    assert_grad_close(g, want_g, tol_g)

@@ -84,3 +84,16 @@ def test_op_lists_are_a_valid_traversal():
                 produced.add(int(op["pre"][c]))
     edges = sorted(int(e) for op in pre for e in op["edge"])
     assert edges == list(range(98))
+
+
+def test_tensor_core_category_limit_is_checked_before_any_device_call(lib):
+    """The tensor-core kernels keep 2 x R x 64 accumulator columns in 512
+    TMEM columns, so TF32 instances take at most four categories; the check
+    runs before the device is touched (so it holds on a machine without one)."""
+    import ctypes as C
+    h = C.c_void_p()
+    rc = lib.tl_create(8, 100, 61, 6, 14, 30, 1, 0x4, None, C.byref(h))
+    assert rc == -8  # TL_ERR_UNSUPPORTED
+    buf = C.create_string_buffer(256)
+    lib.tl_last_error(None, buf, 256)
+    assert b"at most 4 categories" in buf.value
