@@ -114,3 +114,76 @@ def test_autograd_function_matches_oracle_and_finite_differences():
         assert abs(fd - th.grad.numpy()[0]) <= 1e-5 * max(1.0, abs(fd))
     finally:
         tl.close()
+
+
+def sampled(w, n=300, seed=5):
+    """The workload with weight 1 on n sampled patterns and 0 elsewhere: the
+    full-size launch computes a logL and gradient the oracle can evaluate on
+    those n patterns alone."""
+    import dataclasses
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(w.n_patterns, n, replace=False))
+    idx[-1] = w.n_patterns - 1           # the ragged tail
+    wt = np.zeros(w.n_patterns)
+    wt[idx] = 1.0
+    small = dataclasses.replace(w, tips=w.tips[:, idx], pattern_weights=np.ones(n))
+    return dataclasses.replace(w, pattern_weights=wt), small
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,prec", [("gtr_1024x50k", "f32"), ("gy94_64x5k", "tf32x2")])
+def test_autograd_full_size_sampled_patterns(name, prec):
+    """The autograd Function at the benchmark's full sizes (every kernel
+    launched over all patterns and the whole tree), with pattern weights
+    that select 300 patterns: logL, all branch-length and substitution
+    gradients against the oracle on those patterns; central differences of
+    the FP64 GPU path (h = 1e-6) for a few components."""
+    import torch
+
+    from paper_2606_27607_gb300 import LogLikelihood
+    w, small = sampled(synth.workload(name))
+    S = w.n_states
+    Q, pi, dQ = om.build(w.model, w.params, w.freqs)
+    want_l, _ = op.loglik(small.tree, Q, pi, small.rates, small.cat_weights,
+                          small.pattern_weights, small.tips)
+    want_gt = og.branch_gradient(small.tree, Q, pi, small.rates, small.cat_weights,
+                                 small.pattern_weights, small.tips)
+    want_gk = og.subst_gradient(small.tree, Q, dQ, pi, small.rates, small.cat_weights,
+                                small.pattern_weights, small.tips)
+    tl = make(w, prec, S)
+    try:
+        t = torch.tensor(w.tree.edge_len[:-1], dtype=torch.float64, requires_grad=True)
+        th = torch.tensor(w.params, dtype=torch.float64, requires_grad=True)
+        y = LogLikelihood.apply(t, th, tl, w.model, w.freqs)
+        y.backward()
+        gt, gk = t.grad.numpy(), th.grad.numpy()
+    finally:
+        tl.close()
+    assert abs(float(y.detach()) - want_l) <= 1e-5 * abs(want_l)
+    wt = want_gt[:-1]
+    assert np.linalg.norm(gt - wt) <= 1e-3 * np.linalg.norm(wt)
+    assert np.max(np.abs(gt - wt)) <= 1e-3 * np.max(np.abs(wt))
+    assert np.max(np.abs(gk - want_gk)) <= 1e-3 * np.max(np.abs(want_gk))
+    # central differences of the FP64 GPU path at full size
+    t64 = make(w, "f64", S)
+    try:
+        h = 1e-6
+        base_t, base_k = w.tree.edge_len[:-1].copy(), np.array(w.params, float)
+
+        def f(tt, kk):
+            return float(LogLikelihood.apply(torch.tensor(tt), torch.tensor(kk), t64, w.model,
+                                             w.freqs).detach())
+
+        for v in (0, int(np.argmax(np.abs(wt))), len(base_t) - 1):
+            tp, tm = base_t.copy(), base_t.copy()
+            tp[v] += h
+            tm[v] -= h
+            fd = (f(tp, base_k) - f(tm, base_k)) / (2 * h)
+            assert abs(fd - gt[v]) <= 1e-3 * max(abs(fd), 1e-3 * np.max(np.abs(wt))), (v, fd, gt[v])
+        kp, km = base_k.copy(), base_k.copy()
+        kp[0] += h
+        km[0] -= h
+        fd = (f(base_t, kp) - f(base_t, km)) / (2 * h)
+        assert abs(fd - gk[0]) <= 1e-3 * max(abs(fd), 1e-3 * np.max(np.abs(gk)))
+    finally:
+        t64.close()
