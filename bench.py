@@ -391,6 +391,7 @@ def serving_line(args) -> dict:
     t1 = time.perf_counter()
     futs, span = run_open_loop(server, reqs, np.zeros(len(reqs)))
     cap = summarise(futs, span)
+    served = [f.result().logl if f.exception() is None else None for f in futs]
     capacity = cap["req_per_s"]
     loads = []
     for f in [float(x) for x in args.loads.split(",") if x]:
@@ -408,10 +409,10 @@ def serving_line(args) -> dict:
 
     # one request at a time, FP64, no batching (codon through the FP64
     # generic path), in arrival order until the time budget is spent
-    base_lat, base_work = [], 0
+    base_lat, base_work, base_err = [], 0, []
     cache: dict = {}
     tb = time.perf_counter()
-    for r in reqs:
+    for i, r in enumerate(reqs):
         if time.perf_counter() - tb > args.baseline_seconds:
             break
         w = chains[r.chain]
@@ -433,10 +434,12 @@ def serving_line(args) -> dict:
         tl.set_model(w.model, r.params, w.freqs)
         tl.set_tree(w.tree.children, r.edge_len)
         if r.gradient:
-            tl.gradient()
+            l64, _ = tl.gradient()
         else:
-            tl.loglik()
+            l64 = tl.loglik()
         base_lat.append(time.perf_counter() - ts)
+        if served[i] is not None:
+            base_err.append(abs(served[i] - l64) / abs(l64))
         base_work += (w.tree.n_tips - 1) * w.n_patterns
     for tl in cache.values():
         tl.close()
@@ -444,7 +447,11 @@ def serving_line(args) -> dict:
     baseline = {"kind": "fp64 one request at a time, no batching", "requests": len(base_lat),
                 "req_per_s": len(base_lat) / t_base if t_base else None,
                 "pattern_node_per_s": base_work / t_base if t_base else None,
-                "p50_service_s": _pct(base_lat, 50), "p99_service_s": _pct(base_lat, 99)}
+                "p50_service_s": _pct(base_lat, 50), "p99_service_s": _pct(base_lat, 99),
+                # the served logL (FP32 / split TF32, batched) of the same
+                # requests against this FP64 evaluation
+                "served_vs_fp64_rel_err_max": max(base_err) if base_err else None,
+                "served_vs_fp64_rel_err_p99": _pct(base_err, 99)}
     return {"metric": "serving requests/s and p50/p99 latency (s) at offered load",
             "value": capacity, "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
             "dtype": "f32 (4-state), tf32x2 (codon)", "data": "synthetic",
