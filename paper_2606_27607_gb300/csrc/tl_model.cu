@@ -165,6 +165,7 @@ __device__ bool jacobi_sweeps(T* A, T* U, int n, int LD, int max_sweeps, double 
                               double conv_tol, int settle, double stall, T* s_c, T* s_s,
                               int* s_p, int* s_q, double* s_red, int* s_flag) {
     const int t = threadIdx.x, nt = blockDim.x;
+    const int warp_id = t >> 5, ln = t & 31, n_warps = nt >> 5;
     const int m = (n + 1) & ~1;  // players in the tournament (one dummy if n odd)
     int done = 0;
     bool conv = false;
@@ -195,29 +196,31 @@ __device__ bool jacobi_sweeps(T* A, T* U, int n, int LD, int max_sweeps, double 
                 s_q[t] = q;
             }
             __syncthreads();
-            // rows: A <- J^T A
-            for (int idx = t; idx < (m / 2) * n; idx += nt) {
-                int k = idx / n, j = idx % n;
-                int p = s_p[k], q = s_q[k];
+            // rows: A <- J^T A (a warp per rotation, a lane per column)
+            for (int k = warp_id; k < m / 2; k += n_warps) {
+                const int p = s_p[k], q = s_q[k];
                 if (p < 0 || s_s[k] == T(0)) continue;
-                T c = s_c[k], sn = s_s[k];
-                T ap = A[p * LD + j], aq = A[q * LD + j];
-                A[p * LD + j] = c * ap - sn * aq;
-                A[q * LD + j] = sn * ap + c * aq;
+                const T c = s_c[k], sn = s_s[k];
+                for (int j = ln; j < n; j += 32) {
+                    const T ap = A[p * LD + j], aq = A[q * LD + j];
+                    A[p * LD + j] = c * ap - sn * aq;
+                    A[q * LD + j] = sn * ap + c * aq;
+                }
             }
             __syncthreads();
-            // columns: A <- A J, U <- U J
-            for (int idx = t; idx < (m / 2) * n; idx += nt) {
-                int k = idx / n, i = idx % n;
-                int p = s_p[k], q = s_q[k];
+            // columns: A <- A J, U <- U J (a warp per rotation, a lane per row)
+            for (int k = warp_id; k < m / 2; k += n_warps) {
+                const int p = s_p[k], q = s_q[k];
                 if (p < 0 || s_s[k] == T(0)) continue;
-                T c = s_c[k], sn = s_s[k];
-                T ap = A[i * LD + p], aq = A[i * LD + q];
-                A[i * LD + p] = c * ap - sn * aq;
-                A[i * LD + q] = sn * ap + c * aq;
-                T up = U[i * LD + p], uq = U[i * LD + q];
-                U[i * LD + p] = c * up - sn * uq;
-                U[i * LD + q] = sn * up + c * uq;
+                const T c = s_c[k], sn = s_s[k];
+                for (int i = ln; i < n; i += 32) {
+                    const T ap = A[i * LD + p], aq = A[i * LD + q];
+                    A[i * LD + p] = c * ap - sn * aq;
+                    A[i * LD + q] = sn * ap + c * aq;
+                    const T up = U[i * LD + p], uq = U[i * LD + q];
+                    U[i * LD + p] = c * up - sn * uq;
+                    U[i * LD + q] = sn * up + c * uq;
+                }
             }
             __syncthreads();
         }
