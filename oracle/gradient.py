@@ -111,3 +111,62 @@ def subst_gradient(tree, Q, dQs, pi, rates, cat_weights, pattern_weights,
             for k, d in enumerate(dPs):
                 g[k] += np.dot(w[lo:lo + chunk], _edge_ratio(uv, d[v], P[v], pv, cw))
     return g
+
+
+def edge_adjoints(tree, Q, pi, rates, cat_weights, pattern_weights, tip_states,
+                  rescale: bool = True, chunk: int = 8192) -> np.ndarray:
+    """M[v, r] = dlogL/dP_r(t_v) ([2N-2, R, S, S]) for every non-root node v.
+
+    L_p is linear in each transition matrix (the pattern likelihood is
+    sum_r w_r u_v^T P_v p_v for any edge v), so
+      M[v, r] = w_r sum_p (w_p / L_p) u_v[r, p] p_v[r, p]^T,
+    with L_p taken as that same-edge denominator (the power-of-two scales of
+    u and p cancel in the ratio)."""
+    S = Q.shape[0]
+    n_tips = tree.n_tips
+    R = len(rates)
+    P = transition_matrices(Q, tree.edge_len, rates)
+    cw = np.asarray(cat_weights, float)
+    w = np.asarray(pattern_weights, float)
+    M = np.zeros((2 * n_tips - 2, R, S, S))
+    for lo in range(0, tip_states.shape[1], chunk):
+        tips = tip_partials(tip_states[:, lo:lo + chunk], S)
+        post, _ = post_order(tree.children, n_tips, P, tips, rescale)
+        _, u = pre_order(tree.children, n_tips, P, post, tips, pi, R, rescale)
+        for v, uv in u.items():
+            pv = tips[v] if v < n_tips else post[v]
+            den = np.einsum("r,rpi,rpi->p", cw, uv, child_product(P[v], pv))
+            coef = w[lo:lo + chunk] / den
+            pr = np.broadcast_to(pv, uv.shape)
+            M[v] += np.einsum("r,p,rpi,rpj->rij", cw, coef, uv, pr)
+    return M
+
+
+def rate_matrix_gradient(tree, Q, pi, rates, cat_weights, pattern_weights, tip_states,
+                         rescale: bool = True, first_order: bool = False,
+                         chunk: int = 8192) -> np.ndarray:
+    """dlogL/dQ ([S, S]): the derivative of logL with respect to every entry
+    of Q, with P_r(t) = expm(rho_r t Q) and the root distribution pi fixed.
+
+    By the chain rule, dlogL/dQ = sum_{v,r} of the adjoint of the Frechet
+    derivative of expm at A = rho_r t_v Q applied to M[v, r] (edge_adjoints),
+    scaled by rho_r t_v. For expm that adjoint is the Frechet derivative at
+    A^T: <M, L(A, E)> = <L(A^T, M), E> (Sec. "Discussion": reverse-mode
+    gradients through the adjoint of the matrix exponential).
+
+    first_order: the approximation the paper describes for random-effects
+    models (Sec. "Algorithmic advances"), dP ~ rho t dQ P, which gives
+    sum_{v,r} rho_r t_v M[v, r] P_r(t_v)^T."""
+    M = edge_adjoints(tree, Q, pi, rates, cat_weights, pattern_weights, tip_states,
+                      rescale, chunk)
+    rates = np.asarray(rates, float)
+    S = Q.shape[0]
+    G = np.zeros((S, S))
+    for v, t in enumerate(tree.edge_len[: len(M)]):
+        for r, rho in enumerate(rates):
+            A = rho * t * Q
+            if first_order:
+                G += rho * t * M[v, r] @ expm_frechet(A, np.zeros_like(A))[0].T
+            else:
+                G += rho * t * expm_frechet(A.T, M[v, r], compute_expm=False)
+    return G

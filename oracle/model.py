@@ -53,14 +53,14 @@ def _normalise(R: np.ndarray, pi: np.ndarray, dR: list[np.ndarray]):
     R = R.copy()
     np.fill_diagonal(R, 0.0)
     np.fill_diagonal(R, -R.sum(axis=1))
-    mu = -float(np.dot(pi, np.diag(R)))
+    mu = -np.dot(pi, np.diag(R))
     Q = R / mu
     dQ = []
     for D in dR:
         D = D.copy()
         np.fill_diagonal(D, 0.0)
         np.fill_diagonal(D, -D.sum(axis=1))
-        dmu = -float(np.dot(pi, np.diag(D)))
+        dmu = -np.dot(pi, np.diag(D))
         dQ.append(D / mu - R * dmu / mu**2)
     return Q, dQ
 
@@ -69,7 +69,7 @@ def hky(kappa: float, pi) -> tuple[np.ndarray, list[np.ndarray]]:
     """HKY85: s_ij = kappa for transitions, 1 for transversions.
     Returns (Q, [dQ/dkappa])."""
     pi = np.asarray(pi, float)
-    R = np.zeros((4, 4))
+    R = np.zeros((4, 4), dtype=np.result_type(kappa, float))
     D = np.zeros((4, 4))
     for i in range(4):
         for j in range(4):
@@ -87,8 +87,9 @@ def gtr(rates, pi) -> tuple[np.ndarray, list[np.ndarray]]:
     """GTR: symmetric exchangeabilities s_ij in the order AC, AG, AT, CG, CT, GT.
     Returns (Q, [dQ/drate_k for k in 0..5])."""
     pi = np.asarray(pi, float)
-    rates = np.asarray(rates, float)
-    R = np.zeros((4, 4))
+    rates = np.asarray(rates)
+    rates = rates.astype(np.result_type(rates.dtype, float))
+    R = np.zeros((4, 4), dtype=rates.dtype)
     dR = [np.zeros((4, 4)) for _ in range(6)]
     for k, (i, j) in enumerate(GTR_PAIRS):
         R[i, j] = rates[k] * pi[j]
@@ -107,18 +108,35 @@ def f3x4_frequencies(f3x4) -> np.ndarray:
     return pi / pi.sum()
 
 
-def gy94(kappa: float, omega: float, f3x4) -> tuple[np.ndarray, np.ndarray, list[np.ndarray]]:
+def gy94_pairs() -> list[tuple[int, int]]:
+    """Unordered pairs (i < j, lexicographic) of sense codons that differ at
+    exactly one position: the non-zero off-diagonal elements of GY94 (263)."""
+    codons, _ = genetic_code()
+    return [(i, j) for i in range(len(codons)) for j in range(i + 1, len(codons))
+            if sum(codons[i][k] != codons[j][k] for k in range(3)) == 1]
+
+
+def gy94(kappa, omega, f3x4, eps=None):
     """Goldman-Yang 1994 codon model on the 61 sense codons.
 
     s_ij = 0 unless codons i and j differ at exactly one position; otherwise
     s_ij = kappa^[transition] * omega^[nonsynonymous]. pi is F3x4.
-    Returns (Q, pi, [dQ/dkappa, dQ/domega])."""
+    ``eps`` (one value per pair of gy94_pairs()) adds random effects: s_ij
+    and s_ji are multiplied by exp(eps_k) (Sec. "Algorithmic advances":
+    multiplicative random effects on the non-diagonal elements; symmetric
+    here, so Q stays reversible). Any argument may be complex (complex-step
+    derivatives). Returns (Q, pi, [dQ/dkappa, dQ/domega])."""
     codons, amino = genetic_code()
     pi = f3x4_frequencies(f3x4)
     n = len(codons)
-    R = np.zeros((n, n))
-    Dk = np.zeros((n, n))
-    Dw = np.zeros((n, n))
+    dt = np.result_type(kappa, omega, float if eps is None else np.asarray(eps).dtype)
+    mult = np.ones((n, n), dtype=dt)
+    if eps is not None:
+        for k, (i, j) in enumerate(gy94_pairs()):
+            mult[i, j] = mult[j, i] = np.exp(eps[k])
+    R = np.zeros((n, n), dtype=dt)
+    Dk = np.zeros((n, n), dtype=dt)
+    Dw = np.zeros((n, n), dtype=dt)
     for i, ci in enumerate(codons):
         for j, cj in enumerate(codons):
             diff = [k for k in range(3) if ci[k] != cj[k]]
@@ -129,21 +147,38 @@ def gy94(kappa: float, omega: float, f3x4) -> tuple[np.ndarray, np.ndarray, list
             ns = amino[i] != amino[j]
             k_ = kappa if ts else 1.0
             w_ = omega if ns else 1.0
-            R[i, j] = k_ * w_ * pi[j]
-            Dk[i, j] = (1.0 if ts else 0.0) * w_ * pi[j]
-            Dw[i, j] = k_ * (1.0 if ns else 0.0) * pi[j]
+            R[i, j] = k_ * w_ * pi[j] * mult[i, j]
+            Dk[i, j] = (1.0 if ts else 0.0) * w_ * pi[j] * mult[i, j]
+            Dw[i, j] = k_ * (1.0 if ns else 0.0) * pi[j] * mult[i, j]
     Q, dQ = _normalise(R, pi, [Dk, Dw])
     return Q, pi, dQ
 
 
 def build(model: str, params, freqs):
-    """(Q, pi, [dQ/dtheta]) for model in {"hky", "gtr", "gy94"}."""
+    """(Q, pi, [dQ/dtheta]) for model in {"hky", "gtr", "gy94", "gy94re"}
+    ("gy94re": params kappa, omega, then one random effect per pair of
+    gy94_pairs(); the dQ list covers kappa and omega)."""
     if model == "hky":
-        Q, dQ = hky(float(params[0]), freqs)
+        Q, dQ = hky(params[0], freqs)
         return Q, np.asarray(freqs, float), dQ
     if model == "gtr":
         Q, dQ = gtr(params, freqs)
         return Q, np.asarray(freqs, float), dQ
     if model == "gy94":
-        return gy94(float(params[0]), float(params[1]), freqs)
+        return gy94(params[0], params[1], freqs)
+    if model == "gy94re":
+        return gy94(params[0], params[1], freqs, np.asarray(params[2:]))
     raise ValueError(model)
+
+
+def rate_jacobian(model: str, params, freqs, h: float = 1e-30) -> np.ndarray:
+    """dQ/dtheta_k for every parameter k ([K, S, S]) by complex-step
+    differentiation of the builder: Im Q(theta + i h e_k) / h, exact to
+    rounding (no subtraction), independent of the hand-written dQ."""
+    params = np.asarray(params, float)
+    out = []
+    for k in range(len(params)):
+        z = params.astype(complex)
+        z[k] += 1j * h
+        out.append(build(model, z, freqs)[0].imag / h)
+    return np.array(out)

@@ -469,3 +469,143 @@ def test_codon_gradients_vs_finite_differences():
     for v in (0, 3, 6):
         fd = _fd_branch(tree, v, 1e-6, fl)
         assert abs(gb[v] - fd) < 1e-6 * max(1.0, abs(fd))
+
+
+# ----------------------------------------------------------------------------
+# dlogL/dP per edge and dlogL/dQ (the reverse-mode substitution gradient)
+# ----------------------------------------------------------------------------
+
+def test_edge_adjoints_vs_brute_force_derivative():
+    """M[v, r][i, j] = dlogL/dP_r(t_v)[i, j]: the likelihood by enumeration is
+    linear in each matrix entry, so the derivative is exact from one
+    perturbed evaluation; also sum_r <M[v, r], rho_r Q P> = dlogL/dt_v."""
+    rng = np.random.default_rng(31)
+    tree = small_tree(4, 31)
+    pi = rng.dirichlet(np.ones(4))
+    Q = model.gtr(rng.dirichlet(np.ones(6)) * 6, pi)[0]
+    rates = synth.gamma_rates(0.5, 3)
+    cw = np.array([0.2, 0.5, 0.3])
+    states = rand_states(rng, 4, 25, 4)
+    w = rng.integers(1, 4, size=25).astype(float)
+    M = gradient.edge_adjoints(tree, Q, pi, rates, cw, w, states)
+    P = pruning.transition_matrices(Q, tree.edge_len, rates)
+    tips = pruning.tip_partials(states, 4)
+    L = brute.site_likelihood(tree.children, 4, P, pi, cw, tips)
+    for v in (0, 2, 4, 5):
+        for r in range(3):
+            for i, j in ((0, 0), (1, 3), (3, 2)):
+                E = np.zeros_like(P)
+                E[v, r, i, j] = 1.0
+                # L is linear in P[v, r]: the derivative is L(E-only) (the
+                # other matrices unchanged, this one replaced by E)
+                Pd = P.copy()
+                Pd[v] = 0.0
+                Pd[v, r] = E[v, r]
+                dL = brute.site_likelihood(tree.children, 4, Pd, pi, cw, tips)
+                assert abs(M[v, r, i, j] - np.dot(w, dL / L)) < 1e-11 * max(1, abs(M[v, r, i, j]))
+    g = gradient.branch_gradient(tree, Q, pi, rates, cw, w, states)
+    for v in range(6):
+        gv = sum(rates[r] * np.sum(M[v, r] * (Q @ P[v, r])) for r in range(3))
+        assert abs(gv - g[v]) < 1e-11 * max(1, abs(g[v]))
+
+
+def test_rate_matrix_gradient_vs_finite_differences():
+    """dlogL/dQ against central differences of logL in single entries of Q,
+    diagonal and off-diagonal, including directions that break
+    reversibility (expm of any Q is defined)."""
+    rng = np.random.default_rng(32)
+    tree = small_tree(7, 32)
+    pi = rng.dirichlet(np.ones(4))
+    Q = model.gtr(rng.dirichlet(np.ones(6)) * 6, pi)[0]
+    rates = synth.gamma_rates(0.5)
+    cw = np.full(4, 0.25)
+    states = rand_states(rng, 7, 50, 4)
+    w = rng.integers(1, 3, size=50).astype(float)
+    G = gradient.rate_matrix_gradient(tree, Q, pi, rates, cw, w, states)
+    h = 1e-6
+    for i, j in ((0, 1), (1, 0), (2, 2), (3, 1), (0, 3)):
+        Qp, Qm = Q.copy(), Q.copy()
+        Qp[i, j] += h
+        Qm[i, j] -= h
+        fd = (pruning.loglik(tree, Qp, pi, rates, cw, w, states)[0]
+              - pruning.loglik(tree, Qm, pi, rates, cw, w, states)[0]) / (2 * h)
+        assert abs(G[i, j] - fd) < 1e-6 * max(1, abs(fd)), (i, j, G[i, j], fd)
+
+
+def test_rate_matrix_gradient_euler_identity_and_first_order():
+    """Scaling Q by (1 + e) is scaling every branch length by (1 + e), so
+    <dlogL/dQ, Q> = sum_v t_v dlogL/dt_v. The first-order approximation is
+    exact in any direction that commutes with Q (Q itself; dQ/dkappa of HKY,
+    whose eigenvectors do not depend on kappa) and not in general."""
+    rng = np.random.default_rng(33)
+    tree = small_tree(9, 33)
+    pi = rng.dirichlet(np.ones(4))
+    rates = synth.gamma_rates(0.5)
+    cw = np.full(4, 0.25)
+    states = rand_states(rng, 9, 40, 4)
+    w = np.ones(40)
+    Q, dQ = model.hky(3.0, pi)
+    args = (tree, Q, pi, rates, cw, w, states)
+    G = gradient.rate_matrix_gradient(*args)
+    Ga = gradient.rate_matrix_gradient(*args, first_order=True)
+    g = gradient.branch_gradient(*args)
+    ref = np.dot(tree.edge_len[:16], g[:16])
+    assert abs(np.sum(G * Q) - ref) < 1e-10 * abs(ref)
+    assert abs(np.sum(Ga * Q) - ref) < 1e-10 * abs(ref)
+    gk = gradient.subst_gradient(tree, Q, dQ, pi, rates, cw, w, states)[0]
+    assert abs(np.sum(G * dQ[0]) - gk) < 1e-10 * max(1, abs(gk))
+    assert abs(np.sum(Ga * dQ[0]) - gk) < 1e-10 * max(1, abs(gk))
+    Q2, dQ2 = model.gtr(rng.dirichlet(np.ones(6)) * 6, pi)
+    G2 = gradient.rate_matrix_gradient(tree, Q2, pi, rates, cw, w, states)
+    Ga2 = gradient.rate_matrix_gradient(tree, Q2, pi, rates, cw, w, states, first_order=True)
+    assert np.max(np.abs(G2 - Ga2)) > 1e-3 * np.max(np.abs(G2))
+
+
+def test_complex_step_jacobian_matches_hand_derivatives():
+    f = np.stack([np.random.default_rng(34 + k).dirichlet(np.ones(4)) for k in range(3)])
+    pi4 = np.array([0.1, 0.2, 0.3, 0.4])
+    for name, params, freqs in (("hky", [2.5], pi4), ("gtr", [1, 2, 0.5, 0.7, 3, 1], pi4),
+                                ("gy94", [2.0, 0.3], f)):
+        J = model.rate_jacobian(name, params, freqs)
+        D = np.array(model.build(name, params, freqs)[2])
+        assert np.max(np.abs(J - D)) < 1e-13 * np.max(np.abs(D))
+    # random effects: Q(eps) by central differences of the builder
+    eps = np.random.default_rng(35).normal(0, 0.3, 263)
+    p0 = np.r_[2.0, 0.3, eps]
+    J = model.rate_jacobian("gy94re", p0, f)
+    for k in (2, 50, 264):
+        pp, pm = p0.copy(), p0.copy()
+        pp[k] += 1e-6
+        pm[k] -= 1e-6
+        fd = (model.build("gy94re", pp, f)[0] - model.build("gy94re", pm, f)[0]) / 2e-6
+        assert np.max(np.abs(J[k] - fd)) < 1e-8   # entries of Q are O(1)
+        assert np.max(np.abs(J[k])) > 1e-5
+    Q0 = model.build("gy94re", np.r_[2.0, 0.3, np.zeros(263)], f)[0]
+    assert np.array_equal(Q0, model.gy94(2.0, 0.3, f)[0])
+    assert len(model.gy94_pairs()) == 263
+
+
+@pytest.mark.slow
+def test_random_effects_gradient_vs_finite_differences():
+    """dlogL/deps_k = <dlogL/dQ, dQ/deps_k> against central differences of
+    logL through the random-effects GY94 builder (3 taxa, 61 states)."""
+    rng = np.random.default_rng(36)
+    tree = small_tree(3, 36)
+    f = np.stack([rng.dirichlet(np.ones(4)) for _ in range(3)])
+    eps = rng.normal(0, 0.3, 263)
+    p0 = np.r_[2.0, 0.3, eps]
+    Q, pi, _ = model.build("gy94re", p0, f)
+    rates = synth.gamma_rates(0.5, 2)
+    cw = np.full(2, 0.5)
+    states = rand_states(rng, 3, 10, 61, 0.0)
+    w = np.ones(10)
+    G = gradient.rate_matrix_gradient(tree, Q, pi, rates, cw, w, states)
+    J = model.rate_jacobian("gy94re", p0, f)
+    h = 1e-6
+    for k in (0, 1, 2, 77, 264):
+        pp, pm = p0.copy(), p0.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (pruning.loglik(tree, model.build("gy94re", pp, f)[0], pi, rates, cw, w, states)[0]
+              - pruning.loglik(tree, model.build("gy94re", pm, f)[0], pi, rates, cw, w, states)[0]) / (2 * h)
+        assert abs(np.sum(G * J[k]) - fd) < 1e-6 * max(1, abs(fd)), (k, np.sum(G * J[k]), fd)
