@@ -80,6 +80,17 @@ extern "C" {
 #define TL_MODEL_GY94  3  /* S=61. params: kappa, omega.  freqs: F3x4 [3][4]   */
 #define TL_MODEL_REV   4  /* any S. params: symmetric S x S exchangeabilities
                              (row-major, diagonal ignored).  freqs: pi[S]      */
+#define TL_MODEL_GY94RE 5 /* S=61. GY94 with a multiplicative random effect on
+                             every non-zero off-diagonal element (Sec.
+                             "Algorithmic advances": random-effects models),
+                             s_ij = s_ji scaled by exp(eps_k) so Q stays
+                             reversible. params: kappa, omega, then eps_k for
+                             the TL_GY94_PAIRS unordered pairs (i < j) of sense
+                             codons that differ at one position, in
+                             lexicographic (i, j) order (any real eps).
+                             freqs: F3x4 [3][4]. dQ/dtheta is kept for kappa
+                             and omega; tl_adjoint returns all 265.         */
+#define TL_GY94_PAIRS 263
 
 typedef struct tl_instance tl_instance;
 
@@ -237,6 +248,54 @@ int tl_pre_order_derivative(tl_instance* inst, const tl_pre_op* ops, int count, 
  *   g_c = sum_p w_p [sum_r w_r rho_r q_c^T Q p_c] / [sum_r w_r q_c^T p_c]. */
 int tl_edge_derivatives(tl_instance* inst, const tl_edge* edges, int count, int model,
                         double* out_grad, int n_grad);
+
+/* ---- reverse-mode adjoint ----------------------------------------------
+ * One parent of tl_adjoint: its pre-order partial (parent_pre, a buffer; -1
+ * for the root, q = pi), its two children (post-order buffers or tips) with
+ * the matrix slots of their edges, and for each child the output slot of its
+ * edge (edge >= 0) or -1 to leave the edge out. */
+typedef struct {
+    int parent_pre;
+    int child[2];
+    int mat[2];
+    int edge[2];
+} tl_adj_op;
+
+#define TL_ADJ_FIRST_ORDER 0x1u  /* dlogL/dQ by the first-order approximation
+                                    dP = rho t dQ P instead of the exact
+                                    adjoint (for comparison)                  */
+
+/* Reverse-mode gradient of logL with respect to every branch length, every
+ * entry of Q and every model parameter, from one pass over the stored
+ * partials (Sec. "Discussion": reverse-mode gradients through the adjoint
+ * of the matrix exponential; Sec. "Algorithmic advances": gradients for
+ * random-effects models as dlogL/dQ times dQ/dtheta). For each listed edge
+ * c (parent n, sibling s) and category r the pattern likelihood is linear in
+ * P_c,r, so
+ *   M_c,r = dlogL/dP_c,r = w_r sum_p (w_p / L_p) u_c[r,p] p_c[r,p]^T,
+ *   u_c = q_n o (P_s p_s);
+ * then, with W = V^T M_c,r V^-T and a = rho_r t_c lambda (V, lambda the
+ * model's eigensystem, t_c the length the slot mat[c] was last computed with
+ * by tl_update_matrices for this model):
+ *   out_grad[edge]  = sum_r sum_i W_ii rho_r lambda_i exp(a_i)   (dlogL/dt_c)
+ *   out_dQ          = V^-T [sum_{c,r} rho_r t_c W o Phi] V^T     (dlogL/dQ)
+ *     Phi_ij = (e^{a_i} - e^{a_j}) / (a_i - a_j), e^{a_i} when a_i = a_j;
+ *     with TL_ADJ_FIRST_ORDER: sum_{c,r} rho_r t_c M_c,r P_c,r^T
+ *   out_dtheta[k]   = <dlogL/dQ, dQ/dtheta_k>  (k < n_theta; HKY 1, GTR 6,
+ *                     GY94 2, GY94RE 265 parameters in tl_set_model order).
+ * L_p is formed from the same products, sum_r w_r q_n . (v_a o v_b) with
+ * v_c = P_c p_c, so its scale cancels. Inputs: post-order partials of every
+ * child and the pre-order partials of every parent_pre
+ * (tl_update_pre_partials of the same post-order partials). Root
+ * frequencies are held fixed. Outputs are host
+ * arrays (each may be NULL): out_grad [n_grad] (slots not listed are zeroed),
+ * out_dQ [S*S] row-major, out_dtheta [n_theta] (n_theta must equal the
+ * model's parameter count; models set by tl_set_rate_matrix or tl_set_eigen
+ * have none). Errors: TL_ERR_STATE for a buffer or matrix slot that holds no
+ * data or a slot computed for another model, TL_ERR_INDEX, TL_ERR_ARG,
+ * TL_ERR_NUMERIC for a pattern with zero likelihood. */
+int tl_adjoint(tl_instance* inst, const tl_adj_op* ops, int count, int model, unsigned flags,
+               double* out_grad, int n_grad, double* out_dQ, double* out_dtheta, int n_theta);
 
 /* Read back one buffer in FP64: out [R][n_patterns][S] partials as stored
  * (post-order partials carry their accumulated power-of-two exponents

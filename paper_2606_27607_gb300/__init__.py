@@ -50,7 +50,7 @@ class TreeLikelihood:
         for t in range(self.N):
             self.inst.set_tip_states(t, tips[t])
 
-    N_PARAMS = {"hky": 1, "gtr": 6, "gy94": 2}
+    N_PARAMS = {"hky": 1, "gtr": 6, "gy94": 2, "gy94re": 265, "rev": 0}
 
     def set_model(self, kind: str, params, freqs) -> None:
         self.inst.set_model(0, kind, params, freqs)
@@ -70,6 +70,8 @@ class TreeLikelihood:
             self.children = children.copy()
             self._post = _tree.post_ops(children, self.N)
             self._pre = _tree.pre_ops(children, self.N, self.pre_base)
+            self._preq = _tree.q_ops(children, self.N, self.pre_base)
+            self._adj = _tree.adj_ops(children, self.N, self.pre_base)
         self.edge_len = np.asarray(edge_len, dtype=np.float64)
 
     # evaluation ------------------------------------------------------------
@@ -115,10 +117,20 @@ class TreeLikelihood:
             out[k] = self.inst.pre_order_derivative(self._pre, self.nn, 0).sum()
         return out
 
+    def adjoint(self, first_order: bool = False):
+        """Reverse-mode gradient after loglik(): one pre-order pass storing q,
+        then one pass over the partials (tl_adjoint). Returns (dlogL/dt per
+        node (root 0), dlogL/dQ [S, S], dlogL/dtheta). ``first_order`` takes
+        dlogL/dQ by the approximation dP = rho t dQ P."""
+        self.inst.update_pre_partials(self._preq, 0)
+        n = self.N_PARAMS.get(getattr(self, "kind", None), 0)
+        return self.inst.adjoint(self._adj, self.nn, n, 0, first_order)
+
     def value_and_grad(self):
         """(logL, dlogL/dt per node, dlogL/dtheta) in one forward/backward."""
-        logl, g = self.gradient()
-        return logl, g, self.subst_gradient()
+        logl = self.loglik()
+        g, _, th = self.adjoint()
+        return logl, g, th
 
 
 def __getattr__(name):

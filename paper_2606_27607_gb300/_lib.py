@@ -23,17 +23,22 @@ ERRORS = {-1: "TL_ERR_ARG", -2: "TL_ERR_INDEX", -3: "TL_ERR_ORDER", -4: "TL_ERR_
 TL_PREC_F64, TL_PREC_F32, TL_PREC_TF32, TL_PREC_BF16X3 = 0x1, 0x2, 0x4, 0x8
 TL_SCALE_NONE = 0x100
 TL_SPLIT_MATRICES = 0x200
-TL_MODEL_HKY, TL_MODEL_GTR, TL_MODEL_GY94, TL_MODEL_REV = 1, 2, 3, 4
+TL_MODEL_HKY, TL_MODEL_GTR, TL_MODEL_GY94, TL_MODEL_REV, TL_MODEL_GY94RE = 1, 2, 3, 4, 5
+TL_GY94_PAIRS = 263
+TL_ADJ_FIRST_ORDER = 0x1
 PRECISIONS = {"f64": TL_PREC_F64, "f32": TL_PREC_F32, "tf32": TL_PREC_TF32,
               "tf32x2": TL_PREC_TF32 | TL_SPLIT_MATRICES,
               "bf16x3": TL_PREC_BF16X3}
-MODELS = {"hky": TL_MODEL_HKY, "gtr": TL_MODEL_GTR, "gy94": TL_MODEL_GY94, "rev": TL_MODEL_REV}
+MODELS = {"hky": TL_MODEL_HKY, "gtr": TL_MODEL_GTR, "gy94": TL_MODEL_GY94, "rev": TL_MODEL_REV,
+          "gy94re": TL_MODEL_GY94RE}
 
 OP_DTYPE = np.dtype([("dest", "<i4"), ("child1", "<i4"), ("mat1", "<i4"),
                      ("child2", "<i4"), ("mat2", "<i4")])
 PRE_OP_DTYPE = np.dtype([("parent_pre", "<i4"), ("child", "<i4", 2), ("mat", "<i4", 2),
                          ("dmat", "<i4", 2), ("pre", "<i4", 2), ("edge", "<i4", 2)])
 EDGE_DTYPE = np.dtype([("post", "<i4"), ("pre", "<i4"), ("edge", "<i4")])
+ADJ_OP_DTYPE = np.dtype([("parent_pre", "<i4"), ("child", "<i4", 2), ("mat", "<i4", 2),
+                         ("edge", "<i4", 2)])
 
 
 class TreelikError(RuntimeError):
@@ -74,6 +79,7 @@ SIGNATURES = {
     "tl_update_param_matrices": [_VP, _I, _I, _VP, _VP, _I],
     "tl_pre_order_derivative": [_VP, _VP, _I, _I, _VP, _I],
     "tl_sync": [_VP],
+    "tl_adjoint": [_VP, _VP, _I, _I, _U, _VP, _I, _VP, _VP, _I],
     "tl_batch_create": [_VP, C.POINTER(_VP)],
     "tl_batch_destroy": [_VP],
     "tl_batch_last_error": [_VP, C.c_char_p, C.c_size_t],
@@ -323,6 +329,18 @@ class Instance:
         _check(load().tl_edge_derivatives(self.h, _ptr(a), a.size, model, _ptr(g), n_grad),
                self.h)
         return g
+
+    def adjoint(self, ops: np.ndarray, n_grad: int, n_theta: int, model: int = 0,
+                first_order: bool = False):
+        """(dlogL/dt [n_grad], dlogL/dQ [S, S], dlogL/dtheta [n_theta])."""
+        a = _arr(ops, ADJ_OP_DTYPE)
+        g = np.zeros(n_grad)
+        dq = np.zeros((self.n_states, self.n_states))
+        th = np.zeros(n_theta)
+        flags = TL_ADJ_FIRST_ORDER if first_order else 0
+        _check(load().tl_adjoint(self.h, _ptr(a), a.size, model, flags, _ptr(g), n_grad,
+                                 _ptr(dq), _ptr(th) if n_theta else None, n_theta), self.h)
+        return g, dq, th
 
 
 def _batch_check(rc: int, handle) -> None:

@@ -1,9 +1,10 @@
 """torch.autograd.Function over the library: forward = post-order pass and
-root log-likelihood; backward = the pre-order pass (branch lengths) and one
-pre-order pass per substitution parameter with dP/dtheta (Sec. "Algorithmic
-advances": linear-time gradients; Sec. "Discussion": exact substitution
-gradients through the matrix exponential). All arithmetic runs in the
-library's kernels; this module moves tensors across the boundary."""
+root log-likelihood; backward = one pre-order pass and one adjoint pass,
+which give dlogL/dt for every branch and dlogL/dQ, hence every
+substitution parameter (Sec. "Algorithmic advances": linear-time gradients;
+Sec. "Discussion": exact substitution gradients through the adjoint of the
+matrix exponential). All arithmetic runs in the library's kernels; this
+module moves tensors across the boundary."""
 from __future__ import annotations
 
 import numpy as np
@@ -14,7 +15,8 @@ class LogLikelihood(torch.autograd.Function):
     """logL(t, theta) for a TreeLikelihood whose tips, frequencies, rates and
     topology are set. ``edge_len`` holds one length per non-root node;
     ``params`` are the model parameters (kappa | six GTR exchangeabilities |
-    kappa, omega). Returns a 0-d float64 tensor."""
+    kappa, omega | kappa, omega and 263 random effects). Returns a 0-d
+    float64 tensor."""
 
     @staticmethod
     def forward(ctx, edge_len: torch.Tensor, params: torch.Tensor, tl, kind: str, freqs):
@@ -24,7 +26,7 @@ class LogLikelihood(torch.autograd.Function):
         full = np.zeros(tl.nn)
         full[: tl.nn - 1] = t
         tl.set_tree(tl.children, full)
-        logl = tl.loglik(derivatives=True)
+        logl = tl.loglik()
         ctx.tl = tl
         ctx.dev = edge_len.device
         return torch.tensor(logl, dtype=torch.float64)
@@ -32,10 +34,8 @@ class LogLikelihood(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         tl = ctx.tl
-        # the forward pass left the post-order partials and dP/dt in place:
-        # one pre-order pass for the branch lengths, then one per parameter
-        g = tl.branch_gradient()
-        gth = tl.subst_gradient()
+        # the forward pass left the post-order partials and P in place
+        g, _, gth = tl.adjoint()
         s = float(grad_out)
         gt = torch.from_numpy(s * g[: tl.nn - 1]).to(ctx.dev)
         gp = torch.from_numpy(s * gth).to(ctx.dev)

@@ -751,6 +751,7 @@ int tl_destroy(tl_instance* inst) {
         fr(M.G);
         fr(M.piw);
         fr(M.Qw);
+        fr(M.pairs);
     }
     fr(I->d_red);
     fr(I->d_err);
@@ -878,6 +879,8 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
     if ((rc = dev_alloc(I, &I->d_matw, (size_t)I->elt * matw_elems, "matrix copies")))
         return bail(rc);
     I->mat_set.assign(n_matrices, 0);
+    I->mat_len.assign(n_matrices, 0.0);
+    I->mat_model.assign(n_matrices, -1);
     I->models.resize(n_models);
     const size_t SS = (size_t)I->Spad * I->Spad;
     for (ModelDev& M : I->models) {
@@ -889,7 +892,8 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
             (rc = dev_alloc(I, &M.dQ, sizeof(double) * SS * kMaxDq, "dQ")) ||
             (rc = dev_alloc(I, &M.G, sizeof(double) * SS * kMaxDq * 2, "parameter basis")) ||
             (rc = dev_alloc(I, &M.piw, (size_t)I->elt * I->Spad, "pi copy")) ||
-            (rc = dev_alloc(I, &M.Qw, (size_t)I->elt * SS, "Q copy")))
+            (rc = dev_alloc(I, &M.Qw, (size_t)I->elt * SS, "Q copy")) ||
+            (rc = dev_alloc(I, &M.pairs, sizeof(int) * 2 * TL_GY94_PAIRS, "pair table")))
             return bail(rc);
     }
     if (prec == kTF32) {
@@ -1057,16 +1061,17 @@ static int set_model(tl_instance* inst, int model, int kind, const double* param
         case TL_MODEL_GTR: want_p = 6; want_f = 4; break;
         case TL_MODEL_GY94: want_p = 2; want_f = 12; break;
         case TL_MODEL_REV: want_p = I->S * I->S; want_f = I->S; break;
+        case TL_MODEL_GY94RE: want_p = 2 + TL_GY94_PAIRS; want_f = 12; break;
         default: return fail(I, TL_ERR_ARG, "unknown model kind %d", kind);
     }
     if ((kind == TL_MODEL_HKY || kind == TL_MODEL_GTR) && I->S != 4)
         return fail(I, TL_ERR_ARG, "nucleotide model on a %d-state instance", I->S);
-    if (kind == TL_MODEL_GY94 && I->S != 61)
+    if ((kind == TL_MODEL_GY94 || kind == TL_MODEL_GY94RE) && I->S != 61)
         return fail(I, TL_ERR_ARG, "GY94 needs 61 states, instance has %d", I->S);
     if (n_params != want_p || n_freqs != want_f || !params || !freqs)
         return fail(I, TL_ERR_ARG, "model kind %d takes %d params and %d freqs", kind, want_p, want_f);
-    for (int i = 0; i < n_params; ++i)
-        if (!std::isfinite(params[i]) || params[i] < 0)
+    for (int i = 0; i < n_params; ++i)  // random effects (after kappa, omega) may be negative
+        if (!std::isfinite(params[i]) || (params[i] < 0 && !(kind == TL_MODEL_GY94RE && i >= 2)))
             return fail(I, TL_ERR_NUMERIC, "parameter %d is negative or not finite", i);
     for (int i = 0; i < n_freqs; ++i)
         if (!std::isfinite(freqs[i]) || freqs[i] <= 0)
@@ -1080,6 +1085,8 @@ static int set_model(tl_instance* inst, int model, int kind, const double* param
     int rc = stage(I, params, n_params, freqs, n_freqs);
     if (rc) return rc;
     I->models[model].ready = false;
+    I->models[model].kind = kind;
+    I->models[model].n_params = kind == TL_MODEL_REV ? 0 : n_params;
     return launch_build_model(I, model, kind, I->d_tmp, n_params, I->d_tmp + n_params, n_freqs,
                               check);
 }
@@ -1113,6 +1120,8 @@ int tl_set_rate_matrix(tl_instance* inst, int model, const double* Q, const doub
     cudaMemcpyAsync(M.Q, q.data(), sizeof(double) * q.size(), cudaMemcpyHostToDevice, I->stream);
     cudaMemcpyAsync(M.pi, p.data(), sizeof(double) * Sp, cudaMemcpyHostToDevice, I->stream);
     M.n_dq = 0;
+    M.kind = 0;
+    M.n_params = 0;
     M.ready = false;
     return launch_eigen_from_q(I, model, true);
 }
@@ -1141,6 +1150,8 @@ int tl_set_eigen(tl_instance* inst, int model, const double* V, const double* Vi
     cudaMemcpyAsync(M.lam, l.data(), sizeof(double) * Sp, cudaMemcpyHostToDevice, I->stream);
     cudaMemcpyAsync(M.pi, p.data(), sizeof(double) * Sp, cudaMemcpyHostToDevice, I->stream);
     M.n_dq = 0;
+    M.kind = 0;
+    M.n_params = 0;
     int rc = launch_q_from_eigen(I, model);
     if (rc) return rc;
     return launch_model_working_copies(I, model);
@@ -1210,8 +1221,14 @@ int tl_update_matrices(tl_instance* inst, int model, const int* p_idx, const int
     if (rc) return rc;
     for (int i = 0; i < count; ++i) {
         I->mat_set[p_idx[i]] = 1;
-        if (dp_idx && dp_idx[i] >= 0) I->mat_set[dp_idx[i]] = 1;
+        I->mat_len[p_idx[i]] = edge_len[i];
+        I->mat_model[p_idx[i]] = model;
     }
+    for (int i = 0; i < count; ++i)
+        if (dp_idx && dp_idx[i] >= 0) {
+            I->mat_set[dp_idx[i]] = 1;
+            I->mat_model[dp_idx[i]] = -1;
+        }
     return TL_OK;
 }
 
@@ -1230,6 +1247,141 @@ int tl_get_matrix(tl_instance* inst, int mat, double* out) {
         for (int i = 0; i < S; ++i)
             for (int j = 0; j < S; ++j)
                 out[((size_t)r * S + i) * S + j] = h[((size_t)r * Sp + i) * Sp + j];
+    return TL_OK;
+}
+
+extern "C++" {
+template <typename T>
+static void adj_fill(const Instance* I, const tl_adj_op& o, const double* P0, const double* P1,
+                     const int row[2], std::vector<char>& table, size_t at) {
+    AdjOp<T> d;
+    std::memset(&d, 0, sizeof d);
+    d.q = o.parent_pre >= 0 ? reinterpret_cast<const T*>(I->h_buf[o.parent_pre]) : nullptr;
+    for (int c = 0; c < 2; ++c) {
+        const int v = o.child[c];
+        if (v < I->n_tips && I->tip_set[v] == 1) {
+            d.st[c] = I->h_tipst[v];
+        } else {
+            d.part[c] = reinterpret_cast<const T*>(I->h_buf[v]);
+        }
+        d.row[c] = row[c];
+    }
+    d.P[0] = P0;
+    d.P[1] = P1;
+    std::memcpy(table.data() + at * sizeof d, &d, sizeof d);
+}
+}  // extern "C++"
+
+int tl_adjoint(tl_instance* inst, const tl_adj_op* ops, int count, int model, unsigned flags,
+               double* out_grad, int n_grad, double* out_dQ, double* out_dtheta, int n_theta) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (model < 0 || model >= I->n_models || !I->models[model].ready)
+        return fail(I, TL_ERR_STATE, "model %d not set", model);
+    if (count < 0 || (count > 0 && !ops)) return fail(I, TL_ERR_ARG, "bad op list");
+    if (n_grad < 0 || (n_grad > 0 && !out_grad)) return fail(I, TL_ERR_ARG, "bad out_grad");
+    if (flags & ~TL_ADJ_FIRST_ORDER) return fail(I, TL_ERR_ARG, "unknown flags 0x%x", flags);
+    const ModelDev& Mo = I->models[model];
+    if (out_dtheta && n_theta != Mo.n_params)
+        return fail(I, TL_ERR_ARG, "model %d has %d parameters, n_theta is %d", model, Mo.n_params,
+                    n_theta);
+    const int NB = I->n_bufs, SS = I->Spad * I->Spad;
+    const size_t mat_doubles = (size_t)I->R * SS;
+    const size_t op_bytes = I->elt == 8 ? sizeof(AdjOp<double>) : sizeof(AdjOp<float>);
+    std::vector<char> table(op_bytes * std::max(count, 1));
+    std::vector<AdjEdge> edges;
+    std::vector<int> edge_id, seen(std::max(n_grad, 1), 0);
+    for (int k = 0; k < count; ++k) {
+        const tl_adj_op& o = ops[k];
+        if (o.parent_pre != -1 && (o.parent_pre < I->n_tips || o.parent_pre >= NB ||
+                                   !I->buf_written[o.parent_pre - I->n_tips]))
+            return fail(I, TL_ERR_STATE, "adjoint op %d: parent_pre %d holds no pre-order partial",
+                        k, o.parent_pre);
+        const double* P[2];
+        int row[2];
+        for (int c = 0; c < 2; ++c) {
+            const int v = o.child[c], m = o.mat[c];
+            if (v < 0 || v >= NB) return fail(I, TL_ERR_INDEX, "adjoint op %d: child %d", k, v);
+            if (v < I->n_tips ? !I->tip_set[v] : !I->buf_written[v - I->n_tips])
+                return fail(I, TL_ERR_STATE, "adjoint op %d: child %d holds no data", k, v);
+            if (m < 0 || m >= I->n_mats) return fail(I, TL_ERR_INDEX, "adjoint op %d: matrix %d", k, m);
+            if (!I->mat_set[m] || I->mat_model[m] != model)
+                return fail(I, TL_ERR_STATE, "adjoint op %d: matrix %d is not a transition matrix "
+                            "of model %d", k, m, model);
+            P[c] = I->d_mat64 + (size_t)m * mat_doubles;
+            row[c] = -1;
+            const int e = o.edge[c];
+            if (e >= 0) {
+                if (e >= n_grad) return fail(I, TL_ERR_INDEX, "adjoint op %d: edge %d >= n_grad", k, e);
+                if (seen[e]) return fail(I, TL_ERR_ORDER, "adjoint op %d: edge %d listed twice", k, e);
+                seen[e] = 1;
+                row[c] = (int)edges.size();
+                edges.push_back({P[c], I->mat_len[m]});
+                edge_id.push_back(e);
+            }
+        }
+        if (I->elt == 8) adj_fill<double>(I, o, P[0], P[1], row, table, k);
+        else adj_fill<float>(I, o, P[0], P[1], row, table, k);
+    }
+    const int E = (int)edges.size();
+    int rc;
+    if ((size_t)I->R > I->tmp_cap) {
+        dev_free(I, I->d_tmp);
+        I->tmp_cap = I->R + 1024;
+        if ((rc = dev_alloc(I, &I->d_tmp, sizeof(double) * I->tmp_cap, "staging"))) return rc;
+    }
+    if ((rc = stage(I, I->h_rates, I->R, nullptr, 0))) return rc;
+    // scratch: [coef | mpart | M | gpart | G | grad | dQ | theta]
+    const int n_chunks = adj_chunks(I, std::max(count, 1));
+    const bool nuc = use_nuc(I);
+    const size_t n_coef = nuc ? 0 : (size_t)count * I->Ppad;
+    const size_t n_mpart = (size_t)E * mat_doubles * n_chunks;
+    const size_t n_M = (size_t)E * mat_doubles;
+    const size_t n_gpart = (size_t)SS * std::max(E, 1);
+    const size_t n_theta_dev = 2 + TL_GY94_PAIRS + kMaxDq;
+    if ((rc = ensure_scratch(I, n_coef + n_mpart + n_M + n_gpart + SS + E + SS + n_theta_dev)))
+        return rc;
+    double* d_coef = I->d_red;
+    double* d_mpart = d_coef + n_coef;
+    double* d_M = d_mpart + n_mpart;
+    double* d_gpart = d_M + n_M;
+    double* d_G = d_gpart + n_gpart;
+    double* d_grad = d_G + SS;
+    double* d_dQ = d_grad + E;
+    double* d_theta = d_dQ + SS;
+    void* d_ops = area(I, 1, table.size() + sizeof(AdjEdge) * std::max(E, 1) + 16, &rc);
+    if (rc) return rc;
+    AdjEdge* d_edges = reinterpret_cast<AdjEdge*>((char*)d_ops + ((table.size() + 15) / 16) * 16);
+    if ((rc = h2d(I, d_ops, table.data(), table.size()))) return rc;
+    if (E > 0 && (rc = h2d(I, d_edges, edges.data(), sizeof(AdjEdge) * E))) return rc;
+    if (count > 0 && E > 0) {
+        if ((rc = launch_adj_accumulate(I, d_ops, count, n_chunks, d_coef, d_mpart, model)))
+            return rc;
+        if ((rc = reduce_fixed(I, d_mpart, (int)n_M, n_chunks, d_M))) return rc;
+        const bool first = flags & TL_ADJ_FIRST_ORDER;
+        if ((rc = launch_adj_finish(I, model, d_M, d_edges, E, first, d_gpart, d_grad))) return rc;
+        if ((rc = reduce_fixed(I, d_gpart, SS, E, d_G))) return rc;
+    } else {
+        cudaMemsetAsync(d_G, 0, sizeof(double) * SS, I->stream);
+    }
+    if ((rc = launch_adj_params(I, model, d_G, flags & TL_ADJ_FIRST_ORDER, d_dQ, d_theta)))
+        return rc;
+    std::vector<double> h_grad(std::max(E, 1)), h_dQ(SS), h_theta(n_theta_dev);
+    if (E > 0) cudaMemcpyAsync(h_grad.data(), d_grad, sizeof(double) * E, cudaMemcpyDeviceToHost, I->stream);
+    cudaMemcpyAsync(h_dQ.data(), d_dQ, sizeof(double) * SS, cudaMemcpyDeviceToHost, I->stream);
+    cudaMemcpyAsync(h_theta.data(), d_theta, sizeof(double) * n_theta_dev, cudaMemcpyDeviceToHost,
+                    I->stream);
+    if ((rc = cuda_check(I, cudaStreamSynchronize(I->stream), "tl_adjoint"))) return rc;
+    if ((rc = check_numeric_flag(I))) return rc;
+    if (out_grad) {
+        for (int i = 0; i < n_grad; ++i) out_grad[i] = 0.0;
+        for (int e = 0; e < E; ++e) out_grad[edge_id[e]] = h_grad[e];
+    }
+    if (out_dQ)
+        for (int i = 0; i < I->S; ++i)
+            for (int j = 0; j < I->S; ++j) out_dQ[i * I->S + j] = h_dQ[(size_t)i * I->Spad + j];
+    if (out_dtheta)
+        for (int k = 0; k < n_theta; ++k) out_dtheta[k] = h_theta[k];
     return TL_OK;
 }
 
@@ -1478,7 +1630,10 @@ int tl_update_param_matrices(tl_instance* inst, int model, int param, const int*
     if ((rc = upload(I, extra(I).areas[3], idx, sizeof(int) * count, &d_idx))) return rc;
     if ((rc = launch_param_matrices(I, model, param, (const int*)d_idx, I->d_tmp + I->R, count)))
         return rc;
-    for (int i = 0; i < count; ++i) I->mat_set[idx[i]] = 1;
+    for (int i = 0; i < count; ++i) {
+        I->mat_set[idx[i]] = 1;
+        I->mat_model[idx[i]] = -1;
+    }
     return TL_OK;
 }
 

@@ -133,7 +133,10 @@ struct ModelDev {
     double* G = nullptr;      // [kMaxDq][Spad][Spad]: Vinv dQ V, then as much scratch
     void* piw = nullptr;      // pi in working precision [Spad]
     void* Qw = nullptr;       // Q in working precision [Spad][Spad]
+    int* pairs = nullptr;     // GY94RE: [TL_GY94_PAIRS][2] codon indices (i < j)
     int n_dq = 0;
+    int kind = 0;             // TL_MODEL_* (0: set from Q or an eigensystem)
+    int n_params = 0;         // parameters of tl_set_model
     bool ready = false;
     bool basis_ready = false;  // G computed for the current V, Vinv, dQ
 };
@@ -171,6 +174,8 @@ struct Instance {
     void* d_matw = nullptr;          // working copies
     size_t matw_stride = 0;          // elements per matrix slot in d_matw
     std::vector<char> mat_set;
+    std::vector<double> mat_len;     // length each P slot was last computed with
+    std::vector<int> mat_model;      // and its model (-1: not a P, or a derivative)
     std::vector<ModelDev> models;
 
     // scratch
@@ -281,6 +286,29 @@ int launch_pre_tc(Instance* I, const tl_pre_op* ops, int n, const int* edge_row,
                   double* d_gpart, void* d_ops_area, size_t cap, int dgen);
 int launch_q_tc(Instance* I, int model);
 size_t tc_matw_floats(const Instance* I);
+
+// tl_adjoint.cu (reverse-mode adjoint): one parent as the device reads it.
+// Partials are [R][Ppad][Spad] in the working precision; a tip with states
+// has part == nullptr and st set.
+template <typename T>
+struct __align__(16) AdjOp {
+    const T* q;            // parent's pre-order partial; nullptr at the root (q = pi)
+    const T* part[2];      // children's partials (nullptr: tip states)
+    const int8_t* st[2];   // children's tip states
+    const double* P[2];    // FP64 transition matrices of the edges [R][Spad][Spad]
+    int row[2];            // output row of each edge (-1: not listed)
+};
+struct AdjEdge {           // one listed edge for the eigenbasis finish
+    const double* P;       // [R][Spad][Spad]
+    double t;
+};
+int adj_chunks(const Instance* I, int n_ops);
+int launch_adj_accumulate(Instance* I, const void* d_ops, int n_ops, int n_chunks, double* d_coef,
+                          double* d_mpart, int model);
+int launch_adj_finish(Instance* I, int model, const double* d_M, const AdjEdge* d_edges, int E,
+                      bool first_order, double* d_gpart, double* d_grad);
+int launch_adj_params(Instance* I, int model, const double* d_G, bool first_order, double* d_dQ,
+                      double* d_theta);
 
 // tl_api.cu helpers used by the other units
 int upload_bytes(Instance* I, void* dst, const void* src, size_t bytes);

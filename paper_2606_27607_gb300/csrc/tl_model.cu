@@ -26,12 +26,22 @@ __device__ __forceinline__ bool is_transition(int x, int y) {
 }
 
 // Build Q, pi and dQ/dtheta for one model slot. One block.
+__device__ __forceinline__ bool one_difference(int ci, int cj) {
+    const int x = ci ^ cj;  // two bits per position
+    return ((x & 0x30) != 0) + ((x & 0x0c) != 0) + ((x & 0x03) != 0) == 1;
+}
+
+// Build Q, pi and dQ/dtheta for one model slot. One block. Random-effects
+// GY94 numbers the unordered one-difference pairs (i < j) lexicographically
+// (row counts, a prefix sum, then each row's pairs) and writes that list.
 __global__ void k_build_model(int kind, int S, int Spad, const double* __restrict__ params,
                               const double* __restrict__ freqs, double* __restrict__ Q,
                               double* __restrict__ pi, double* __restrict__ dQ, int n_dq,
-                              int* __restrict__ err) {
+                              int* __restrict__ pairs, int* __restrict__ err) {
     __shared__ int codon_nt[64];   // sense codon -> 16*n1 + 4*n2 + n3
     __shared__ char codon_aa[64];
+    __shared__ short pair_of[61 * 61];  // random effects: pair index of (i, j), i < j
+    __shared__ int row_start[62];
     __shared__ double s_pi[64];
     __shared__ double s_red[256];
     __shared__ double s_mu[1 + kMaxDq];
@@ -48,8 +58,33 @@ __global__ void k_build_model(int kind, int S, int Spad, const double* __restric
         }
     }
     __syncthreads();
+    const bool codon = kind == TL_MODEL_GY94 || kind == TL_MODEL_GY94RE;
+    if (kind == TL_MODEL_GY94RE) {
+        if (t < 61) {
+            int n = 0;
+            for (int j = t + 1; j < 61; ++j) n += one_difference(codon_nt[t], codon_nt[j]);
+            row_start[t + 1] = n;
+        }
+        __syncthreads();
+        if (t == 0) {
+            row_start[0] = 0;
+            for (int i = 1; i <= 61; ++i) row_start[i] += row_start[i - 1];
+        }
+        __syncthreads();
+        if (t < 61) {
+            int k = row_start[t];
+            for (int j = t + 1; j < 61; ++j)
+                if (one_difference(codon_nt[t], codon_nt[j])) {
+                    pair_of[t * 61 + j] = (short)k;
+                    pairs[2 * k] = t;
+                    pairs[2 * k + 1] = j;
+                    ++k;
+                }
+        }
+        __syncthreads();
+    }
     // stationary frequencies
-    if (kind == TL_MODEL_GY94) {
+    if (codon) {
         for (int i = t; i < 61; i += nt) {
             int c = codon_nt[i];
             s_pi[i] = freqs[c >> 4] * freqs[4 + ((c >> 2) & 3)] * freqs[8 + (c & 3)];
@@ -83,7 +118,7 @@ __global__ void k_build_model(int kind, int S, int Spad, const double* __restric
                 int k = (a == 0) ? (b - 1) : (a == 1 ? (b + 1) : 5);
                 r = params[k] * s_pi[j];
                 d[k] = s_pi[j];
-            } else if (kind == TL_MODEL_GY94) {
+            } else if (codon) {
                 int ci = codon_nt[i], cj = codon_nt[j];
                 int ndiff = 0, pos = -1;
                 for (int q = 0; q < 3; ++q) {
@@ -98,9 +133,12 @@ __global__ void k_build_model(int kind, int S, int Spad, const double* __restric
                     bool ns = codon_aa[i] != codon_aa[j];
                     double kap = ts ? params[0] : 1.0;
                     double om = ns ? params[1] : 1.0;
-                    r = kap * om * s_pi[j];
-                    d[0] = (ts ? 1.0 : 0.0) * om * s_pi[j];
-                    d[1] = kap * (ns ? 1.0 : 0.0) * s_pi[j];
+                    const double m = (kind == TL_MODEL_GY94RE)
+                                         ? exp(params[2 + pair_of[min(i, j) * 61 + max(i, j)]])
+                                         : 1.0;
+                    r = kap * om * s_pi[j] * m;
+                    d[0] = (ts ? 1.0 : 0.0) * om * s_pi[j] * m;
+                    d[1] = kap * (ns ? 1.0 : 0.0) * s_pi[j] * m;
                 }
             } else {  // TL_MODEL_REV
                 r = 0.5 * (params[i * S + j] + params[j * S + i]) * s_pi[j];
@@ -567,10 +605,11 @@ int launch_build_model(Instance* I, int m, int kind, const double* d_params, int
     (void)n_params;
     (void)n_freqs;
     ModelDev& M = I->models[m];
-    int n_dq = kind == TL_MODEL_HKY ? 1 : kind == TL_MODEL_GTR ? 6 : kind == TL_MODEL_GY94 ? 2 : 0;
+    int n_dq = kind == TL_MODEL_HKY ? 1 : kind == TL_MODEL_GTR ? 6
+               : (kind == TL_MODEL_GY94 || kind == TL_MODEL_GY94RE) ? 2 : 0;
     M.n_dq = n_dq;
     k_build_model<<<1, 256, 0, I->stream>>>(kind, I->S, I->Spad, d_params, d_freqs, M.Q, M.pi,
-                                            M.dQ, n_dq, I->d_err);
+                                            M.dQ, n_dq, M.pairs, I->d_err);
     I->launches += 1;
     int rc = cuda_check(I, cudaGetLastError(), "build model");
     if (rc) return rc;

@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from ._lib import EDGE_DTYPE, OP_DTYPE, PRE_OP_DTYPE
+from ._lib import ADJ_OP_DTYPE, EDGE_DTYPE, OP_DTYPE, PRE_OP_DTYPE
 
 
 def n_nodes(n_tips: int) -> int:
@@ -41,6 +41,28 @@ def pre_ops(children, n_tips: int, pre_base: int, with_edges: bool = True,
         pre = [pre_base + c if (c >= N or tip_pre) else -1 for c in (a, b)]
         edge = [a, b] if with_edges else [-1, -1]
         ops[i] = (parent_pre, (a, b), (a, b), (nn + a, nn + b), pre, edge)
+    return ops
+
+
+def q_ops(children, n_tips: int, pre_base: int) -> np.ndarray:
+    """Pre-order ops that only store q of every internal node (no edges, no
+    derivative matrices): the input of the adjoint."""
+    ops = pre_ops(children, n_tips, pre_base, with_edges=False)
+    ops["dmat"] = -1
+    return ops
+
+
+def adj_ops(children, n_tips: int, pre_base: int) -> np.ndarray:
+    """Adjoint ops, one per internal node: its q buffer (-1 at the root),
+    both children, their edges' matrix slots and output slots (node
+    indices)."""
+    children = np.asarray(children)
+    N = n_tips
+    root = 2 * N - 2
+    ops = np.zeros(N - 1, dtype=ADJ_OP_DTYPE)
+    for k, (a, b) in enumerate(children):
+        v = N + k
+        ops[k] = (-1 if v == root else pre_base + v, (a, b), (a, b), (a, b))
     return ops
 
 
