@@ -466,12 +466,18 @@ def serving_line(args) -> dict:
 
 
 def autograd_line(args) -> dict:
-    """logL and its gradient (every branch length and the substitution
-    parameters) through the torch.autograd Function, one forward + backward
+    """logL and its gradient (every branch length and every substitution
+    parameter) through the torch.autograd Function, one forward + backward
     per evaluation (host-synchronous: the loss comes back as a number), on
-    GTR+G4 1,024 taxa x 50,000 patterns (FP32, FP64) and GY94 64 taxa x 5,000
-    patterns (TF32, split TF32, FP64 generic). Latency per evaluation, and
-    the error of each precision against the FP64 GPU path."""
+    GTR+G4 1,024 taxa x 50,000 patterns (FP32, FP64), GY94 64 taxa x 5,000
+    patterns (TF32, split TF32, FP64 generic) and the same GY94 with a random
+    effect on each of its 263 non-zero rate pairs (265 parameters). The
+    backward is one pre-order pass plus the adjoint pass. Latency per
+    evaluation and the error of each precision against the FP64 GPU path;
+    then, per workload, the backward's substitution gradient by three
+    methods: the exact adjoint, the first-order approximation of the
+    matrix-exponential derivative, and one pre-order pass per parameter
+    (not available for the 263 random effects), with time and error."""
     import numpy as np
     import torch
 
@@ -479,15 +485,18 @@ def autograd_line(args) -> dict:
     from paper_2606_27607_gb300 import LogLikelihood, TreeLikelihood, build
     build.build()
     torch.cuda.set_device(0)
-    out = {}
-    for name, precs, S in (("gtr_1024x50k", ("f64", "f32"), 4),
-                           ("gy94_64x5k", ("f64", "tf32", "tf32x2"), 61)):
-        w = synth.workload(name)
+    out, methods = {}, {}
+    eps = synth.random_effects()
+    for name, base, precs, model in (("gtr_1024x50k", "gtr_1024x50k", ("f64", "f32"), "gtr"),
+                                     ("gy94_64x5k", "gy94_64x5k", ("f64", "tf32", "tf32x2"), "gy94"),
+                                     ("gy94re_64x5k", "gy94_64x5k", ("f64", "tf32x2"), "gy94re")):
+        w = synth.workload(base)
+        params = np.r_[w.params, eps] if model == "gy94re" else np.asarray(w.params, float)
         res, ref = {}, None
         for prec in precs:
-            tl = TreeLikelihood(w.tree.n_tips, w.n_patterns, S, 4, prec)
+            tl = TreeLikelihood(w.tree.n_tips, w.n_patterns, w.n_states, 4, prec)
             tl.set_tips(w.tips)
-            tl.set_model(w.model, w.params, w.freqs)
+            tl.set_model(model, params, w.freqs)
             tl.set_rates(w.rates, w.cat_weights)
             tl.set_pattern_weights(w.pattern_weights)
             tl.set_tree(w.tree.children, w.tree.edge_len)
@@ -495,16 +504,15 @@ def autograd_line(args) -> dict:
             n_it = max(3, min(args.steps, 20))
             for it in range(3 + n_it):
                 t = torch.tensor(w.tree.edge_len[:-1], dtype=torch.float64, requires_grad=True)
-                th = torch.tensor(w.params, dtype=torch.float64, requires_grad=True)
+                th = torch.tensor(params, dtype=torch.float64, requires_grad=True)
                 t0 = time.perf_counter()
-                y = LogLikelihood.apply(t, th, tl, w.model, w.freqs)
+                y = LogLikelihood.apply(t, th, tl, model, w.freqs)
                 y.backward()
                 gt, gk = t.grad.numpy().copy(), th.grad.numpy().copy()
                 if it >= 3:
                     lat.append(time.perf_counter() - t0)
-            tl.close()
             r = {"evals_per_s": len(lat) / sum(lat), "p50_ms": 1e3 * _pct(lat, 50),
-                 "p99_ms": 1e3 * _pct(lat, 99), "logL": float(y.detach())}
+                 "p99_ms": 1e3 * _pct(lat, 99), "logL": float(y.detach()), "n_params": len(params)}
             if prec == "f64":
                 ref = (float(y.detach()), gt, gk)
             else:
@@ -513,10 +521,38 @@ def autograd_line(args) -> dict:
                 r["rel_err_grad_theta"] = float(np.max(np.abs(gk - ref[2])) /
                                                 np.max(np.abs(ref[2])))
             res[prec] = r
+            if prec == precs[-1]:
+                # the substitution gradient of the backward by three methods
+                m = {}
+                tl.loglik()
+
+                def timed(f, n=5):
+                    f()
+                    torch.cuda.synchronize()
+                    t1 = time.perf_counter()
+                    for _ in range(n):
+                        val = f()
+                    torch.cuda.synchronize()
+                    return 1e3 * (time.perf_counter() - t1) / n, val
+
+                ms, (_, _, g_ex) = timed(lambda: tl.adjoint())
+                m["adjoint_exact"] = {"backward_ms": ms, "rel_err_theta_vs_f64": float(
+                    np.max(np.abs(g_ex - ref[2])) / np.max(np.abs(ref[2])))}
+                ms, (_, _, g_fo) = timed(lambda: tl.adjoint(first_order=True))
+                m["adjoint_first_order"] = {"backward_ms": ms, "rel_err_theta_vs_f64": float(
+                    np.max(np.abs(g_fo - ref[2])) / np.max(np.abs(ref[2])))}
+                if model != "gy94re":
+                    ms, g_pp = timed(lambda: tl.subst_gradient(), 2)
+                    m["pre_order_pass_per_parameter"] = {
+                        "backward_ms": ms, "passes": len(params),
+                        "rel_err_theta_vs_f64": float(np.max(np.abs(g_pp - ref[2])) /
+                                                      np.max(np.abs(ref[2])))}
+                methods[f"{name}/{prec}"] = m
+            tl.close()
         out[name] = res
     return {"metric": "autograd forward+backward evaluations/s and latency", "unit": "evals/s",
             "n_gpus": 1, "data": "synthetic", "config": {"workload": "autograd"},
-            "results": out}
+            "results": out, "substitution_gradient_methods": methods}
 
 
 def main() -> None:

@@ -250,11 +250,13 @@ int tl_edge_derivatives(tl_instance* inst, const tl_edge* edges, int count, int 
                         double* out_grad, int n_grad);
 
 /* ---- reverse-mode adjoint ----------------------------------------------
- * One parent of tl_adjoint: its pre-order partial (parent_pre, a buffer; -1
- * for the root, q = pi), its two children (post-order buffers or tips) with
- * the matrix slots of their edges, and for each child the output slot of its
- * edge (edge >= 0) or -1 to leave the edge out. */
+ * One parent of tl_adjoint: its post-order buffer (parent_post), its
+ * pre-order partial (parent_pre, a buffer; -1 for the root, q = pi), its two
+ * children (post-order buffers or tips) with the matrix slots of their edges,
+ * and for each child the output slot of its edge (edge >= 0) or -1 to leave
+ * the edge out. */
 typedef struct {
+    int parent_post;
     int parent_pre;
     int child[2];
     int mat[2];
@@ -283,9 +285,11 @@ typedef struct {
  *     with TL_ADJ_FIRST_ORDER: sum_{c,r} rho_r t_c M_c,r P_c,r^T
  *   out_dtheta[k]   = <dlogL/dQ, dQ/dtheta_k>  (k < n_theta; HKY 1, GTR 6,
  *                     GY94 2, GY94RE 265 parameters in tl_set_model order).
- * L_p is formed from the same products, sum_r w_r q_n . (v_a o v_b) with
- * v_c = P_c p_c, so its scale cancels. Inputs: post-order partials of every
- * child and the pre-order partials of every parent_pre
+ * L_p is taken at the parent, up to the scales that cancel: from the same
+ * products sum_r w_r q_n . (v_a o v_b), v_c = P_c p_c (four states), or
+ * from the stored post-order partial of parent_post and its rescaling
+ * exponents (any S). Inputs: post-order partials of every parent_post and
+ * child, and the pre-order partials of every parent_pre
  * (tl_update_pre_partials of the same post-order partials). Root
  * frequencies are held fixed. Outputs are host
  * arrays (each may be NULL): out_grad [n_grad] (slots not listed are zeroed),

@@ -37,8 +37,8 @@ OP_DTYPE = np.dtype([("dest", "<i4"), ("child1", "<i4"), ("mat1", "<i4"),
 PRE_OP_DTYPE = np.dtype([("parent_pre", "<i4"), ("child", "<i4", 2), ("mat", "<i4", 2),
                          ("dmat", "<i4", 2), ("pre", "<i4", 2), ("edge", "<i4", 2)])
 EDGE_DTYPE = np.dtype([("post", "<i4"), ("pre", "<i4"), ("edge", "<i4")])
-ADJ_OP_DTYPE = np.dtype([("parent_pre", "<i4"), ("child", "<i4", 2), ("mat", "<i4", 2),
-                         ("edge", "<i4", 2)])
+ADJ_OP_DTYPE = np.dtype([("parent_post", "<i4"), ("parent_pre", "<i4"), ("child", "<i4", 2),
+                         ("mat", "<i4", 2), ("edge", "<i4", 2)])
 
 
 class TreelikError(RuntimeError):

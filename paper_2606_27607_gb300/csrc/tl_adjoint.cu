@@ -21,12 +21,16 @@
 // models as dlogL/dQ times dQ/dtheta, with a first-order approximation of
 // the exponential's derivative, dP ~ rho t dQ P, kept here for comparison).
 //
-// The scales of u and p cancel against L_p's, which is formed from the same
-// products, L_p ~ sum_r w_r q_n . (v_a o v_b), v_c = P_c p_c (so that
-// sum_r <M_c,r, P_c,r> = sum_p w_p holds in the working arithmetic, as in
-// the fused gradient's ratio): the four-state kernel has all categories of a
-// pattern in neighbouring lanes; for any S a first kernel sums L_p over the
-// categories and stores w_p / L_p per parent and pattern.
+// The scales of u and p cancel against L_p's. The four-state kernel forms
+// L_p from the same products, sum_r w_r q_n . (v_a o v_b) (all categories
+// of a pattern in neighbouring lanes); for any S a first kernel takes it
+// from the parent's stored post-order partial, L_p ~ 2^{s_n} sum_r w_r
+// q_n . p_n, with s_n the parent's own rescaling exponent (its cumulative
+// exponent minus its children's): one read of q_n and p_n instead of the
+// two products per category. The stored p_n is v_a o v_b rounded to the
+// working precision, so the two forms differ by that rounding (about 1e-5
+// relative over 64 states for TF32 storage, 1e-16 in FP64).
+#include <algorithm>
 #include <cmath>
 
 #include "tl_internal.cuh"
@@ -39,6 +43,7 @@ struct AdjArgs {
     const double* coef;   // generic path: [n_ops][Ppad] w_p / L_p (scaled)
     int* err;             // numeric flag (zero pattern likelihood)
     int R, Ppad, Spad, S, chunk, n_chunks;
+    size_t n_rows;        // rows of the per-chunk outputs: listed edges x R x Spad^2
     double catw[kMaxCat];
 };
 
@@ -84,25 +89,43 @@ __global__ void __launch_bounds__(128) k_adj4(const AdjOp<T>* __restrict__ ops, 
 #pragma unroll
     for (int k = 0; k < 16; ++k) accA[k] = accB[k] = T(0);
     bool bad = false;
-    for (int base = p_begin + warp * PPW; base < p_end; base += 4 * PPW) {
+    // software pipeline: the loads of the next pattern are issued before the
+    // arithmetic of this one
+    T nq[4] = {}, nx[2][4] = {};
+    int ns[2] = {0, 0};
+    auto fetch = [&](int base) {
+        const int p = base + ps;
+        const int pl = p < p_end ? p : p_begin;
+        if (q) load4(q + ((size_t)rr * a.Ppad + pl) * 4, nq);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (op.st[c]) ns[c] = op.st[c][pl];
+            else load4(op.part[c] + ((size_t)rr * a.Ppad + pl) * 4, nx[c]);
+        }
+    };
+    const int first = p_begin + warp * PPW;
+    if (first < p_end) fetch(first);
+    for (int base = first; base < p_end; base += 4 * PPW) {
         const int p = base + ps;
         const bool inb = p < p_end;
-        const int pl = inb ? p : p_begin;
         T qv[4], x[2][4], v[2][4];
-        if (q) load4(q + ((size_t)rr * a.Ppad + pl) * 4, qv);
-        else {
+        int sv[2];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) qv[i] = spi[i];
+        for (int i = 0; i < 4; ++i) qv[i] = q ? nq[i] : spi[i];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            sv[c] = ns[c];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[c][j] = nx[c][j];
         }
+        if (base + 4 * PPW < p_end) fetch(base + 4 * PPW);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             if (op.st[c]) {
-                const int s = op.st[c][pl];
+                const int s = sv[c];
                 const bool amb = s < 0 || s >= 4;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) x[c][j] = (amb || s == j) ? T(1) : T(0);
-            } else {
-                load4(op.part[c] + ((size_t)rr * a.Ppad + pl) * 4, x[c]);
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -157,7 +180,7 @@ __global__ void __launch_bounds__(128) k_adj4(const AdjOp<T>* __restrict__ ops, 
         const double s = ((red[0][rc][k] + red[1][rc][k]) + red[2][rc][k]) + red[3][rc][k];
         const int row = op.row[c];
         if (row >= 0)
-            mpart[((size_t)(row * a.R + rc) * 16 + (k & 15)) * a.n_chunks + blockIdx.y] = s;
+            mpart[(size_t)blockIdx.y * a.n_rows + (size_t)(row * a.R + rc) * 16 + (k & 15)] = s;
     }
 }
 
@@ -235,57 +258,48 @@ __device__ __forceinline__ void adj_tile_v(const T* Pt, const T* XT, T* Vs) {
         for (int ii = 0; ii < 4; ++ii) Vs[(vc * kGT + vp + pp) * 64 + vi + ii] = acc[pp * 4 + ii];
 }
 
-// w_p / L_p per parent and pattern, L_p = sum_r w_r sum_i q_i v_a,i v_b,i in
-// the same arithmetic as the outer products. Block: one parent, one chunk
-// (at most kMaxChunk patterns); categories outermost so that each tile of
-// each category is read once; L_p accumulates in shared memory in category
-// order.
-constexpr int kMaxChunk = 4096;
+// w_p / L_p per parent and pattern from the stored q_n and p_n. Block: one
+// parent, 16 patterns; a half-warp per pattern, a lane per four states
+// (one 16-byte load of q and of p_n per category), fixed-order shuffle sums.
+constexpr int kCoefPat = 16;
 template <typename T>
-__global__ void __launch_bounds__(256) k_adj_den(const AdjOp<T>* __restrict__ ops, AdjArgs a,
-                                                 double* __restrict__ coef) {
-    extern __shared__ __align__(16) unsigned char sm_den[];
-    T* Pt = reinterpret_cast<T*>(sm_den);        // [2][64][64]
-    T* XT = Pt + 2 * 64 * 64;                    // [2][64][kGP]
-    T* Qs = XT + 2 * 64 * kGP;                   // [kGT][64]
-    T* Vs = Qs + kGT * 64;                       // [2][kGT][64]
-    double* den = reinterpret_cast<double*>(Vs + 2 * kGT * 64);  // [kMaxChunk]
+__global__ void __launch_bounds__(256) k_adj_coef(const AdjOp<T>* __restrict__ ops, AdjArgs a,
+                                                  double* __restrict__ coef) {
     const AdjOp<T>& op = ops[blockIdx.x];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int p_begin = blockIdx.y * a.chunk;
-    const int p_end = min(a.Ppad, p_begin + a.chunk);
-    for (int k = t; k < kMaxChunk; k += blockDim.x) den[k] = 0.0;
+    const int lane = threadIdx.x & 31, half = threadIdx.x >> 4, l16 = lane & 15;
+    const int p = blockIdx.y * kCoefPat + half;
+    const bool inb = p < a.Ppad;
+    const int pl = inb ? p : 0;
+    double den = 0.0;
     for (int r = 0; r < a.R; ++r) {
-        __syncthreads();
-        adj_load_mats(op, a, r, Pt);
-        for (int p0 = p_begin; p0 < p_end; p0 += kGT) {
-            __syncthreads();
-            adj_load_tile<T>(op, a, r, p0, nullptr, XT, Qs);
-            __syncthreads();
-            adj_tile_v(Pt, XT, Vs);
-            __syncthreads();
-            for (int pp = warp; pp < kGT; pp += blockDim.x >> 5) {
-                T d = Qs[pp * 64 + lane] * Vs[pp * 64 + lane] * Vs[(kGT + pp) * 64 + lane] +
-                      Qs[pp * 64 + 32 + lane] * Vs[pp * 64 + 32 + lane] *
-                          Vs[(kGT + pp) * 64 + 32 + lane];
+        T s = T(0);
+        for (int i0 = 4 * l16; i0 < a.Spad; i0 += 64) {
+            const size_t off = ((size_t)r * a.Ppad + pl) * a.Spad + i0;
+            T q4[4], p4[4];
+            if (op.q) load4(op.q + off, q4);
+            else {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-                if (lane == 0) den[p0 - p_begin + pp] += a.catw[r] * (double)d;
+                for (int k = 0; k < 4; ++k) q4[k] = i0 + k < a.S ? (T)a.pi[i0 + k] : T(0);
             }
+            load4(op.pn + off, p4);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s += q4[k] * p4[k];
         }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        den += a.catw[r] * (double)s;
     }
-    __syncthreads();
-    bool bad = false;
-    for (int p = p_begin + t; p < p_end; p += blockDim.x) {
-        const double wp = a.patw[p], d = den[p - p_begin];
+    if (l16 == 0 && inb) {
+        const double wp = a.patw[p];
         double cf = 0.0;
         if (wp != 0.0) {
-            if (d > 0.0) cf = wp / d;
-            else bad = true;
+            int sn = op.en ? op.en[p] : 0;
+            for (int c = 0; c < 2; ++c) sn -= op.ec[c] ? op.ec[c][p] : 0;
+            if (den > 0.0) cf = ldexp(wp / den, -sn);
+            else atomicOr(a.err, 1);
         }
         coef[(size_t)blockIdx.x * a.Ppad + p] = cf;
     }
-    if (bad) atomicOr(a.err, 1);
 }
 
 template <typename T>
@@ -352,7 +366,7 @@ __global__ void __launch_bounds__(256) k_adj_gen(const AdjOp<T>* __restrict__ op
             for (int jj = 0; jj < 4; ++jj) {
                 const int i = mi + ii, j = mj + jj;
                 if (i < Spad && j < Spad)
-                    mpart[((size_t)(row * a.R + r) * SS + i * Spad + j) * a.n_chunks + blockIdx.z] =
+                    mpart[(size_t)blockIdx.z * a.n_rows + (size_t)(row * a.R + r) * SS + i * Spad + j] =
                         (double)acc[ii * 4 + jj];
             }
     }
@@ -360,6 +374,189 @@ __global__ void __launch_bounds__(256) k_adj_gen(const AdjOp<T>* __restrict__ op
 
 static size_t adj_gen_smem(int elt) {
     return (size_t)elt * (2 * 64 * 64 + 2 * kGT * 64 + 2 * 64 * kGP + kGT * 64 + 2 * kGT * 64 + kGT);
+}
+
+// ---- TF32 instances: the same two products on the tensor cores ---------------
+// mma.sync m16n8k8 with TF32 operands and FP32 accumulators. The child
+// partials are stored TF32-rounded, so they enter exactly; P and U are split
+// as hi + lo (hi = TF32 nearest, lo = TF32 nearest of the remainder) and
+// each product is issued twice, which keeps about 21 bits of every operand.
+// Tiles of 16 patterns; 8 warps:
+//   v_c = x_c P_c^T  (warp: child w/4, output columns 16 (w%4) .. +16),
+//       written straight into U of the sibling: U_s = coef w_r q o v_c;
+//   M_c += U_c^T x_c (warp: child w/4, rows 16 (w%4) .. +16, all 64 columns,
+//       32 FP32 accumulators per thread across the chunk).
+// Fragment layouts (PTX ISA, mma.m16n8k8 .tf32): lane = 4 g + t;
+// A: a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4);
+// B: b0 (k=t, n=g), b1 (k=t+4, n=g); C: c0,c1 (g, 2t..2t+1), c2,c3 (g+8, ...).
+constexpr int kMT = 16;    // patterns per tile
+constexpr int kPP = 68;    // pitch of P and x rows (conflict-free row-g, column-t reads)
+constexpr int kUP = 72;    // pitch of U rows (conflict-free row-t, column-g reads)
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+        "{%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(256, 2) k_adj_mma(const AdjOp<float>* __restrict__ ops, AdjArgs a,
+                                                    double* __restrict__ mpart) {
+    extern __shared__ __align__(16) unsigned char sm_mma[];
+    uint32_t* Ph = reinterpret_cast<uint32_t*>(sm_mma);   // [2][64][kPP]  P_c[i][j] hi
+    uint32_t* Pl = Ph + 2 * 64 * kPP;                       // lo
+    float* X = reinterpret_cast<float*>(Pl + 2 * 64 * kPP); // [2][kMT][kPP] x_c[p][j]
+    float* Qs = X + 2 * kMT * kPP;                          // [kMT][kPP]
+    uint32_t* Uh = reinterpret_cast<uint32_t*>(Qs + kMT * kPP);  // [2][kMT][kUP] U_c[p][i]
+    uint32_t* Ul = Uh + 2 * kMT * kUP;
+    float* Cs = reinterpret_cast<float*>(Ul + 2 * kMT * kUP);    // [kMT]
+    const AdjOp<float>& op = ops[blockIdx.x];
+    const int r = blockIdx.y;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int g = lane >> 2, tq = lane & 3;
+    const int S = a.S, Spad = a.Spad;
+    for (int idx = t; idx < 2 * 64 * 64; idx += blockDim.x) {
+        const int c = idx >> 12, i = (idx >> 6) & 63, j = idx & 63;
+        const double pv = (i < S && j < S) ? op.P[c][((size_t)r * Spad + i) * Spad + j] : 0.0;
+        const float pf = (float)pv;
+        const uint32_t h = tf32_rna(pf);
+        Ph[(c * 64 + i) * kPP + j] = h;
+        Pl[(c * 64 + i) * kPP + j] = tf32_rna(pf - __uint_as_float(h));
+    }
+    const float wr = (float)a.catw[r];
+    const int p_begin = blockIdx.z * a.chunk;
+    const int p_end = min(a.Ppad, p_begin + a.chunk);
+    const int wc = warp >> 2, wq = warp & 3;
+    float acc[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[nt][k] = 0.f;
+    // Registers hold the next tile's loads while this tile is multiplied.
+    const int lp = t >> 4, lj4 = (t & 15) * 4;
+    float4 rx[2], rq;
+    double rc = 0.0;
+    auto fetch = [&](int p0) {
+        const int p = p0 + lp;
+        const size_t off = ((size_t)r * a.Ppad + p) * Spad + lj4;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (op.st[c]) {
+                const int s = op.st[c][p];
+                const bool amb = s < 0 || s >= S;
+                rx[c].x = (lj4 + 0 < S && (amb || s == lj4 + 0)) ? 1.f : 0.f;
+                rx[c].y = (lj4 + 1 < S && (amb || s == lj4 + 1)) ? 1.f : 0.f;
+                rx[c].z = (lj4 + 2 < S && (amb || s == lj4 + 2)) ? 1.f : 0.f;
+                rx[c].w = (lj4 + 3 < S && (amb || s == lj4 + 3)) ? 1.f : 0.f;
+            } else {
+                rx[c] = *reinterpret_cast<const float4*>(op.part[c] + off);
+            }
+        }
+        if (op.q) {
+            rq = *reinterpret_cast<const float4*>(op.q + off);
+        } else {
+            rq.x = lj4 + 0 < S ? (float)a.pi[lj4 + 0] : 0.f;
+            rq.y = lj4 + 1 < S ? (float)a.pi[lj4 + 1] : 0.f;
+            rq.z = lj4 + 2 < S ? (float)a.pi[lj4 + 2] : 0.f;
+            rq.w = lj4 + 3 < S ? (float)a.pi[lj4 + 3] : 0.f;
+        }
+        if (t < kMT) rc = a.coef[(size_t)blockIdx.x * a.Ppad + p0 + t];
+    };
+    if (p_begin < p_end) fetch(p_begin);
+    for (int p0 = p_begin; p0 < p_end; p0 += kMT) {
+        __syncthreads();  // the previous tile's readers are done
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+            *reinterpret_cast<float4*>(X + (c * kMT + lp) * kPP + lj4) = rx[c];
+        *reinterpret_cast<float4*>(Qs + lp * kPP + lj4) = rq;
+        if (t < kMT) Cs[t] = (float)rc * wr;
+        __syncthreads();
+        if (p0 + kMT < p_end) fetch(p0 + kMT);
+        {   // v_wc = x_wc P_wc^T on columns [16 wq, 16 wq + 16); U of the sibling
+            float v[2][4];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v[nt][k] = 0.f;
+            const float* xa = X + wc * kMT * kPP;
+            const uint32_t* ph = Ph + wc * 64 * kPP;
+            const uint32_t* pl = Pl + wc * 64 * kPP;
+#pragma unroll
+            for (int ks = 0; ks < 8; ++ks) {
+                const int k0 = ks * 8;
+                uint32_t af[4];
+                af[0] = __float_as_uint(xa[g * kPP + k0 + tq]);
+                af[1] = __float_as_uint(xa[(g + 8) * kPP + k0 + tq]);
+                af[2] = __float_as_uint(xa[g * kPP + k0 + tq + 4]);
+                af[3] = __float_as_uint(xa[(g + 8) * kPP + k0 + tq + 4]);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    const int n = 16 * wq + 8 * nt + g;
+                    mma_tf32(v[nt], af, ph[n * kPP + k0 + tq], ph[n * kPP + k0 + tq + 4]);
+                    mma_tf32(v[nt], af, pl[n * kPP + k0 + tq], pl[n * kPP + k0 + tq + 4]);
+                }
+            }
+            const int sib = 1 - wc;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int p = g + (k >> 1) * 8, i = 16 * wq + 8 * nt + 2 * tq + (k & 1);
+                    const float u = Cs[p] * Qs[p * kPP + i] * v[nt][k];
+                    const uint32_t h = tf32_rna(u);
+                    Uh[(sib * kMT + p) * kUP + i] = h;
+                    Ul[(sib * kMT + p) * kUP + i] = tf32_rna(u - __uint_as_float(h));
+                }
+        }
+        __syncthreads();
+        {   // M_wc[16 wq .. +16][0 .. 64) += U_wc^T x_wc
+            const uint32_t* uh = Uh + wc * kMT * kUP;
+            const uint32_t* ul = Ul + wc * kMT * kUP;
+            const float* xb = X + wc * kMT * kPP;
+            const int m0 = 16 * wq;
+#pragma unroll
+            for (int ks = 0; ks < kMT / 8; ++ks) {
+                const int k0 = ks * 8;
+                uint32_t ah[4], al[4];
+                ah[0] = uh[(k0 + tq) * kUP + m0 + g];
+                ah[1] = uh[(k0 + tq) * kUP + m0 + g + 8];
+                ah[2] = uh[(k0 + tq + 4) * kUP + m0 + g];
+                ah[3] = uh[(k0 + tq + 4) * kUP + m0 + g + 8];
+                al[0] = ul[(k0 + tq) * kUP + m0 + g];
+                al[1] = ul[(k0 + tq) * kUP + m0 + g + 8];
+                al[2] = ul[(k0 + tq + 4) * kUP + m0 + g];
+                al[3] = ul[(k0 + tq + 4) * kUP + m0 + g + 8];
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) {
+                    const uint32_t b0 = __float_as_uint(xb[(k0 + tq) * kPP + 8 * nt + g]);
+                    const uint32_t b1 = __float_as_uint(xb[(k0 + tq + 4) * kPP + 8 * nt + g]);
+                    mma_tf32(acc[nt], ah, b0, b1);
+                    mma_tf32(acc[nt], al, b0, b1);
+                }
+            }
+        }
+    }
+    const int row = op.row[wc];
+    if (row < 0) return;
+    const int SS = Spad * Spad;
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = 16 * wq + g + (k >> 1) * 8, j = 8 * nt + 2 * tq + (k & 1);
+            mpart[(size_t)blockIdx.z * a.n_rows + (size_t)(row * a.R + r) * SS + i * Spad + j] =
+                (double)acc[nt][k];
+        }
+}
+
+static size_t adj_mma_smem() {
+    return sizeof(uint32_t) * (4 * 64 * kPP + 2 * kMT * kPP + kMT * kPP + 4 * kMT * kUP + kMT);
 }
 
 static bool adj_nuc(const Instance* I) { return I->S == 4 && (I->prec == kF32 || I->prec == kF64); }
@@ -373,7 +570,7 @@ int adj_chunks(const Instance* I, int n_ops) {
     const int per = adj_nuc(I) ? n_ops : n_ops * I->R;
     const int step = adj_nuc(I) ? 128 : kGT;
     int n = std::max(1, (4 * sms + per - 1) / std::max(per, 1));
-    const int cap = adj_nuc(I) ? (I->elt == 4 ? 2048 : (1 << 30)) : kMaxChunk;
+    const int cap = adj_nuc(I) ? (I->elt == 4 ? 2048 : (1 << 30)) : 4096;
     n = std::max(n, (I->Ppad + cap - 1) / cap);
     n = std::min(n, (I->Ppad + step - 1) / step);
     return n;
@@ -387,7 +584,7 @@ static int adj_chunk_len(const Instance* I, int n_chunks) {
 
 template <typename T>
 static int adj_accumulate_t(Instance* I, const void* d_ops, int n_ops, int n_chunks,
-                            double* d_coef, double* d_mpart, int model) {
+                            size_t n_rows, double* d_coef, double* d_mpart, int model) {
     AdjArgs a;
     a.pi = I->models[model].pi;
     a.patw = I->d_patw;
@@ -398,6 +595,7 @@ static int adj_accumulate_t(Instance* I, const void* d_ops, int n_ops, int n_chu
     a.Spad = I->Spad;
     a.S = I->S;
     a.n_chunks = n_chunks;
+    a.n_rows = n_rows;
     a.chunk = adj_chunk_len(I, n_chunks);
     for (int r = 0; r < kMaxCat; ++r) a.catw[r] = r < I->R ? I->h_catw[r] : 0.0;
     const AdjOp<T>* ops = reinterpret_cast<const AdjOp<T>*>(d_ops);
@@ -412,10 +610,16 @@ static int adj_accumulate_t(Instance* I, const void* d_ops, int n_ops, int n_chu
         I->launches += 1;
         return cuda_check(I, cudaGetLastError(), "adjoint (four states)");
     }
-    const size_t smem_den = sizeof(T) * (2 * 64 * 64 + 2 * 64 * kGP + kGT * 64 + 2 * kGT * 64) +
-                            sizeof(double) * kMaxChunk;
-    cudaFuncSetAttribute(k_adj_den<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_den);
-    k_adj_den<T><<<dim3(n_ops, n_chunks), 256, smem_den, I->stream>>>(ops, a, d_coef);
+    k_adj_coef<T><<<dim3(n_ops, (I->Ppad + kCoefPat - 1) / kCoefPat), 256, 0, I->stream>>>(
+        ops, a, d_coef);
+    if (I->prec == kTF32 && I->Spad == 64) {
+        const size_t smem = adj_mma_smem();
+        cudaFuncSetAttribute(k_adj_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_adj_mma<<<dim3(n_ops, I->R, n_chunks), 256, smem, I->stream>>>(
+            reinterpret_cast<const AdjOp<float>*>(d_ops), a, d_mpart);
+        I->launches += 2;
+        return cuda_check(I, cudaGetLastError(), "adjoint (tensor cores)");
+    }
     const size_t smem = adj_gen_smem(sizeof(T));
     cudaFuncSetAttribute(k_adj_gen<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_adj_gen<T><<<dim3(n_ops, I->R, n_chunks), 256, smem, I->stream>>>(ops, a, d_mpart);
@@ -423,12 +627,32 @@ static int adj_accumulate_t(Instance* I, const void* d_ops, int n_ops, int n_chu
     return cuda_check(I, cudaGetLastError(), "adjoint (any S)");
 }
 
-int launch_adj_accumulate(Instance* I, const void* d_ops, int n_ops, int n_chunks, double* d_coef,
-                          double* d_mpart, int model) {
+int launch_adj_accumulate(Instance* I, const void* d_ops, int n_ops, int n_chunks, size_t n_rows,
+                          double* d_coef, double* d_mpart, int model) {
     if (I->Spad > 64) return fail(I, TL_ERR_UNSUPPORTED, "adjoint built for at most 64 states");
     if (I->elt == 8)
-        return adj_accumulate_t<double>(I, d_ops, n_ops, n_chunks, d_coef, d_mpart, model);
-    return adj_accumulate_t<float>(I, d_ops, n_ops, n_chunks, d_coef, d_mpart, model);
+        return adj_accumulate_t<double>(I, d_ops, n_ops, n_chunks, n_rows, d_coef, d_mpart, model);
+    return adj_accumulate_t<float>(I, d_ops, n_ops, n_chunks, n_rows, d_coef, d_mpart, model);
+}
+
+// out[row] = sum over chunks of in[chunk][row], in chunk order.
+__global__ void k_sum_chunks(const double* __restrict__ in, size_t n_rows, int n_chunks,
+                             double* __restrict__ out) {
+    for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < n_rows;
+         row += (size_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < n_chunks; ++c) s += in[(size_t)c * n_rows + row];
+        out[row] = s;
+    }
+}
+
+int launch_adj_sum_chunks(Instance* I, const double* d_in, size_t n_rows, int n_chunks,
+                          double* d_out) {
+    if (n_rows == 0) return TL_OK;
+    const int blocks = (int)std::min<size_t>((n_rows + 255) / 256, 152 * 16);
+    k_sum_chunks<<<blocks, 256, 0, I->stream>>>(d_in, n_rows, n_chunks, d_out);
+    I->launches += 1;
+    return cuda_check(I, cudaGetLastError(), "adjoint chunk sums");
 }
 
 // ---- the finish in the eigenbasis, one block per edge ----------------------

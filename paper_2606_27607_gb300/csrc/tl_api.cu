@@ -1257,12 +1257,15 @@ static void adj_fill(const Instance* I, const tl_adj_op& o, const double* P0, co
     AdjOp<T> d;
     std::memset(&d, 0, sizeof d);
     d.q = o.parent_pre >= 0 ? reinterpret_cast<const T*>(I->h_buf[o.parent_pre]) : nullptr;
+    d.pn = reinterpret_cast<const T*>(I->h_buf[o.parent_post]);
+    d.en = I->h_scale[o.parent_post];
     for (int c = 0; c < 2; ++c) {
         const int v = o.child[c];
         if (v < I->n_tips && I->tip_set[v] == 1) {
             d.st[c] = I->h_tipst[v];
         } else {
             d.part[c] = reinterpret_cast<const T*>(I->h_buf[v]);
+            d.ec[c] = v < I->n_tips ? nullptr : I->h_scale[v];
         }
         d.row[c] = row[c];
     }
@@ -1293,6 +1296,10 @@ int tl_adjoint(tl_instance* inst, const tl_adj_op* ops, int count, int model, un
     std::vector<int> edge_id, seen(std::max(n_grad, 1), 0);
     for (int k = 0; k < count; ++k) {
         const tl_adj_op& o = ops[k];
+        if (o.parent_post < I->n_tips || o.parent_post >= NB ||
+            !I->buf_written[o.parent_post - I->n_tips])
+            return fail(I, TL_ERR_STATE, "adjoint op %d: parent_post %d holds no post-order partial",
+                        k, o.parent_post);
         if (o.parent_pre != -1 && (o.parent_pre < I->n_tips || o.parent_pre >= NB ||
                                    !I->buf_written[o.parent_pre - I->n_tips]))
             return fail(I, TL_ERR_STATE, "adjoint op %d: parent_pre %d holds no pre-order partial",
@@ -1355,9 +1362,9 @@ int tl_adjoint(tl_instance* inst, const tl_adj_op* ops, int count, int model, un
     if ((rc = h2d(I, d_ops, table.data(), table.size()))) return rc;
     if (E > 0 && (rc = h2d(I, d_edges, edges.data(), sizeof(AdjEdge) * E))) return rc;
     if (count > 0 && E > 0) {
-        if ((rc = launch_adj_accumulate(I, d_ops, count, n_chunks, d_coef, d_mpart, model)))
+        if ((rc = launch_adj_accumulate(I, d_ops, count, n_chunks, n_M, d_coef, d_mpart, model)))
             return rc;
-        if ((rc = reduce_fixed(I, d_mpart, (int)n_M, n_chunks, d_M))) return rc;
+        if ((rc = launch_adj_sum_chunks(I, d_mpart, n_M, n_chunks, d_M))) return rc;
         const bool first = flags & TL_ADJ_FIRST_ORDER;
         if ((rc = launch_adj_finish(I, model, d_M, d_edges, E, first, d_gpart, d_grad))) return rc;
         if ((rc = reduce_fixed(I, d_gpart, SS, E, d_G))) return rc;

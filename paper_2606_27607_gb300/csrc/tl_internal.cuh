@@ -289,11 +289,14 @@ size_t tc_matw_floats(const Instance* I);
 
 // tl_adjoint.cu (reverse-mode adjoint): one parent as the device reads it.
 // Partials are [R][Ppad][Spad] in the working precision; a tip with states
-// has part == nullptr and st set.
+// has part == nullptr and st set; exponents are cumulative (nullptr: 0).
 template <typename T>
 struct __align__(16) AdjOp {
     const T* q;            // parent's pre-order partial; nullptr at the root (q = pi)
+    const T* pn;           // parent's post-order partial
+    const int* en;         // its cumulative exponents
     const T* part[2];      // children's partials (nullptr: tip states)
+    const int* ec[2];      // children's cumulative exponents (nullptr: 0)
     const int8_t* st[2];   // children's tip states
     const double* P[2];    // FP64 transition matrices of the edges [R][Spad][Spad]
     int row[2];            // output row of each edge (-1: not listed)
@@ -303,8 +306,10 @@ struct AdjEdge {           // one listed edge for the eigenbasis finish
     double t;
 };
 int adj_chunks(const Instance* I, int n_ops);
-int launch_adj_accumulate(Instance* I, const void* d_ops, int n_ops, int n_chunks, double* d_coef,
-                          double* d_mpart, int model);
+int launch_adj_accumulate(Instance* I, const void* d_ops, int n_ops, int n_chunks, size_t n_rows,
+                          double* d_coef, double* d_mpart, int model);
+int launch_adj_sum_chunks(Instance* I, const double* d_in, size_t n_rows, int n_chunks,
+                          double* d_out);
 int launch_adj_finish(Instance* I, int model, const double* d_M, const AdjEdge* d_edges, int E,
                       bool first_order, double* d_gpart, double* d_grad);
 int launch_adj_params(Instance* I, int model, const double* d_G, bool first_order, double* d_dQ,

@@ -53,16 +53,16 @@ def q_ops(children, n_tips: int, pre_base: int) -> np.ndarray:
 
 
 def adj_ops(children, n_tips: int, pre_base: int) -> np.ndarray:
-    """Adjoint ops, one per internal node: its q buffer (-1 at the root),
-    both children, their edges' matrix slots and output slots (node
-    indices)."""
+    """Adjoint ops, one per internal node: its post-order buffer, its q
+    buffer (-1 at the root), both children, their edges' matrix slots and
+    output slots (node indices)."""
     children = np.asarray(children)
     N = n_tips
     root = 2 * N - 2
     ops = np.zeros(N - 1, dtype=ADJ_OP_DTYPE)
     for k, (a, b) in enumerate(children):
         v = N + k
-        ops[k] = (-1 if v == root else pre_base + v, (a, b), (a, b), (a, b))
+        ops[k] = (v, -1 if v == root else pre_base + v, (a, b), (a, b), (a, b))
     return ops
 
 

@@ -297,6 +297,15 @@ def workload(name: str, **override) -> Workload:
     return make_workload(name=name, **kw)
 
 
+N_GY94_PAIRS = 263   # codon pairs one nucleotide apart (the non-zero rates)
+
+
+def random_effects(config: int = 3, sd: float = 0.3) -> np.ndarray:
+    """One log-scale random effect per non-zero GY94 off-diagonal pair,
+    i.i.d. Normal(0, sd), from the configuration's "extra" substream."""
+    return rng_for(config, "extra").normal(0.0, sd, N_GY94_PAIRS)
+
+
 # ---------------------------------------------------------------------------
 # serving stream: requests from many MCMC chains
 # ---------------------------------------------------------------------------
