@@ -62,13 +62,30 @@ __device__ __forceinline__ void load4(const double* p, double* o) {
 // patterns with the R categories of a pattern in LPP neighbouring lanes, so
 // L_p is a butterfly sum over those lanes. Each lane accumulates both
 // children's 4 x 4 outer products for its category; the sums over a warp's
-// patterns and then over the four warps are in a fixed order.
+// patterns and then over the four warps are in a fixed order. Each lane
+// streams its own q and child partials (16 or 32 bytes per pattern) through a
+// kAdjStages-deep cp.async ring in shared memory, so that several patterns'
+// loads are in flight per lane without holding registers.
+constexpr int kAdjStages = 4;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <typename T, int LPP>
 __global__ void __launch_bounds__(128) k_adj4(const AdjOp<T>* __restrict__ ops, AdjArgs a,
                                               double* __restrict__ mpart) {
-    __shared__ T sP[2][kMaxCat][16];
+    __shared__ T sP[2][kMaxCat][17];   // pitch 17: lanes of 4 categories hit 4 banks
     __shared__ T spi[4];
     __shared__ double red[4][kMaxCat][32];
+    // ring: [warp][stage][array (q, x_a, x_b)][lane][4] (two stages in FP64: static
+    // shared memory stays under 48 KB)
+    constexpr int NST = sizeof(T) == 8 ? 2 : kAdjStages;
+    __shared__ __align__(16) T ring[4][NST][3][32][4];
     const AdjOp<T>& op = ops[blockIdx.x];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (int idx = t; idx < 2 * a.R * 16; idx += blockDim.x) {
@@ -84,48 +101,74 @@ __global__ void __launch_bounds__(128) k_adj4(const AdjOp<T>* __restrict__ ops, 
     const T wr = act ? (T)a.catw[r] : T(0);
     const int p_begin = blockIdx.y * a.chunk;
     const int p_end = min(a.Ppad, p_begin + a.chunk);
+    // the op's pointers in registers (the copies' memory clobbers would
+    // otherwise reload them every pattern)
     const T* q = op.q;
+    const int8_t* st[2] = {op.st[0], op.st[1]};
+    const T* part[2] = {op.part[0], op.part[1]};
+    const double* patw = a.patw;
+    const bool st0 = st[0] != nullptr, st1 = st[1] != nullptr;
     T accA[16], accB[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) accA[k] = accB[k] = T(0);
     bool bad = false;
-    // software pipeline: the loads of the next pattern are issued before the
-    // arithmetic of this one
-    T nq[4] = {}, nx[2][4] = {};
-    int ns[2] = {0, 0};
-    auto fetch = [&](int base) {
-        const int p = base + ps;
-        const int pl = p < p_end ? p : p_begin;
-        if (q) load4(q + ((size_t)rr * a.Ppad + pl) * 4, nq);
+    const int first = p_begin + warp * PPW, step = 4 * PPW;
+    const int n_it = first < p_end ? (p_end - first + step - 1) / step : 0;
+    // issue the copies of iteration k into its stage (an empty group past the end)
+    auto issue = [&](int k) {
+        if (k < n_it) {
+            const int p = first + k * step + ps;
+            const int pl = p < p_end ? p : p_begin;
+            const size_t off = ((size_t)rr * a.Ppad + pl) * 4;
+            T(*stg)[32][4] = ring[warp][k % NST];
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            if (op.st[c]) ns[c] = op.st[c][pl];
-            else load4(op.part[c] + ((size_t)rr * a.Ppad + pl) * 4, nx[c]);
+            for (int h = 0; h < (int)sizeof(T) * 4 / 16; ++h) {
+                if (q) cp_async16(&stg[0][lane][h * 16 / sizeof(T)], q + off + h * 16 / sizeof(T));
+                if (!st0) cp_async16(&stg[1][lane][h * 16 / sizeof(T)],
+                                     part[0] + off + h * 16 / sizeof(T));
+                if (!st1) cp_async16(&stg[2][lane][h * 16 / sizeof(T)],
+                                     part[1] + off + h * 16 / sizeof(T));
+            }
         }
+        cp_async_commit();
     };
-    const int first = p_begin + warp * PPW;
-    if (first < p_end) fetch(first);
-    for (int base = first; base < p_end; base += 4 * PPW) {
-        const int p = base + ps;
+    // tip states and pattern weights: registers, one pattern ahead
+    int nst[2] = {0, 0};
+    double nwp = 0.0;
+    auto fetch_small = [&](int k) {
+        const int p = first + k * step + ps;
+        const int pl = p < p_end ? p : p_begin;
+        if (st0) nst[0] = st[0][pl];
+        if (st1) nst[1] = st[1][pl];
+        nwp = p < p_end ? patw[pl] : 0.0;
+    };
+#pragma unroll
+    for (int k = 0; k < NST - 1; ++k) issue(k);
+    if (n_it > 0) fetch_small(0);
+    for (int k = 0; k < n_it; ++k) {
+        issue(k + NST - 1);
+        const int sv[2] = {nst[0], nst[1]};
+        const double wp = nwp;
+        if (k + 1 < n_it) fetch_small(k + 1);
+        cp_async_wait<NST - 1>();
+        const int p = first + k * step + ps;
         const bool inb = p < p_end;
+        const T(*stg)[32][4] = ring[warp][k % NST];
         T qv[4], x[2][4], v[2][4];
-        int sv[2];
+        if (q) load4(&stg[0][lane][0], qv);
+        else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) qv[i] = q ? nq[i] : spi[i];
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            sv[c] = ns[c];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) x[c][j] = nx[c][j];
+            for (int i = 0; i < 4; ++i) qv[i] = spi[i];
         }
-        if (base + 4 * PPW < p_end) fetch(base + 4 * PPW);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            if (op.st[c]) {
+            if (c == 0 ? st0 : st1) {
                 const int s = sv[c];
                 const bool amb = s < 0 || s >= 4;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) x[c][j] = (amb || s == j) ? T(1) : T(0);
+            } else {
+                load4(&stg[1 + c][lane][0], x[c]);
             }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -141,7 +184,6 @@ __global__ void __launch_bounds__(128) k_adj4(const AdjOp<T>* __restrict__ ops, 
         d = (act && inb) ? wr * d : T(0);
 #pragma unroll
         for (int o = 1; o < LPP; o <<= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-        const double wp = inb ? a.patw[p] : 0.0;
         T coef = T(0);
         if (wp != 0.0) {
             if (d > T(0)) coef = (T)wp / d;
@@ -158,6 +200,7 @@ __global__ void __launch_bounds__(128) k_adj4(const AdjOp<T>* __restrict__ ops, 
             }
         }
     }
+    cp_async_wait<0>();
     if (bad) atomicOr(a.err, 1);
 #pragma unroll
     for (int o = LPP; o < 32; o <<= 1) {
