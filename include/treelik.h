@@ -59,7 +59,7 @@ extern "C" {
 /* ---- creation flags ---------------------------------------------------- */
 #define TL_PREC_F64    0x1u   /* FP64 partials and matrices (any S <= 64)      */
 #define TL_PREC_F32    0x2u   /* FP32 partials (S == 4), FP64 reductions       */
-#define TL_PREC_TF32   0x4u   /* S in 33..64: tcgen05 kind::tf32 contractions,
+#define TL_PREC_TF32   0x4u   /* S in 5..64: tcgen05 kind::tf32 contractions,
                                  TF32-rounded FP32 partials, FP32 accumulate   */
 #define TL_PREC_BF16X3 0x8u   /* S in 33..64: tcgen05 kind::f16 with a BF16
                                  hi/lo split, three products per contraction   */
@@ -132,8 +132,8 @@ typedef struct {
     int edge;
 } tl_edge;
 
-/* Create an instance. n_states: 1..64 (TL_PREC_F32: 4; TF32/BF16X3: 33..64,
- * stored padded to 64). n_categories: 1..8 (TL_PREC_TF32: 1..4; more
+/* Create an instance. n_states: 1..64 (TL_PREC_F32: 4; TF32: 5..64, stored
+ * padded to 64, e.g. 20 amino acids or 61 codons). n_categories: 1..8 (TL_PREC_TF32: 1..4; more
  * returns TL_ERR_UNSUPPORTED). n_buffers: internal partials
  * buffers. n_matrices: transition-matrix slots (each holds all categories).
  * n_models: model slots (Q, pi, eigensystem, dQ/dtheta). stream: a

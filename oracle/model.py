@@ -154,10 +154,22 @@ def gy94(kappa, omega, f3x4, eps=None):
     return Q, pi, dQ
 
 
+def rev(exch, pi):
+    """General reversible model on len(pi) states: s_ij = (E_ij + E_ji) / 2 for
+    the S x S exchangeability matrix E (diagonal ignored). Returns Q."""
+    pi = np.asarray(pi, float)
+    S = len(pi)
+    E = np.asarray(exch).reshape(S, S)
+    E = 0.5 * (E + E.T)
+    R = E * pi[None, :]
+    return _normalise(R, pi, [])[0]
+
+
 def build(model: str, params, freqs):
-    """(Q, pi, [dQ/dtheta]) for model in {"hky", "gtr", "gy94", "gy94re"}
+    """(Q, pi, [dQ/dtheta]) for model in {"hky", "gtr", "gy94", "gy94re", "rev"}
     ("gy94re": params kappa, omega, then one random effect per pair of
-    gy94_pairs(); the dQ list covers kappa and omega)."""
+    gy94_pairs(); the dQ list covers kappa and omega; "rev": params the S x S
+    exchangeabilities, no dQ list)."""
     if model == "hky":
         Q, dQ = hky(params[0], freqs)
         return Q, np.asarray(freqs, float), dQ
@@ -168,6 +180,8 @@ def build(model: str, params, freqs):
         return gy94(params[0], params[1], freqs)
     if model == "gy94re":
         return gy94(params[0], params[1], freqs, np.asarray(params[2:]))
+    if model == "rev":
+        return rev(params, freqs), np.asarray(freqs, float), []
     raise ValueError(model)
 
 

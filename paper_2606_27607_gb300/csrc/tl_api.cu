@@ -792,8 +792,8 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
         return fail(nullptr, TL_ERR_UNSUPPORTED, "TL_PREC_F32 is built for 4 states");
     if (prec == kBF16X3)
         return fail(nullptr, TL_ERR_UNSUPPORTED, "TL_PREC_BF16X3 is not built in this library");
-    if (prec == kTF32 && (n_states < 33 || n_states > 64))
-        return fail(nullptr, TL_ERR_UNSUPPORTED, "TL_PREC_TF32 is built for 33..64 states");
+    if (prec == kTF32 && (n_states < 5 || n_states > 64))
+        return fail(nullptr, TL_ERR_UNSUPPORTED, "TL_PREC_TF32 is built for 5..64 states");
     // the tensor-core kernels hold both children's products of every
     // category in the 512 TMEM columns (2 x R x 64)
     if (prec == kTF32 && n_categories > 4)

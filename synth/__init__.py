@@ -186,6 +186,21 @@ def simulate_nucleotide(tree: Tree, pi: np.ndarray, rates: np.ndarray,
                      rng, sparse).astype(np.int8)
 
 
+def simulate_states(tree: Tree, pi: np.ndarray, rates: np.ndarray, n_sites: int,
+                    rng: np.random.Generator) -> np.ndarray:
+    """int8 [n_tips, n_sites] states 0..S-1 (S = len(pi)) under the
+    equal-input jump process with stationary pi (amino acids: S = 20)."""
+    pi = np.asarray(pi, dtype=float)
+    beta = 1.0 / (1.0 - float(np.sum(pi * pi)))
+    cats = rng.integers(len(rates), size=n_sites)
+
+    def draw(n):
+        return rng.choice(len(pi), size=n, p=pi)
+
+    return _f81_down(tree, n_sites, len(pi), cats, np.asarray(rates), beta, draw,
+                     rng).astype(np.int8)
+
+
 def simulate_codon(tree: Tree, f3x4: np.ndarray, rates: np.ndarray,
                    n_sites: int, rng: np.random.Generator, sparse: bool = False) -> np.ndarray:
     """int8 [n_tips, n_sites] sense-codon states (0..60, ACGT-lexicographic
@@ -251,7 +266,7 @@ class Workload:
 
 def make_workload(config: int, *, model: str, n_tips: int, n_patterns: int,
                   alpha: float = 0.5, kappa: float = 2.0, omega: float = 0.3,
-                  pi=None, name: str | None = None) -> Workload:
+                  pi=None, name: str | None = None, n_states: int = 20) -> Workload:
     """Draw a workload from configuration ``config``'s seed streams."""
     rt, rp, rs = rng_for(config, "tree"), rng_for(config, "params"), rng_for(config, "sites")
     tree = yule_tree(n_tips, rt)
@@ -272,6 +287,14 @@ def make_workload(config: int, *, model: str, n_tips: int, n_patterns: int,
         freqs = np.stack([rp.dirichlet(np.ones(4)) for _ in range(3)])
         tips = simulate_codon(tree, freqs, rates, n_patterns, rs)
         S = 61
+    elif model == "rev":
+        # amino acids: symmetric exchangeabilities ~ Exp(1) (row-major S x S,
+        # mirrored), frequencies ~ Dirichlet(1)
+        S = n_states
+        e = rp.exponential(1.0, size=(S, S))
+        params = np.triu(e, 1) + np.triu(e, 1).T
+        freqs = rp.dirichlet(np.ones(S))
+        tips = simulate_states(tree, freqs, rates, n_patterns, rs)
     else:
         raise ValueError(model)
     return Workload(name or f"config{config}", tree, model, params, freqs, alpha,
@@ -288,6 +311,8 @@ CONFIGS = {
     "gtr_1024x50k": dict(config=3, model="gtr", n_tips=1024, n_patterns=50_000),
     "gy94_64x5k": dict(config=3, model="gy94", n_tips=64, n_patterns=5_000,
                        kappa=2.0, omega=0.3),
+    # amino acids (20 states, a general reversible model): a "next" workload
+    "aa20_256x10k": dict(config=5, model="rev", n_tips=256, n_patterns=10_000, n_states=20),
 }
 
 

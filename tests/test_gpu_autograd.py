@@ -96,7 +96,7 @@ def test_autograd_function_matches_oracle_and_finite_differences():
                                      w.tips)
         want_gk = og.subst_gradient(w.tree, Q, dQ, pi, w.rates, w.cat_weights,
                                     w.pattern_weights, w.tips)
-        assert abs(float(y) - want_l) <= 1e-11 * abs(want_l)
+        assert abs(float(y.detach()) - want_l) <= 1e-11 * abs(want_l)
         assert np.allclose(t.grad.numpy(), want_gt[:-1], rtol=1e-10, atol=1e-10)
         assert np.allclose(th.grad.numpy(), want_gk, rtol=1e-10, atol=1e-10)
         # central differences of the GPU FP64 path itself, h = 1e-6

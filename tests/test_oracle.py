@@ -609,3 +609,21 @@ def test_random_effects_gradient_vs_finite_differences():
         fd = (pruning.loglik(tree, model.build("gy94re", pp, f)[0], pi, rates, cw, w, states)[0]
               - pruning.loglik(tree, model.build("gy94re", pm, f)[0], pi, rates, cw, w, states)[0]) / (2 * h)
         assert abs(np.sum(G * J[k]) - fd) < 1e-6 * max(1, abs(fd)), (k, np.sum(G * J[k]), fd)
+
+
+def test_general_reversible_model_pins():
+    """The general reversible model with GTR's exchangeabilities is GTR; on
+    20 states its Q has zero row sums, unit mean rate and detailed balance."""
+    g = [1.0, 2.0, 0.5, 0.7, 3.0, 1.2]
+    pi4 = np.array([0.1, 0.2, 0.3, 0.4])
+    E = np.zeros((4, 4))
+    for k, (i, j) in enumerate(model.GTR_PAIRS):
+        E[i, j] = E[j, i] = g[k]
+    assert np.allclose(model.rev(E, pi4), model.gtr(g, pi4)[0], rtol=1e-15, atol=1e-15)
+    w = synth.workload("aa20_256x10k", n_tips=5, n_patterns=20)
+    Q, pi, dQ = model.build("rev", w.params, w.freqs)
+    assert Q.shape == (20, 20) and dQ == []
+    assert np.max(np.abs(Q.sum(axis=1))) < 1e-14
+    assert abs(-np.dot(pi, np.diag(Q)) - 1.0) < 1e-14
+    D = pi[:, None] * Q
+    assert np.max(np.abs(D - D.T)) < 1e-16
