@@ -627,3 +627,50 @@ def test_general_reversible_model_pins():
     assert abs(-np.dot(pi, np.diag(Q)) - 1.0) < 1e-14
     D = pi[:, None] * Q
     assert np.max(np.abs(D - D.T)) < 1e-16
+
+
+def test_ratio_transform_chain_rule_vs_finite_differences():
+    """Ratios, root height and branch rates: the chain rule against central
+    differences of logL through the transform (tips at different heights)."""
+    from oracle import ratio
+    rng = np.random.default_rng(41)
+    tree = small_tree(9, 41)
+    n = 9
+    tip_h = rng.uniform(0.0, 0.3, n)
+    r = rng.uniform(0.2, 0.8, n - 1)
+    root_h = 1.5
+    rate = rng.uniform(0.5, 1.5, 2 * n - 1)
+    pi = rng.dirichlet(np.ones(4))
+    Q = model.hky(2.0, pi)[0]
+    rates = synth.gamma_rates(0.5)
+    cw = np.full(4, 0.25)
+    states = rand_states(rng, n, 40, 4)
+    w = np.ones(40)
+
+    def f(rr, rh, rt):
+        h = ratio.heights(tree.children, n, tip_h, rr, rh)
+        assert np.all(h[n:] > ratio.anchors(tree.children, n, tip_h)[n:])
+        t = ratio.branch_lengths(tree.children, n, h, rt)
+        tr = SimpleNamespace(n_tips=n, children=tree.children, edge_len=t)
+        return pruning.loglik(tr, Q, pi, rates, cw, w, states)[0]
+
+    h = ratio.heights(tree.children, n, tip_h, r, root_h)
+    t = ratio.branch_lengths(tree.children, n, h, rate)
+    tr = SimpleNamespace(n_tips=n, children=tree.children, edge_len=t)
+    g = gradient.branch_gradient(tr, Q, pi, rates, cw, w, states)
+    gr, grh, grate = ratio.ratio_gradient(tree.children, n, tip_h, r, root_h, rate, g)
+    eps = 1e-6
+    for k in range(n - 2):
+        rp, rm = r.copy(), r.copy()
+        rp[k] += eps
+        rm[k] -= eps
+        fd = (f(rp, root_h, rate) - f(rm, root_h, rate)) / (2 * eps)
+        assert abs(gr[k] - fd) < 1e-6 * max(1.0, abs(fd)), (k, gr[k], fd)
+    fd = (f(r, root_h + eps, rate) - f(r, root_h - eps, rate)) / (2 * eps)
+    assert abs(grh - fd) < 1e-6 * max(1.0, abs(fd))
+    for v in (0, 5, 12):
+        pp, pm = rate.copy(), rate.copy()
+        pp[v] += eps
+        pm[v] -= eps
+        fd = (f(r, root_h, pp) - f(r, root_h, pm)) / (2 * eps)
+        assert abs(grate[v] - fd) < 1e-6 * max(1.0, abs(fd))
