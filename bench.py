@@ -60,6 +60,8 @@ def parse():
                     help="offered loads as fractions of the measured capacity")
     ap.add_argument("--baseline-seconds", type=float, default=60.0,
                     help="time budget of the one-at-a-time FP64 baseline")
+    ap.add_argument("--phylogeo", action="store_true",
+                    help="one pattern, 64 states, 1,024 taxa: stored vs on-the-fly matrices")
     ap.add_argument("--autograd", action="store_true",
                     help="forward + backward through the autograd Function (GTR 1,024 x 50,000 "
                          "and GY94 64 x 5,000) in each precision against FP64")
@@ -555,8 +557,59 @@ def autograd_line(args) -> dict:
             "results": out, "substitution_gradient_methods": methods}
 
 
+def phylogeo_line(args) -> dict:
+    """One site pattern on 64 states (a discrete-location model), 1,024 taxa,
+    FP64: logL with the transition matrices formed and stored (S^3 per edge
+    and category, then pruning) against forming them on the fly inside
+    pruning from the eigensystem (two S^2 products per edge and category).
+    Both from the same eigensystem and partials buffers."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2606_27607_gb300 import TreeLikelihood, build, tree
+    build.build()
+    torch.cuda.set_device(0)
+    w = synth.workload("geo64_1024x1")
+    tl = TreeLikelihood(w.tree.n_tips, w.n_patterns, w.n_states, 4, "f64")
+    tl.set_tips(w.tips)
+    tl.set_model(w.model, w.params, w.freqs)
+    tl.set_rates(w.rates, w.cat_weights)
+    tl.set_tree(w.tree.children, w.tree.edge_len)
+    ops = tree.eig_ops(w.tree.children, w.tree.n_tips, w.tree.edge_len)
+
+    def stored():
+        return tl.loglik()
+
+    def fly():
+        tl.inst.update_partials_eigen(ops)
+        return tl.inst.root_loglik(tl.nn - 1, 0)
+
+    res = {}
+    for name, f in (("stored_matrices", stored), ("on_the_fly", fly)):
+        for _ in range(3):
+            val = f()
+        lat = []
+        for _ in range(max(5, min(args.steps, 50))):
+            t0 = time.perf_counter()
+            val = f()
+            lat.append(time.perf_counter() - t0)
+        res[name] = {"ms": 1e3 * _pct(lat, 50), "logL": val}
+    tl.close()
+    res["speedup"] = res["stored_matrices"]["ms"] / res["on_the_fly"]["ms"]
+    res["rel_diff_logL"] = abs(res["on_the_fly"]["logL"] - res["stored_matrices"]["logL"]) / abs(
+        res["stored_matrices"]["logL"])
+    return {"metric": "single-pattern logL latency (host-synchronous)", "unit": "ms",
+            "n_gpus": 1, "data": "synthetic", "dtype": "f64",
+            "config": {"workload": "geo64_1024x1", "taxa": 1024, "states": 64, "patterns": 1},
+            "results": res}
+
+
 def main() -> None:
     args = parse()
+    if getattr(args, "phylogeo", False):
+        print(json.dumps(phylogeo_line(args)), flush=True)
+        return
     if args.autograd:
         print(json.dumps(autograd_line(args)), flush=True)
         return

@@ -205,6 +205,26 @@ int tl_get_matrix(tl_instance* inst, int mat, double* out);
  * dependencies; the results do not depend on that order. */
 int tl_update_partials(tl_instance* inst, const tl_op* ops, int count);
 
+/* Post-order partials with the transition matrices formed on the fly from
+ * model `model`'s eigensystem (Sec. "Discussion": with a large state space
+ * and a single site pattern no matrix is reused, so P(t) is better formed
+ * inside pruning). For each op, child c with edge length len_c and each
+ * category r:  v_c = V (exp(lambda rho_r len_c) o (V^-1 p_c)), two S x S
+ * products per pattern instead of the S^3 matrix; dest = v_1 o v_2, rescaled
+ * as by tl_update_partials (the same buffers, exponents and tip rules, so
+ * tl_root_loglik follows). TL_PREC_F64 instances (any S); other precisions
+ * return TL_ERR_UNSUPPORTED. Ops in dependency order (TL_ERR_ORDER as for
+ * tl_update_partials); the ops of one tree level share a launch. */
+typedef struct {
+    int dest;
+    int child1;
+    int child2;
+    int pad;
+    double len1;
+    double len2;
+} tl_eig_op;
+int tl_update_partials_eigen(tl_instance* inst, int model, const tl_eig_op* ops, int count);
+
 /* Root log-likelihood (Sec. "Introduction"):
  *   l_p = log(sum_r w_r sum_s pi_s root[r,p,s]) + ln2 * E_p,
  *   logL = sum_p w_p l_p   (FP64, fixed-order two-stage reduction),
@@ -300,6 +320,36 @@ typedef struct {
  * TL_ERR_NUMERIC for a pattern with zero likelihood. */
 int tl_adjoint(tl_instance* inst, const tl_adj_op* ops, int count, int model, unsigned flags,
                double* out_grad, int n_grad, double* out_dQ, double* out_dtheta, int n_theta);
+
+/* ---- node-height ratio transform ------------------------------------------
+ * Node heights and branch-specific rates inferred together through a ratio
+ * transform of the node heights that keeps every node older than its
+ * descendants (Sec. "Algorithmic advances"). Tree: parent[v] for the
+ * 2 n_tips - 1 nodes, tips 0..n_tips-1, every internal node numbered after
+ * its children (parent[v] > v), the root last with parent -1. Tip heights
+ * tip_height[n_tips] are fixed; internal node n_tips + k has the ratio
+ * ratio[k] in (0, 1) (the root's entry is ignored); rate[v] is the rate of
+ * the branch above v (the root's ignored). With a_v the largest tip height
+ * below v:
+ *   h_v = a_v + r_v (h_parent(v) - a_v),   h_root = root_height,
+ *   t_v = rate_v (h_parent(v) - h_v)   (expected substitutions).
+ * tl_ratio_heights writes out_height and out_len ([2 n_tips - 1]; the
+ * root's length 0; either may be NULL). tl_ratio_gradient takes dlogL/dt
+ * (grad_len [2 n_tips - 1], e.g. from tl_pre_order_gradient) and writes, by
+ * the chain rule through the transform, dlogL/dratio [n_tips - 1] (root
+ * entry 0), dlogL/droot_height [1] and dlogL/drate [2 n_tips - 1] (root 0;
+ * any may be NULL). Host arrays; the arithmetic runs in one device block,
+ * level by level, on `stream` (a cudaStream_t or NULL), synchronously.
+ * Errors (TL_ERR_ARG: malformed tree, a ratio outside (0, 1), a root height
+ * not above every tip, non-finite input) are reported by
+ * tl_last_error(NULL, ...). */
+int tl_ratio_heights(int n_tips, const int* parent, const double* tip_height, const double* ratio,
+                     double root_height, const double* rate, double* out_height,
+                     double* out_len, void* stream);
+int tl_ratio_gradient(int n_tips, const int* parent, const double* tip_height, const double* ratio,
+                      double root_height, const double* rate, const double* grad_len,
+                      double* out_grad_ratio, double* out_grad_root_height,
+                      double* out_grad_rate, void* stream);
 
 /* Read back one buffer in FP64: out [R][n_patterns][S] partials as stored
  * (post-order partials carry their accumulated power-of-two exponents

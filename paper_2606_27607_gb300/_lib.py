@@ -37,6 +37,8 @@ OP_DTYPE = np.dtype([("dest", "<i4"), ("child1", "<i4"), ("mat1", "<i4"),
 PRE_OP_DTYPE = np.dtype([("parent_pre", "<i4"), ("child", "<i4", 2), ("mat", "<i4", 2),
                          ("dmat", "<i4", 2), ("pre", "<i4", 2), ("edge", "<i4", 2)])
 EDGE_DTYPE = np.dtype([("post", "<i4"), ("pre", "<i4"), ("edge", "<i4")])
+EIG_OP_DTYPE = np.dtype([("dest", "<i4"), ("child1", "<i4"), ("child2", "<i4"), ("pad", "<i4"),
+                         ("len1", "<f8"), ("len2", "<f8")])
 ADJ_OP_DTYPE = np.dtype([("parent_post", "<i4"), ("parent_pre", "<i4"), ("child", "<i4", 2),
                          ("mat", "<i4", 2), ("edge", "<i4", 2)])
 
@@ -80,6 +82,9 @@ SIGNATURES = {
     "tl_pre_order_derivative": [_VP, _VP, _I, _I, _VP, _I],
     "tl_sync": [_VP],
     "tl_adjoint": [_VP, _VP, _I, _I, _U, _VP, _I, _VP, _VP, _I],
+    "tl_update_partials_eigen": [_VP, _I, _VP, _I],
+    "tl_ratio_heights": [_I, _VP, _VP, _VP, C.c_double, _VP, _VP, _VP, _VP],
+    "tl_ratio_gradient": [_I, _VP, _VP, _VP, C.c_double, _VP, _VP, _VP, _VP, _VP, _VP],
     "tl_batch_create": [_VP, C.POINTER(_VP)],
     "tl_batch_destroy": [_VP],
     "tl_batch_last_error": [_VP, C.c_char_p, C.c_size_t],
@@ -137,6 +142,35 @@ def root_loglik_static(root_ptr: int, exps_ptr: int | None, pi_ptr: int, catw_pt
                                       C.c_void_p(patw_ptr), n_patterns, stride, n_categories,
                                       C.c_void_p(out_ptr), C.c_void_p(stream or 0))
     _check(rc, None)
+
+
+def ratio_heights(parent, tip_height, ratio, root_height: float, rate,
+                  stream: int | None = None):
+    """tl_ratio_heights: (node heights, branch lengths), each [2 n_tips - 1]."""
+    par = _arr(parent, np.int32)
+    n_tips = (par.size + 1) // 2
+    th, r, rt = (_arr(x, np.float64) for x in (tip_height, ratio, rate))
+    h = np.zeros(par.size)
+    t = np.zeros(par.size)
+    _check(load().tl_ratio_heights(n_tips, _ptr(par), _ptr(th), _ptr(r), float(root_height),
+                                   _ptr(rt), _ptr(h), _ptr(t), C.c_void_p(stream or 0)), None)
+    return h, t
+
+
+def ratio_gradient(parent, tip_height, ratio, root_height: float, rate, grad_len,
+                   stream: int | None = None):
+    """tl_ratio_gradient: (dlogL/dratio [n_tips - 1], dlogL/droot_height,
+    dlogL/drate [2 n_tips - 1]) from dlogL/dt."""
+    par = _arr(parent, np.int32)
+    n_tips = (par.size + 1) // 2
+    th, r, rt, g = (_arr(x, np.float64) for x in (tip_height, ratio, rate, grad_len))
+    gr = np.zeros(n_tips - 1)
+    groot = np.zeros(1)
+    grate = np.zeros(par.size)
+    _check(load().tl_ratio_gradient(n_tips, _ptr(par), _ptr(th), _ptr(r), float(root_height),
+                                    _ptr(rt), _ptr(g), _ptr(gr), _ptr(groot), _ptr(grate),
+                                    C.c_void_p(stream or 0)), None)
+    return gr, float(groot[0]), grate
 
 
 class Instance:
@@ -329,6 +363,10 @@ class Instance:
         _check(load().tl_edge_derivatives(self.h, _ptr(a), a.size, model, _ptr(g), n_grad),
                self.h)
         return g
+
+    def update_partials_eigen(self, ops: np.ndarray, model: int = 0) -> None:
+        a = _arr(ops, EIG_OP_DTYPE)
+        _check(load().tl_update_partials_eigen(self.h, model, _ptr(a), a.size), self.h)
 
     def adjoint(self, ops: np.ndarray, n_grad: int, n_theta: int, model: int = 0,
                 first_order: bool = False):

@@ -1392,6 +1392,26 @@ int tl_adjoint(tl_instance* inst, const tl_adj_op* ops, int count, int model, un
     return TL_OK;
 }
 
+int tl_ratio_heights(int n_tips, const int* parent, const double* tip_height, const double* ratio,
+                     double root_height, const double* rate, double* out_height,
+                     double* out_len, void* stream) {
+    return ratio_run(n_tips, parent, tip_height, ratio, root_height, rate, nullptr, out_height,
+                     out_len, nullptr, nullptr, nullptr, stream, &g_create_err);
+}
+
+int tl_ratio_gradient(int n_tips, const int* parent, const double* tip_height, const double* ratio,
+                      double root_height, const double* rate, const double* grad_len,
+                      double* out_grad_ratio, double* out_grad_root_height,
+                      double* out_grad_rate, void* stream) {
+    if (!grad_len) {
+        g_create_err = "grad_len is null";
+        return TL_ERR_ARG;
+    }
+    return ratio_run(n_tips, parent, tip_height, ratio, root_height, rate, grad_len, nullptr,
+                     nullptr, out_grad_ratio, out_grad_root_height, out_grad_rate, stream,
+                     &g_create_err);
+}
+
 int tl_get_partials(tl_instance* inst, int buf, double* out, int32_t* exponents) {
     CHECK_INST(inst);
     Instance* I = reinterpret_cast<Instance*>(inst);
@@ -1444,6 +1464,76 @@ int tl_update_partials(tl_instance* inst, const tl_op* ops, int count) {
         if ((rc = plan_post(I, ops, count, &plan, true))) return rc;
         if ((rc = launch_post_generic(I, ops, count))) return rc;
     }
+    for (int k = 0; k < count; ++k) I->buf_written[ops[k].dest - I->n_tips] = 1;
+    return TL_OK;
+}
+
+int tl_update_partials_eigen(tl_instance* inst, int model, const tl_eig_op* ops, int count) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (I->prec != kF64) return fail(I, TL_ERR_UNSUPPORTED, "on-the-fly matrices need TL_PREC_F64");
+    if (model < 0 || model >= I->n_models || !I->models[model].ready)
+        return fail(I, TL_ERR_STATE, "model %d not set", model);
+    if (count < 0 || (count > 0 && !ops)) return fail(I, TL_ERR_ARG, "bad op list");
+    if (count == 0) return TL_OK;
+    const int NB = I->n_bufs;
+    std::vector<int> prod(NB, -1), level(count, 0);
+    for (int k = 0; k < count; ++k) {
+        const int d = ops[k].dest;
+        if (d < I->n_tips || d >= NB) return fail(I, TL_ERR_INDEX, "op %d: dest %d", k, d);
+        if (prod[d] >= 0) return fail(I, TL_ERR_ORDER, "op %d: buffer %d written twice", k, d);
+        prod[d] = k;
+    }
+    for (int k = 0; k < count; ++k) {
+        const tl_eig_op& o = ops[k];
+        const int ch[2] = {o.child1, o.child2};
+        const double len[2] = {o.len1, o.len2};
+        for (int c = 0; c < 2; ++c) {
+            const int v = ch[c];
+            if (v < 0 || v >= NB) return fail(I, TL_ERR_INDEX, "op %d: child %d", k, v);
+            if (!std::isfinite(len[c]) || len[c] < 0)
+                return fail(I, TL_ERR_NUMERIC, "op %d: edge length not finite and >= 0", k);
+            if (v < I->n_tips) {
+                if (!I->tip_set[v]) return fail(I, TL_ERR_STATE, "op %d: tip %d not set", k, v);
+            } else if (prod[v] >= 0) {
+                if (prod[v] >= k)
+                    return fail(I, TL_ERR_ORDER, "op %d reads buffer %d before it is written", k, v);
+                level[k] = std::max(level[k], level[prod[v]] + 1);
+            } else if (!I->buf_written[v - I->n_tips]) {
+                return fail(I, TL_ERR_STATE, "op %d: child %d holds no data", k, v);
+            }
+        }
+    }
+    const int n_levels = *std::max_element(level.begin(), level.end()) + 1;
+    std::vector<int> start(n_levels + 1, 0);
+    for (int k = 0; k < count; ++k) start[level[k] + 1]++;
+    for (int L = 0; L < n_levels; ++L) start[L + 1] += start[L];
+    std::vector<EigOp> dev(count);
+    {
+        std::vector<int> fill(start.begin(), start.end() - 1);
+        for (int k = 0; k < count; ++k) {
+            EigOp e;
+            e.dest = ops[k].dest;
+            e.child[0] = ops[k].child1;
+            e.child[1] = ops[k].child2;
+            e.pad = 0;
+            e.len[0] = ops[k].len1;
+            e.len[1] = ops[k].len2;
+            dev[fill[level[k]]++] = e;
+        }
+    }
+    int rc;
+    if ((size_t)I->R > I->tmp_cap) {
+        dev_free(I, I->d_tmp);
+        I->tmp_cap = I->R + 1024;
+        if ((rc = dev_alloc(I, &I->d_tmp, sizeof(double) * I->tmp_cap, "staging"))) return rc;
+    }
+    void* d_ops = area(I, 0, sizeof(EigOp) * count, &rc);
+    if (rc) return rc;
+    if ((rc = h2d(I, d_ops, dev.data(), sizeof(EigOp) * count))) return rc;
+    if ((rc = launch_post_eig(I, model, reinterpret_cast<const EigOp*>(d_ops), start.data(),
+                              n_levels)))
+        return rc;
     for (int k = 0; k < count; ++k) I->buf_written[ops[k].dest - I->n_tips] = 1;
     return TL_OK;
 }

@@ -351,6 +351,110 @@ static GenArgs gen_args(const Instance* I) {
 
 static int gen_threads(const Instance* I) { return ((I->R * I->Spad + 31) / 32) * 32; }
 
+// ---- on-the-fly transition matrices -----------------------------------------
+// For a large state space with a single site pattern no transition matrix is
+// reused, so forming P(t) (S^3 per edge and category) costs more than the
+// pruning itself (Sec. "Discussion"). Here a child's product is taken in the
+// eigenbasis: v = V (e^{lambda rho_r t_c} o (V^-1 p_c)), two S^2 products per
+// pattern. A block per op (the ops of one tree level per launch), thread
+// (category r, state i); V and V^-1 in shared memory. Rescaling and the
+// cumulative exponents are those of the generic post-order kernel; padding
+// patterns get all-ones partials and exponent 0.
+__global__ void k_post_eig(const EigOp* __restrict__ ops, GenArgs a, const double* __restrict__ V,
+                           const double* __restrict__ Vinv, const double* __restrict__ lam) {
+    extern __shared__ double sm_eig[];
+    const int S = a.S, Spad = a.Spad, R = a.R;
+    const int SS = Spad * Spad;
+    double* Vs = sm_eig;              // [Spad][Spad]
+    double* Vi = Vs + SS;             // [Spad][Spad]
+    double* ex = Vi + SS;             // [2][R][Spad] e^{lambda rho t}
+    double* xs = ex + 2 * R * Spad;   // [R][Spad] child partial of this pattern
+    double* ws = xs + R * Spad;       // [R][Spad] V^-1 p, scaled
+    __shared__ double red[32];
+    const EigOp op = ops[blockIdx.x];
+    const int t = threadIdx.x, nt = blockDim.x;
+    const bool act = t < R * Spad;
+    const int r = act ? t / Spad : 0, i = act ? t % Spad : 0;
+    for (int idx = t; idx < SS; idx += nt) {
+        Vs[idx] = V[idx];
+        Vi[idx] = Vinv[idx];
+    }
+    for (int idx = t; idx < 2 * R * Spad; idx += nt) {
+        const int c = idx / (R * Spad), rr = (idx / Spad) % R, k = idx % Spad;
+        ex[idx] = k < S ? exp(lam[k] * a.rates[rr] * op.len[c]) : 0.0;
+    }
+    double* dst = a.buf[op.dest];
+    for (int p = 0; p < a.Ppad; ++p) {
+        if (p >= a.P) {  // padding
+            if (act) dst[((size_t)r * a.Ppad + p) * Spad + i] = i < S ? 1.0 : 0.0;
+            if (t == 0) a.scale[op.dest][p] = 0;
+            continue;
+        }
+        double prod = 1.0;
+        int cum = 0;
+        for (int c = 0; c < 2; ++c) {
+            const int ch = op.child[c];
+            __syncthreads();  // xs, ws free
+            const int8_t* ts = ch < a.n_tips ? a.tipst[ch] : nullptr;
+            if (act) {
+                double x = 0.0;
+                if (i < S) {
+                    if (ts) {
+                        const int s = ts[p];
+                        x = (s < 0 || s >= S || s == i) ? 1.0 : 0.0;
+                    } else {
+                        x = a.buf[ch][((size_t)r * a.Ppad + p) * Spad + i];
+                    }
+                }
+                xs[t] = x;
+            }
+            if (!ts && a.scale[ch]) cum += a.scale[ch][p];
+            __syncthreads();
+            if (act) {
+                double w = 0.0;
+                if (i < S)
+                    for (int j = 0; j < S; ++j) w += Vi[i * Spad + j] * xs[r * Spad + j];
+                ws[t] = w * ex[(c * R + r) * Spad + i];
+            }
+            __syncthreads();
+            double v = 0.0;
+            if (act && i < S)
+                for (int k = 0; k < S; ++k) v += Vs[i * Spad + k] * ws[r * Spad + k];
+            prod *= v;
+        }
+        if (!act || i >= S) prod = 0.0;
+        int e = 0;
+        if (a.rescale) {
+            double m = prod;
+            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if ((t & 31) == 0) red[t >> 5] = m;
+            __syncthreads();
+            m = red[0];
+            for (int w = 1; w < (nt >> 5); ++w) m = fmax(m, red[w]);
+            e = gen_frexp(m);
+            __syncthreads();  // red read by every thread before the next pattern
+        }
+        if (act) dst[((size_t)r * a.Ppad + p) * Spad + i] = e ? gen_scale(prod, -e) : prod;
+        if (t == 0) a.scale[op.dest][p] = cum + e;
+    }
+}
+
+int launch_post_eig(Instance* I, int model, const EigOp* d_ops, const int* level_start,
+                    int n_levels) {
+    GenArgs a = gen_args(I);
+    const ModelDev& M = I->models[model];
+    const size_t smem = (2 * (size_t)I->Spad * I->Spad + 4 * (size_t)I->R * I->Spad) * sizeof(double);
+    cudaFuncSetAttribute(k_post_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int L = 0; L < n_levels; ++L) {
+        const int n = level_start[L + 1] - level_start[L];
+        if (n <= 0) continue;
+        k_post_eig<<<n, gen_threads(I), smem, I->stream>>>(d_ops + level_start[L], a, M.V, M.Vinv,
+                                                          M.lam);
+        I->launches += 1;
+    }
+    return cuda_check(I, cudaGetLastError(), "on-the-fly post-order kernel");
+}
+
 int generic_parts(const Instance* I) { return I->Ppad / kPT; }
 
 int launch_post_generic(Instance* I, const tl_op* ops, int n_ops) {

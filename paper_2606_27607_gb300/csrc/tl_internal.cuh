@@ -273,6 +273,12 @@ int launch_pre_generic(Instance* I, const tl_pre_op* h_ops, int n_ops, int model
 int launch_edge_generic(Instance* I, const tl_edge* h_edges, int n_edges, int model,
                         double* d_gpart, int n_parts);
 int generic_parts(const Instance* I);
+struct EigOp {             // one post-order op with its children's edge lengths
+    int dest, child[2], pad;
+    double len[2];
+};
+int launch_post_eig(Instance* I, int model, const EigOp* d_ops, const int* level_start,
+                    int n_levels);
 
 // tl_codon_tc.cu (tcgen05 codon path)
 constexpr size_t kTcOpBytes = 64;  // one tensor-core work descriptor
@@ -314,6 +320,12 @@ int launch_adj_finish(Instance* I, int model, const double* d_M, const AdjEdge* 
                       bool first_order, double* d_gpart, double* d_grad);
 int launch_adj_params(Instance* I, int model, const double* d_G, bool first_order, double* d_dQ,
                       double* d_theta);
+
+// tl_ratio.cu: the node-height ratio transform (host arrays in and out)
+int ratio_run(int n_tips, const int* parent, const double* tip_h, const double* ratio,
+              double root_h, const double* rate, const double* grad, double* out_h,
+              double* out_len, double* out_gr, double* out_groot, double* out_grate,
+              void* stream, std::string* err);
 
 // tl_api.cu helpers used by the other units
 int upload_bytes(Instance* I, void* dst, const void* src, size_t bytes);

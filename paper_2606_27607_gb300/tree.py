@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from ._lib import ADJ_OP_DTYPE, EDGE_DTYPE, OP_DTYPE, PRE_OP_DTYPE
+from ._lib import ADJ_OP_DTYPE, EDGE_DTYPE, EIG_OP_DTYPE, OP_DTYPE, PRE_OP_DTYPE
 
 
 def n_nodes(n_tips: int) -> int:
@@ -41,6 +41,16 @@ def pre_ops(children, n_tips: int, pre_base: int, with_edges: bool = True,
         pre = [pre_base + c if (c >= N or tip_pre) else -1 for c in (a, b)]
         edge = [a, b] if with_edges else [-1, -1]
         ops[i] = (parent_pre, (a, b), (a, b), (nn + a, nn + b), pre, edge)
+    return ops
+
+
+def eig_ops(children, n_tips: int, edge_len) -> np.ndarray:
+    """Post-order ops carrying their children's edge lengths (matrices formed
+    on the fly)."""
+    children = np.asarray(children)
+    ops = np.zeros(len(children), dtype=EIG_OP_DTYPE)
+    for k, (a, b) in enumerate(children):
+        ops[k] = (n_tips + k, a, b, 0, edge_len[a], edge_len[b])
     return ops
 
 

@@ -313,6 +313,8 @@ CONFIGS = {
                        kappa=2.0, omega=0.3),
     # amino acids (20 states, a general reversible model): a "next" workload
     "aa20_256x10k": dict(config=5, model="rev", n_tips=256, n_patterns=10_000, n_states=20),
+    # phylogeography: 64 discrete locations, one site pattern
+    "geo64_1024x1": dict(config=6, model="rev", n_tips=1024, n_patterns=1, n_states=64),
 }
 
 

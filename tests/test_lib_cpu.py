@@ -97,3 +97,19 @@ def test_tensor_core_category_limit_is_checked_before_any_device_call(lib):
     buf = C.create_string_buffer(256)
     lib.tl_last_error(None, buf, 256)
     assert b"at most 4 categories" in buf.value
+
+
+def test_ratio_transform_validates_on_the_host():
+    """Malformed input is rejected before any device call."""
+    from paper_2606_27607_gb300._lib import TreelikError, ratio_heights
+    par = np.array([4, 4, 5, 5, 6, 6, -1])  # 4 tips: 0,1 -> 4; 2,3 -> 5; 4,5 -> root 6
+    tip_h = np.zeros(4)
+    rate = np.ones(7)
+    with pytest.raises(TreelikError, match="TL_ERR_ARG"):
+        ratio_heights(par, tip_h, [0.5, 1.5, 0.5], 2.0, rate)      # ratio outside (0, 1)
+    with pytest.raises(TreelikError, match="TL_ERR_ARG"):
+        ratio_heights(par, tip_h, [0.5, 0.5, 0.5], -1.0, rate)     # root below the tips
+    bad = par.copy()
+    bad[0] = 6
+    with pytest.raises(TreelikError, match="TL_ERR_ARG"):
+        ratio_heights(bad, tip_h, [0.5, 0.5, 0.5], 2.0, rate)      # root with three children
