@@ -526,6 +526,7 @@ struct PrePlan {
     std::vector<DevPreOp> dev;
     int n_slots = 0;
     std::vector<int> edge_map;   // compact row -> user edge index
+    std::vector<int> stored;     // pool indices of q written to memory
 };
 
 int plan_pre(Instance* I, const tl_pre_op* ops, int n, int n_grad, bool store_all,
@@ -535,6 +536,7 @@ int plan_pre(Instance* I, const tl_pre_op* ops, int n, int n_grad, bool store_al
     std::vector<int> child_op(2 * n, -1);   // op consuming output c of op k
     std::vector<int> edge_row(std::max(n_grad, 1), -1);
     plan->edge_map.clear();
+    plan->stored.clear();
     for (int k = 0; k < n; ++k) {
         const tl_pre_op& o = ops[k];
         if (o.parent_pre != -1) {
@@ -678,11 +680,14 @@ int plan_pre(Instance* I, const tl_pre_op* ops, int n, int n_grad, bool store_al
             d.q_slot_out[c] = -1;
             d.q_buf_out[c] = -1;
             const int cons = child_op[2 * k + c];
-            if (o.pre[c] >= 0 && (cons >= 0 || store_all)) {
+            if (o.pre[c] >= 0) {
+                // a named q is kept on chip when a later op of this list
+                // consumes it, and written to its buffer otherwise (a later
+                // call reads it) or when every q is to be stored
                 d.need_q[c] = 1;
                 const bool next = cons >= 0 && pos[cons] == idx + 1;
                 if (next) d.q_reg = c;  // the next op takes q_c from registers
-                if (store_all) {
+                if (store_all || cons < 0) {
                     d.q_buf_out[c] = o.pre[c] - I->n_tips;
                 } else if (next) {
                     // registers only
@@ -694,6 +699,7 @@ int plan_pre(Instance* I, const tl_pre_op* ops, int n, int n_grad, bool store_al
                 } else {
                     d.q_buf_out[c] = o.pre[c] - I->n_tips;
                 }
+                if (d.q_buf_out[c] >= 0) plan->stored.push_back(o.pre[c]);
             }
         }
         plan->dev[idx] = d;
@@ -1641,10 +1647,13 @@ static int pre_common(Instance* I, const tl_pre_op* ops, int count, int model, i
         if ((rc = ensure_out(I, (size_t)E))) return rc;
         if ((rc = reduce_fixed(I, I->d_red, E, parts, extra(I).d_out))) return rc;
     }
-    for (int k = 0; k < count; ++k)
-        for (int c = 0; c < 2; ++c)
-            if (ops[k].pre[c] >= 0 && (store_all || !use_nuc(I) || use_tc(I)))
-                I->buf_written[ops[k].pre[c] - I->n_tips] = 1;
+    if (use_nuc(I)) {
+        for (int b : plan.stored) I->buf_written[b - I->n_tips] = 1;
+    } else {
+        for (int k = 0; k < count; ++k)
+            for (int c = 0; c < 2; ++c)
+                if (ops[k].pre[c] >= 0) I->buf_written[ops[k].pre[c] - I->n_tips] = 1;
+    }
     if (d_grad_out && n_grad > 0) {
         void* d_map = nullptr;
         if (E > 0 && (rc = upload(I, extra(I).areas[4], plan.edge_map.data(), sizeof(int) * E, &d_map)))
