@@ -664,8 +664,12 @@ static int adj_accumulate_t(Instance* I, const void* d_ops, int n_ops, int n_chu
         return cuda_check(I, cudaGetLastError(), "adjoint (tensor cores)");
     }
     const size_t smem = adj_gen_smem(sizeof(T));
-    cudaFuncSetAttribute(k_adj_gen<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_adj_gen<T><<<dim3(n_ops, I->R, n_chunks), 256, smem, I->stream>>>(ops, a, d_mpart);
+    if constexpr (sizeof(T) == 8) {  // FP64 instances; FP32 storage is four-state or TF32
+        cudaFuncSetAttribute(k_adj_gen<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_adj_gen<T><<<dim3(n_ops, I->R, n_chunks), 256, smem, I->stream>>>(ops, a, d_mpart);
+    } else {
+        return fail(I, TL_ERR_UNSUPPORTED, "adjoint: no kernel for this precision and S");
+    }
     I->launches += 2;
     return cuda_check(I, cudaGetLastError(), "adjoint (any S)");
 }
