@@ -51,5 +51,5 @@ def test_checkpointed_gradient_is_bit_identical(name, prec, kw, band):
         ck.close()
     assert logl == want_l
     assert np.array_equal(g, want_g)
-    if band >= 2 and w.tree.n_tips >= 40:
+    if band >= 2 and w.tree.n_tips >= 90:
         assert nbuf < 0.75 * 2 * (w.tree.n_tips - 1)
