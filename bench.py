@@ -60,6 +60,9 @@ def parse():
                     help="offered loads as fractions of the measured capacity")
     ap.add_argument("--baseline-seconds", type=float, default=60.0,
                     help="time budget of the one-at-a-time FP64 baseline")
+    ap.add_argument("--adjoint-probe", default=None, metavar="WORKLOAD:PREC[:TAXA:PATTERNS]",
+                    help="two forward + adjoint evaluations of one workload (a small launch "
+                         "sequence for profiling the adjoint kernels)")
     ap.add_argument("--phylogeo", action="store_true",
                     help="one pattern, 64 states, 1,024 taxa: stored vs on-the-fly matrices")
     ap.add_argument("--autograd", action="store_true",
@@ -605,8 +608,36 @@ def phylogeo_line(args) -> dict:
             "results": res}
 
 
+def adjoint_probe(spec: str) -> dict:
+    """Forward pass and reverse-mode adjoint of one workload, twice."""
+    import torch
+
+    import synth
+    from paper_2606_27607_gb300 import TreeLikelihood, build
+    build.build()
+    torch.cuda.set_device(0)
+    parts = spec.split(":")
+    kw = {} if len(parts) < 4 else dict(n_tips=int(parts[2]), n_patterns=int(parts[3]))
+    w = synth.workload(parts[0], **kw)
+    tl = TreeLikelihood(w.tree.n_tips, w.n_patterns, w.n_states, 4, parts[1])
+    tl.set_tips(w.tips)
+    tl.set_model(w.model, w.params, w.freqs)
+    tl.set_rates(w.rates, w.cat_weights)
+    tl.set_pattern_weights(w.pattern_weights)
+    tl.set_tree(w.tree.children, w.tree.edge_len)
+    for _ in range(2):
+        logl = tl.loglik()
+        g, _, th = tl.adjoint()
+    torch.cuda.synchronize()
+    tl.close()
+    return {"workload": spec, "logL": logl, "dlogL_dtheta": [float(x) for x in th]}
+
+
 def main() -> None:
     args = parse()
+    if args.adjoint_probe:
+        print(json.dumps(adjoint_probe(args.adjoint_probe)), flush=True)
+        return
     if getattr(args, "phylogeo", False):
         print(json.dumps(phylogeo_line(args)), flush=True)
         return
