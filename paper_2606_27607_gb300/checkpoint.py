@@ -40,6 +40,32 @@ def depths(children, n_tips: int) -> np.ndarray:
     return d
 
 
+def layout(children, n_tips: int, band: int) -> dict:
+    """Checkpoint set, bands and buffer counts for a band length (no device
+    work): ``n_buffers`` internal buffers replace the 2 (N - 1) of the
+    whole-tree layout."""
+    children = np.asarray(children)
+    band = max(1, int(band))
+    d = depths(children, n_tips)
+    internal = np.arange(n_tips, 2 * n_tips - 1)
+    bandof = d // band
+    ckpt = {int(v) for v in internal if d[v] % band == 0}
+    n_bands = int(bandof[internal].max()) + 1
+    bands = [[int(v) for v in internal if bandof[v] == b] for b in range(n_bands)]
+    tr_size = max(sum(1 for v in b if v not in ckpt) for b in bands)
+    q_size = max(len(b) + sum(1 for v in internal if bandof[v] == k + 1 and int(v) in ckpt)
+                 for k, b in enumerate(bands))
+    return dict(band=band, depth=d, bandof=bandof, ckpt=ckpt, bands=bands, tr_size=tr_size,
+                q_size=q_size, n_buffers=len(ckpt) + tr_size + q_size)
+
+
+def best_band(children, n_tips: int, candidates=(2, 3, 4, 6, 8)) -> tuple[int, int]:
+    """(band, internal buffers) of the candidate band length needing the
+    fewest buffers."""
+    return min(((b, layout(children, n_tips, b)["n_buffers"]) for b in candidates),
+               key=lambda x: (x[1], x[0]))
+
+
 class CheckpointedLikelihood:
     """One tree on one instance, post-order partials kept at checkpoint
     depths 0, band, 2 band, ... (internal nodes only)."""
@@ -49,14 +75,9 @@ class CheckpointedLikelihood:
                  stream: int | None = None):
         self.N, self.nn = n_tips, 2 * n_tips - 1
         self.children = np.asarray(children)
-        self.band = max(1, int(band))
-        d = depths(self.children, n_tips)
-        self.depth = d
-        internal = np.arange(n_tips, self.nn)
-        self.bandof = d // self.band            # band of every node
-        self.ckpt = {v for v in internal if d[v] % self.band == 0}
-        n_bands = int(self.bandof[internal].max()) + 1
-        self.bands = [[v for v in internal if self.bandof[v] == b] for b in range(n_bands)]
+        lay = layout(self.children, n_tips, band)
+        self.band, self.depth, self.bandof = lay["band"], lay["depth"], lay["bandof"]
+        self.ckpt, self.bands = lay["ckpt"], lay["bands"]
         # buffers: one per checkpoint, a reusable pool for a band's other
         # nodes, and q buffers for a band's internal nodes plus the next
         # band's top depth
@@ -65,12 +86,9 @@ class CheckpointedLikelihood:
         for v in sorted(self.ckpt):
             self.ck_buf[v] = nxt
             nxt += 1
-        self.tr_base = nxt
-        self.tr_size = max(sum(1 for v in b if v not in self.ckpt) for b in self.bands)
+        self.tr_base, self.tr_size = nxt, lay["tr_size"]
         nxt += self.tr_size
-        self.q_base = nxt
-        self.q_size = max(len(b) + sum(1 for v in internal if self.bandof[v] == k + 1
-                                       and v in self.ckpt) for k, b in enumerate(self.bands))
+        self.q_base, self.q_size = nxt, lay["q_size"]
         nxt += self.q_size
         self.n_buffers = nxt - n_tips
         self.inst = Instance(n_tips, n_patterns, n_states, n_categories, self.n_buffers,
@@ -101,7 +119,6 @@ class CheckpointedLikelihood:
             self.re_ops.append(ops[[post_buf(v) >= self.tr_base for v in sorted(nodes)]])
             # pre-order: parents of this band, root first (decreasing labels)
             qb = {}
-            nxt = iter(range(self.q_base, self.q_base + self.q_size))
             for v in nodes:
                 if v in q_of_top:
                     qb[v] = q_of_top[v]
@@ -125,7 +142,6 @@ class CheckpointedLikelihood:
                     outs.append(buf)
                 pre[i] = (parent_pre, (post_buf(a), post_buf(c)), (a, c),
                           (self.nn + a, self.nn + c), outs, (a, c))
-            del nxt
             self.pre_ops.append(pre)
             q_of_top = q_of_top_next
 
@@ -140,6 +156,14 @@ class CheckpointedLikelihood:
             self.inst.set_category_weights(weights)
         if pattern_weights is not None:
             self.inst.set_pattern_weights(pattern_weights)
+
+    def loglik(self, edge_len) -> float:
+        """logL: the banded post-order pass (no derivative matrices)."""
+        v = np.arange(self.nn - 1, dtype=np.int32)
+        self.inst.update_matrices(0, v, np.asarray(edge_len, float)[: self.nn - 1], None)
+        for b in range(len(self.bands) - 1, -1, -1):
+            self.inst.update_partials(self.post_ops[b])
+        return self.inst.root_loglik(self.ck_buf[self.nn - 1], 0)
 
     def gradient(self, edge_len):
         """(logL, dlogL/dt for every node (root 0)) with checkpointing."""

@@ -15,8 +15,11 @@ step:
    a device instance is admitted when its partials memory fits the budget,
    or, once its request has waited a while, by evicting idle chains least
    recently used first; once a request is blocked on memory, no other
-   chain is newly admitted ahead of it. A chain that could never fit is
-   rejected;
+   chain is newly admitted ahead of it. A chain whose whole-tree buffers
+   could never fit is served with subtree checkpointing (``checkpoint``:
+   post-order partials kept at every few depths, recomputed in the
+   pre-order pass; its requests run one at a time, the host waiting for
+   each) when that form fits, and rejected otherwise;
 3. launch: per request the model (when it changed) and the transition
    matrices; then every four-state request of the step goes through the
    batched calls (one launch per pass for all of them), and codon requests
@@ -38,21 +41,23 @@ import numpy as np
 
 from . import TreeLikelihood
 from ._lib import Batch
+from .checkpoint import CheckpointedLikelihood, best_band
 
 R_CATEGORIES = 4
 
 
-def footprint(n_tips: int, n_patterns: int, n_states: int, precision: str) -> int:
-    """Device bytes of a chain's instance (partials of 2(N-1) buffers, their
-    scale exponents, tip states and 2(2N-1) matrix slots), with a 2% margin
-    for scratch that grows with use."""
+def footprint(n_tips: int, n_patterns: int, n_states: int, precision: str,
+              n_buffers: int | None = None) -> int:
+    """Device bytes of a chain's instance (partials of 2(N-1) buffers, or
+    ``n_buffers`` with checkpointing, their scale exponents, tip states and
+    2(2N-1) matrix slots), with a 2% margin for scratch that grows with use."""
     N, R = n_tips, R_CATEGORIES
     if n_states == 4:
         ppad, spad = -(-n_patterns // 32) * 32, 4
     else:
         ppad, spad = -(-n_patterns // 128) * 128, 64
     elt = 8 if precision == "f64" else 4
-    nb = 2 * (N - 1)
+    nb = 2 * (N - 1) if n_buffers is None else n_buffers
     partials = nb * R * ppad * spad * elt + nb * ppad * 4
     copies = 4 if precision == "tf32x2" else 2   # working copies per matrix slot
     mats = 2 * (2 * N - 1) * R * spad * spad * (8 + copies * elt)
@@ -78,6 +83,8 @@ class _Chain:
     params: np.ndarray | None = None  # parameters currently on the device
     stream: object = None
     queued: int = 0
+    band: int = 0                     # > 0: served with subtree checkpointing
+    n_buffers: int | None = None
 
 
 @dataclass
@@ -141,12 +148,24 @@ class Server:
         return len(self.chains) - 1
 
     def need(self, k: int) -> int:
-        d = self.chains[k].data
-        return footprint(d.tree.n_tips, d.n_patterns, d.n_states, self.chains[k].precision)
+        c = self.chains[k]
+        d = c.data
+        return footprint(d.tree.n_tips, d.n_patterns, d.n_states, c.precision, c.n_buffers)
 
     def _create(self, k: int) -> None:
         c = self.chains[k]
         d = c.data
+        if c.band:
+            tl = CheckpointedLikelihood(d.tree.n_tips, d.n_patterns, d.tree.children, d.n_states,
+                                        R_CATEGORIES, c.precision, band=c.band,
+                                        stream=c.stream.cuda_stream)
+            tl.set_data(d.tips, d.model, d.params, d.freqs, d.rates, d.cat_weights,
+                        d.pattern_weights)
+            c.tl, c.params = tl, np.asarray(d.params, dtype=float).copy()
+            c.bytes = max(tl.inst.device_bytes(), self.need(k))
+            self.used += c.bytes
+            self.stats["admitted"] += 1
+            return
         tl = TreeLikelihood(d.tree.n_tips, d.n_patterns, d.n_states, R_CATEGORIES, c.precision,
                             stream=c.stream.cuda_stream)
         tl.inst.set_tip_states_all(d.tips)
@@ -219,6 +238,12 @@ class Server:
     def submit(self, req, arrival: float | None = None) -> Future:
         f: Future = Future()
         p = _Pending(req, f, time.perf_counter() if arrival is None else arrival, req.chain)
+        c = self.chains[req.chain]
+        if self.need(req.chain) > self.budget and not c.band:
+            d = c.data
+            band, nbuf = best_band(d.tree.children, d.tree.n_tips)
+            if footprint(d.tree.n_tips, d.n_patterns, d.n_states, c.precision, nbuf) <= self.budget:
+                c.band, c.n_buffers = band, nbuf
         if self.need(req.chain) > self.budget:
             self.stats["rejected"] += 1
             f.set_exception(MemoryError(
@@ -341,12 +366,40 @@ class Server:
 
         self._group(items, stream, launch)
 
+    def _run_checkpointed(self, p: _Pending) -> None:
+        """A checkpointed chain's request, start to finish (the host waits)."""
+        c = self.chains[p.chain]
+        d, r = c.data, p.req
+        try:
+            if not np.array_equal(r.params, c.params):
+                c.tl.inst.set_model(0, d.model, r.params, d.freqs)
+                c.params = np.asarray(r.params, dtype=float).copy()
+            if r.gradient:
+                logl, grad = c.tl.gradient(r.edge_len)
+            else:
+                logl, grad = c.tl.loglik(r.edge_len), None
+            now = time.perf_counter()
+            if not np.isfinite(logl):
+                p.future.set_exception(FloatingPointError("non-finite log-likelihood"))
+            else:
+                p.future.set_result(Result(logl, grad, now - p.arrival, 1))
+        except Exception as exc:          # reported on the request's future
+            p.future.set_exception(exc)
+        c.busy = False
+        c.last_used = time.perf_counter()
+        self.stats["checkpointed"] += 1
+
     def step(self) -> bool:
         """One scheduling step; True if anything completed or launched."""
         done = self._complete()
         picked = self._admit()
         if not picked:
             return done > 0
+        for p in [q for q in picked if self.chains[q.chain].band]:
+            self._run_checkpointed(p)
+        picked = [p for p in picked if not self.chains[p.chain].band]
+        if not picked:
+            return True
         for p in picked:
             self._prepare(p)
         nuc = [p for p in picked if self.chains[p.chain].data.n_states == 4]

@@ -2,7 +2,8 @@
 the mix (bit-identical: four-state requests share batched launches whose
 per-instance arithmetic does not depend on the batch, codon requests run
 their own passes), matches the FP64 oracle, and survives admission under a
-memory budget small enough to force evictions and a rejection."""
+memory budget small enough to force evictions, checkpointed service of a
+chain too large for its whole-tree buffers, and a rejection."""
 import numpy as np
 import pytest
 
@@ -101,13 +102,25 @@ def test_admission_under_a_small_budget(stream):
     assert stats.get("evicted", 0) > 0
     for a, b in zip(base, got):
         assert a.logl == b.logl
-    # a budget below the largest chain rejects that chain's requests only
+    # a budget below the largest chain's whole-tree buffers serves it with
+    # subtree checkpointing, with bit-identical results
+    from paper_2606_27607_gb300.checkpoint import best_band
     big = max(range(len(chains)), key=lambda k: footprint(
         chains[k].tree.n_tips, chains[k].n_patterns, chains[k].n_states,
         "f32" if chains[k].n_states == 4 else "tf32x2"))
     got, stats, _ = serve(chains, reqs, budget=sizes[-1] - 1)
+    assert stats.get("checkpointed", 0) > 0
     for r, a, b in zip(reqs, base, got):
+        assert not isinstance(b, Exception)
+        assert a.logl == b.logl
+        if r.gradient:
+            assert np.array_equal(a.gradient, b.gradient)
+    # below even the checkpointed form the chain's requests are rejected
+    wb = chains[big]
+    nb = best_band(wb.tree.children, wb.tree.n_tips)[1]
+    tight = footprint(wb.tree.n_tips, wb.n_patterns, wb.n_states,
+                      "f32" if wb.n_states == 4 else "tf32x2", nb) - 1
+    got, stats, _ = serve(chains, reqs, budget=tight)
+    for r, b in zip(reqs, got):
         if r.chain == big:
             assert isinstance(b, MemoryError)
-        else:
-            assert not isinstance(b, Exception) and a.logl == b.logl
