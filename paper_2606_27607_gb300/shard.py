@@ -33,3 +33,49 @@ def allreduce_sum(values: np.ndarray, group=None) -> np.ndarray:
         t = t.cuda()
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t.cpu().numpy()
+
+
+class ChunkedLikelihood:
+    """One tree whose patterns are evaluated in consecutive blocks on one
+    instance sized for the largest block (the partials of all patterns need
+    not fit at once). Each evaluation uploads every block's tip states and
+    pattern weights before its passes; logL and the gradient are the sums
+    over blocks (patterns are conditionally independent given the tree)."""
+
+    def __init__(self, n_tips: int, n_patterns: int, n_blocks: int, n_states: int = 4,
+                 n_categories: int = 4, precision: str = "f32", stream: int | None = None):
+        from . import TreeLikelihood
+        self.blocks = pattern_blocks(n_patterns, n_blocks)
+        self.width = max(hi - lo for lo, hi in self.blocks)
+        self.tl = TreeLikelihood(n_tips, self.width, n_states, n_categories, precision, stream)
+
+    def close(self):
+        self.tl.close()
+
+    def set_data(self, tips, model: str, params, freqs, rates, weights=None,
+                 pattern_weights=None):
+        self.tips = np.asarray(tips)
+        self.pw = (np.ones(self.tips.shape[1]) if pattern_weights is None
+                   else np.asarray(pattern_weights, float))
+        self.tl.set_model(model, params, freqs)
+        self.tl.set_rates(rates, weights)
+
+    def _block(self, lo: int, hi: int) -> None:
+        n = hi - lo
+        tips = np.full((self.tips.shape[0], self.width), -1, dtype=np.int8)
+        tips[:, :n] = self.tips[:, lo:hi]
+        w = np.zeros(self.width)
+        w[:n] = self.pw[lo:hi]          # the unused tail of the last block weighs 0
+        self.tl.inst.set_tip_states_all(tips)
+        self.tl.set_pattern_weights(w)
+
+    def gradient(self, children, edge_len):
+        """(logL, dlogL/dt per node) summed over the blocks."""
+        self.tl.set_tree(children, edge_len)
+        logl, g = 0.0, None
+        for lo, hi in self.blocks:
+            self._block(lo, hi)
+            lb, gb = self.tl.gradient()
+            logl += lb
+            g = gb if g is None else g + gb
+        return logl, g

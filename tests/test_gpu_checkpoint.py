@@ -53,3 +53,21 @@ def test_checkpointed_gradient_is_bit_identical(name, prec, kw, band):
     assert np.array_equal(g, want_g)
     if band >= 2 and w.tree.n_tips >= 90:
         assert nbuf < 0.75 * 2 * (w.tree.n_tips - 1)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_pattern_chunks_sum_to_the_whole(prec, tol):
+    """Patterns in consecutive blocks on one instance sized for a block:
+    logL and gradient equal the whole-alignment evaluation up to the order
+    of the pattern sums."""
+    from paper_2606_27607_gb300.shard import ChunkedLikelihood
+    w = synth.workload("gtr_512x100k", n_tips=60, n_patterns=5003)
+    want_l, want_g = whole(w, prec)
+    ch = ChunkedLikelihood(w.tree.n_tips, w.n_patterns, 3, 4, 4, prec)
+    try:
+        ch.set_data(w.tips, w.model, w.params, w.freqs, w.rates, w.cat_weights)
+        logl, g = ch.gradient(w.tree.children, w.tree.edge_len)
+    finally:
+        ch.close()
+    assert abs(logl - want_l) <= tol * abs(want_l)
+    assert np.max(np.abs(g - want_g)) <= tol * np.max(np.abs(want_g))
