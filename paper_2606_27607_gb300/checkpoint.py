@@ -165,6 +165,29 @@ class CheckpointedLikelihood:
             self.inst.update_partials(self.post_ops[b])
         return self.inst.root_loglik(self.ck_buf[self.nn - 1], 0)
 
+    def n_bands(self) -> int:
+        return len(self.bands)
+
+    def launch(self, edge_len, gradient: bool, out_ptr: int) -> None:
+        """Queue one evaluation on the instance's stream without waiting:
+        logL to the device double at out_ptr and, with ``gradient``, band b's
+        share of dlogL/dt (2N - 1 doubles, zeros outside the band) at
+        out_ptr + 8 (1 + b (2N - 1)); the gradient is the sum of the band
+        vectors (every edge appears in exactly one)."""
+        v = np.arange(self.nn - 1, dtype=np.int32)
+        el = np.asarray(edge_len, float)[: self.nn - 1]
+        self.inst.update_matrices(0, v, el, (self.nn + v).astype(np.int32) if gradient else None)
+        for b in range(len(self.bands) - 1, -1, -1):
+            self.inst.update_partials(self.post_ops[b])
+        self.inst.root_loglik_dev(self.ck_buf[self.nn - 1], 0, out_ptr)
+        if not gradient:
+            return
+        for b in range(len(self.bands)):
+            if b > 0 and len(self.re_ops[b]):
+                self.inst.update_partials(self.re_ops[b])
+            self.inst.pre_order_gradient_dev(self.pre_ops[b], self.nn, 0,
+                                             out_ptr + 8 * (1 + b * self.nn))
+
     def gradient(self, edge_len):
         """(logL, dlogL/dt for every node (root 0)) with checkpointing."""
         v = np.arange(self.nn - 1, dtype=np.int32)

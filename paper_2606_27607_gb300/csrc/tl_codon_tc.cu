@@ -645,7 +645,7 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
 __global__ void k_root_tc(const float* __restrict__ x, const int* __restrict__ ep,
                           const double* __restrict__ pi, TcArgs a, const double* __restrict__ patw,
                           int P, double* __restrict__ site, double* __restrict__ part,
-                          const double* __restrict__ catw) {
+                          const double* __restrict__ catw, int* __restrict__ numeric_err) {
     __shared__ double wsum[32];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     double contrib = 0.0;
@@ -659,7 +659,7 @@ __global__ void k_root_tc(const float* __restrict__ x, const int* __restrict__ e
         }
         const double l = log(L) + 0.69314718055994530942 * (double)(ep ? ep[p] : 0);
         if (p < P) {
-            if (!(L > 0.0) || !isfinite(l)) atomicOr(a.err, 1);
+            if (!(L > 0.0) || !isfinite(l)) atomicOr(numeric_err, 1);
             if (site) site[p] = l;
             contrib = patw[p] * l;
         }
@@ -953,7 +953,7 @@ int launch_root_tc(Instance* I, int root_pool, int model, double* d_site, double
     const int* ep = a.epool + (size_t)root_pool * a.Ppad;
     double* catw = I->d_tmp;  // staged by the caller
     k_root_tc<<<n_parts, 128, 0, I->stream>>>(x, ep, I->models[model].pi, a, I->d_patw, I->P,
-                                              d_site, d_part, catw);
+                                              d_site, d_part, catw, I->d_err + 1);
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "tensor-core root kernel");
 }

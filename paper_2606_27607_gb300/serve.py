@@ -18,8 +18,8 @@ step:
    chain is newly admitted ahead of it. A chain whose whole-tree buffers
    could never fit is served with subtree checkpointing (``checkpoint``:
    post-order partials kept at every few depths, recomputed in the
-   pre-order pass; its requests run one at a time, the host waiting for
-   each) when that form fits, and rejected otherwise;
+   pre-order pass; each request its own launch group on the chain's
+   stream) when that form fits, and rejected otherwise;
 3. launch: per request the model (when it changed) and the transition
    matrices; then every four-state request of the step goes through the
    batched calls (one launch per pass for all of them), and codon requests
@@ -28,7 +28,9 @@ step:
    copy.
 
 The loop never waits for the GPU: a step is queued while earlier ones run,
-so requests that arrive meanwhile join the next step.
+so requests that arrive meanwhile join the next step. A reduced-precision
+result that comes back non-finite (a pattern whose likelihood underflowed)
+is evaluated again in FP64 before it is returned.
 """
 from __future__ import annotations
 
@@ -265,12 +267,22 @@ class Server:
                 continue
             now = time.perf_counter()
             host = g.host.numpy()
-            for p, (li, gi, ng) in zip(g.items, g.offsets):
+            for p, off in zip(g.items, g.offsets):
+                li, gi, ng = off[:3]
+                nb = off[3] if len(off) > 3 else 1   # checkpointed: one vector per band
                 c = self.chains[p.chain]
                 c.busy = False
                 c.last_used = now
                 logl = float(host[li])
-                grad = host[gi:gi + ng].copy() if gi >= 0 else None
+                grad = host[gi:gi + ng * nb].reshape(nb, ng).sum(axis=0) if gi >= 0 else None
+                if not np.isfinite(logl) and c.precision != "f64":
+                    # reduced precision can lose a pattern entirely: one
+                    # exponent per pattern spans all categories, so categories
+                    # whose likelihoods differ by more than FP32's range at a
+                    # node underflow, and two children may keep disjoint ones.
+                    # The request is evaluated again in FP64.
+                    logl, grad = self._fp64(p)
+                    now = time.perf_counter()
                 if not np.isfinite(logl):
                     p.future.set_exception(FloatingPointError("non-finite log-likelihood"))
                 else:
@@ -366,27 +378,55 @@ class Server:
 
         self._group(items, stream, launch)
 
-    def _run_checkpointed(self, p: _Pending) -> None:
-        """A checkpointed chain's request, start to finish (the host waits)."""
+    def _fp64(self, p: _Pending):
+        """(logL, gradient or None) of one request on a temporary FP64
+        instance (the host waits); (nan, None) if that fails too."""
+        from ._lib import TreelikError
         c = self.chains[p.chain]
         d, r = c.data, p.req
+        self.stats["fp64_fallback"] += 1
         try:
-            if not np.array_equal(r.params, c.params):
-                c.tl.inst.set_model(0, d.model, r.params, d.freqs)
-                c.params = np.asarray(r.params, dtype=float).copy()
+            tl = TreeLikelihood(d.tree.n_tips, d.n_patterns, d.n_states, R_CATEGORIES, "f64",
+                                stream=c.stream.cuda_stream)
+        except TreelikError:
+            return float("nan"), None
+        try:
+            tl.inst.set_tip_states_all(d.tips)
+            tl.set_model(d.model, r.params, d.freqs)
+            tl.set_rates(d.rates, d.cat_weights)
+            tl.set_pattern_weights(d.pattern_weights)
+            tl.set_tree(d.tree.children, r.edge_len)
             if r.gradient:
-                logl, grad = c.tl.gradient(r.edge_len)
-            else:
-                logl, grad = c.tl.loglik(r.edge_len), None
-            now = time.perf_counter()
-            if not np.isfinite(logl):
-                p.future.set_exception(FloatingPointError("non-finite log-likelihood"))
-            else:
-                p.future.set_result(Result(logl, grad, now - p.arrival, 1))
-        except Exception as exc:          # reported on the request's future
-            p.future.set_exception(exc)
-        c.busy = False
-        c.last_used = time.perf_counter()
+                return tl.gradient()
+            return tl.loglik(), None
+        except TreelikError:
+            return float("nan"), None
+        finally:
+            tl.close()
+
+    def _launch_checkpointed(self, p: _Pending) -> None:
+        """A checkpointed chain's request as its own launch group on the
+        chain's stream: logL, then (gradient) one vector per band, summed on
+        the host when the group completes."""
+        c = self.chains[p.chain]
+        d, r = c.data, p.req
+        if not np.array_equal(r.params, c.params):
+            c.tl.inst.set_model_async(0, d.model, r.params, d.freqs)
+            c.params = np.asarray(r.params, dtype=float).copy()
+        torch = self.torch
+        nb = c.tl.n_bands() if r.gradient else 0
+        n = 1 + nb * c.tl.nn
+        with torch.cuda.stream(c.stream):
+            arena = torch.empty(n, dtype=torch.float64, device=self.dev)
+        c.tl.launch(r.edge_len, r.gradient, arena.data_ptr())
+        host = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        with torch.cuda.stream(c.stream):
+            host.copy_(arena, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(c.stream)
+        self.inflight.append(_Group(ev, [p], host, arena,
+                                    [(0, 1 if r.gradient else -1, c.tl.nn, nb)]))
+        self.group_sizes.append(1)
         self.stats["checkpointed"] += 1
 
     def step(self) -> bool:
@@ -396,7 +436,7 @@ class Server:
         if not picked:
             return done > 0
         for p in [q for q in picked if self.chains[q.chain].band]:
-            self._run_checkpointed(p)
+            self._launch_checkpointed(p)
         picked = [p for p in picked if not self.chains[p.chain].band]
         if not picked:
             return True
