@@ -72,7 +72,7 @@ class CheckpointedLikelihood:
 
     def __init__(self, n_tips: int, n_patterns: int, children, n_states: int = 4,
                  n_categories: int = 4, precision: str = "f32", band: int = 4,
-                 stream: int | None = None):
+                 stream: int | None = None, create: bool = True):
         self.N, self.nn = n_tips, 2 * n_tips - 1
         self.children = np.asarray(children)
         lay = layout(self.children, n_tips, band)
@@ -91,12 +91,15 @@ class CheckpointedLikelihood:
         self.q_base, self.q_size = nxt, lay["q_size"]
         nxt += self.q_size
         self.n_buffers = nxt - n_tips
-        self.inst = Instance(n_tips, n_patterns, n_states, n_categories, self.n_buffers,
-                             2 * self.nn, 1, precision, True, stream)
+        self.inst = None
+        if create:   # create=False: the op lists only (no device)
+            self.inst = Instance(n_tips, n_patterns, n_states, n_categories, self.n_buffers,
+                                 2 * self.nn, 1, precision, True, stream)
         self._plan()
 
     def close(self):
-        self.inst.close()
+        if self.inst is not None:
+            self.inst.close()
 
     # ---- buffer plan ------------------------------------------------------
     def _plan(self):
