@@ -720,6 +720,135 @@ __global__ void __launch_bounds__(256) k_adj_finish(int S, int Spad, int R, int 
                                                     const AdjEdge* __restrict__ edges,
                                                     int first_order, double* __restrict__ gpart,
                                                     double* __restrict__ grad) {
+    // 256 threads as a 16 x 16 grid; thread (ti, tj) owns the 4 x 4 block of
+    // rows 4 ti.. and columns 4 tj.. of Y and W (padded to 64 x 64, entries
+    // beyond S are zero), so each shared-memory value it reads feeds four
+    // multiply-adds
+    extern __shared__ __align__(16) unsigned char sm_fin[];
+    constexpr int L = 64, LP = 65;           // padded size, row pitch
+    T* Vs = reinterpret_cast<T*>(sm_fin);    // [L][LP]
+    T* Vi = Vs + L * LP;
+    T* Ms = Vi + L * LP;
+    T* Ys = Ms + L * LP;
+    __shared__ double ea[64], la[64], gsum[8];
+    const int e = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+    const int ti = t >> 4, tj = t & 15;
+    const int SS = Spad * Spad;
+    const AdjEdge ed = edges[e];
+    for (int idx = t; idx < L * L; idx += nt) {
+        const int i = idx >> 6, j = idx & 63;
+        const bool in = i < S && j < S;
+        Vs[i * LP + j] = in ? (T)V[i * Spad + j] : T(0);
+        Vi[i * LP + j] = in ? (T)Vinv[i * Spad + j] : T(0);
+    }
+    double g[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) g[a][b] = 0.0;
+    double dsum = 0.0;
+    for (int r = 0; r < R; ++r) {
+        const double rt = rates[r] * ed.t;
+        __syncthreads();
+        for (int idx = t; idx < L * L; idx += nt) {
+            const int i = idx >> 6, j = idx & 63;
+            Ms[i * LP + j] = (i < S && j < S) ? (T)Mall[((size_t)e * R + r) * SS + i * Spad + j]
+                                             : T(0);
+        }
+        if (t < 64) {
+            la[t] = t < S ? lam[t] * rt : 0.0;
+            ea[t] = t < S ? exp(la[t]) : 0.0;
+        }
+        __syncthreads();
+        // Y = V^T M: Y[i][l] = sum_k V[k][i] M[k][l]
+        T y[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) y[a][b] = T(0);
+        for (int k = 0; k < S; ++k) {
+            T va[4], mb[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) va[a] = Vs[k * LP + 4 * ti + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) mb[b] = Ms[k * LP + 4 * tj + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) y[a][b] += va[a] * mb[b];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) Ys[(4 * ti + a) * LP + 4 * tj + b] = y[a][b];
+        __syncthreads();
+        // W = Y V^-T: W[i][j] = sum_l Y[i][l] Vinv[j][l]
+        T wv[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) wv[a][b] = T(0);
+        for (int l = 0; l < S; ++l) {
+            T ya[4], vb[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) ya[a] = Ys[(4 * ti + a) * LP + l];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) vb[b] = Vi[(4 * tj + b) * LP + l];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) wv[a][b] += ya[a] * vb[b];
+        }
+        // the edge derivative (diagonal of W) and this edge's share of G
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int i = 4 * ti + a, j = 4 * tj + b;
+                if (i >= S || j >= S) continue;
+                const double w = (double)wv[a][b];
+                if (i == j) dsum += w * rates[r] * lam[i] * ea[i];
+                if (!first_order) {
+                    const double d = la[i] - la[j];
+                    const double phi = (fabs(d) < 1e-12) ? ea[i] : ea[j] * expm1(d) / d;
+                    g[a][b] += rt * w * phi;
+                } else {
+                    const double* P = ed.P + (size_t)r * SS;
+                    double mp = 0.0;
+                    for (int l = 0; l < S; ++l) mp += (double)Ms[i * LP + l] * P[j * Spad + l];
+                    g[a][b] += rt * mp;
+                }
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = 4 * ti + a, j = 4 * tj + b;
+            if (i < Spad && j < Spad) gpart[(size_t)(i * Spad + j) * E + e] = g[a][b];
+        }
+    // fixed-order block sum of the diagonal terms
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    if ((t & 31) == 0) gsum[t >> 5] = dsum;
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (nt >> 5); ++w) s += gsum[w];
+        grad[e] = s;
+    }
+}
+
+// Small state spaces (S <= 16): a thread per entry of Y and W.
+template <typename T>
+__global__ void __launch_bounds__(256) k_adj_finish_small(int S, int Spad, int R, int E,
+                                                    const double* __restrict__ V,
+                                                    const double* __restrict__ Vinv,
+                                                    const double* __restrict__ lam,
+                                                    const double* __restrict__ rates,
+                                                    const double* __restrict__ Mall,
+                                                    const AdjEdge* __restrict__ edges,
+                                                    int first_order, double* __restrict__ gpart,
+                                                    double* __restrict__ grad) {
     extern __shared__ __align__(16) unsigned char sm_fin[];
     const int SS = Spad * Spad;
     T* Vs = reinterpret_cast<T*>(sm_fin);   // [Spad][Spad]
@@ -792,12 +921,19 @@ int launch_adj_finish(Instance* I, int model, const double* d_M, const AdjEdge* 
     const int SS = I->Spad * I->Spad;
     if (SS > 16 * 256) return fail(I, TL_ERR_UNSUPPORTED, "adjoint built for at most 64 states");
     const double* d_rates = I->d_tmp;  // staged by the caller
-    const size_t smem = 4 * (size_t)SS * sizeof(double);
-    cudaFuncSetAttribute(k_adj_finish<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    k_adj_finish<double><<<E, 256, smem, I->stream>>>(I->S, I->Spad, I->R, E, M.V, M.Vinv, M.lam,
-                                                      d_rates, d_M, d_edges, first_order, d_gpart,
-                                                      d_grad);
+    if (I->Spad <= 16) {
+        const size_t smem = 4 * (size_t)SS * sizeof(double);
+        k_adj_finish_small<double><<<E, 256, smem, I->stream>>>(
+            I->S, I->Spad, I->R, E, M.V, M.Vinv, M.lam, d_rates, d_M, d_edges, first_order,
+            d_gpart, d_grad);
+    } else {
+        const size_t smem = 4 * (size_t)64 * 65 * sizeof(double);
+        cudaFuncSetAttribute(k_adj_finish<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_adj_finish<double><<<E, 256, smem, I->stream>>>(I->S, I->Spad, I->R, E, M.V, M.Vinv,
+                                                          M.lam, d_rates, d_M, d_edges,
+                                                          first_order, d_gpart, d_grad);
+    }
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "adjoint finish");
 }
