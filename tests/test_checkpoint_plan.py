@@ -64,3 +64,16 @@ def test_best_band_saves_buffers_on_the_benchmark_trees():
         w = synth.workload(name, n_patterns=4)
         band, nb = best_band(w.tree.children, w.tree.n_tips)
         assert nb <= 0.6 * 2 * (w.tree.n_tips - 1), (name, band, nb)
+
+
+def test_checkpointed_footprint_admits_what_the_whole_tree_cannot():
+    """The server's footprint with checkpoint buffers is the smaller one it
+    compares against its budget."""
+    pytest.importorskip("torch")
+    from paper_2606_27607_gb300.serve import footprint
+    w = synth.workload("gy94_128x20k", n_patterns=4)
+    band, nb = best_band(w.tree.children, w.tree.n_tips)
+    whole = footprint(w.tree.n_tips, 20000, 61, "tf32x2")
+    ck = footprint(w.tree.n_tips, 20000, 61, "tf32x2", nb)
+    assert ck < 0.6 * whole
+    assert footprint(w.tree.n_tips, 20000, 61, "tf32x2", 2 * (w.tree.n_tips - 1)) == whole
