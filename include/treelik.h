@@ -61,8 +61,9 @@ extern "C" {
 #define TL_PREC_F32    0x2u   /* FP32 partials (S == 4), FP64 reductions       */
 #define TL_PREC_TF32   0x4u   /* S in 5..64: tcgen05 kind::tf32 contractions,
                                  TF32-rounded FP32 partials, FP32 accumulate   */
-#define TL_PREC_BF16X3 0x8u   /* S in 33..64: tcgen05 kind::f16 with a BF16
-                                 hi/lo split, three products per contraction   */
+#define TL_PREC_BF16X3 0x8u   /* reserved for a BF16 hi/lo split (three
+                                 products per contraction); not built:
+                                 tl_create returns TL_ERR_UNSUPPORTED          */
 #define TL_SCALE_NONE  0x100u /* no per-pattern rescaling (FP64 only)          */
 #define TL_SPLIT_MATRICES 0x200u /* with TL_PREC_TF32: every transition matrix
                                  (and Q, dP) is the exact FP32 sum of two TF32

@@ -52,6 +52,34 @@ def test_struct_layouts_match_header():
     assert _lib.OP_DTYPE.itemsize == 5 * 4
     assert _lib.PRE_OP_DTYPE.itemsize == 11 * 4
     assert _lib.EDGE_DTYPE.itemsize == 3 * 4
+    assert _lib.ADJ_OP_DTYPE.itemsize == 8 * 4           # tl_adj_op: 8 ints
+    assert _lib.EIG_OP_DTYPE.itemsize == 4 * 4 + 2 * 8   # tl_eig_op: 4 ints, 2 doubles
+    assert _lib.EIG_OP_DTYPE.fields["len1"][1] == 16     # doubles 8-aligned after 4 ints
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """The numpy dtypes of the op structs against sizeof/offsetof from the
+    host C compiler reading include/treelik.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2606_27607_gb300 import _lib
+    src = tmp_path / "layout.c"
+    src.write_text(
+        "#include <stddef.h>\n#include <stdio.h>\n#include \"treelik.h\"\n"
+        "int main(void) { printf(\"%zu %zu %zu %zu %zu %zu\\n\", sizeof(tl_op), sizeof(tl_pre_op),"
+        " sizeof(tl_edge), sizeof(tl_adj_op), sizeof(tl_eig_op), offsetof(tl_eig_op, len1));"
+        " return 0; }\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    assert got == [_lib.OP_DTYPE.itemsize, _lib.PRE_OP_DTYPE.itemsize, _lib.EDGE_DTYPE.itemsize,
+                   _lib.ADJ_OP_DTYPE.itemsize, _lib.EIG_OP_DTYPE.itemsize,
+                   _lib.EIG_OP_DTYPE.fields["len1"][1]]
 
 
 def test_create_without_gpu_fails_cleanly(lib):
@@ -97,6 +125,20 @@ def test_tensor_core_category_limit_is_checked_before_any_device_call(lib):
     buf = C.create_string_buffer(256)
     lib.tl_last_error(None, buf, 256)
     assert b"at most 4 categories" in buf.value
+
+
+def test_unbuilt_and_out_of_range_precisions_are_rejected_before_any_device_call(lib):
+    """BF16X3 is reserved and not built; TF32 covers 5..64 states; FP32 is
+    four-state only. Each is refused by tl_create before the device is
+    touched."""
+    import ctypes as C
+    h = C.c_void_p()
+    buf = C.create_string_buffer(256)
+    for states, flags, text in ((61, 0x8, b"BF16X3"), (4, 0x4, b"5..64"), (20, 0x2, b"4 states")):
+        rc = lib.tl_create(8, 100, states, 4, 14, 30, 1, flags, None, C.byref(h))
+        assert rc == -8, (states, flags, rc)   # TL_ERR_UNSUPPORTED
+        lib.tl_last_error(None, buf, 256)
+        assert text in buf.value, buf.value
 
 
 def test_ratio_transform_validates_on_the_host():
