@@ -20,6 +20,10 @@ class LogLikelihood(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, edge_len: torch.Tensor, params: torch.Tensor, tl, kind: str, freqs):
+        from . import TreeLikelihood
+        if params.requires_grad and TreeLikelihood.N_PARAMS.get(kind, 0) == 0:
+            raise ValueError(f"model {kind!r} has no parameter derivatives; take dlogL/dQ from "
+                             "TreeLikelihood.adjoint() instead")
         t = edge_len.detach().cpu().double().numpy()
         th = params.detach().cpu().double().numpy()
         tl.set_model(kind, th, freqs)

@@ -155,3 +155,14 @@ def test_ratio_transform_validates_on_the_host():
     bad[0] = 6
     with pytest.raises(TreelikError, match="TL_ERR_ARG"):
         ratio_heights(bad, tip_h, [0.5, 0.5, 0.5], 2.0, rate)      # root with three children
+
+
+def test_autograd_refuses_parameter_gradients_it_cannot_give():
+    """A general reversible model has no built-in parameter derivatives: the
+    autograd Function says so before touching the device."""
+    torch = pytest.importorskip("torch")
+    from paper_2606_27607_gb300 import LogLikelihood
+    t = torch.ones(5, dtype=torch.float64, requires_grad=True)
+    th = torch.ones(16, dtype=torch.float64, requires_grad=True)
+    with pytest.raises(ValueError, match="dlogL/dQ"):
+        LogLikelihood.apply(t, th, None, "rev", np.full(4, 0.25))
