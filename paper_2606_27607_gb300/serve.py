@@ -386,11 +386,22 @@ class Server:
         d, r = c.data, p.req
         self.stats["fp64_fallback"] += 1
         try:
-            tl = TreeLikelihood(d.tree.n_tips, d.n_patterns, d.n_states, R_CATEGORIES, "f64",
-                                stream=c.stream.cuda_stream)
+            if c.band:   # a chain served with checkpointing keeps that form in FP64
+                tl = CheckpointedLikelihood(d.tree.n_tips, d.n_patterns, d.tree.children,
+                                            d.n_states, R_CATEGORIES, "f64", band=c.band,
+                                            stream=c.stream.cuda_stream)
+            else:
+                tl = TreeLikelihood(d.tree.n_tips, d.n_patterns, d.n_states, R_CATEGORIES,
+                                    "f64", stream=c.stream.cuda_stream)
         except TreelikError:
             return float("nan"), None
         try:
+            if c.band:
+                tl.set_data(d.tips, d.model, r.params, d.freqs, d.rates, d.cat_weights,
+                            d.pattern_weights)
+                if r.gradient:
+                    return tl.gradient(r.edge_len)
+                return tl.loglik(r.edge_len), None
             tl.inst.set_tip_states_all(d.tips)
             tl.set_model(d.model, r.params, d.freqs)
             tl.set_rates(d.rates, d.cat_weights)
