@@ -111,3 +111,30 @@ def test_server_falls_back_to_fp64():
     assert stats.get("fp64_fallback", 0) == 1
     assert got.logl == want_l
     assert np.array_equal(got.gradient, want_g)
+
+
+def test_server_falls_back_to_fp64_on_a_checkpointed_chain():
+    """The same pattern on a chain whose whole-tree buffers exceed the
+    budget: served with checkpointing, re-evaluated in FP64 in that form."""
+    from paper_2606_27607_gb300.checkpoint import best_band
+    from paper_2606_27607_gb300.serve import Server, footprint
+    w = crafted()
+    whole = footprint(64, 2, 61, "tf32x2")
+    band, nb = best_band(w.tree.children, 64)
+    budget = (whole + footprint(64, 2, 61, "tf32x2", nb)) // 2
+    req = synth.ServingRequest(chain=0, edge_len=w.tree.edge_len, params=np.asarray(w.params),
+                               gradient=True)
+    s = Server(memory_budget=budget)
+    try:
+        s.add_chain(w)
+        f = s.submit(req)
+        s.drain()
+        got = f.result()
+        stats = dict(s.stats)
+    finally:
+        s.close()
+    Q, pi, _ = om.build(w.model, w.params, w.freqs)
+    want = op.loglik(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights, w.tips)[0]
+    assert stats.get("checkpointed", 0) == 1 and stats.get("fp64_fallback", 0) == 1
+    assert abs(got.logl - want) <= 1e-11 * abs(want)
+    assert got.gradient is not None and np.all(np.isfinite(got.gradient))
