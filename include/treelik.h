@@ -305,7 +305,9 @@ typedef struct {
  *     Phi_ij = (e^{a_i} - e^{a_j}) / (a_i - a_j), e^{a_i} when a_i = a_j;
  *     with TL_ADJ_FIRST_ORDER: sum_{c,r} rho_r t_c M_c,r P_c,r^T
  *   out_dtheta[k]   = <dlogL/dQ, dQ/dtheta_k>  (k < n_theta; HKY 1, GTR 6,
- *                     GY94 2, GY94RE 265 parameters in tl_set_model order).
+ *                     GY94 2, GY94RE 265 parameters in tl_set_model order;
+ *                     TL_MODEL_REV S*S, the exchangeability matrix row-major,
+ *                     0 on its diagonal).
  * L_p is taken at the parent, up to the scales that cancel: from the same
  * products sum_r w_r q_n . (v_a o v_b), v_c = P_c p_c (four states), or
  * from the stored post-order partial of parent_post and its rescaling

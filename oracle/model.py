@@ -189,7 +189,7 @@ def rate_jacobian(model: str, params, freqs, h: float = 1e-30) -> np.ndarray:
     """dQ/dtheta_k for every parameter k ([K, S, S]) by complex-step
     differentiation of the builder: Im Q(theta + i h e_k) / h, exact to
     rounding (no subtraction), independent of the hand-written dQ."""
-    params = np.asarray(params, float)
+    params = np.asarray(params, float).ravel()
     out = []
     for k in range(len(params)):
         z = params.astype(complex)

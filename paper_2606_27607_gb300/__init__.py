@@ -50,7 +50,7 @@ class TreeLikelihood:
         for t in range(self.N):
             self.inst.set_tip_states(t, tips[t])
 
-    N_PARAMS = {"hky": 1, "gtr": 6, "gy94": 2, "gy94re": 265, "rev": 0}
+    N_PARAMS = {"hky": 1, "gtr": 6, "gy94": 2, "gy94re": 265}
 
     def set_model(self, kind: str, params, freqs) -> None:
         self.inst.set_model(0, kind, params, freqs)
@@ -107,9 +107,7 @@ class TreeLikelihood:
         post-order partials of the current tree. One pre-order pass per
         parameter with dP/dtheta in the derivative slots; the next gradient()
         recomputes dP/dt there."""
-        n = self.N_PARAMS.get(getattr(self, "kind", None))
-        if n is None:
-            n = len(self.inst.get_model(0)[2])
+        n = len(self.inst.get_model(0)[2])   # the model's dQ/dtheta matrices
         v = np.arange(self.nn - 1, dtype=np.int32)
         out = np.zeros(n)
         for k in range(n):
@@ -123,8 +121,13 @@ class TreeLikelihood:
         node (root 0), dlogL/dQ [S, S], dlogL/dtheta). ``first_order`` takes
         dlogL/dQ by the approximation dP = rho t dQ P."""
         self.inst.update_pre_partials(self._preq, 0)
-        n = self.N_PARAMS.get(getattr(self, "kind", None), 0)
-        return self.inst.adjoint(self._adj, self.nn, n, 0, first_order)
+        return self.inst.adjoint(self._adj, self.nn, self.n_params(), 0, first_order)
+
+    def n_params(self) -> int:
+        """Parameters of the current model (S x S exchangeabilities for the
+        general reversible model)."""
+        kind = getattr(self, "kind", None)
+        return self.S * self.S if kind == "rev" else self.N_PARAMS.get(kind, 0)
 
     def value_and_grad(self):
         """(logL, dlogL/dt per node, dlogL/dtheta) in one forward/backward."""

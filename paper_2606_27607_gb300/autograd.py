@@ -15,13 +15,13 @@ class LogLikelihood(torch.autograd.Function):
     """logL(t, theta) for a TreeLikelihood whose tips, frequencies, rates and
     topology are set. ``edge_len`` holds one length per non-root node;
     ``params`` are the model parameters (kappa | six GTR exchangeabilities |
-    kappa, omega | kappa, omega and 263 random effects). Returns a 0-d
-    float64 tensor."""
+    kappa, omega | kappa, omega and 263 random effects | the S x S
+    exchangeabilities of a general reversible model). Returns a 0-d float64
+    tensor."""
 
     @staticmethod
     def forward(ctx, edge_len: torch.Tensor, params: torch.Tensor, tl, kind: str, freqs):
-        from . import TreeLikelihood
-        if params.requires_grad and TreeLikelihood.N_PARAMS.get(kind, 0) == 0:
+        if params.requires_grad and kind not in ("hky", "gtr", "gy94", "gy94re", "rev"):
             raise ValueError(f"model {kind!r} has no parameter derivatives; take dlogL/dQ from "
                              "TreeLikelihood.adjoint() instead")
         t = edge_len.detach().cpu().double().numpy()

@@ -953,6 +953,7 @@ __global__ void __launch_bounds__(256) k_adj_params(int S, int Spad, const doubl
                                                     const double* __restrict__ pi,
                                                     const double* __restrict__ dQk, int n_dq,
                                                     const int* __restrict__ pairs, int n_pairs,
+                                                    int n_exch, const double* __restrict__ mu,
                                                     double* __restrict__ dQ,
                                                     double* __restrict__ theta) {
     extern __shared__ double sm_par[];
@@ -1000,6 +1001,17 @@ __global__ void __launch_bounds__(256) k_adj_params(int S, int Spad, const doubl
         }
         __syncthreads();
     }
+    // general reversible model, exchangeability E_ab (a != b; s_ab = s_ba =
+    // (E_ab + E_ba) / 2, normaliser mu of the unnormalised rates):
+    //   dlogL/dE_ab = [pi_b (dQ_ab - dQ_aa) + pi_a (dQ_ba - dQ_bb)] / (2 mu)
+    //                 - pi_a pi_b <dQ, Q> / mu
+    for (int k = t; k < n_exch; k += nt) {
+        const int i = k / S, j = k % S;
+        theta[k] = (i == j) ? 0.0
+                            : (pi[j] * (D[i * Spad + j] - D[i * Spad + i]) +
+                               pi[i] * (D[j * Spad + i] - D[j * Spad + j])) / (2.0 * mu[0]) -
+                                  pi[i] * pi[j] * gq / mu[0];
+    }
     for (int k = t; k < n_pairs; k += nt) {
         const int i = pairs[2 * k], j = pairs[2 * k + 1];
         const double qij = Q[i * Spad + j], qji = Q[j * Spad + i];
@@ -1015,8 +1027,10 @@ int launch_adj_params(Instance* I, int model, const double* d_G, bool first_orde
     const size_t smem = 2 * (size_t)I->Spad * I->Spad * sizeof(double);
     cudaFuncSetAttribute(k_adj_params, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int n_pairs = M.kind == TL_MODEL_GY94RE ? TL_GY94_PAIRS : 0;
+    const int n_exch = M.kind == TL_MODEL_REV ? I->S * I->S : 0;
     k_adj_params<<<1, 256, smem, I->stream>>>(I->S, I->Spad, M.V, M.Vinv, d_G, first_order, M.Q,
-                                              M.pi, M.dQ, M.n_dq, M.pairs, n_pairs, d_dQ, d_theta);
+                                              M.pi, M.dQ, M.n_dq, M.pairs, n_pairs, n_exch, M.mu,
+                                              d_dQ, d_theta);
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "adjoint parameters");
 }

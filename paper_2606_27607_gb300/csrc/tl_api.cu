@@ -758,6 +758,7 @@ int tl_destroy(tl_instance* inst) {
         fr(M.piw);
         fr(M.Qw);
         fr(M.pairs);
+        fr(M.mu);
     }
     fr(I->d_red);
     fr(I->d_err);
@@ -899,7 +900,8 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
             (rc = dev_alloc(I, &M.G, sizeof(double) * SS * kMaxDq * 2, "parameter basis")) ||
             (rc = dev_alloc(I, &M.piw, (size_t)I->elt * I->Spad, "pi copy")) ||
             (rc = dev_alloc(I, &M.Qw, (size_t)I->elt * SS, "Q copy")) ||
-            (rc = dev_alloc(I, &M.pairs, sizeof(int) * 2 * TL_GY94_PAIRS, "pair table")))
+            (rc = dev_alloc(I, &M.pairs, sizeof(int) * 2 * TL_GY94_PAIRS, "pair table")) ||
+            (rc = dev_alloc(I, &M.mu, sizeof(double), "mean rate")))
             return bail(rc);
     }
     if (prec == kTF32) {
@@ -1092,7 +1094,7 @@ static int set_model(tl_instance* inst, int model, int kind, const double* param
     if (rc) return rc;
     I->models[model].ready = false;
     I->models[model].kind = kind;
-    I->models[model].n_params = kind == TL_MODEL_REV ? 0 : n_params;
+    I->models[model].n_params = n_params;
     return launch_build_model(I, model, kind, I->d_tmp, n_params, I->d_tmp + n_params, n_freqs,
                               check);
 }
@@ -1351,7 +1353,7 @@ int tl_adjoint(tl_instance* inst, const tl_adj_op* ops, int count, int model, un
     const size_t n_mpart = (size_t)E * mat_doubles * n_chunks;
     const size_t n_M = (size_t)E * mat_doubles;
     const size_t n_gpart = (size_t)SS * std::max(E, 1);
-    const size_t n_theta_dev = 2 + TL_GY94_PAIRS + kMaxDq;
+    const size_t n_theta_dev = std::max<size_t>(2 + TL_GY94_PAIRS + kMaxDq, SS);
     if ((rc = ensure_scratch(I, n_coef + n_mpart + n_M + n_gpart + SS + E + SS + n_theta_dev)))
         return rc;
     double* d_coef = I->d_red;

@@ -134,6 +134,7 @@ struct ModelDev {
     void* piw = nullptr;      // pi in working precision [Spad]
     void* Qw = nullptr;       // Q in working precision [Spad][Spad]
     int* pairs = nullptr;     // GY94RE: [TL_GY94_PAIRS][2] codon indices (i < j)
+    double* mu = nullptr;     // [1] mean rate of the unnormalised Q (tl_set_model)
     int n_dq = 0;
     int kind = 0;             // TL_MODEL_* (0: set from Q or an eigensystem)
     int n_params = 0;         // parameters of tl_set_model

@@ -37,7 +37,8 @@ __device__ __forceinline__ bool one_difference(int ci, int cj) {
 __global__ void k_build_model(int kind, int S, int Spad, const double* __restrict__ params,
                               const double* __restrict__ freqs, double* __restrict__ Q,
                               double* __restrict__ pi, double* __restrict__ dQ, int n_dq,
-                              int* __restrict__ pairs, int* __restrict__ err) {
+                              int* __restrict__ pairs, double* __restrict__ mu_out,
+                              int* __restrict__ err) {
     __shared__ int codon_nt[64];   // sense codon -> 16*n1 + 4*n2 + n3
     __shared__ char codon_aa[64];
     __shared__ short pair_of[61 * 61];  // random effects: pair index of (i, j), i < j
@@ -179,6 +180,7 @@ __global__ void k_build_model(int kind, int S, int Spad, const double* __restric
     }
     const double mu = s_mu[0];
     if (t == 0 && !(mu > 0.0 && isfinite(mu))) err[0] = 1;
+    if (t == 0) mu_out[0] = mu;
     for (int idx = t; idx < Spad * Spad; idx += nt) {
         double r = Q[idx];
         for (int k = 0; k < n_dq; ++k) {
@@ -609,7 +611,7 @@ int launch_build_model(Instance* I, int m, int kind, const double* d_params, int
                : (kind == TL_MODEL_GY94 || kind == TL_MODEL_GY94RE) ? 2 : 0;
     M.n_dq = n_dq;
     k_build_model<<<1, 256, 0, I->stream>>>(kind, I->S, I->Spad, d_params, d_freqs, M.Q, M.pi,
-                                            M.dQ, n_dq, M.pairs, I->d_err);
+                                            M.dQ, n_dq, M.pairs, M.mu, I->d_err);
     I->launches += 1;
     int rc = cuda_check(I, cudaGetLastError(), "build model");
     if (rc) return rc;

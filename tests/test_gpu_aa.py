@@ -1,6 +1,7 @@
 """Twenty states (amino acids under a general reversible model): the
 tensor-core path with states padded to 64 and the FP64 generic path,
-against the oracle: logL, branch gradients and dlogL/dQ."""
+against the oracle: logL, branch gradients, dlogL/dQ and the gradient with
+respect to every exchangeability (complex-step dQ/dE in the oracle)."""
 import numpy as np
 import pytest
 
@@ -31,6 +32,7 @@ def test_amino_acid_loglik_gradient_and_adjoint(prec, tol_l, tol_g):
     want_l = op.loglik(*args)[0]
     want_g = og.branch_gradient(*args)
     want_q = og.rate_matrix_gradient(*args)
+    want_th = np.einsum("kij,ij->k", om.rate_jacobian("rev", w.params, w.freqs), want_q)
     tl = TreeLikelihood(w.tree.n_tips, w.n_patterns, 20, 4, prec)
     try:
         tl.set_tips(tips)
@@ -44,8 +46,9 @@ def test_amino_acid_loglik_gradient_and_adjoint(prec, tol_l, tol_g):
     finally:
         tl.close()
     assert abs(logl - want_l) <= tol_l * abs(want_l)
-    assert th.size == 0
-    for got, want in ((g[:-1], want_g[:-1]), (g2[:-1], want_g[:-1]), (dq, want_q)):
+    assert th.size == 400           # the exchangeability matrix, diagonal 0
+    assert np.all(th.reshape(20, 20).diagonal() == 0)
+    for got, want in ((g[:-1], want_g[:-1]), (g2[:-1], want_g[:-1]), (dq, want_q), (th, want_th)):
         if prec == "f64":
             scale = np.max(np.abs(want))
             assert np.max(np.abs(got - want) / np.maximum(np.abs(want), 1e-3 * scale)) <= tol_g

@@ -158,11 +158,11 @@ def test_ratio_transform_validates_on_the_host():
 
 
 def test_autograd_refuses_parameter_gradients_it_cannot_give():
-    """A general reversible model has no built-in parameter derivatives: the
-    autograd Function says so before touching the device."""
+    """A model kind without parameter derivatives: the autograd Function
+    says so before touching the device."""
     torch = pytest.importorskip("torch")
     from paper_2606_27607_gb300 import LogLikelihood
     t = torch.ones(5, dtype=torch.float64, requires_grad=True)
     th = torch.ones(16, dtype=torch.float64, requires_grad=True)
     with pytest.raises(ValueError, match="dlogL/dQ"):
-        LogLikelihood.apply(t, th, None, "rev", np.full(4, 0.25))
+        LogLikelihood.apply(t, th, None, "custom", np.full(4, 0.25))
