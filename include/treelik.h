@@ -8,8 +8,9 @@
  * is the likelihood; Sec. "Discussion": the branch-length gradient is a
  * sandwich of a pre-order partial, the rate matrix and a post-order partial;
  * transition matrices come from an eigendecomposition of Q, cached across
- * patterns; exact substitution-parameter gradients through the matrix
- * exponential).
+ * patterns, or formed inside pruning for single-pattern problems; exact
+ * substitution-parameter gradients through the adjoint of the matrix
+ * exponential; random-effects models; the node-height ratio transform).
  *
  * Conventions shared by every call
  *  - Every function returns an int status: TL_OK (0) or a negative TL_ERR_*
@@ -30,7 +31,8 @@
  *  - Layouts: host matrices are row-major S x S doubles; tip states are one
  *    int8 code per pattern; tip partials are [pattern][state] doubles.
  *    Device partials are [category][pattern][state] in the instance's
- *    working precision, patterns padded to a multiple of 32.
+ *    working precision, patterns padded to a multiple of 64 (128 for
+ *    TL_PREC_TF32), states to a multiple of 4 (64 for TL_PREC_TF32).
  */
 #ifndef TREELIK_H
 #define TREELIK_H
