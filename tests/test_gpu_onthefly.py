@@ -3,7 +3,6 @@ eigensystem (one or a few site patterns, large state spaces) against the
 oracle (expm) and against the stored-matrix path of the same instance."""
 import dataclasses
 
-import numpy as np
 import pytest
 
 import synth
