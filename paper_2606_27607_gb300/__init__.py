@@ -41,30 +41,42 @@ class TreeLikelihood:
         self.children = None
         self._post = None
         self._pre = None
+        # bumped by every call that changes the device state an adjoint
+        # reads (inputs, model, tree, post-order partials), so a caller that
+        # saved the state of one evaluation can tell whether it is current
+        self.generation = 0
+
+    def _touch(self) -> None:
+        self.generation += 1
 
     def close(self):
         self.inst.close()
 
     # inputs ----------------------------------------------------------------
     def set_tips(self, tips: np.ndarray) -> None:
+        self._touch()
         for t in range(self.N):
             self.inst.set_tip_states(t, tips[t])
 
     N_PARAMS = {"hky": 1, "gtr": 6, "gy94": 2, "gy94re": 265}
 
     def set_model(self, kind: str, params, freqs) -> None:
+        self._touch()
         self.inst.set_model(0, kind, params, freqs)
         self.kind = kind
 
     def set_rates(self, rates, weights=None) -> None:
+        self._touch()
         self.inst.set_category_rates(rates)
         if weights is not None:
             self.inst.set_category_weights(weights)
 
     def set_pattern_weights(self, w) -> None:
+        self._touch()
         self.inst.set_pattern_weights(w)
 
     def set_tree(self, children, edge_len) -> None:
+        self._touch()
         children = np.asarray(children)
         if self.children is None or not np.array_equal(children, self.children):
             self.children = children.copy()
@@ -84,6 +96,7 @@ class TreeLikelihood:
         """logL (and per-pattern values); ``derivatives`` also fills the
         dP/dt slots so that branch_gradient() can follow without a second
         post-order pass."""
+        self._touch()
         self.update_matrices(derivatives)
         self.inst.update_partials(self._post)
         return self.inst.root_loglik(self.nn - 1, 0, site)
@@ -95,6 +108,7 @@ class TreeLikelihood:
 
     def gradient(self):
         """(logL, dlogL/dt for every node, root entry 0)."""
+        self._touch()
         self.update_matrices(True)
         self.inst.update_partials(self._post)
         logl = self.inst.root_loglik(self.nn - 1, 0)
@@ -107,6 +121,7 @@ class TreeLikelihood:
         post-order partials of the current tree. One pre-order pass per
         parameter with dP/dtheta in the derivative slots; the next gradient()
         recomputes dP/dt there."""
+        self._touch()   # the derivative slots now hold dP/dtheta
         n = len(self.inst.get_model(0)[2])   # the model's dQ/dtheta matrices
         v = np.arange(self.nn - 1, dtype=np.int32)
         out = np.zeros(n)

@@ -26,19 +26,31 @@ class LogLikelihood(torch.autograd.Function):
                              "TreeLikelihood.adjoint() instead")
         t = edge_len.detach().cpu().double().numpy()
         th = params.detach().cpu().double().numpy()
+        LogLikelihood._evaluate(tl, kind, th, freqs, t)
+        ctx.tl = tl
+        ctx.dev = edge_len.device
+        ctx.saved = (kind, th, freqs, t)
+        ctx.generation = tl.generation
+        return torch.tensor(tl.last_logl, dtype=torch.float64)
+
+    @staticmethod
+    def _evaluate(tl, kind, th, freqs, t):
         tl.set_model(kind, th, freqs)
         full = np.zeros(tl.nn)
         full[: tl.nn - 1] = t
         tl.set_tree(tl.children, full)
-        logl = tl.loglik()
-        ctx.tl = tl
-        ctx.dev = edge_len.device
-        return torch.tensor(logl, dtype=torch.float64)
+        tl.last_logl = tl.loglik()
 
     @staticmethod
     def backward(ctx, grad_out):
         tl = ctx.tl
-        # the forward pass left the post-order partials and P in place
+        # The adjoint reads the post-order partials and matrices on the
+        # device. They are this forward's unless another evaluation on the
+        # same instance ran since (two forwards before one backward, a
+        # finite-difference probe in between): then this forward's state is
+        # rebuilt from its saved inputs first.
+        if tl.generation != ctx.generation:
+            LogLikelihood._evaluate(tl, *ctx.saved)
         g, _, gth = tl.adjoint()
         s = float(grad_out)
         gt = torch.from_numpy(s * g[: tl.nn - 1]).to(ctx.dev)

@@ -187,3 +187,33 @@ def test_autograd_full_size_sampled_patterns(name, prec):
         assert abs(fd - gk[0]) <= 1e-3 * max(abs(fd), 1e-3 * np.max(np.abs(gk)))
     finally:
         t64.close()
+
+
+def test_two_forwards_then_one_backward():
+    """loss = f(t1) + f(t2) on one instance: each backward must see its own
+    forward's partials, not those of the last evaluation on the instance."""
+    import torch
+
+    from paper_2606_27607_gb300 import LogLikelihood
+    w = synth.workload("hky_8x1000", n_tips=10, n_patterns=200)
+    Q, pi, dQ = om.build(w.model, w.params, w.freqs)
+    t1 = w.tree.edge_len[:-1].copy()
+    t2 = t1 * np.linspace(0.5, 1.7, len(t1))
+    want = []
+    for tt in (t1, t2):
+        full = np.append(tt, 0.0)
+        tree = synth.Tree(w.tree.n_tips, w.tree.children, w.tree.parent, full)
+        want.append(og.branch_gradient(tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights,
+                                       w.tips)[:-1])
+    tl = make(w, "f64", 4)
+    try:
+        a = torch.tensor(t1, dtype=torch.float64, requires_grad=True)
+        b = torch.tensor(t2, dtype=torch.float64, requires_grad=True)
+        th = torch.tensor(w.params, dtype=torch.float64)
+        loss = LogLikelihood.apply(a, th, tl, "hky", w.freqs) + \
+            2.0 * LogLikelihood.apply(b, th, tl, "hky", w.freqs)
+        loss.backward()
+    finally:
+        tl.close()
+    assert np.allclose(a.grad.numpy(), want[0], rtol=1e-10, atol=1e-10)
+    assert np.allclose(b.grad.numpy(), 2.0 * want[1], rtol=1e-10, atol=1e-10)

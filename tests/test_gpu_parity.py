@@ -305,6 +305,38 @@ def test_gtr_512x100k_f32_full_size():
     assert abs(logl - want_l) <= 1e-5 * abs(want_l)
 
 
+@pytest.mark.slow
+def test_gtr_512x100k_f32_gradient_full_size_sampled():
+    """The benchmark's headline configuration (512 taxa x 100,000 patterns,
+    FP32 partials) with every kernel launched over all patterns: pattern
+    weights select 300 patterns (the ragged tail among them) and are 0
+    elsewhere, so the oracle evaluates logL and all 1,022 branch derivatives
+    on those patterns alone; every component meets the reduced-precision
+    bound. With weight 1 everywhere, the FP32 gradient matches the FP64 GPU
+    path (itself oracle-checked) in the same per-component bound."""
+    import dataclasses
+    w = synth.workload("gtr_512x100k")
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(w.n_patterns, 300, replace=False))
+    idx[-1] = w.n_patterns - 1
+    wt = np.zeros(w.n_patterns)
+    wt[idx] = 1.0
+    sel = dataclasses.replace(w, pattern_weights=wt)
+    small = dataclasses.replace(w, tips=w.tips[:, idx], pattern_weights=np.ones(len(idx)))
+    Q, pi, _ = om.build(w.model, w.params, w.freqs)
+    want_l, _ = op.loglik(small.tree, Q, pi, w.rates, w.cat_weights, small.pattern_weights,
+                          small.tips)
+    want_g = og.branch_gradient(small.tree, Q, pi, w.rates, w.cat_weights,
+                                small.pattern_weights, small.tips)
+    logl, _, g = gpu_run(sel, "f32")
+    assert abs(logl - want_l) <= 1e-5 * abs(want_l), (logl, want_l)
+    assert_grad_close(g[:-1], want_g[:-1], 1e-3)
+    l32, _, g32 = gpu_run(w, "f32")
+    l64, _, g64 = gpu_run(w, "f64")
+    assert abs(l32 - l64) <= 1e-5 * abs(l64)
+    assert_grad_close(g32[:-1], g64[:-1], 1e-3)
+
+
 # ---------------------------------------------------------------------------
 # errors
 # ---------------------------------------------------------------------------

@@ -674,3 +674,48 @@ def test_ratio_transform_chain_rule_vs_finite_differences():
         pm[v] -= eps
         fd = (f(r, root_h, pp) - f(r, root_h, pm)) / (2 * eps)
         assert abs(grate[v] - fd) < 1e-6 * max(1.0, abs(fd))
+
+
+def _f3x4_worked():
+    """The hand-worked F3x4 example of tests/golden/f3x4_worked.txt."""
+    f, rows = [], []
+    with open(os.path.join(GOLDEN, "f3x4_worked.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].split()
+            if not line:
+                continue
+            if line[0] in ("f1", "f2", "f3"):
+                f.append([float(x) for x in line[1:]])
+            else:
+                rows.append((line[0], int(line[1]), float(line[2])))
+    return np.array(f), rows
+
+
+def test_f3x4_frequencies_match_the_worked_example():
+    """Non-uniform position frequencies, so a position mix-up (f1 used at
+    every position, positions swapped) or a missing stop renormalisation
+    changes the pinned values."""
+    f, rows = _f3x4_worked()
+    pi = model.f3x4_frequencies(f)
+    codons, _ = model.genetic_code()
+    assert len(pi) == 61 and abs(pi.sum() - 1.0) < 1e-15
+    for name, idx, num in rows:
+        assert "".join(model.BASES[b] for b in codons[idx]) == name
+        assert abs(pi[idx] - num / 0.908) <= 1e-15, (name, pi[idx], num / 0.908)
+
+
+def test_gy94_rate_ratios_on_the_worked_frequencies():
+    """Off-diagonal GY94 rates out of one codon are kappa^[ts] omega^[ns] pi_j
+    up to the common normaliser: AAA (Lys) -> AAG (Lys) is a synonymous
+    transition, AAA -> AAC (Asn) a nonsynonymous transversion, AAA -> GAA
+    (Glu) a nonsynonymous transition, AAA -> AAT (Asn) a nonsynonymous
+    transversion; AAA -> ACC (two changes) has rate zero."""
+    f, rows = _f3x4_worked()
+    kappa, omega = 2.5, 0.3
+    Q, pi, _ = model.gy94(kappa, omega, f)
+    idx = {"".join(model.BASES[b] for b in c): i for i, c in enumerate(model.genetic_code()[0])}
+    # pi by hand: AAG = .1*.4*.2, AAC = .1*.4*.15, GAA = .3*.4*.25, AAT = .1*.4*.4 (over .908)
+    q = lambda a, b: Q[idx[a], idx[b]]
+    assert abs(q("AAA", "AAG") / q("AAA", "AAC") - (kappa * 0.008) / (omega * 0.006)) < 1e-12
+    assert abs(q("AAA", "GAA") / q("AAA", "AAT") - (kappa * omega * 0.030) / (omega * 0.016)) < 1e-12
+    assert q("AAA", "ACC") == 0.0
