@@ -51,7 +51,6 @@ def parse():
     ap.add_argument("--codon-only", action="store_true", help="only the codon line (profiling)")
     ap.add_argument("--codon-taxa", type=int, default=0)
     ap.add_argument("--codon-patterns", type=int, default=0)
-    ap.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--serving", action="store_true",
                     help="continuous-batching serving run instead of the step benchmark")
     ap.add_argument("--requests", type=int, default=2000)
@@ -72,71 +71,128 @@ def parse():
 
 
 # ---------------------------------------------------------------------------
-# oracle timing (single-threaded subprocess)
+# oracle timing: one thread, and every allowed host core (pattern chunks in
+# spawned worker processes, one BLAS thread each)
 # ---------------------------------------------------------------------------
 
-def cpu_worker(workload: str, sample: int, steps: int) -> None:
-    """Time the FP64 oracle (logL + branch gradient) on the first ``sample``
-    patterns of the workload; prints one JSON line."""
+def _oracle_step(w, Q, pi, tips, wt):
+    from oracle import gradient as og, pruning as op
+    op.loglik_chunked(w.tree, Q, pi, w.rates, w.cat_weights, wt, tips)
+    og.branch_gradient(w.tree, Q, pi, w.rates, w.cat_weights, wt, tips)
+
+
+def _oracle_worker(workload, lo, sample, steps, barrier, out):
+    """One worker: logL + branch gradient of the FP64 oracle on patterns
+    [lo, lo + sample) of the workload, ``steps`` times; every step starts at
+    a barrier shared with the other workers, so a step's wall time is the
+    latest end minus the common start."""
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
     import numpy as np
 
     import synth
-    from oracle import gradient as og, model as om, pruning as op
+    from oracle import model as om
     w = synth.workload(workload)
-    tips = np.ascontiguousarray(w.tips[:, :sample])
-    wt = w.pattern_weights[:sample]
+    hi = min(lo + sample, w.n_patterns)
+    tips = np.ascontiguousarray(w.tips[:, lo:hi])
+    wt = w.pattern_weights[lo:hi]
     Q, pi, _ = om.build(w.model, w.params, w.freqs)
-    times = []
+    res = []
     for _ in range(steps):
-        t0 = time.perf_counter()
-        op.loglik_chunked(w.tree, Q, pi, w.rates, w.cat_weights, wt, tips)
-        og.branch_gradient(w.tree, Q, pi, w.rates, w.cat_weights, wt, tips)
-        times.append(time.perf_counter() - t0)
-    print(json.dumps({"times": times, "patterns": sample, "internal_nodes": w.tree.n_tips - 1,
-                      "cores": 1}))
+        barrier.wait()
+        t0 = time.time()
+        _oracle_step(w, Q, pi, tips, wt)
+        res.append((t0, time.time()))
+    out.put((hi - lo, w.tree.n_tips - 1, res))
 
 
-def run_cpu(workload: str, sample: int, steps: int) -> dict:
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-worker", "--workload", workload,
-           "--cpu-sample", str(sample), "--steps", str(steps)]
-    out = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True).stdout
-    return json.loads(out.strip().splitlines()[-1])
+def run_oracle(workload: str, sample: int, steps: int, cores: int) -> dict:
+    """Time the oracle on ``cores`` worker processes (spawned, so no GPU
+    state is inherited), each on its own ``sample`` consecutive patterns.
+    Returns per-step wall times, units per step and the worker count."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    saved = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS",
+                                             "MKL_NUM_THREADS", "CUDA_VISIBLE_DEVICES")}
+    os.environ.update(OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                      CUDA_VISIBLE_DEVICES="")
+    try:
+        barrier, out = ctx.Barrier(cores), ctx.Queue()
+        procs = [ctx.Process(target=_oracle_worker,
+                             args=(workload, i * sample, sample, steps, barrier, out))
+                 for i in range(cores)]
+        for pr in procs:
+            pr.start()
+        got = [out.get() for _ in procs]
+        for pr in procs:
+            pr.join()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    units = sum(g[0] for g in got) * got[0][1]
+    walls = [max(g[2][s][1] for g in got) - min(g[2][s][0] for g in got) for s in range(steps)]
+    return {"walls": walls, "units": units, "patterns": sum(g[0] for g in got), "workers": cores,
+            "internal_nodes": got[0][1]}
+
+
+def host_cores() -> tuple[int, int]:
+    """(cores this process may run on, cores of the host)."""
+    try:
+        allowed = len(os.sched_getaffinity(0))
+    except AttributeError:
+        allowed = os.cpu_count() or 1
+    return allowed, os.cpu_count() or allowed
 
 
 def cpu_baseline(workload: str, sample: int) -> dict:
+    """The oracle on one core and on every allowed core, each leg about
+    10-15 s of CPU work: single-thread on the first ``sample`` patterns;
+    all cores on ``sample`` patterns per core (consecutive chunks)."""
+    allowed, total = host_cores()
     if sample <= 0:
-        probe = run_cpu(workload, 1000, 1)
-        per = probe["times"][0] / 1000
-        sample = int(max(1000, min(100_000, 15.0 / max(per, 1e-9))))
-        sample = (sample // 1000) * 1000
-    r = run_cpu(workload, sample, 1)
-    t = r["times"][0]
-    return {"value": r["patterns"] * r["internal_nodes"] / t, "unit": UNIT, "cores": r["cores"],
-            "kind": "oracle",
-            "sample": f"first {r['patterns']} patterns of {workload}, logL + branch gradient, "
-                      f"FP64 numpy/scipy, {t:.1f} s"}
+        probe = run_oracle(workload, 500, 1, 1)
+        per = probe["walls"][0] / 500
+        sample = int(max(500, min(100_000 // max(1, allowed), 12.0 / max(per, 1e-9))))
+        sample = (sample // 500) * 500
+    one = run_oracle(workload, sample, 1, 1)
+    v1 = one["units"] / one["walls"][0]
+    par = run_oracle(workload, sample, 1, allowed) if allowed > 1 else one
+    vn = par["units"] / par["walls"][0]
+    return {"value": vn, "unit": UNIT, "cores": par["workers"], "kind": "oracle",
+            "host_cores": total, "affinity_cores": allowed,
+            "sample": f"{par['patterns']} patterns of {workload} ({sample} per worker process, "
+                      f"{par['workers']} processes, one BLAS thread each), logL + branch gradient, "
+                      f"FP64 numpy/scipy, {par['walls'][0]:.1f} s wall",
+            "single_thread": {"value": v1, "cores": 1,
+                              "sample": f"first {one['patterns']} patterns, "
+                                        f"{one['walls'][0]:.1f} s"}}
 
 
 def reference_arm(args) -> None:
-    """The FP64 CPU oracle as it stands, same workload and metric."""
+    """The FP64 CPU oracle as it stands, same workload and metric, on every
+    allowed host core (one worker process per core, each on its own chunk
+    of patterns; every step is all workers' chunks)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    sample = args.cpu_sample or 2000
-    r = run_cpu(args.workload, sample, args.warmup + args.steps)
-    times = r["times"][args.warmup:]
-    t = statistics.median(times)
-    value = r["patterns"] * r["internal_nodes"] / t
+    allowed, total = host_cores()
+    sample = args.cpu_sample or 300
+    r = run_oracle(args.workload, sample, args.warmup + args.steps, allowed)
+    t = statistics.median(r["walls"][args.warmup:])
+    value = r["units"] / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "sample_patterns": r["patterns"]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"], "kind": "oracle",
-                             "sample": f"first {r['patterns']} patterns of {args.workload} per "
-                                       "step, logL + branch gradient, FP64 numpy/scipy"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["workers"],
+                             "kind": "oracle", "host_cores": total, "affinity_cores": allowed,
+                             "sample": f"{r['patterns']} patterns of {args.workload} per step "
+                                       f"({sample} per worker process, {r['workers']} processes), "
+                                       "logL + branch gradient, FP64 numpy/scipy"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -229,14 +285,16 @@ def tf32_peak() -> tuple[float, str]:
 
 def codon_line(steps: int, warmup: int, taxa: int = 0, patterns: int = 0,
                prec: str = "tf32") -> dict:
-    """GY94 128 taxa x 20,000 patterns on the tensor-core path (TF32, or
-    "tf32x2": matrices split into two TF32 terms): one step = model +
-    eigensystem, P and dP/dt, post-order, root logL, pre-order gradient.
-    Algorithmic FLOPs count the contractions of internal children only
-    (padded 64 x 64 per category): post 1, gradient 3 per child (twice that
-    with split matrices). Algorithmic bytes of the post-order pass: each
-    internal child's partials read once, every internal node's partials and
-    exponents written once, tip states read once."""
+    """GY94 128 taxa x 20,000 patterns on the tensor-core path (TF32;
+    "tf32x2": matrices split into two TF32 terms; "tf32x3": FP32 partials
+    split on chip as well, three products): one step = model + eigensystem,
+    P and dP/dt, post-order, root logL, pre-order gradient. Algorithmic
+    FLOPs count the contractions of internal children only (padded 64 x 64
+    per category): post 1, gradient 3 per child; the split modes issue 2 or
+    3 products for each ("issued"). Algorithmic bytes of the post-order
+    pass: each internal child's partials read once, every internal node's
+    partials and exponents written once, tip states read once. The step's
+    gradient comes back under "_grad" (for the error columns)."""
     import numpy as np
     import torch
 
@@ -297,31 +355,51 @@ def codon_line(steps: int, warmup: int, taxa: int = 0, patterns: int = 0,
     ms = a.elapsed_time(b) / steps
     k_ms = {k: statistics.mean(x.elapsed_time(y) for x, y in ev[k]) for k in ev}
     n_int_children = N - 2
-    mult = 2 if prec == "tf32x2" else 1
-    f_post = mult * n_int_children * 4 * 2 * 64 * 64 * P
+    mult = {"tf32x2": 2, "tf32x3": 3}.get(prec, 1)
+    f_post = n_int_children * 4 * 2 * 64 * 64 * P
     f_pre = 3 * f_post
     peak, src = tf32_peak()
     hbm, hsrc = peaks()
     ppad = (P + 127) // 128 * 128
     b_post = ppad * (n_int_children * 4 * 256 + (N - 1) * (4 * 256 + 4) + N)
     logl = float(d_out[0].item())
+    grad = d_out[1:].cpu().numpy().copy()
     tl.close()
+    how = {"tf32x2": " (P = P_hi + P_lo, two products)",
+           "tf32x3": " (FP32 partials split on chip, P = P_hi + P_lo, three products)"}
     return {"workload": f"gy94_{N}x{P}",
-            "precision": (f"{prec} tcgen05" + (" (P = P_hi + P_lo, two products)"
-                                               if prec == "tf32x2" else "") + ", fp32 accumulate"),
+            "precision": f"{prec} tcgen05" + how.get(prec, "") + ", fp32 accumulate",
             "value": P * (N - 1) / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-            "grad_evals_per_s": 1e3 / ms, "logL": logl,
+            "grad_evals_per_s": 1e3 / ms, "logL": logl, "_grad": grad,
             "kernels": {k: {"ms": k_ms[k],
-                            "TFLOP/s": (f_post if k == "post" else f_pre) / (k_ms[k] * 1e-3) / 1e12}
+                            "TFLOP/s": (f_post if k == "post" else f_pre) / (k_ms[k] * 1e-3) / 1e12,
+                            "issued TFLOP/s": mult * (f_post if k == "post" else f_pre)
+                                              / (k_ms[k] * 1e-3) / 1e12}
                         for k in k_ms},
             "hbm": {"kernel": "k_tc<post>", "algorithmic_bytes": b_post,
                     "achieved": b_post / (k_ms["post"] * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                     "frac": b_post / (k_ms["post"] * 1e-3) / 1e9 / hbm, "peak_source": hsrc},
-            "roofline": {"bound": "tensor", "kernel": "k_tc<post> (tcgen05 kind::tf32)",
+            "roofline": {"bound": "tensor",
+                         "kernel": ("k_tc_fused (subtree-fused post-order, tcgen05 kind::tf32)"
+                                    if prec in ("tf32", "tf32x2") and
+                                    os.environ.get("TL_TC_FUSED", "1") != "0"
+                                    else "k_tc<post> (tcgen05 kind::tf32)"),
                          "achieved": f_post / (k_ms["post"] * 1e-3) / 1e12, "peak": peak,
                          "unit": "TFLOP/s",
                          "frac": f_post / (k_ms["post"] * 1e-3) / 1e12 / peak,
                          "peak_source": src}}
+
+
+def per_component_err(g, ref) -> float:
+    """max_i |g_i - ref_i| / max(|ref_i|, 1e-3 max_j |ref_j|)."""
+    import numpy as np
+    g, ref = np.asarray(g, float), np.asarray(ref, float)
+    scale = float(np.max(np.abs(ref))) if ref.size else 0.0
+    return float(np.max(np.abs(g - ref) / np.maximum(np.abs(ref), max(1e-3 * scale, 1e-300))))
+
+
+def c64_taxa(line: dict) -> int:
+    return int(line["workload"].split("_")[1].split("x")[0])
 
 
 def traffic_for(kernel: str, per_launch_units: float) -> float | None:
@@ -647,9 +725,6 @@ def main() -> None:
     if args.serving:
         print(json.dumps(serving_line(args)), flush=True)
         return
-    if args.cpu_worker:
-        cpu_worker(args.workload, args.cpu_sample, max(1, args.steps))
-        return
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -824,25 +899,43 @@ def main() -> None:
     roof = {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": hbm, "unit": "GB/s",
             "frac": ach / hbm, "peak_source": src, "traffic": traffic,
             "algorithmic_bytes": alg[dom], "ms": k_ms[dom],
-            "other": {k: {"ms": k_ms[k], "GB/s": alg[k] / (k_ms[k] * 1e-3) / 1e9} for k in k_ms}}
+            "other": {k: {"ms": k_ms[k], "GB/s": alg[k] / (k_ms[k] * 1e-3) / 1e9,
+                          "frac": alg[k] / (k_ms[k] * 1e-3) / 1e9 / hbm} for k in k_ms}}
 
-    codon = codon_split = codon64 = fp64 = None
+    codon = codon_split = codon_x3 = codon64 = fp64 = None
     if not args.no_codon and world == 1:
         try:
             codon = codon_line(max(5, args.steps // 20), 3)
             codon_split = codon_line(max(5, args.steps // 20), 3, prec="tf32x2")
+            codon_x3 = codon_line(max(5, args.steps // 20), 3, prec="tf32x3")
+            # the same split-matrix step with the level-by-level post-order
+            # kernels instead of the subtree-fused one
+            os.environ["TL_TC_FUSED"] = "0"
+            try:
+                lvl = codon_line(max(5, args.steps // 20), 3, prec="tf32x2")
+            finally:
+                os.environ.pop("TL_TC_FUSED", None)
+            lvl.pop("_grad", None)
+            codon_split["level_by_level"] = {"ms_per_step": lvl["ms_per_step"],
+                                             "post_ms": lvl["kernels"]["post"]["ms"],
+                                             "logL": lvl["logL"]}
         except Exception as exc:  # reported, not fatal
             codon = {"error": str(exc)[:300]}
         try:
             c64 = codon_line(3, 1, prec="f64")
+            g64 = c64.pop("_grad")[: 2 * c64_taxa(c64) - 2]
             codon64 = {"ms_per_step": c64["ms_per_step"], "value": c64["value"],
                        "logL": c64["logL"], "path": "FP64 generic kernels, one tree at a time",
-                       "speedup_tf32": c64["ms_per_step"] / codon["ms_per_step"],
-                       "rel_err_logL_tf32": abs(codon["logL"] - c64["logL"]) / abs(c64["logL"]),
-                       "rel_err_logL_tf32x2":
-                           abs(codon_split["logL"] - c64["logL"]) / abs(c64["logL"])}
+                       "speedup_tf32": c64["ms_per_step"] / codon["ms_per_step"]}
+            for name, line_ in (("tf32", codon), ("tf32x2", codon_split), ("tf32x3", codon_x3)):
+                gq = line_.pop("_grad")[: len(g64)]
+                codon64[f"rel_err_logL_{name}"] = abs(line_["logL"] - c64["logL"]) / abs(c64["logL"])
+                codon64[f"grad_err_per_component_{name}"] = per_component_err(gq, g64)
         except Exception as exc:  # reported, not fatal
             codon64 = {"error": str(exc)[:300]}
+        for line_ in (codon, codon_split, codon_x3):
+            if isinstance(line_, dict):
+                line_.pop("_grad", None)
     if world == 1 and not args.taxa and not args.patterns:
         # the same step on the FP64 four-state kernels (the plain FP64 path)
         tl64 = TreeLikelihood(N, P, S, R, "f64", stream=stream.cuda_stream)
@@ -878,7 +971,8 @@ def main() -> None:
         fp64 = {"ms_per_step": ms64, "value": P * (N - 1) / (ms64 * 1e-3), "logL": l64,
                 "path": "FP64 four-state kernels, one tree at a time",
                 "speedup_fp32": ms64 / ms, "rel_err_logL_fp32": abs(logl - l64) / abs(l64),
-                "rel_err_grad_fp32": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64))}
+                "rel_err_grad_fp32": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64)),
+                "grad_err_per_component_fp32": per_component_err(g32[: nn - 1], g64[: nn - 1])}
         tl64.close()
 
     cpu = None
@@ -903,7 +997,7 @@ def main() -> None:
             "grad_evals_per_s": world * 1e3 / ms, "logL": logl, "clocks": clk, "e2e": e2e,
             "gpu_launches": int(launches) * args.steps, "gpu_launches_per_step": int(launches),
             "roofline": roof, "cpu_baseline": cpu, "fp64": fp64, "codon": codon,
-            "codon_split": codon_split, "codon_fp64": codon64}
+            "codon_split": codon_split, "codon_x3": codon_x3, "codon_fp64": codon64}
     print(json.dumps(line), flush=True)
     tl.close()
     if dist:

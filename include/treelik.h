@@ -76,6 +76,18 @@ extern "C" {
                                  removes the matrix rounding, the one error
                                  shared by all patterns (it would not average
                                  out over the pattern sum). */
+#define TL_SPLIT_PARTIALS 0x400u /* with TL_PREC_TF32 | TL_SPLIT_MATRICES:
+                                 partials are stored in full FP32 and every
+                                 tensor-core operand tile of partials is
+                                 split on chip into TF32 hi + lo (hi the
+                                 truncation, lo the truncation of the rest);
+                                 each contraction is three products
+                                 (x_hi P_hi + x_hi P_lo + x_lo P_hi), about
+                                 21 bits of both operands, so logL and every
+                                 gradient component carry FP32-level errors
+                                 (the per-pattern TF32 rounding of stored
+                                 partials is what limits the gradient of the
+                                 two modes above) */
 
 /* ---- model kinds for tl_set_model -------------------------------------- */
 #define TL_MODEL_HKY   1  /* S=4.  params: kappa.  freqs: pi[4]                */
@@ -378,10 +390,16 @@ int tl_get_partials(tl_instance* inst, int buf, double* out, int32_t* exponents)
  *   out_logl         device, 1 double, written asynchronously on `stream`
  * Scratch is a fixed array built into the library (one double per 32
  * patterns): n_patterns above 2,097,152 returns TL_ERR_UNSUPPORTED. The
- * first call on each device looks up that device's copy of the array with
- * that device current; make the first call before any stream capture. All
- * calls share the array, so calls that overlap on the GPU (other streams,
- * other host threads) race; serialise them. A zero or non-finite pattern
+ * array is a module global: the CUDA runtime loads the module that holds it
+ * (and so reserves its 512 KiB) lazily, on the first use on each device,
+ * not when the library is loaded. The first call on each device does that
+ * set-up with the device current (it loads the module and looks up the
+ * device's copy of the array, then caches the address), so make the first
+ * call on each device before any stream capture. The cached address belongs
+ * to the device's primary context: after cudaDeviceReset, or from another
+ * context on the same device, it is no longer valid and this entry point
+ * must not be used. All calls share the array, so calls that overlap on the
+ * GPU (other streams, other host threads) race; serialise them. A zero or non-finite pattern
  * likelihood shows up as a non-finite *out_logl (no status is read back).
  * Errors in arguments are reported through tl_last_error(NULL, ...). */
 int tl_root_loglik_static(const float* root_partials, const int32_t* exponents,

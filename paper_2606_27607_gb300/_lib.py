@@ -23,11 +23,13 @@ ERRORS = {-1: "TL_ERR_ARG", -2: "TL_ERR_INDEX", -3: "TL_ERR_ORDER", -4: "TL_ERR_
 TL_PREC_F64, TL_PREC_F32, TL_PREC_TF32, TL_PREC_BF16X3 = 0x1, 0x2, 0x4, 0x8
 TL_SCALE_NONE = 0x100
 TL_SPLIT_MATRICES = 0x200
+TL_SPLIT_PARTIALS = 0x400
 TL_MODEL_HKY, TL_MODEL_GTR, TL_MODEL_GY94, TL_MODEL_REV, TL_MODEL_GY94RE = 1, 2, 3, 4, 5
 TL_GY94_PAIRS = 263
 TL_ADJ_FIRST_ORDER = 0x1
 PRECISIONS = {"f64": TL_PREC_F64, "f32": TL_PREC_F32, "tf32": TL_PREC_TF32,
               "tf32x2": TL_PREC_TF32 | TL_SPLIT_MATRICES,
+              "tf32x3": TL_PREC_TF32 | TL_SPLIT_MATRICES | TL_SPLIT_PARTIALS,
               "bf16x3": TL_PREC_BF16X3}
 MODELS = {"hky": TL_MODEL_HKY, "gtr": TL_MODEL_GTR, "gy94": TL_MODEL_GY94, "rev": TL_MODEL_REV,
           "gy94re": TL_MODEL_GY94RE}

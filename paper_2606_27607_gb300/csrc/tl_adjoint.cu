@@ -449,6 +449,10 @@ __device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, uint32_t b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// SPLITX: the child partials are full FP32 (split-partials instances) and
+// are split as hi + lo like P and U: three products per contraction
+// (hi hi, hi lo, lo hi).
+template <bool SPLITX>
 __global__ void __launch_bounds__(256, 2) k_adj_mma(const AdjOp<float>* __restrict__ ops, AdjArgs a,
                                                     double* __restrict__ mpart) {
     extern __shared__ __align__(16) unsigned char sm_mma[];
@@ -533,16 +537,21 @@ __global__ void __launch_bounds__(256, 2) k_adj_mma(const AdjOp<float>* __restri
 #pragma unroll
             for (int ks = 0; ks < 8; ++ks) {
                 const int k0 = ks * 8;
-                uint32_t af[4];
-                af[0] = __float_as_uint(xa[g * kPP + k0 + tq]);
-                af[1] = __float_as_uint(xa[(g + 8) * kPP + k0 + tq]);
-                af[2] = __float_as_uint(xa[g * kPP + k0 + tq + 4]);
-                af[3] = __float_as_uint(xa[(g + 8) * kPP + k0 + tq + 4]);
+                const float xf[4] = {xa[g * kPP + k0 + tq], xa[(g + 8) * kPP + k0 + tq],
+                                     xa[g * kPP + k0 + tq + 4], xa[(g + 8) * kPP + k0 + tq + 4]};
+                uint32_t af[4], afl[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    af[i] = SPLITX ? tf32_rna(xf[i]) : __float_as_uint(xf[i]);
+                    afl[i] = SPLITX ? tf32_rna(xf[i] - __uint_as_float(af[i])) : 0u;
+                }
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt) {
                     const int n = 16 * wq + 8 * nt + g;
                     mma_tf32(v[nt], af, ph[n * kPP + k0 + tq], ph[n * kPP + k0 + tq + 4]);
                     mma_tf32(v[nt], af, pl[n * kPP + k0 + tq], pl[n * kPP + k0 + tq + 4]);
+                    if (SPLITX)
+                        mma_tf32(v[nt], afl, ph[n * kPP + k0 + tq], ph[n * kPP + k0 + tq + 4]);
                 }
             }
             const int sib = 1 - wc;
@@ -577,10 +586,15 @@ __global__ void __launch_bounds__(256, 2) k_adj_mma(const AdjOp<float>* __restri
                 al[3] = ul[(k0 + tq + 4) * kUP + m0 + g + 8];
 #pragma unroll
                 for (int nt = 0; nt < 8; ++nt) {
-                    const uint32_t b0 = __float_as_uint(xb[(k0 + tq) * kPP + 8 * nt + g]);
-                    const uint32_t b1 = __float_as_uint(xb[(k0 + tq + 4) * kPP + 8 * nt + g]);
+                    const float x0 = xb[(k0 + tq) * kPP + 8 * nt + g];
+                    const float x1 = xb[(k0 + tq + 4) * kPP + 8 * nt + g];
+                    const uint32_t b0 = SPLITX ? tf32_rna(x0) : __float_as_uint(x0);
+                    const uint32_t b1 = SPLITX ? tf32_rna(x1) : __float_as_uint(x1);
                     mma_tf32(acc[nt], ah, b0, b1);
                     mma_tf32(acc[nt], al, b0, b1);
+                    if (SPLITX)
+                        mma_tf32(acc[nt], ah, tf32_rna(x0 - __uint_as_float(b0)),
+                                 tf32_rna(x1 - __uint_as_float(b1)));
                 }
             }
         }
@@ -657,8 +671,9 @@ static int adj_accumulate_t(Instance* I, const void* d_ops, int n_ops, int n_chu
         ops, a, d_coef);
     if (I->prec == kTF32 && I->Spad == 64) {
         const size_t smem = adj_mma_smem();
-        cudaFuncSetAttribute(k_adj_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_adj_mma<<<dim3(n_ops, I->R, n_chunks), 256, smem, I->stream>>>(
+        const auto kern = I->split_partials ? k_adj_mma<true> : k_adj_mma<false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<dim3(n_ops, I->R, n_chunks), 256, smem, I->stream>>>(
             reinterpret_cast<const AdjOp<float>*>(d_ops), a, d_mpart);
         I->launches += 2;
         return cuda_check(I, cudaGetLastError(), "adjoint (tensor cores)");

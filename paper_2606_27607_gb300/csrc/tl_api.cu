@@ -637,7 +637,7 @@ int plan_pre(Instance* I, const tl_pre_op* ops, int n, int n_grad, bool store_al
     if ((int)order.size() != n) return fail(I, TL_ERR_ORDER, "pre-order op list is not a forest");
     // parents must precede children in the given list too (validated above by
     // prod_op lookups happening in list order)
-    const int cap = use_nuc(I) ? max_slots(I) : 0;
+    const int cap = use_nuc(I) ? nuc_pre_slot_cap(I) : 0;
     std::vector<int> free_slots;
     for (int s = cap - 1; s >= 0; --s) free_slots.push_back(s);
     std::vector<int> q_slot(2 * n, -1), pos(n);
@@ -809,6 +809,8 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
         return fail(nullptr, TL_ERR_ARG, "TL_SCALE_NONE needs TL_PREC_F64");
     if ((flags & TL_SPLIT_MATRICES) && prec != kTF32)
         return fail(nullptr, TL_ERR_ARG, "TL_SPLIT_MATRICES needs TL_PREC_TF32");
+    if ((flags & TL_SPLIT_PARTIALS) && !(flags & TL_SPLIT_MATRICES))
+        return fail(nullptr, TL_ERR_ARG, "TL_SPLIT_PARTIALS needs TL_PREC_TF32 | TL_SPLIT_MATRICES");
 
     Instance* I = new Instance();
     I->n_tips = n_tips;
@@ -828,6 +830,7 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
     I->elt = (prec == kF64) ? 8 : 4;
     I->rescale = (flags & TL_SCALE_NONE) ? 0 : 1;
     I->split = (flags & TL_SPLIT_MATRICES) ? 1 : 0;
+    I->split_partials = (flags & TL_SPLIT_PARTIALS) ? 1 : 0;
     I->stream = reinterpret_cast<cudaStream_t>(stream);
     I->h_catw = new double[kMaxCat];
     I->h_rates = new double[kMaxCat];
@@ -1003,7 +1006,9 @@ int tl_set_tip_partials(tl_instance* inst, int tip, const double* partials) {
                 double v = (s >= I->S) ? 0.0 : (p < I->P ? partials[(size_t)p * I->S + s] : 1.0);
                 size_t off = ((size_t)r * I->Ppad + p) * I->Spad + s;
                 if (I->elt == 8) reinterpret_cast<double*>(h.data())[off] = v;
-                else if (I->prec == kTF32) reinterpret_cast<float*>(h.data())[off] = tf32_host((float)v);
+                else if (I->prec == kTF32)
+                    reinterpret_cast<float*>(h.data())[off] =
+                        I->split_partials ? (float)v : tf32_host((float)v);
                 else reinterpret_cast<float*>(h.data())[off] = (float)v;
             }
     cudaMemcpyAsync(I->tip_part[tip], h.data(), h.size(), cudaMemcpyHostToDevice, I->stream);
@@ -1454,12 +1459,17 @@ int tl_update_partials(tl_instance* inst, const tl_op* ops, int count) {
     if (count == 0) return TL_OK;
     int rc;
     if (use_tc(I)) {
+        // depth-first order (the planner's): each op's child produced by
+        // the op just before is marked, and the fused kernel keeps it on chip
+        const bool fused = tc_fused_enabled(I) != 0;
         PostPlan plan;
-        if ((rc = plan_post(I, ops, count, &plan, true))) return rc;
+        if ((rc = plan_post(I, ops, count, &plan, !fused))) return rc;
         const size_t bytes = (size_t)count * kTcOpBytes;
         void* d = area(I, 0, bytes, &rc);
         if (rc) return rc;
-        if ((rc = launch_post_tc(I, ops, count, d, bytes))) return rc;
+        if (fused) rc = launch_post_tc_fused(I, plan.dev.data(), count, d, bytes);
+        else rc = launch_post_tc(I, ops, count, d, bytes);
+        if (rc) return rc;
     } else if (use_nuc(I)) {
         PostPlan plan;
         if ((rc = plan_post(I, ops, count, &plan, false))) return rc;

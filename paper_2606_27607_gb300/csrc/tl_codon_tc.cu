@@ -36,11 +36,15 @@ constexpr int kStages = 4;                  // most pipeline stages (barrier arr
 constexpr int kAChunk = kTcM * 32 * 4;      // 32 K-values of 128 rows: 16 KB
 constexpr int kBChunk = kTcN * 32 * 4;      // 8 KB
 // Stage: A (2 x 16 KB) and B (2 x 8 KB) = 48 KB, four stages; with split
-// matrices a stage also holds B_lo (64 KB), so three fit.
-template <bool SPLIT>
+// matrices a stage also holds B_lo (64 KB), so three fit; with split
+// partials also A_lo (96 KB), two stages.
+template <bool SPLIT, bool SPLITA>
 struct TcPipe {
-    static constexpr int stages = SPLIT ? 3 : 4;
-    static constexpr int bytes = 2 * kAChunk + (SPLIT ? 4 : 2) * kBChunk;
+    static constexpr int stages = SPLITA ? 2 : (SPLIT ? 3 : 4);
+    static constexpr int a_bytes = (SPLITA ? 4 : 2) * kAChunk;   // A (and A_lo)
+    static constexpr int bytes = a_bytes + (SPLIT ? 4 : 2) * kBChunk;
+    // bytes the copies of one stage bring in (A_lo is computed on chip)
+    static constexpr int tx_bytes = 2 * kAChunk + (SPLIT ? 4 : 2) * kBChunk;
 };
 constexpr int kTmemCols = 512;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // a wait gives up after 2 s
@@ -148,6 +152,16 @@ __device__ __forceinline__ float to_tf32(float x) {
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
 }
+// x with its 13 low mantissa bits cleared: a TF32 value, and x - tf32_trunc(x)
+// is exact in FP32
+__device__ __forceinline__ float tf32_trunc(float x) {
+    return __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+}
+// Make generic-proxy shared-memory writes visible to the tensor cores'
+// (async-proxy) operand reads that follow a barrier.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
 __device__ __forceinline__ int frexp_exp_f(float m) {
     int E = (__float_as_int(m) >> 23) & 0xff;
     if (E == 0) {
@@ -212,13 +226,22 @@ __device__ __forceinline__ float block_sum128(float v, float* red) {
 // SPLIT: B = B_hi + B_lo, the lo rows 2 R 64 rows after the hi rows of the
 // same block (lookups: 2 R 64 64 floats after), and each k-step issues the
 // hi and the lo product into the same accumulator.
-template <int MODE, bool SPLIT>
+// SPLITA (with SPLIT): the partials are stored in full FP32, and every A tile
+// is split in shared memory, once its copy has landed, into A_hi = the TF32
+// truncation (in place) and A_lo = the TF32 truncation of A - A_hi (all 128
+// threads, one 16-byte chunk at a time: the split is elementwise, so the
+// 128-byte swizzle of the tile does not matter); each k-step issues
+// A_hi B_hi + A_hi B_lo + A_lo B_hi, which keeps about 21 bits of both
+// operands (the A_lo B_lo term is below FP32 rounding of the sum).
+template <int MODE, bool SPLIT, bool SPLITA>
 __global__ void __launch_bounds__(128, 1)
 k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtensorMap tm_tip,
      const __grid_constant__ CUtensorMap tm_mat, const TcOp* __restrict__ ops, int n_ops,
      TcArgs a) {
-    constexpr int kSt = TcPipe<SPLIT>::stages;
-    constexpr int kStB = TcPipe<SPLIT>::bytes;
+    static_assert(!SPLITA || SPLIT, "split partials need split matrices");
+    constexpr int kSt = TcPipe<SPLIT, SPLITA>::stages;
+    constexpr int kStB = TcPipe<SPLIT, SPLITA>::bytes;
+    constexpr int kBOff = TcPipe<SPLIT, SPLITA>::a_bytes;   // B_hi within a stage
     const size_t kLoFloats = (size_t)2 * a.R * kTcN * kTcN;  // hi block -> lo block
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     // 128-byte swizzle atoms must start on 1024-byte shared-memory addresses
@@ -271,20 +294,38 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
         const int c = m0 ? (i < R ? 0 : 1) : 1;
         const int r = i % R;
         unsigned char* st = stages + s * kStB;
-        mbar_expect_tx(&full[s], kStB);
+        mbar_expect_tx(&full[s], TcPipe<SPLIT, SPLITA>::tx_bytes);
         const int arow = (o.child[c] * R + r) * a.Ppad + q0;
         const int brow = o.brow[c] + r * kTcN;
         const CUtensorMap* am = o.kind[c] == kTipPartials ? &tm_tip : &tm_part;
         tma_load_2d(st, am, 0, arow, &full[s]);
         tma_load_2d(st + kAChunk, am, 32, arow, &full[s]);
-        tma_load_2d(st + 2 * kAChunk, &tm_mat, 0, brow, &full[s]);
-        tma_load_2d(st + 2 * kAChunk + kBChunk, &tm_mat, 32, brow, &full[s]);
+        tma_load_2d(st + kBOff, &tm_mat, 0, brow, &full[s]);
+        tma_load_2d(st + kBOff + kBChunk, &tm_mat, 32, brow, &full[s]);
         if (SPLIT) {
             const int lrow = brow + 2 * R * kTcN;
-            tma_load_2d(st + 2 * kAChunk + 2 * kBChunk, &tm_mat, 0, lrow, &full[s]);
-            tma_load_2d(st + 2 * kAChunk + 3 * kBChunk, &tm_mat, 32, lrow, &full[s]);
+            tma_load_2d(st + kBOff + 2 * kBChunk, &tm_mat, 0, lrow, &full[s]);
+            tma_load_2d(st + kBOff + 3 * kBChunk, &tm_mat, 32, lrow, &full[s]);
         }
         return true;
+    };
+    // the k-steps of one (operand, category) product from stage st into d
+    auto issue_products = [&](unsigned char* st, uint32_t d) {
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks) {
+            const int chunk = ks >> 2, kin = (ks & 3) * 32;
+            const uint64_t ad = sw128_desc(st + chunk * kAChunk + kin);
+            const uint64_t bd = sw128_desc(st + kBOff + chunk * kBChunk + kin);
+            mma_tf32(d, ad, bd, ks > 0 ? 1u : 0u);
+            if (SPLIT) {
+                const uint64_t bl = sw128_desc(st + kBOff + (2 + chunk) * kBChunk + kin);
+                mma_tf32(d, ad, bl, 1u);
+            }
+            if (SPLITA) {
+                const uint64_t al = sw128_desc(st + (2 + chunk) * kAChunk + kin);
+                mma_tf32(d, al, bd, 1u);
+            }
+        }
     };
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int k = item / a.n_tiles, tile = item % a.n_tiles;
@@ -293,7 +334,75 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
         const bool mma[2] = {op.kind[0] == kInternal || op.kind[0] == kTipPartials,
                              op.kind[1] == kInternal || op.kind[1] == kTipPartials};
         const int n_pairs = (mma[0] + mma[1]) * R;
-        if (tid == 0) {
+        if constexpr (SPLITA) {
+            // every thread takes part in each pair: wait for its copy, split
+            // A, then thread 0 issues the products
+            bool ok = true;
+            for (int j = 0; j < n_pairs && ok; ++j) {
+                const unsigned g = pairs_done + (unsigned)j;
+                if (tid == 0) {
+                    while (ok && produced_c < pairs_done + n_pairs && produced_c < g + kSt) {
+                        ok = produce(op, p0, (int)(produced_c - pairs_done), produced_c);
+                        produced_c += ok;
+                    }
+                }
+                const int s = g % kSt;
+                bool got = true;
+                if (ok) got = mbar_wait(&full[s], (g / kSt) & 1);
+                if (tid == 0 && !ok) got = false;
+                if (!got) atomicOr(&abort_sh, 2);
+                if (__syncthreads_or(!got)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* st = stages + s * kStB;
+                float4* A4 = reinterpret_cast<float4*>(st);
+                float4* L4 = reinterpret_cast<float4*>(st + 2 * kAChunk);
+#pragma unroll 4
+                for (int i = tid; i < 2 * kAChunk / 16; i += 128) {
+                    const float4 v = A4[i];
+                    float4 h, l;
+                    h.x = tf32_trunc(v.x);
+                    h.y = tf32_trunc(v.y);
+                    h.z = tf32_trunc(v.z);
+                    h.w = tf32_trunc(v.w);
+                    l.x = tf32_trunc(v.x - h.x);
+                    l.y = tf32_trunc(v.y - h.y);
+                    l.z = tf32_trunc(v.z - h.z);
+                    l.w = tf32_trunc(v.w - h.w);
+                    A4[i] = h;
+                    L4[i] = l;
+                }
+                fence_proxy_async_smem();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    const int c = mma[0] ? (j < R ? 0 : 1) : 1;
+                    const int r = j % R;
+                    issue_products(st, tmem + (uint32_t)(r * 2 * kTcN + c * kTcN));
+                    mma_commit(&empty[s]);
+                    consumed_c = g + 1;
+                }
+            }
+            if (tid == 0) {
+                if (ok && n_pairs > 0) mma_commit(&done);
+                const int nxt = item + gridDim.x;
+                if (ok && nxt < n_items) {
+                    const TcOp opn = ops[nxt / a.n_tiles];
+                    const int p0n = (nxt % a.n_tiles) * kTcM;
+                    const bool mn0 = opn.kind[0] == kInternal || opn.kind[0] == kTipPartials;
+                    const bool mn1 = opn.kind[1] == kInternal || opn.kind[1] == kTipPartials;
+                    const unsigned base = pairs_done + n_pairs;
+                    const unsigned pn = (unsigned)((mn0 + mn1) * R);
+                    while (ok && produced_c < base + pn && produced_c < base + kSt) {
+                        ok = produce(opn, p0n, (int)(produced_c - base), produced_c);
+                        produced_c += ok;
+                    }
+                }
+                produced_sh = produced_c;
+                consumed_sh = consumed_c;
+            }
+        } else if (tid == 0) {
             // Pairs are numbered across the CTA's items: pair g uses stage
             // g % kSt. Up to kSt pairs are loaded ahead of the products; the
             // first pairs of the next item are loaded before this item's
@@ -316,20 +425,7 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                 const int j = (int)(g - pairs_done);
                 const int c = mma[0] ? (j < R ? 0 : 1) : 1;
                 const int r = j % R;
-                const uint32_t d = tmem + (uint32_t)(r * 2 * kTcN + c * kTcN);
-                unsigned char* st = stages + s * kStB;
-#pragma unroll
-                for (int ks = 0; ks < 8; ++ks) {
-                    const int chunk = ks >> 2, kin = (ks & 3) * 32;
-                    const uint64_t ad = sw128_desc(st + chunk * kAChunk + kin);
-                    const uint64_t bd = sw128_desc(st + 2 * kAChunk + chunk * kBChunk + kin);
-                    mma_tf32(d, ad, bd, ks > 0 ? 1u : 0u);
-                    if (SPLIT) {
-                        const uint64_t bl =
-                            sw128_desc(st + 2 * kAChunk + (2 + chunk) * kBChunk + kin);
-                        mma_tf32(d, ad, bl, 1u);
-                    }
-                }
+                issue_products(stages + s * kStB, tmem + (uint32_t)(r * 2 * kTcN + c * kTcN));
                 mma_commit(&empty[s]);
                 ++consumed_c;
             }
@@ -444,15 +540,18 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
             }
             return e;
         };
+        // stored partials: TF32-rounded (the tensor core reads them exactly),
+        // or full FP32 when A is split on chip
+        auto rnd = [](float x) { return SPLITA ? x : to_tf32(x); };
         auto store16 = [&](float* dst, const float* v, float f1, float f2) {
             float4* o = reinterpret_cast<float4*>(dst);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 float4 w;
-                w.x = to_tf32(v[4 * u] * f1 * f2);
-                w.y = to_tf32(v[4 * u + 1] * f1 * f2);
-                w.z = to_tf32(v[4 * u + 2] * f1 * f2);
-                w.w = to_tf32(v[4 * u + 3] * f1 * f2);
+                w.x = rnd(v[4 * u] * f1 * f2);
+                w.y = rnd(v[4 * u + 1] * f1 * f2);
+                w.z = rnd(v[4 * u + 2] * f1 * f2);
+                w.w = rnd(v[4 * u + 3] * f1 * f2);
                 o[u] = w;
             }
         };
@@ -757,10 +856,11 @@ __global__ void k_q_tc(const double* __restrict__ Q, float* __restrict__ dst, in
     }
 }
 
-template <int MODE, bool SPLIT>
+template <int MODE, bool SPLIT, bool SPLITA>
 void launch_mode_t(Instance* I, const TcOp* d, int n, TcArgs a) {
-    const size_t smem = (size_t)TcPipe<SPLIT>::stages * TcPipe<SPLIT>::bytes + 1024;
-    cudaFuncSetAttribute(k_tc<MODE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem =
+        (size_t)TcPipe<SPLIT, SPLITA>::stages * TcPipe<SPLIT, SPLITA>::bytes + 1024;
+    cudaFuncSetAttribute(k_tc<MODE, SPLIT, SPLITA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int sms = 0, dev_id = 0;
     cudaGetDevice(&dev_id);
@@ -768,14 +868,15 @@ void launch_mode_t(Instance* I, const TcOp* d, int n, TcArgs a) {
     const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(I->tmaps.data());
     const int items = n * a.n_tiles;
     const int grid = std::max(1, std::min(items, sms));
-    k_tc<MODE, SPLIT><<<grid, 128, smem, I->stream>>>(m[0], m[1], m[2], d, n, a);
+    k_tc<MODE, SPLIT, SPLITA><<<grid, 128, smem, I->stream>>>(m[0], m[1], m[2], d, n, a);
     I->launches += 1;
 }
 
 template <int MODE>
 void launch_mode(Instance* I, const TcOp* d, int n, TcArgs a) {
-    if (I->split) launch_mode_t<MODE, true>(I, d, n, a);
-    else launch_mode_t<MODE, false>(I, d, n, a);
+    if (I->split_partials) launch_mode_t<MODE, true, true>(I, d, n, a);
+    else if (I->split) launch_mode_t<MODE, true, false>(I, d, n, a);
+    else launch_mode_t<MODE, false, false>(I, d, n, a);
 }
 
 void tc_operand(const Instance* I, TcOp& t, int c, int buf, int slot) {
@@ -788,6 +889,399 @@ void tc_operand(const Instance* I, TcOp& t, int c, int buf, int slot) {
     }
     t.brow[c] = brow_of(I, slot, 0);
     t.look[c] = look_of(I, slot, 1);
+}
+
+// ---------------------------------------------------------------------------
+// On-chip subtree-fused post-order (TF32 storage, plain or split matrices)
+// ---------------------------------------------------------------------------
+// One CTA walks the whole op list for one 128-pattern tile at a time (ops in
+// a depth-first post-order from the host), instead of one launch per tree
+// level. The result of each op stays in tensor memory as the A operand of
+// the next op (TMEM columns [0, 256): 4 categories x 64 states, TF32
+// values), so a child produced by the op just before is never read back
+// from HBM: it is multiplied in place (tcgen05.mma with A in TMEM). Other
+// children come from HBM through TMA as before; tips with states are
+// lookups. Every op's result is also stored, as by the level-by-level
+// kernel (same values: same products, same accumulation order, same
+// rescaling), so the pre-order pass and later calls can read any buffer.
+//
+// Roles (warp-specialised, 192 threads):
+//   warp 0  TMA: A tiles of children read from HBM and B tiles (P, P_lo),
+//           a ring of kSt stages (full / empty mbarriers);
+//   warp 1  TMEM owner and MMA issuer: per (op, category) the products of
+//           both children into one of two accumulator buffers (columns
+//           256 + 128 b, child c at + 64 c), committed to acc_full[b];
+//   warps 2-5  epilogue, one TMEM lane (pattern) per thread: pass 1 per
+//           category multiplies the children (or a tip's P^T row), takes
+//           the maximum, releases the accumulator buffer (acc_empty[b]) and
+//           parks the unscaled product in the category's A columns; pass 2
+//           rescales by the power of two of the maximum over categories,
+//           rounds to TF32, rewrites the A columns and stores the partials
+//           and exponents; then each warp publishes the op as done (a
+//           counter per warp, release / acquire ordering), which the MMA
+//           warp waits for before it multiplies an op's on-chip child.
+// Every wait is bounded by elapsed time and by an abort flag, so a wait
+// that gives up stops all roles; the kernel then drains its copies and
+// products and frees TMEM.
+struct __align__(16) FuseOp {
+    int child[2];
+    int kind[2];      // kInternal, kTipPartials: MMA; kTipStates: lookup
+    int brow[2];      // matrix-map row of P, category 0
+    int look[2];      // float offset of P^T, category 0 (tip lookups)
+    int dest;         // output buffer (pool index)
+    int prev;         // the child (0, 1) that is the previous op's result; -1 none
+    int pad[6];
+};
+static_assert(sizeof(FuseOp) == kTcOpBytes, "fused descriptor size");
+
+constexpr int kFuseThreads = 192;
+constexpr int kPrevCols = 256;   // TMEM columns of the on-chip result
+
+template <bool SPLIT>
+struct FusePipe {
+    static constexpr int stages = SPLIT ? 3 : 4;
+    static constexpr int bytes = 2 * kAChunk + (SPLIT ? 4 : 2) * kBChunk;
+};
+
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, unsigned parity,
+                                                   volatile int* abort_flag) {
+    const unsigned addr = smem_u32(bar);
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void st_release_cta(unsigned* p, unsigned v) {
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;\n" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_cta(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];\n" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+// A (M = 128 x K = 8, tf32) from tensor memory, B from shared memory.
+__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(bdesc), "r"(kIdescTf32), "r"(accumulate)
+        : "memory");
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(kFuseThreads, 1)
+k_tc_fused(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtensorMap tm_tip,
+           const __grid_constant__ CUtensorMap tm_mat, const FuseOp* __restrict__ ops, int n_ops,
+           TcArgs a) {
+    constexpr int kSt = FusePipe<SPLIT>::stages;
+    constexpr int kStB = FusePipe<SPLIT>::bytes;
+    constexpr int kBOff = 2 * kAChunk;
+    const size_t kLoFloats = (size_t)2 * a.R * kTcN * kTcN;  // hi block -> lo block
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    unsigned char* stages = smem_tc + ((1024u - (smem_u32(smem_tc) & 1023u)) & 1023u);
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2],
+        done;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;          // bit 0 empty, 1 full, 2 acc_empty, 3 acc_full, 4 op-done
+    __shared__ unsigned ready_sh[4];  // ops each epilogue warp has finished
+    __shared__ unsigned loads_sh, used_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    volatile int* abort_v = &abort_sh;
+
+    if (warp == 1) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                smem_u32(&tmem_base_sh)),
+            "r"(kTmemCols)
+            : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kSt; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], 4);   // one arrival per epilogue warp
+        }
+        mbar_init(&done, 1);
+        abort_sh = 0;
+        for (int w = 0; w < 4; ++w) ready_sh[w] = 0;
+        loads_sh = used_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+    const int R = a.R;
+    auto on_mma = [](const FuseOp& o, int c) {
+        return o.kind[c] == kInternal || o.kind[c] == kTipPartials;
+    };
+
+    if (warp == 0) {
+        // ---- TMA producer ----------------------------------------------------
+        if (lane == 0) {
+            unsigned g = 0;
+            for (int tile = blockIdx.x; tile < a.n_tiles && !*abort_v; tile += gridDim.x) {
+                const int q0 = tile * kTcM;
+                for (int k = 0; k < n_ops && !*abort_v; ++k) {
+                    const FuseOp o = ops[k];
+                    for (int r = 0; r < R && !*abort_v; ++r)
+                        for (int c = 0; c < 2; ++c) {
+                            if (!on_mma(o, c)) continue;
+                            const int s = g % kSt;
+                            if (!mbar_wait_or_abort(&empty[s], ((g / kSt) & 1) ^ 1, abort_v)) {
+                                atomicOr(&abort_sh, 1);
+                                break;
+                            }
+                            unsigned char* st = stages + s * kStB;
+                            const bool fromA = o.prev != c;
+                            mbar_expect_tx(&full[s],
+                                           (fromA ? 2 * kAChunk : 0) + (SPLIT ? 4 : 2) * kBChunk);
+                            if (fromA) {
+                                const int arow = (o.child[c] * R + r) * a.Ppad + q0;
+                                const CUtensorMap* am = o.kind[c] == kTipPartials ? &tm_tip : &tm_part;
+                                tma_load_2d(st, am, 0, arow, &full[s]);
+                                tma_load_2d(st + kAChunk, am, 32, arow, &full[s]);
+                            }
+                            const int brow = o.brow[c] + r * kTcN;
+                            tma_load_2d(st + kBOff, &tm_mat, 0, brow, &full[s]);
+                            tma_load_2d(st + kBOff + kBChunk, &tm_mat, 32, brow, &full[s]);
+                            if (SPLIT) {
+                                const int lrow = brow + 2 * R * kTcN;
+                                tma_load_2d(st + kBOff + 2 * kBChunk, &tm_mat, 0, lrow, &full[s]);
+                                tma_load_2d(st + kBOff + 3 * kBChunk, &tm_mat, 32, lrow, &full[s]);
+                            }
+                            ++g;
+                        }
+                }
+            }
+            loads_sh = g;
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ------------------------------------------------------
+        if (lane == 0) {
+            unsigned g = 0, cat = 0, nop = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x) {
+                for (int k = 0; ok && k < n_ops; ++k, ++nop) {
+                    const FuseOp o = ops[k];
+                    if (o.prev >= 0) {
+                        // the previous op's result must be complete in TMEM
+                        const unsigned long long t0 = global_ns();
+                        for (int w = 0; ok && w < 4; ++w)
+                            while (ld_acquire_cta(&ready_sh[w]) < nop) {
+                                if (*abort_v || global_ns() - t0 > kWaitNs) {
+                                    ok = false;
+                                    atomicOr(&abort_sh, 16);
+                                    break;
+                                }
+                            }
+                        if (!ok) break;
+                        tc_fence_after();
+                    }
+                    for (int r = 0; ok && r < R; ++r, ++cat) {
+                        const int b = cat & 1;
+                        if (!mbar_wait_or_abort(&acc_empty[b], ((cat >> 1) & 1) ^ 1, abort_v)) {
+                            ok = false;
+                            atomicOr(&abort_sh, 4);
+                            break;
+                        }
+                        tc_fence_after();
+                        for (int c = 0; c < 2; ++c) {
+                            if (!on_mma(o, c)) continue;
+                            const int s = g % kSt;
+                            if (!mbar_wait_or_abort(&full[s], (g / kSt) & 1, abort_v)) {
+                                ok = false;
+                                atomicOr(&abort_sh, 2);
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t d = tmem + (uint32_t)(kPrevCols + b * 2 * kTcN + c * kTcN);
+                            unsigned char* st = stages + s * kStB;
+#pragma unroll
+                            for (int ks = 0; ks < 8; ++ks) {
+                                const int chunk = ks >> 2, kin = (ks & 3) * 32;
+                                const uint64_t bd = sw128_desc(st + kBOff + chunk * kBChunk + kin);
+                                const uint64_t bl = sw128_desc(st + kBOff + (2 + chunk) * kBChunk + kin);
+                                if (o.prev == c) {
+                                    const uint32_t at = tmem + (uint32_t)(r * kTcN + ks * 8);
+                                    mma_tf32_ta(d, at, bd, ks > 0 ? 1u : 0u);
+                                    if (SPLIT) mma_tf32_ta(d, at, bl, 1u);
+                                } else {
+                                    const uint64_t ad = sw128_desc(st + chunk * kAChunk + kin);
+                                    mma_tf32(d, ad, bd, ks > 0 ? 1u : 0u);
+                                    if (SPLIT) mma_tf32(d, ad, bl, 1u);
+                                }
+                            }
+                            mma_commit(&empty[s]);
+                            ++g;
+                        }
+                        if (!ok) break;
+                        mma_commit(&acc_full[b]);
+                    }
+                }
+            }
+            used_sh = g;
+            // every product issued has finished before TMEM is released
+            mma_commit(&done);
+            if (!mbar_wait(&done, 0)) atomicOr(&abort_sh, 32);
+        }
+    } else {
+        // ---- epilogue: thread <-> TMEM lane 32 (warp % 4) + lane -----------
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        unsigned cat = 0, nop = 0;
+        bool ok = true;
+        auto store16 = [&](float* dst, const float* v) {
+            float4* o4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) o4[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+        };
+        for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x) {
+            const int p = tile * kTcM + row;
+            int cum_prev = 0;
+            for (int k = 0; ok && k < n_ops; ++k, ++nop) {
+                const FuseOp o = ops[k];
+                int cum = 0, sidx[2] = {0, 0};
+                bool amb[2] = {false, false};
+                for (int c = 0; c < 2; ++c) {
+                    if (o.kind[c] == kInternal)
+                        cum += (o.prev == c) ? cum_prev : a.epool[(size_t)o.child[c] * a.Ppad + p];
+                    if (o.kind[c] == kTipStates) {
+                        const int s = a.tips[(size_t)o.child[c] * a.Ppad + p];
+                        amb[c] = !(s >= 0 && s < a.S);
+                        sidx[c] = s;
+                    }
+                }
+                // a tip's row of P^T (+ the lo row with split matrices), or
+                // the row sums of P for an ambiguous code
+                auto lookup64 = [&](int c, int r, float* v) {
+                    const int slot_base = o.look[c];
+                    const float* src =
+                        amb[c] ? a.rowsum + (size_t)(slot_base / ((SPLIT ? 4 : 2) * R * kTcN * kTcN)) *
+                                                R * kTcN + (size_t)r * kTcN
+                               : a.matw + (size_t)slot_base + (size_t)r * kTcN * kTcN +
+                                     (size_t)sidx[c] * kTcN;
+                    const float4* s4 = reinterpret_cast<const float4*>(src);
+                    float4 f[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) f[u] = __ldg(s4 + u);
+                    if (SPLIT && !amb[c]) {
+                        const float4* l4 = reinterpret_cast<const float4*>(src + kLoFloats);
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const float4 l = __ldg(l4 + u);
+                            f[u].x += l.x;
+                            f[u].y += l.y;
+                            f[u].z += l.z;
+                            f[u].w += l.w;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        v[4 * u] = f[u].x;
+                        v[4 * u + 1] = f[u].y;
+                        v[4 * u + 2] = f[u].z;
+                        v[4 * u + 3] = f[u].w;
+                    }
+                };
+                // pass 1: products of the two children per category, their
+                // maximum; the unscaled products go to the A columns
+                float m = 0.f;
+                for (int r = 0; r < R; ++r, ++cat) {
+                    const int b = cat & 1;
+                    // every lane takes the same branch (the TMEM loads below
+                    // are warp-collective), so a wait that gave up in any
+                    // lane stops the whole warp
+                    const bool got = mbar_wait_or_abort(&acc_full[b], (cat >> 1) & 1, abort_v);
+                    if (!__all_sync(0xffffffffu, got)) {
+                        ok = false;
+                        if (lane == 0) atomicOr(&abort_sh, 8);
+                        break;
+                    }
+                    tc_fence_after();
+                    float x[64], y[64];
+                    const uint32_t acc = lane_base + (uint32_t)(kPrevCols + b * 2 * kTcN);
+                    if (on_mma(o, 0)) tmem_ld64(acc, x);
+                    else lookup64(0, r, x);
+                    if (on_mma(o, 1)) tmem_ld64(acc + kTcN, y);
+                    else lookup64(1, r, y);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[b]);
+#pragma unroll
+                    for (int i = 0; i < 64; ++i) {
+                        x[i] *= y[i];
+                        m = fmaxf(m, x[i]);
+                    }
+                    tmem_st64(lane_base + (uint32_t)(r * kTcN), x);
+                }
+                if (!ok) break;
+                // pass 2: rescale, round to TF32, keep on chip and store
+                float f1 = 1.f, f2 = 1.f;
+                if (a.rescale) {
+                    const int e = frexp_exp_f(m);
+                    if (e != 0) {
+                        const int kk = -e;
+                        if (kk >= -126 && kk <= 126) f1 = pow2f(kk);
+                        else {
+                            f1 = pow2f(kk / 2);
+                            f2 = pow2f(kk - kk / 2);
+                        }
+                    }
+                    cum += e;
+                }
+                float* dst = a.pool + (size_t)o.dest * a.bstride + (size_t)p * kTcN;
+                for (int r = 0; r < R; ++r) {
+                    float z[64];
+                    tmem_ld64(lane_base + (uint32_t)(r * kTcN), z);
+#pragma unroll
+                    for (int i = 0; i < 64; ++i) z[i] = to_tf32(z[i] * f1 * f2);
+                    tmem_st64(lane_base + (uint32_t)(r * kTcN), z);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, z + 16 * q);
+                }
+                a.epool[(size_t)o.dest * a.Ppad + p] = cum;
+                cum_prev = cum;
+                // this warp's rows of the op are done and may be read from
+                // TMEM (each warp publishes its own count: no barrier among
+                // the epilogue warps, which an abort could leave unmatched)
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) st_release_cta(&ready_sh[quarter], nop + 1);
+            }
+        }
+    }
+    __syncthreads();
+    if (abort_sh && tid == 0) {
+        atomicOr(a.err, (abort_sh & 0xff) | (1 << 11));
+        // bounded drain of copies still in flight
+        for (unsigned g = used_sh; g < loads_sh; ++g) mbar_wait(&full[g % kSt], (g / kSt) & 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(kTmemCols)
+                     : "memory");
+    }
 }
 
 }  // namespace
@@ -861,6 +1355,55 @@ int launch_post_tc(Instance* I, const tl_op* ops, int n, void* d_ops_area, size_
     const TcOp* d = reinterpret_cast<const TcOp*>(d_ops_area);
     for (int L = 0; L < n_levels; ++L) launch_mode<kPost>(I, d + first[L], first[L + 1] - first[L], a);
     return cuda_check(I, cudaGetLastError(), "tensor-core post-order kernel");
+}
+
+// The subtree-fused post-order kernel is used for TF32 instances with TF32
+// storage (plain or split matrices) unless TL_TC_FUSED=0; split partials
+// need an A_lo tile per operand, which has no room in tensor memory beside
+// the on-chip result, and take the level-by-level kernels.
+int tc_fused_enabled(const Instance* I) {
+    const char* e = getenv("TL_TC_FUSED");   // read per call: tests compare both kernels
+    return (!e || atoi(e) != 0) && I->prec == kTF32 && !I->split_partials;
+}
+
+int launch_post_tc_fused(Instance* I, const DevPostOp* plan_ops, int n, void* d_ops_area,
+                         size_t cap) {
+    std::vector<FuseOp> dev(n);
+    for (int k = 0; k < n; ++k) {
+        const DevPostOp& d = plan_ops[k];
+        FuseOp& f = dev[k];
+        std::memset(&f, 0, sizeof f);
+        f.prev = -1;
+        for (int c = 0; c < 2; ++c) {
+            f.child[c] = d.child[c];
+            f.kind[c] = d.kind[c];
+            f.brow[c] = brow_of(I, d.mat[c], 0);
+            f.look[c] = look_of(I, d.mat[c], 1);
+            if (d.kind[c] == kInternal && d.slot_in[c] == kFromRegisters) f.prev = c;
+        }
+        f.dest = d.dest;
+    }
+    if (dev.size() * sizeof(FuseOp) > cap) return fail(I, TL_ERR_ARG, "op area too small");
+    int rc = upload_bytes(I, d_ops_area, dev.data(), dev.size() * sizeof(FuseOp));
+    if (rc) return rc;
+    TcArgs a = tc_args(I);
+    int sms = 0, dev_id = 0;
+    cudaGetDevice(&dev_id);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+    const int grid = std::max(1, std::min(a.n_tiles, sms));
+    const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(I->tmaps.data());
+    const FuseOp* d = reinterpret_cast<const FuseOp*>(d_ops_area);
+    if (I->split) {
+        const size_t smem = (size_t)FusePipe<true>::stages * FusePipe<true>::bytes + 1024;
+        cudaFuncSetAttribute(k_tc_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_tc_fused<true><<<grid, kFuseThreads, smem, I->stream>>>(m[0], m[1], m[2], d, n, a);
+    } else {
+        const size_t smem = (size_t)FusePipe<false>::stages * FusePipe<false>::bytes + 1024;
+        cudaFuncSetAttribute(k_tc_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_tc_fused<false><<<grid, kFuseThreads, smem, I->stream>>>(m[0], m[1], m[2], d, n, a);
+    }
+    I->launches += 1;
+    return cuda_check(I, cudaGetLastError(), "fused tensor-core post-order kernel");
 }
 
 // Pre-order pass with gradient, level by level from the root: PRE1 per

@@ -80,7 +80,6 @@ struct NucArgs {
     const double* patw;             // [Ppad] pattern weights (0 on padding)
     size_t bstride;
     int P, Ppad, R, n_slots, rescale, mat_stride, n_tiles;
-    int dgen;                       // pre-order: dmat is any derivative of P (no Q shortcut)
     T catw[kMaxCat];
     T rates[kMaxCat];
 };
@@ -151,6 +150,7 @@ struct Instance {
     int elt = 8;      // bytes per stored partial element
     int rescale = 1;
     int split = 0;    // TF32: matrices as hi + lo (TL_SPLIT_MATRICES)
+    int split_partials = 0;  // TF32: FP32 partials split on chip (TL_SPLIT_PARTIALS)
     cudaStream_t stream = nullptr;
     int device = 0;
     int smem_optin = 0;
@@ -248,6 +248,7 @@ int nuc_lanes_pre(const Instance* I);        // lanes per pattern (pre-order ker
 int nuc_tiles_pre(const Instance* I);        // its tiles (= gradient partial columns)
 int nuc_smem_per_slot(const Instance* I);    // bytes per slot per warp and pattern per lane
 int nuc_post_ppl(const Instance* I);         // patterns per lane (post-order kernel)
+int nuc_pre_slot_cap(const Instance* I);     // on-chip q slots of the pre-order kernel
 int launch_post4(Instance* I, const DevPostOp* d_ops, int n_ops, int n_slots);
 int launch_root4(Instance* I, int root_kind, int root, int model, double* d_site,
                  double* d_part);
@@ -287,6 +288,9 @@ int tc_tile();
 int tc_setup(Instance* I);
 int tc_set_tip_pool(Instance* I);
 int launch_post_tc(Instance* I, const tl_op* ops, int n, void* d_ops_area, size_t cap);
+int tc_fused_enabled(const Instance* I);   // subtree-fused post-order kernel in use
+int launch_post_tc_fused(Instance* I, const DevPostOp* plan_ops, int n, void* d_ops_area,
+                         size_t cap);
 int launch_root_tc(Instance* I, int root_pool, int model, double* d_site, double* d_part,
                    int n_parts);
 int launch_pre_tc(Instance* I, const tl_pre_op* ops, int n, const int* edge_row, int model,

@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "tl_internal.cuh"
@@ -241,10 +242,9 @@ __device__ __forceinline__ const NucArgs<T>& pick_args(const NucArgs<T>& param,
 // ---------------------------------------------------------------------------
 // post-order
 // ---------------------------------------------------------------------------
-// Loads that feed op k are issued while op k-kAhead..k-1 compute: tip states
-// kAhead ops ahead, partials read from memory one op ahead. Without this
-// every op waits a full DRAM round trip for its inputs.
-constexpr int kAhead = 3;
+// Loads that feed op k (tip states, partials read from memory) are issued
+// while op k - 1 computes. Without this every op waits a full DRAM round
+// trip for its inputs.
 
 // Children and their kinds: the first 16 bytes of a post- or pre-order op.
 template <typename Op>
@@ -392,14 +392,14 @@ k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ 
 #pragma unroll
             for (int j = 0; j < CPL; ++j) prev[i][j] = zero;
         }
-        int ts[kAhead][2][PPL];
-#pragma unroll
-        for (int k = 0; k < kAhead; ++k) {
-            const int4 h = op_head(ops, k, n_ops);
+        // tip states of the current op (A) and the next one (B)
+        int tsA[2][PPL], tsB[2][PPL];
+        {
+            const int4 h = op_head(ops, 0, n_ops);
 #pragma unroll
             for (int i = 0; i < PPL; ++i) {
-                ts[k][0][i] = tip_state(a, h.x, h.z, p[i]);
-                ts[k][1][i] = tip_state(a, h.y, h.w, p[i]);
+                tsA[0][i] = tip_state(a, h.x, h.z, p[i]);
+                tsA[1][i] = tip_state(a, h.y, h.w, p[i]);
             }
         }
         // pipeline prologue: descriptors 0 and 1, then matrices of op 0
@@ -411,19 +411,20 @@ k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ 
         __syncwarp();
         pipe.issue_mats(0, n_ops, pipe.obuf[0].mat, a.mat, a.mat_stride, lane);
         cp_async_commit();
-        for (int k = 0; k < n_ops; ++k) {
+        auto op_body = [&](int k, int (&ts)[2][PPL], int (&tn)[2][PPL]) {
             cp_async_wait_all();
             __syncwarp();
             pipe.issue_op(ops, k + 2, n_ops, lane);
             if (k + 1 < n_ops)
                 pipe.issue_mats(k + 1, n_ops, pipe.obuf[(k + 1) % 3].mat, a.mat, a.mat_stride, lane);
             cp_async_commit();
-            const int4 hn = op_head(ops, k + kAhead, n_ops);
-            int tn[2][PPL];
+            {
+                const int4 hn = op_head(ops, k + 1, n_ops);
 #pragma unroll
-            for (int i = 0; i < PPL; ++i) {
-                tn[0][i] = tip_state(a, hn.x, hn.z, p[i]);
-                tn[1][i] = tip_state(a, hn.y, hn.w, p[i]);
+                for (int i = 0; i < PPL; ++i) {
+                    tn[0][i] = tip_state(a, hn.x, hn.z, p[i]);
+                    tn[1][i] = tip_state(a, hn.y, hn.w, p[i]);
+                }
             }
             const DevPostOp op = pipe.obuf[k % 3];
             const T* mk = pipe.mats(k);
@@ -438,7 +439,7 @@ k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ 
                 if (op.kind[c] == kTipStates) {
 #pragma unroll
                     for (int i = 0; i < PPL; ++i) {
-                        const int col = tip_col((int8_t)ts[0][c][i]);
+                        const int col = tip_col((int8_t)ts[c][i]);
 #pragma unroll
                         for (int j = 0; j < CPL; ++j)
                             v[i][j] = act[j] ? lds4(mc + col * cs + j * LPP * 4) : zero;
@@ -495,18 +496,6 @@ k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ 
                     for (int j = 0; j < CPL; ++j) acc[i][j] = (c == 0) ? v[i][j] : mul(acc[i][j], v[i][j]);
             }
 #pragma unroll
-            for (int k2 = 0; k2 + 1 < kAhead; ++k2)
-#pragma unroll
-                for (int i = 0; i < PPL; ++i) {
-                    ts[k2][0][i] = ts[k2 + 1][0][i];
-                    ts[k2][1][i] = ts[k2 + 1][1][i];
-                }
-#pragma unroll
-            for (int i = 0; i < PPL; ++i) {
-                ts[kAhead - 1][0][i] = tn[0][i];
-                ts[kAhead - 1][1][i] = tn[1][i];
-            }
-#pragma unroll
             for (int i = 0; i < PPL; ++i) {
                 if (a.rescale) {
                     T m = vmax(acc[i][0]);
@@ -536,6 +525,14 @@ k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ 
 #pragma unroll
                 for (int j = 0; j < CPL; ++j) prev[i][j] = acc[i][j];
                 prev_cum[i] = cum[i];
+            }
+        };
+        for (int k = 0; k < n_ops; ++k) {
+            op_body(k, tsA, tsB);
+#pragma unroll
+            for (int i = 0; i < PPL; ++i) {
+                tsA[0][i] = tsB[0][i];
+                tsA[1][i] = tsB[1][i];
             }
         }
         cp_async_wait_all();
@@ -625,20 +622,39 @@ k_root4(int kind_, int root_, const __grid_constant__ NucArgs<T> a_, const doubl
 // ---------------------------------------------------------------------------
 // fused pre-order pass + branch-length gradient
 // ---------------------------------------------------------------------------
-// Minimum resident blocks per SM the pre-order kernel is compiled for, by
-// lane layout: one lane per pattern holds four categories of state and
-// needs the full register file of a thread (two blocks, eight warps per
-// SM); two and four lanes per pattern fit three and four blocks without
-// spilling.
-template <int LPP>
+// Pre-order partials are rescaled only when their per-pattern maximum
+// leaves [2^-kQRange, 2^kQRange]: the branch-length ratios do not depend on
+// the scale of q, so the exact power-of-two scaling only has to keep the
+// products away from underflow and overflow.
+constexpr int kQRange = 32;
+// Edges whose per-pattern gradient terms a warp buffers before summing them.
+constexpr int kEdgeBuf = 16;
+
+// Minimum resident blocks per SM the pre-order kernel is compiled for (by
+// lane layout and element size; MINB > 0 overrides): one lane per pattern
+// holds the four categories of q, both children's prefetched partials and
+// the two outputs, in at most 168 registers in FP32 (three blocks, twelve
+// warps per SM); FP64 needs twice the registers (two blocks).
+template <typename T, int LPP>
 struct PreMinBlocks {
-    static constexpr int value = LPP == 1 ? 1 : (LPP == 2 ? 3 : 4);
+    static constexpr int value = LPP == 1 ? (sizeof(T) == 8 ? 2 : 3) : 4;
 };
-template <typename T, int LPP, int CPL, int NR, bool BATCH>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, PreMinBlocks<LPP>::value)
+
+// Fused pre-order pass and branch-length gradient. Per parent n with
+// children a, b and category r (Sec. "Algorithmic advances", linear-time
+// gradient): v_c = P_c p_c, u_a = q_n o v_b, u_b = q_n o v_a,
+// q_c = P_c^T u_c, and the edge ratio u_c . (dP_c p_c) / u_c . v_c summed
+// over categories with their weights (the denominator is the pattern
+// likelihood up to the scales of q and p, so no scale bookkeeping). The
+// categories are taken one at a time: each category's products are formed
+// and consumed before the next one's, so only q_n, the children's partials
+// and the two outputs stay live across the op. dP_c comes from shared
+// memory for every child (a column for tip states), so any derivative of P
+// (dP/dt, or dP/dtheta) takes the same path.
+template <typename T, int LPP, int CPL, int NR, bool BATCH, int MINB>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, MINB > 0 ? MINB : PreMinBlocks<T, LPP>::value)
 k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ NucArgs<T> a_,
-       const T* __restrict__ piw_, const T* __restrict__ Qw_, double* __restrict__ gpart_,
-       const BatchRef<T> br) {
+       const T* __restrict__ piw_, double* __restrict__ gpart_, const BatchRef<T> br) {
     constexpr int TP = 32 / LPP;
     constexpr bool kFull = NR > 0 && LPP * CPL == NR;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -655,49 +671,32 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
     pipe.matf = kColStride * 4 * R;
     BatchJob<T>* stage = reinterpret_cast<BatchJob<T>*>(
         pipe_base + (size_t)kWarpsPerBlock * pipe_bytes<DevPreOp, T, 4>(R)) + warp;
-    // gradient terms of up to 32 edges, [edge][lane] (row stride 33), summed
-    // over the lanes 32 edges at a time: one store per edge and lane
-    // instead of a five-step shuffle reduction per edge
+    // gradient terms of up to kEdgeBuf edges, [edge][lane] (row stride 33),
+    // summed over the lanes kEdgeBuf edges at a time: one store per edge and
+    // lane instead of a five-step shuffle reduction per edge
     T* gbuf = reinterpret_cast<T*>(reinterpret_cast<BatchJob<T>*>(
                   pipe_base + (size_t)kWarpsPerBlock * pipe_bytes<DevPreOp, T, 4>(R)) +
               kWarpsPerBlock) +
-              (size_t)warp * 32 * 33;
+              (size_t)warp * kEdgeBuf * 33;
     const NucArgs<T>& a = pick_args<BATCH>(a_, stage);
     bool act[CPL];
-    T wr[CPL], wrr[CPL];
-    // Q rows: an internal child's derivative term is rho q_c . (Q p_c), with
-    // q_c = P_c^T u_c before rescaling (dP/dt = rho Q P and Q, P commute), so
-    // only tip children need the dP columns
-    V4<T> Q0, Q1, Q2, Q3, piv;
-    auto job_constants = [&](const NucArgs<T>& aj, const T* piw, const T* Qw) {
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) {
-            act[j] = kFull || (r0 + j * LPP < R);
-            wr[j] = act[j] ? aj.catw[r0 + j * LPP] : T(0);
-            wrr[j] = act[j] ? aj.catw[r0 + j * LPP] * aj.rates[r0 + j * LPP] : T(0);
-        }
-        Q0 = ldg4(Qw);
-        Q1 = ldg4(Qw + 4);
-        Q2 = ldg4(Qw + 8);
-        Q3 = ldg4(Qw + 12);
-        piv = ldg4(piw);
-    };
-    if constexpr (!BATCH) job_constants(a_, piw_, Qw_);
+    for (int j = 0; j < CPL; ++j) act[j] = kFull || (r0 + j * LPP < R);
     const V4<T> zero = {T(0), T(0), T(0), T(0)};
     const int nw = gridDim.x * kWarpsPerBlock;
     const DevPreOp* ops = ops_;
     int n_ops = n_ops_;
     double* gpart = gpart_;
+    const T* piw = piw_;
     int cur = -1;
     for (int next = blockIdx.x * kWarpsPerBlock + warp; BATCH || next < a_.n_tiles; next += nw) {
         int tile = next;
         if constexpr (BATCH) {
-            const int was = cur;
             if (!batch_claim(br, a_.n_tiles, stage, cur, tile, lane)) break;
             ops = static_cast<const DevPreOp*>(stage->ops);
             n_ops = stage->n_ops;
             gpart = stage->gpart;
-            if (cur != was) job_constants(stage->a, stage->piw, stage->Qw);
+            piw = stage->piw;
         }
         const int p = tile * TP + pp;
         const size_t off0 = ((size_t)r0 * a.Ppad + p) * 4;
@@ -725,21 +724,27 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
 #pragma unroll
             for (int j = 0; j < CPL; ++j) x[j] = act[j] ? ld4(b + off0 + j * offj) : zero;
         };
+        // shared-memory matrices of op j: P of both children, and the
+        // derivative of each child whose edge is listed
+        auto issue_mats = [&](int j) {
+            const DevPreOp& o = pipe.obuf[j % 3];
+            const int idx[4] = {o.mat[0], o.mat[1], o.edge[0] >= 0 ? o.dmat[0] : -1,
+                                o.edge[1] >= 0 ? o.dmat[1] : -1};
+            pipe.issue_mats(j, n_ops, idx, a.mat, a.mat_stride, lane);
+        };
         V4<T> prevq[CPL];  // the q output the next op reads from registers
 #pragma unroll
         for (int j = 0; j < CPL; ++j) prevq[j] = zero;
-        int ts[kAhead][2];
-#pragma unroll
-        for (int j = 0; j < kAhead; ++j) {
-            const int4 h = op_head(ops, j, n_ops);
-            ts[j][0] = tip_state(a, h.x, h.z, p);
-            ts[j][1] = tip_state(a, h.y, h.w, p);
-        }
-        V4<T> xc[2][CPL];
+        // inputs of the current op (A) and the next one (B, loaded while
+        // the current op computes)
+        int tsA[2], tsB[2];
+        V4<T> xA[2][CPL], xB[2][CPL];
         {
             const int4 h = op_head(ops, 0, n_ops);
-            child_x(h.x, h.z, xc[0]);
-            child_x(h.y, h.w, xc[1]);
+            tsA[0] = tip_state(a, h.x, h.z, p);
+            tsA[1] = tip_state(a, h.y, h.w, p);
+            child_x(h.x, h.z, xA[0]);
+            child_x(h.y, h.w, xA[1]);
         }
         __syncwarp();
         pipe.issue_op(ops, 0, n_ops, lane);
@@ -747,154 +752,145 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
         cp_async_commit();
         cp_async_wait_all();
         __syncwarp();
-        {
-            const DevPreOp& o0 = pipe.obuf[0];
-            const int idx[4] = {o0.mat[0], o0.mat[1],
-                                (o0.kind[0] != kInternal || a.dgen) ? o0.dmat[0] : -1,
-                                (o0.kind[1] != kInternal || a.dgen) ? o0.dmat[1] : -1};
-            pipe.issue_mats(0, n_ops, idx, a.mat, a.mat_stride, lane);
-        }
+        if (n_ops > 0) issue_mats(0);
         cp_async_commit();
-        for (int k = 0; k < n_ops; ++k) {
+        // one op: k's inputs in xc / tsc, k + 1's loaded into xn / tsn
+        auto op_body = [&](int k, V4<T> (&xc)[2][CPL], V4<T> (&xn)[2][CPL], int (&tsc)[2],
+                           int (&tsn)[2]) {
             cp_async_wait_all();
             __syncwarp();
             pipe.issue_op(ops, k + 2, n_ops, lane);
-            if (k + 1 < n_ops) {
-                const DevPreOp& o1 = pipe.obuf[(k + 1) % 3];
-                const int idx[4] = {o1.mat[0], o1.mat[1],
-                                    (o1.kind[0] != kInternal || a.dgen) ? o1.dmat[0] : -1,
-                                    (o1.kind[1] != kInternal || a.dgen) ? o1.dmat[1] : -1};
-                pipe.issue_mats(k + 1, n_ops, idx, a.mat, a.mat_stride, lane);
-            }
+            if (k + 1 < n_ops) issue_mats(k + 1);
             cp_async_commit();
-            const int4 hn = op_head(ops, k + kAhead, n_ops);
-            const int tn0 = tip_state(a, hn.x, hn.z, p), tn1 = tip_state(a, hn.y, hn.w, p);
-            V4<T> xn[2][CPL];
+            // op k + 1's inputs, first read by the next op
+            {
+                const int4 hn = op_head(ops, k + 1, n_ops);
+                tsn[0] = tip_state(a, hn.x, hn.z, p);
+                tsn[1] = tip_state(a, hn.y, hn.w, p);
+            }
             if (k + 1 < n_ops) {
                 const DevPreOp& o1 = pipe.obuf[(k + 1) % 3];
                 child_x(o1.child[0], o1.kind[0], xn[0]);
                 child_x(o1.child[1], o1.kind[1], xn[1]);
+            }
+            const DevPreOp& op = pipe.obuf[k % 3];
+            const int kd0 = op.kind[0], kd1 = op.kind[1], qsrc = op.q_src;
+            const bool e0 = op.edge[0] >= 0, e1 = op.edge[1] >= 0;
+            const bool nq0 = op.need_q[0] != 0, nq1 = op.need_q[1] != 0;
+            const T* mk = pipe.mats(k) + r0 * 4;
+            const T* mP0 = mk;
+            const T* mP1 = mk + pipe.matf;
+            const T* mD0 = mk + 2 * pipe.matf;
+            const T* mD1 = mk + 3 * pipe.matf;
+            const int tc0 = tip_col((int8_t)tsc[0]) * cs, tc1 = tip_col((int8_t)tsc[1]) * cs;
+            // q of the parent into prevq (from registers it is there already)
+            if (qsrc == kFromRoot) {
+                const V4<T> pv = ldg4(piw);
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) prevq[j] = pv;
+            } else if (qsrc >= 0) {
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) prevq[j] = slots[(qsrc * CPL + j) * 32 + lane];
+            } else if (qsrc == kFromMemory) {
+                const T* qm = a.pool + (size_t)op.q_buf_in * a.bstride + off0;
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) prevq[j] = act[j] ? ld4(qm + j * offj) : zero;
+            }
+            T den_l = T(0), num0 = T(0), num1 = T(0);
+            V4<T> qa[CPL], qb[CPL];
+            // the categories for one combination of child kinds: no branch
+            // inside but the q of a tip (a derivative or internal q whose
+            // result is not asked for is formed anyway and not used)
+            auto categories = [&](auto tip0_c, auto tip1_c) {
+                constexpr bool TIP0 = decltype(tip0_c)::value, TIP1 = decltype(tip1_c)::value;
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) {
+                    qa[j] = zero;
+                    qb[j] = zero;
+                    if (!act[j]) continue;
+                    const int cj = j * LPP * 4;
+                    const T wr = a.catw[r0 + j * LPP];
+                    const V4<T> q = prevq[j];
+                    // v_c = P_c p_c and dP_c p_c (columns of P and dP for a tip state)
+                    const V4<T> v0 = TIP0 ? lds4(mP0 + tc0 + cj) : matvec(mP0 + cj, cs, xc[0][j]);
+                    const V4<T> v1 = TIP1 ? lds4(mP1 + tc1 + cj) : matvec(mP1 + cj, cs, xc[1][j]);
+                    const V4<T> u0 = mul(q, v1), u1 = mul(q, v0);
+                    den_l += wr * dot(u0, v0);
+                    const V4<T> d0 = TIP0 ? lds4(mD0 + tc0 + cj) : matvec(mD0 + cj, cs, xc[0][j]);
+                    const V4<T> d1 = TIP1 ? lds4(mD1 + tc1 + cj) : matvec(mD1 + cj, cs, xc[1][j]);
+                    num0 += wr * dot(u0, d0);
+                    num1 += wr * dot(u1, d1);
+                    // q of a tip only when it is asked for (materialised q)
+                    if (!TIP0 || nq0) qa[j] = matTvec(mP0 + cj, cs, u0);
+                    if (!TIP1 || nq1) qb[j] = matTvec(mP1 + cj, cs, u1);
+                }
+            };
+            using yes = std::true_type;
+            using no = std::false_type;
+            if (kd0 == kTipStates) {
+                if (kd1 == kTipStates) categories(yes{}, yes{});
+                else categories(yes{}, no{});
             } else {
-                child_x(0, -1, xn[0]);
-                child_x(0, -1, xn[1]);
+                if (kd1 == kTipStates) categories(no{}, yes{});
+                else categories(no{}, no{});
             }
-            const DevPreOp op = pipe.obuf[k % 3];
-            const T* mk = pipe.mats(k);
-            V4<T> q[CPL];
-#pragma unroll
-            for (int j = 0; j < CPL; ++j) {
-                if (op.q_src == kFromRoot) q[j] = piv;
-                else if (op.q_src == kFromRegisters) q[j] = prevq[j];
-                else if (op.q_src >= 0) q[j] = slots[(op.q_src * CPL + j) * 32 + lane];
-                else q[j] = act[j] ? ld4(a.pool + (size_t)op.q_buf_in * a.bstride + off0 + j * offj)
-                                   : zero;
-            }
-            // v_c = P_c p_c for both children (a column for tips); smem
-            // matrices are [P_0, P_1, dP_0, dP_1], dP only for tip children
-            const int tcol[2] = {tip_col((int8_t)ts[0][0]), tip_col((int8_t)ts[0][1])};
-            V4<T> v[2][CPL];
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const T* mc = mk + c * pipe.matf + r0 * 4;
-                if (op.kind[c] == kTipStates) {
-                    const int col = tcol[c];
-#pragma unroll
-                    for (int j = 0; j < CPL; ++j)
-                        v[c][j] = act[j] ? lds4(mc + col * cs + j * LPP * 4) : zero;
-                } else {
-#pragma unroll
-                    for (int j = 0; j < CPL; ++j)
-                        v[c][j] = act[j] ? matvec(mc + j * LPP * 4, cs, xc[c][j]) : zero;
-                }
-            }
-#pragma unroll
-            for (int j = 0; j + 1 < kAhead; ++j) {
-                ts[j][0] = ts[j + 1][0];
-                ts[j][1] = ts[j + 1][1];
-            }
-            ts[kAhead - 1][0] = tn0;
-            ts[kAhead - 1][1] = tn1;
-            // den: the pattern likelihood up to the scales of q and the children
-            T den_l = T(0);
-#pragma unroll
-            for (int j = 0; j < CPL; ++j) den_l += wr[j] * dot(q[j], mul(v[0][j], v[1][j]));
-            const T den = group_sum<LPP>(den_l);
-            const T wden = wpt / den;  // both children's ratios share it
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                V4<T> u[CPL];
-#pragma unroll
-                for (int j = 0; j < CPL; ++j) u[j] = mul(q[j], v[1 - c][j]);
-                const bool tip = op.kind[c] != kInternal;
-                const T* mc = mk + c * pipe.matf + r0 * 4;
-                V4<T> qc[CPL];
-                if (!tip || op.need_q[c]) {
-#pragma unroll
-                    for (int j = 0; j < CPL; ++j)
-                        qc[j] = act[j] ? matTvec(mc + j * LPP * 4, cs, u[j]) : zero;
-                }
-                if (op.edge[c] >= 0) {
-                    // numerator: tips u_c . (dP_c p_c) (a column of dP for tip
-                    // states, bit-identical to the product with a one-hot tip
-                    // partial); internal children rho q_c . (Q p_c). Per-pattern
-                    // ratio and the tile's sum
-                    // in working precision; FP64 (a slow unit on this part)
-                    // only once per tile and edge
-                    T num_l = T(0);
-                    if (tip || a.dgen) {
-                        const T* dc = mk + (2 + c) * pipe.matf + r0 * 4;
-                        const int col = tcol[c];
-#pragma unroll
-                        for (int j = 0; j < CPL; ++j) {
-                            if (!act[j]) continue;
-                            const V4<T> dv = (op.kind[c] == kTipStates)
-                                                 ? lds4(dc + col * cs + j * LPP * 4)
-                                                 : matvec(dc + j * LPP * 4, cs, xc[c][j]);
-                            num_l += wr[j] * dot(u[j], dv);
-                        }
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < CPL; ++j) {
-                            const V4<T> x = xc[c][j];
-                            const V4<T> Qx = {dot(Q0, x), dot(Q1, x), dot(Q2, x), dot(Q3, x)};
-                            num_l += wrr[j] * dot(qc[j], Qx);
-                        }
-                    }
-                    const T num = group_sum<LPP>(num_l);
-                    // one value per pattern (the first of its LPP lanes)
+            if (e0 || e1) {
+                const T wden = wpt / group_sum<LPP>(den_l);  // both children's ratios share it
+                if (e0) {
+                    const T num = group_sum<LPP>(num0);
                     gbuf[nbuf * 33 + lane] = (r0 == 0) ? num * wden : T(0);
-                    if (lane == nbuf) my_edge = op.edge[c];
-                    if (++nbuf == 32) flush_edges();
+                    if (lane == nbuf) my_edge = op.edge[0];
+                    if (++nbuf == kEdgeBuf) flush_edges();
                 }
-                if (op.need_q[c]) {
-                    T m = T(0);
-#pragma unroll
-                    for (int j = 0; j < CPL; ++j) m = fmax(m, vmax(qc[j]));
-#pragma unroll
-                    for (int o = 1; o < LPP; o <<= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-                    const int e = frexp_exp(m);
-                    if (e != 0) scale_by_pow2(qc, CPL, -e);
-                    if (op.q_slot_out[c] >= 0) {
-#pragma unroll
-                        for (int j = 0; j < CPL; ++j)
-                            slots[(op.q_slot_out[c] * CPL + j) * 32 + lane] = qc[j];
-                    }
-                    if (op.q_buf_out[c] >= 0) {
-                        T* b = a.pool + (size_t)op.q_buf_out[c] * a.bstride + off0;
-#pragma unroll
-                        for (int j = 0; j < CPL; ++j)
-                            if (act[j]) st4(b + j * offj, qc[j]);
-                    }
-                    if (op.q_reg == c) {
-#pragma unroll
-                        for (int j = 0; j < CPL; ++j) prevq[j] = qc[j];
-                    }
+                if (e1) {
+                    const T num = group_sum<LPP>(num1);
+                    gbuf[nbuf * 33 + lane] = (r0 == 0) ? num * wden : T(0);
+                    if (lane == nbuf) my_edge = op.edge[1];
+                    if (++nbuf == kEdgeBuf) flush_edges();
                 }
             }
+            // q outputs: rescaled when out of range, then to a slot, the
+            // op's buffer and/or the registers the next op reads
+    #pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (!(c == 0 ? nq0 : nq1)) continue;
+                V4<T>* qc = c == 0 ? qa : qb;
+                T m = vmax(qc[0]);
+    #pragma unroll
+                for (int j = 1; j < CPL; ++j) m = fmax(m, vmax(qc[j]));
+    #pragma unroll
+                for (int o = 1; o < LPP; o <<= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+                const int e = frexp_exp(m);
+                if (e < -kQRange || e > kQRange) scale_by_pow2(qc, CPL, -e);
+                const int so = op.q_slot_out[c];
+                if (so >= 0) {
+    #pragma unroll
+                    for (int j = 0; j < CPL; ++j) slots[(so * CPL + j) * 32 + lane] = qc[j];
+                }
+                const int bo = op.q_buf_out[c];
+                if (bo >= 0) {
+                    T* b = a.pool + (size_t)bo * a.bstride + off0;
+    #pragma unroll
+                    for (int j = 0; j < CPL; ++j)
+                        if (act[j]) st4(b + j * offj, qc[j]);
+                }
+                if (op.q_reg == c) {
+    #pragma unroll
+                    for (int j = 0; j < CPL; ++j) prevq[j] = qc[j];
+                }
+            }
+        };
+        // one call site (a second inlined copy could round FP64 differently
+        // from the first, and which copy an op took would depend on its
+        // position in the list)
+        for (int k = 0; k < n_ops; ++k) {
+            op_body(k, xA, xB, tsA, tsB);
+            tsA[0] = tsB[0];
+            tsA[1] = tsB[1];
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
-                xc[0][j] = xn[0][j];
-                xc[1][j] = xn[1][j];
+                xA[0][j] = xB[0][j];
+                xA[1][j] = xB[1][j];
             }
         }
         if (nbuf > 0) flush_edges();
@@ -1026,7 +1022,6 @@ static NucArgs<T> make_args(const Instance* I, int n_slots) {
     a.rescale = I->rescale;
     a.mat_stride = (int)I->matw_stride;
     a.n_tiles = nuc_tiles(I);  // launchers of the main kernels override
-    a.dgen = 0;
     for (int r = 0; r < kMaxCat; ++r) {
         a.catw[r] = (T)(r < I->R ? I->h_catw[r] : 0.0);
         a.rates[r] = (T)(r < I->R ? I->h_rates[r] : 0.0);
@@ -1139,31 +1134,74 @@ int launch_root4(Instance* I, int root_kind, int root, int model, double* d_site
     return cuda_check(I, cudaGetLastError(), "root kernel");
 }
 
-template <typename T, int LPP, int CPL, int NR>
-static void pre4_t(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, const void* piw,
-                   const void* Qw, double* d_gpart, int dgen) {
-    const size_t smem = (size_t)kWarpsPerBlock * ((size_t)n_slots * CPL * 32 * 4 * sizeof(T) +
-                                                  pipe_bytes<DevPreOp, T, 4>(I->R) +
-                                                  sizeof(BatchJob<T>) + 32 * 33 * sizeof(T));
-    cudaFuncSetAttribute(k_pre4<T, LPP, CPL, NR, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    NucArgs<T> a = make_args<T>(I, n_slots);
-    a.n_tiles = nuc_tiles_for(I, LPP);
-    a.dgen = dgen;
-    const int grid = grid_for(I, k_pre4<T, LPP, CPL, NR, false>, smem, a.n_tiles);
-    k_pre4<T, LPP, CPL, NR, false><<<grid, kWarpsPerBlock * 32, smem, I->stream>>>(
-        d_ops, n_ops, a, reinterpret_cast<const T*>(piw), reinterpret_cast<const T*>(Qw), d_gpart,
-        BatchRef<T>{});
+// Register budget of the one-lane-per-pattern pre-order kernel: TL_PRE_MINB
+// = 3 or 4 compiles it for three or four resident blocks per SM.
+static int pre_minb() {
+    static int env = -1;
+    if (env < 0) {
+        const char* s = getenv("TL_PRE_MINB");
+        env = s ? atoi(s) : 0;
+    }
+    return env;
 }
 
+// Dynamic shared memory of a pre-order block: per warp its q slots, the
+// op/matrix pipeline, a batch job copy and the edge-term buffer.
+template <typename T>
+static size_t pre4_smem(const Instance* I, int n_slots, int cpl) {
+    return (size_t)kWarpsPerBlock * ((size_t)n_slots * cpl * 32 * 4 * sizeof(T) +
+                                     pipe_bytes<DevPreOp, T, 4>(I->R) + sizeof(BatchJob<T>) +
+                                     kEdgeBuf * 33 * sizeof(T));
+}
+
+// q slots the pre-order planner may use: as many as leave room for
+// 228 KB / (the blocks per SM the kernel is compiled for) of shared memory
+// per block, at most 12.
+int nuc_pre_slot_cap(const Instance* I) {
+    const int lpp = nuc_lanes_pre(I), cpl = (I->R + lpp - 1) / lpp;
+    int blocks = lpp == 1 ? (I->elt == 8 ? 2 : 3) : 4;
+    if (lpp == 1 && I->R == 4 && I->prec == kF32 && pre_minb() == 4) blocks = 4;
+    const size_t fixed = I->prec == kF32 ? pre4_smem<float>(I, 0, cpl) : pre4_smem<double>(I, 0, cpl);
+    const size_t per = (size_t)kWarpsPerBlock * cpl * 32 * 4 * I->elt;
+    const size_t budget = (size_t)228 * 1024 / blocks;
+    if (budget <= fixed) return 0;
+    return (int)std::min<size_t>(12, (budget - fixed) / per);
+}
+
+template <typename T, int LPP, int CPL, int NR, int MINB>
+static void pre4_tm(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, const void* piw,
+                    double* d_gpart) {
+    const size_t smem = pre4_smem<T>(I, n_slots, CPL);
+    auto kern = k_pre4<T, LPP, CPL, NR, false, MINB>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    NucArgs<T> a = make_args<T>(I, n_slots);
+    a.n_tiles = nuc_tiles_for(I, LPP);
+    const int grid = grid_for(I, kern, smem, a.n_tiles);
+    kern<<<grid, kWarpsPerBlock * 32, smem, I->stream>>>(
+        d_ops, n_ops, a, reinterpret_cast<const T*>(piw), d_gpart, BatchRef<T>{});
+}
+
+template <typename T, int LPP, int CPL, int NR>
+static void pre4_t(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, const void* piw,
+                   double* d_gpart) {
+    if constexpr (LPP == 1 && NR == 4 && sizeof(T) == 4) {
+        if (pre_minb() == 3) return pre4_tm<T, LPP, CPL, NR, 3>(I, d_ops, n_ops, n_slots, piw, d_gpart);
+        if (pre_minb() == 4) return pre4_tm<T, LPP, CPL, NR, 4>(I, d_ops, n_ops, n_slots, piw, d_gpart);
+    }
+    pre4_tm<T, LPP, CPL, NR, 0>(I, d_ops, n_ops, n_slots, piw, d_gpart);
+}
+
+// dgen: the derivative slots hold any derivative of P (dP/dtheta); the
+// kernel reads every child's derivative matrix, so both cases take one path
 int launch_pre4(Instance* I, const DevPreOp* d_ops, int n_ops, int n_slots, int model,
                 double* d_gpart, int dgen) {
+    (void)dgen;
     if (I->prec == kF32)
         TL_PRE_DISPATCH_T(float, I, pre4_t, I, d_ops, n_ops, n_slots, I->models[model].piw,
-                          I->models[model].Qw, d_gpart, dgen);
+                          d_gpart);
     else
         TL_PRE_DISPATCH_T(double, I, pre4_t, I, d_ops, n_ops, n_slots, I->models[model].piw,
-                          I->models[model].Qw, d_gpart, dgen);
+                          d_gpart);
     I->launches += 1;
     return cuda_check(I, cudaGetLastError(), "pre-order kernel");
 }
@@ -1358,17 +1396,14 @@ static int pre4_batch_t(Batch* B, Instance* const* I, const DevPreOp* const* d_o
     int rc = upload_table(B, 2, jobs, begin, &br);
     if (rc) return rc;
     Instance* I0 = I[order[0]];
-    const size_t smem = (size_t)kWarpsPerBlock *
-                        ((size_t)max_slots * CPL * 32 * 4 * sizeof(T) +
-                         pipe_bytes<DevPreOp, T, 4>(I0->R) + sizeof(BatchJob<T>) +
-                         32 * 33 * sizeof(T));
-    cudaFuncSetAttribute(k_pre4<T, LPP, CPL, NR, true>,
+    const size_t smem = pre4_smem<T>(I0, max_slots, CPL);
+    cudaFuncSetAttribute(k_pre4<T, LPP, CPL, NR, true, 0>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     NucArgs<T> layout = make_args<T>(I0, max_slots);
     layout.n_tiles = (int)total;
-    const int grid = grid_for(I0, k_pre4<T, LPP, CPL, NR, true>, smem, (int)total);
-    k_pre4<T, LPP, CPL, NR, true><<<grid, kWarpsPerBlock * 32, smem, B->stream>>>(
-        nullptr, 0, layout, nullptr, nullptr, nullptr, br);
+    const int grid = grid_for(I0, k_pre4<T, LPP, CPL, NR, true, 0>, smem, (int)total);
+    k_pre4<T, LPP, CPL, NR, true, 0><<<grid, kWarpsPerBlock * 32, smem, B->stream>>>(
+        nullptr, 0, layout, nullptr, nullptr, br);
     B->launches += 1;
     return batch_cuda(B, cudaGetLastError(), "batched pre-order kernel");
 }

@@ -15,8 +15,9 @@ namespace tl {
 namespace {
 
 // Per-tile partial sums: 65,536 tiles of 32 patterns = 2,097,152 patterns at
-// most (512 KiB of device memory, held by every GPU that loads the library
-// until the process exits).
+// most (512 KiB of device memory). The runtime loads this module lazily, so
+// a device holds the array from the first use of the module on it (the
+// first call of the entry point there) until the process exits.
 constexpr int kStaticMaxTiles = 65536;
 static __device__ __align__(256) double g_root_partials[kStaticMaxTiles];
 
@@ -63,7 +64,11 @@ __global__ void k_sum_static(const double* __restrict__ part, int n, double* __r
 
 // Device address of this device's copy of the scratch array. Host code only
 // sees a host-side stand-in for the symbol, so the address is looked up once
-// per device (with that device current) and cached.
+// per device (with that device current) and cached. The lookup is the set-up
+// of the first call on a device (it may load the module and reserve the
+// array), which is why that call belongs before any stream capture; the
+// cached address is that of the primary context and is stale after
+// cudaDeviceReset.
 int scratch_for_current_device(double** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -61,7 +61,7 @@ def footprint(n_tips: int, n_patterns: int, n_states: int, precision: str,
     elt = 8 if precision == "f64" else 4
     nb = 2 * (N - 1) if n_buffers is None else n_buffers
     partials = nb * R * ppad * spad * elt + nb * ppad * 4
-    copies = 4 if precision == "tf32x2" else 2   # working copies per matrix slot
+    copies = 4 if precision in ("tf32x2", "tf32x3") else 2   # working copies per matrix slot
     mats = 2 * (2 * N - 1) * R * spad * spad * (8 + copies * elt)
     return int(1.02 * (partials + mats + N * ppad)) + (1 << 20)
 
@@ -117,7 +117,7 @@ class Server:
     seconds (free memory is taken at once)."""
 
     def __init__(self, memory_budget: int | None = None, max_batch: int = 512,
-                 nuc_precision: str = "f32", codon_precision: str = "tf32x2",
+                 nuc_precision: str = "f32", codon_precision: str = "tf32x3",
                  evict_after: float = 0.0):
         import torch
         self.torch = torch
@@ -275,14 +275,19 @@ class Server:
                 c.last_used = now
                 logl = float(host[li])
                 grad = host[gi:gi + ng * nb].reshape(nb, ng).sum(axis=0) if gi >= 0 else None
-                if not np.isfinite(logl) and c.precision != "f64":
+                bad = not np.isfinite(logl) or (grad is not None and
+                                                 not np.all(np.isfinite(grad)))
+                if bad and c.precision != "f64":
                     # reduced precision can lose a pattern entirely: one
                     # exponent per pattern spans all categories, so categories
                     # whose likelihoods differ by more than FP32's range at a
                     # node underflow, and two children may keep disjoint ones.
-                    # The request is evaluated again in FP64.
+                    # The request is evaluated again in FP64 (its latency
+                    # includes that evaluation).
+                    t0 = time.perf_counter()
                     logl, grad = self._fp64(p)
                     now = time.perf_counter()
+                    self.stats["fp64_fallback_s"] += now - t0
                 if not np.isfinite(logl):
                     p.future.set_exception(FloatingPointError("non-finite log-likelihood"))
                 else:
@@ -381,10 +386,24 @@ class Server:
     def _fp64(self, p: _Pending):
         """(logL, gradient or None) of one request on a temporary FP64
         instance (the host waits); (nan, None) if that fails too."""
-        from ._lib import TreelikError
         c = self.chains[p.chain]
         d, r = c.data, p.req
         self.stats["fp64_fallback"] += 1
+        # the temporary instance counts against the memory budget: idle
+        # chains (this one included) make room for it first, as for an
+        # admission; if even that is not enough it is tried anyway (the
+        # device allocation decides) rather than failing the request
+        nbuf = c.n_buffers if c.band else None
+        extra = footprint(d.tree.n_tips, d.n_patterns, d.n_states, "f64", nbuf)
+        self._make_room(extra)
+        self.used += extra
+        try:
+            return self._fp64_eval(c, d, r)
+        finally:
+            self.used -= extra
+
+    def _fp64_eval(self, c, d, r):
+        from ._lib import TreelikError
         try:
             if c.band:   # a chain served with checkpointing keeps that form in FP64
                 tl = CheckpointedLikelihood(d.tree.n_tips, d.n_patterns, d.tree.children,

@@ -1,7 +1,8 @@
-"""Twenty states (amino acids under a general reversible model): the
+"""Twenty states (amino acids under a general reversible model): the split
 tensor-core path with states padded to 64 and the FP64 generic path,
 against the oracle: logL, branch gradients, dlogL/dQ and the gradient with
-respect to every exchangeability (complex-step dQ/dE in the oracle)."""
+respect to every exchangeability (complex-step dQ/dE in the oracle), every
+component within |x - x*| <= tol max(|x*|, 1e-3 |x*|_inf)."""
 import numpy as np
 import pytest
 
@@ -20,8 +21,7 @@ def _gpu():
     build.build()
 
 
-@pytest.mark.parametrize("prec,tol_l,tol_g", [("f64", 1e-11, 1e-10), ("tf32", 1e-5, 1e-3),
-                                              ("tf32x2", 1e-5, 1e-3)])
+@pytest.mark.parametrize("prec,tol_l,tol_g", [("f64", 1e-11, 1e-10), ("tf32x3", 1e-5, 1e-3)])
 def test_amino_acid_loglik_gradient_and_adjoint(prec, tol_l, tol_g):
     from paper_2606_27607_gb300 import TreeLikelihood
     w = synth.workload("aa20_256x10k", n_tips=9, n_patterns=333)
@@ -49,9 +49,5 @@ def test_amino_acid_loglik_gradient_and_adjoint(prec, tol_l, tol_g):
     assert th.size == 400           # the exchangeability matrix, diagonal 0
     assert np.all(th.reshape(20, 20).diagonal() == 0)
     for got, want in ((g[:-1], want_g[:-1]), (g2[:-1], want_g[:-1]), (dq, want_q), (th, want_th)):
-        if prec == "f64":
-            scale = np.max(np.abs(want))
-            assert np.max(np.abs(got - want) / np.maximum(np.abs(want), 1e-3 * scale)) <= tol_g
-        else:
-            assert np.linalg.norm(got - want) <= tol_g * np.linalg.norm(want)
-            assert np.max(np.abs(got - want)) <= tol_g * np.max(np.abs(want))
+        scale = np.max(np.abs(want))
+        assert np.max(np.abs(got - want) / np.maximum(np.abs(want), 1e-3 * scale)) <= tol_g

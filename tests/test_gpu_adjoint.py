@@ -2,7 +2,8 @@
 exponential's derivative) against the FP64 oracle: dlogL/dt for every
 branch, dlogL/dQ, dlogL/dtheta for every model parameter (including the 265
 of random-effects GY94), and the first-order approximation, on the
-four-state kernels, the FP64 generic path and the tensor-core codon paths."""
+four-state kernels, the FP64 generic path and the split tensor-core codon
+path, every component within |x - x*| <= tol max(|x*|, 1e-3 |x*|_inf)."""
 import dataclasses
 
 import numpy as np
@@ -51,13 +52,9 @@ def want(w, first_order=False, model=None, params=None):
     return logl, g, G, np.einsum("kij,ij->k", J, G)
 
 
-def close(got, ref, tol, norm=False):
-    """Per component |x - x*| <= tol max(|x*|, 1e-3 |x*|_inf), or for the
-    TF32 paths the vector and the largest component."""
+def close(got, ref, tol):
+    """Per component |x - x*| <= tol max(|x*|, 1e-3 |x*|_inf)."""
     got, ref = np.ravel(got), np.ravel(ref)
-    if norm:
-        return (np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref)
-                and np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref)))
     scale = np.max(np.abs(ref))
     return np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-3 * scale)) <= tol
 
@@ -73,15 +70,15 @@ def rate_entries(w, model=None, params=None):
     return Q != 0
 
 
-def check(w, prec, tol, first_order=False, norm=False, model=None, params=None):
+def check(w, prec, tol, first_order=False, model=None, params=None):
     gl, gg, gq, gt = run(w, prec, first_order, model, params)
     wl, wg, wq, wt = want(w, first_order, model, params)
     assert abs(gl - wl) <= 1e-5 * abs(wl)
-    assert close(gg[:-1], wg[:-1], tol, norm), (np.max(np.abs(gg - wg)), np.max(np.abs(wg)))
+    assert close(gg[:-1], wg[:-1], tol), (np.max(np.abs(gg - wg)), np.max(np.abs(wg)))
     m = rate_entries(w, model, params) if prec != "f64" else np.ones(gq.shape, bool)
-    assert close(gq[m], wq[m], tol, norm), (np.max(np.abs(gq - wq)), np.max(np.abs(wq)))
+    assert close(gq[m], wq[m], tol), (np.max(np.abs(gq - wq)), np.max(np.abs(wq)))
     if wt.size:
-        assert close(gt, wt, tol, norm), (gt[:8], wt[:8])
+        assert close(gt, wt, tol), (gt[:8], wt[:8])
     return gg, gq, gt
 
 
@@ -144,24 +141,29 @@ def test_ambiguous_tips_zero_weights_and_tip_partials():
         assert close(th, wth, tol)
 
 
-@pytest.mark.parametrize("prec,tol,norm", [("f64", 1e-9, False), ("tf32", 1e-3, True),
-                                           ("tf32x2", 1e-3, True)])
-def test_codon_adjoint(prec, tol, norm):
-    """GY94: the FP64 generic path and the tensor-core paths (TF32 storage:
-    vector and largest-component bounds)."""
-    w = synth.workload("gy94_64x5k", n_tips=7, n_patterns=161)
-    check(w, prec, tol, norm=norm)
+@pytest.mark.parametrize("prec,tol,n_tips,n_pat", [("f64", 1e-9, 7, 161), ("f64", 1e-8, 20, 300),
+                                                   ("tf32x3", 1e-3, 7, 161),
+                                                   ("tf32x3", 1e-3, 20, 300)])
+def test_codon_adjoint(prec, tol, n_tips, n_pat):
+    """GY94: the FP64 generic path and the split tensor-core path (FP32
+    partials split on chip), every component of every gradient. The FP64
+    bound at 20 taxa is the one its eigensystem route reaches (4.5e-9 of
+    the floor 1e-3 |g|_inf, i.e. 4.5e-12 of the largest component, in the
+    fused pre-order gradient and the adjoint alike): F3x4 frequencies make
+    V = D^-1/2 U scale by 1/sqrt(pi_min)."""
+    w = synth.workload("gy94_64x5k", n_tips=n_tips, n_patterns=n_pat)
+    check(w, prec, tol)
 
 
-@pytest.mark.parametrize("prec,tol,norm", [("f64", 1e-9, False), ("tf32x2", 1e-3, True)])
-def test_random_effects_gy94(prec, tol, norm):
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("tf32x3", 1e-3)])
+def test_random_effects_gy94(prec, tol):
     """All 265 parameters of random-effects GY94 (kappa, omega and one
     effect per one-difference codon pair), against <dlogL/dQ, dQ/dtheta> of
     the oracle with complex-step dQ/dtheta; logL checks the device-built Q."""
     w = synth.workload("gy94_64x5k", n_tips=6, n_patterns=130)
     eps = np.random.default_rng(7).normal(0.0, 0.4, 263)
     params = np.r_[w.params, eps]
-    _, _, th = check(w, prec, tol, norm=norm, model="gy94re", params=params)
+    _, _, th = check(w, prec, tol, model="gy94re", params=params)
     assert th.shape == (265,)
 
 
@@ -229,7 +231,7 @@ def sampled(w, n=300, seed=9):
 
 @pytest.mark.slow
 @pytest.mark.parametrize("name,prec,model", [("gtr_1024x50k", "f32", None),
-                                             ("gy94_128x20k", "tf32x2", "gy94re")])
+                                             ("gy94_128x20k", "tf32x3", "gy94re")])
 def test_adjoint_full_size_sampled_patterns(name, prec, model):
     """Full-size launches (the benchmark's trees and pattern counts) with
     weights selecting 300 patterns, so the oracle can evaluate the same
@@ -241,7 +243,7 @@ def test_adjoint_full_size_sampled_patterns(name, prec, model):
     gl, gg, gq, gt = run(w, prec, model=model, params=params)
     wl, wg, wq, wt = want(small, model=model, params=params)
     assert abs(gl - wl) <= 1e-5 * abs(wl)
-    assert close(gg[:-1], wg[:-1], 1e-3, norm=True)
+    assert close(gg[:-1], wg[:-1], 1e-3)
     m = rate_entries(w, model, params)
-    assert close(gq[m], wq[m], 1e-3, norm=True)
-    assert close(gt, wt, 1e-3, norm=True)
+    assert close(gq[m], wq[m], 1e-3)
+    assert close(gt, wt, 1e-3)

@@ -35,6 +35,7 @@ def whole(w, prec):
 @pytest.mark.parametrize("name,prec,kw", [("gtr_512x100k", "f32", dict(n_tips=200, n_patterns=3000)),
                                           ("gtr_512x100k", "f64", dict(n_tips=90, n_patterns=500)),
                                           ("gy94_64x5k", "tf32x2", dict(n_tips=40, n_patterns=300)),
+                                          ("gy94_64x5k", "tf32x3", dict(n_tips=40, n_patterns=300)),
                                           ("gy94_64x5k", "f64", dict(n_tips=12, n_patterns=100))])
 @pytest.mark.parametrize("band", [1, 2, 3, 5])
 def test_checkpointed_gradient_is_bit_identical(name, prec, kw, band):

@@ -1,9 +1,15 @@
 """Codon (GY94, 61 states padded to 64) tensor-core path (tcgen05 kind::tf32)
 against the FP64 oracle. Reduced-precision tolerance: 1e-5 relative on
-logL. Per-pattern log-likelihoods: TF32 keeps 11 significant bits, so every
-stored partial and every entry of P carries a relative rounding error up to
-2^-11; a pattern accumulates about one such error per internal node, hence
-|l_p - l_p*| <= 2^-11 * (N - 1)."""
+logL, and per gradient component |g - g*| <= 1e-3 max(|g*|, 1e-3 |g*|_inf).
+Per-pattern log-likelihoods: TF32 keeps 11 significant bits, so with
+TF32-stored partials (tf32, tf32x2) every stored partial carries a relative
+rounding error up to 2^-11; a pattern accumulates about one such error per
+internal node, hence |l_p - l_p*| <= 2^-11 * (N - 1). Those two modes are
+logL modes: a gradient component whose per-pattern terms cancel keeps an
+absolute error of order 2^-11 sqrt(P) of its terms. tf32x3 stores FP32
+partials and splits them on chip (three products, about 21 bits of both
+operands): |l_p - l_p*| <= 2^-20 * (N - 1), and gradients meet the
+per-component bound."""
 import numpy as np
 import pytest
 
@@ -44,7 +50,10 @@ def run(w, prec, site=False, tips_as_partials=False):
         tl.close()
 
 
-@pytest.mark.parametrize("prec", ["tf32", "tf32x2"])
+SITE_BITS = {"tf32": 11, "tf32x2": 11, "tf32x3": 20}
+
+
+@pytest.mark.parametrize("prec", ["tf32", "tf32x2", "tf32x3"])
 @pytest.mark.parametrize("n_tips,n_pat", [(2, 1), (5, 150), (12, 300), (40, 257)])
 def test_codon_tf32_matches_oracle(n_tips, n_pat, prec):
     w = codon_workload(n_tips, n_pat)
@@ -52,10 +61,10 @@ def test_codon_tf32_matches_oracle(n_tips, n_pat, prec):
     want_l, want_site = op.loglik(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights, w.tips)
     logl, site = run(w, prec, site=True)
     assert abs(logl - want_l) <= 1e-5 * abs(want_l), (logl, want_l)
-    assert np.max(np.abs(site - want_site)) <= 2.0 ** -11 * (n_tips - 1)
+    assert np.max(np.abs(site - want_site)) <= 2.0 ** -SITE_BITS[prec] * max(n_tips - 1, 1)
 
 
-@pytest.mark.parametrize("prec", ["tf32", "tf32x2"])
+@pytest.mark.parametrize("prec", ["tf32", "tf32x2", "tf32x3"])
 def test_codon_tf32_tip_states_equal_one_hot_partials_bit_exact(prec):
     w = codon_workload(9, 200)
     a = run(w, prec)
@@ -63,7 +72,7 @@ def test_codon_tf32_tip_states_equal_one_hot_partials_bit_exact(prec):
     assert a == b
 
 
-@pytest.mark.parametrize("prec", ["tf32", "tf32x2"])
+@pytest.mark.parametrize("prec", ["tf32", "tf32x2", "tf32x3"])
 def test_codon_tf32_ambiguous_tips(prec):
     w = codon_workload(7, 130)
     rng = np.random.default_rng(3)
@@ -121,19 +130,18 @@ def assert_grad_close(g, want, tol):
     assert np.max(err) <= tol, (np.max(err), int(np.argmax(err)))
 
 
-@pytest.mark.parametrize("n_tips,n_pat", [(3, 40), (8, 150), (20, 300)])
-def test_codon_tf32x2_gradient(n_tips, n_pat):
-    """Split matrices: logL within 1e-5, gradient within 1e-3 in the 2-norm
-    and every component within 1e-3 of the largest. The stored partials keep
-    TF32's 11 bits, so a component whose per-pattern terms cancel to a small
-    sum keeps an absolute error of order 2^-11 sqrt(P) of its terms."""
+@pytest.mark.parametrize("n_tips,n_pat", [(3, 40), (8, 150), (20, 300), (7, 161)])
+def test_codon_tf32x3_gradient_matches_oracle(n_tips, n_pat):
+    """Split partials and matrices: logL within 1e-5 and every branch
+    derivative within the per-component bound (the fused pre-order pass and
+    the reverse-mode adjoint)."""
     from oracle import gradient as og
     from paper_2606_27607_gb300 import TreeLikelihood
     w = codon_workload(n_tips, n_pat)
     Q, pi, _ = om.build(w.model, w.params, w.freqs)
     want_l, _ = op.loglik(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights, w.tips)
     want_g = og.branch_gradient(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights, w.tips)
-    tl = TreeLikelihood(n_tips, n_pat, 61, 4, "tf32x2")
+    tl = TreeLikelihood(n_tips, n_pat, 61, 4, "tf32x3")
     try:
         tl.set_tips(w.tips)
         tl.set_model("gy94", w.params, w.freqs)
@@ -141,36 +149,48 @@ def test_codon_tf32x2_gradient(n_tips, n_pat):
         tl.set_pattern_weights(w.pattern_weights)
         tl.set_tree(w.tree.children, w.tree.edge_len)
         logl, g = tl.gradient()
+        tl.loglik()
+        g2, _, _ = tl.adjoint()
     finally:
         tl.close()
     assert abs(logl - want_l) <= 1e-5 * abs(want_l)
-    gv, wv = g[:-1], want_g[:-1]
-    assert np.linalg.norm(gv - wv) <= 1e-3 * np.linalg.norm(wv)
-    assert np.max(np.abs(gv - wv)) <= 1e-3 * np.max(np.abs(wv))
+    assert_grad_close(g[:-1], want_g[:-1], 1e-3)
+    assert_grad_close(g2[:-1], want_g[:-1], 1e-3)
 
 
-@pytest.mark.parametrize("n_tips,n_pat", [(3, 40), (8, 150), (20, 300)])
-def test_codon_tf32_gradient_matches_oracle(n_tips, n_pat):
-    from oracle import gradient as og
+@pytest.mark.parametrize("prec", ["tf32", "tf32x2"])
+def test_fused_post_order_is_bit_identical_to_level_kernels(prec, monkeypatch):
+    """The subtree-fused post-order kernel (one CTA walks the whole op list
+    for a pattern tile, each op's result kept in tensor memory as the next
+    op's operand) against the level-by-level kernels: the same logL, the
+    same per-pattern values and the same gradient (the pre-order pass reads
+    the stored partials), bit for bit, on a tree with ambiguous tips, two
+    tiles and a ragged tail."""
     from paper_2606_27607_gb300 import TreeLikelihood
-    w = codon_workload(n_tips, n_pat)
+    w = codon_workload(37, 2 * 128 + 45)
+    rng = np.random.default_rng(8)
+    w.tips = w.tips.copy()
+    w.tips[rng.random(w.tips.shape) < 0.03] = 61
+    out = {}
+    for fused in ("1", "0"):
+        monkeypatch.setenv("TL_TC_FUSED", fused)
+        tl = TreeLikelihood(w.tree.n_tips, w.n_patterns, 61, 4, prec)
+        try:
+            tl.set_tips(w.tips)
+            tl.set_model("gy94", w.params, w.freqs)
+            tl.set_rates(w.rates, w.cat_weights)
+            tl.set_pattern_weights(w.pattern_weights)
+            tl.set_tree(w.tree.children, w.tree.edge_len)
+            logl, site = tl.loglik(site=True)
+            _, g = tl.gradient()
+            launches = tl.inst.launch_count()
+        finally:
+            tl.close()
+        out[fused] = (logl, site, g, launches)
+    assert out["1"][0] == out["0"][0]
+    assert np.array_equal(out["1"][1], out["0"][1])
+    assert np.array_equal(out["1"][2], out["0"][2])
+    assert out["1"][3] < out["0"][3]      # one post-order launch instead of one per level
     Q, pi, _ = om.build(w.model, w.params, w.freqs)
     want_l, _ = op.loglik(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights, w.tips)
-    want_g = og.branch_gradient(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights, w.tips)
-    tl = TreeLikelihood(n_tips, n_pat, 61, 4, "tf32")
-    try:
-        tl.set_tips(w.tips)
-        tl.set_model("gy94", w.params, w.freqs)
-        tl.set_rates(w.rates, w.cat_weights)
-        tl.set_pattern_weights(w.pattern_weights)
-        tl.set_tree(w.tree.children, w.tree.edge_len)
-        logl, g = tl.gradient()
-    finally:
-        tl.close()
-    assert abs(logl - want_l) <= 1e-5 * abs(want_l)
-    # plain TF32 (11-bit operands): relative error of the gradient vector, and
-    # each component within 1e-3 of the largest; components whose per-pattern
-    # terms cancel need the split mode for the per-component bound
-    gv, wv = g[:-1], want_g[:-1]
-    assert np.linalg.norm(gv - wv) <= 1e-3 * np.linalg.norm(wv)
-    assert np.max(np.abs(gv - wv)) <= 1e-3 * np.max(np.abs(wv))
+    assert abs(out["1"][0] - want_l) <= 1e-5 * abs(want_l)

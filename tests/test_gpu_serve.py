@@ -87,7 +87,8 @@ def test_results_match_oracle(stream):
         if r.gradient:
             wg = og.branch_gradient(tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights,
                                     w.tips)
-            assert np.linalg.norm(g.gradient - wg) <= 1e-3 * np.linalg.norm(wg)
+            scale = np.max(np.abs(wg))
+            assert np.max(np.abs(g.gradient - wg) / np.maximum(np.abs(wg), 1e-3 * scale)) <= 1e-3
 
 
 def test_admission_under_a_small_budget(stream):
@@ -95,7 +96,7 @@ def test_admission_under_a_small_budget(stream):
     chains, reqs, _ = stream
     base, _, _ = serve(chains, reqs)
     sizes = sorted(footprint(w.tree.n_tips, w.n_patterns, w.n_states,
-                             "f32" if w.n_states == 4 else "tf32x2") for w in chains)
+                             "f32" if w.n_states == 4 else "tf32x3") for w in chains)
     # room for the largest chain but not for all of them at once
     budget = sizes[-1] + sizes[-2] // 2
     got, stats, _ = serve(chains, reqs, budget=budget)
@@ -107,7 +108,7 @@ def test_admission_under_a_small_budget(stream):
     from paper_2606_27607_gb300.checkpoint import best_band
     big = max(range(len(chains)), key=lambda k: footprint(
         chains[k].tree.n_tips, chains[k].n_patterns, chains[k].n_states,
-        "f32" if chains[k].n_states == 4 else "tf32x2"))
+        "f32" if chains[k].n_states == 4 else "tf32x3"))
     got, stats, _ = serve(chains, reqs, budget=sizes[-1] - 1)
     assert stats.get("checkpointed", 0) > 0
     for r, a, b in zip(reqs, base, got):
@@ -119,7 +120,7 @@ def test_admission_under_a_small_budget(stream):
     wb = chains[big]
     nb = best_band(wb.tree.children, wb.tree.n_tips)[1]
     tight = footprint(wb.tree.n_tips, wb.n_patterns, wb.n_states,
-                      "f32" if wb.n_states == 4 else "tf32x2", nb) - 1
+                      "f32" if wb.n_states == 4 else "tf32x3", nb) - 1
     got, stats, _ = serve(chains, reqs, budget=tight)
     for r, b in zip(reqs, got):
         if r.chain == big:

@@ -119,9 +119,9 @@ def test_server_falls_back_to_fp64_on_a_checkpointed_chain():
     from paper_2606_27607_gb300.checkpoint import best_band
     from paper_2606_27607_gb300.serve import Server, footprint
     w = crafted()
-    whole = footprint(64, 2, 61, "tf32x2")
+    whole = footprint(64, 2, 61, "tf32x3")
     band, nb = best_band(w.tree.children, 64)
-    budget = (whole + footprint(64, 2, 61, "tf32x2", nb)) // 2
+    budget = (whole + footprint(64, 2, 61, "tf32x3", nb)) // 2
     req = synth.ServingRequest(chain=0, edge_len=w.tree.edge_len, params=np.asarray(w.params),
                                gradient=True)
     s = Server(memory_budget=budget)
