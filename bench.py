@@ -736,8 +736,10 @@ def main() -> None:
         from paper_2606_27607_gb300 import build
         build.build()
         torch.cuda.set_device(0)
-        print(json.dumps(codon_line(args.steps, args.warmup, args.codon_taxa, args.codon_patterns,
-                                    os.environ.get("TL_CODON_PREC", "tf32"))))
+        line = codon_line(args.steps, args.warmup, args.codon_taxa, args.codon_patterns,
+                          os.environ.get("TL_CODON_PREC", "tf32"))
+        line.pop("_grad", None)
+        print(json.dumps(line))
         return
 
     import numpy as np
@@ -840,20 +842,33 @@ def main() -> None:
     # host -> device every step, logL and gradient come back
     e2e = None
     if not args.no_e2e:
-        tips_h = torch.from_numpy(np.ascontiguousarray(w.tips)).pin_memory()
-        tips_np = tips_h.numpy()
+        # Each step's tip states come from page-locked host memory (two
+        # buffers, as a producer filling the next batch would use) through
+        # the asynchronous double-buffered upload: step k queues its
+        # kernels, then the upload of step k + 1's tips (it overlaps step k's
+        # kernels), then reads its logL and gradient back to the host.
+        tips_h = [torch.from_numpy(np.ascontiguousarray(w.tips)).pin_memory() for _ in range(2)]
+        tips_np = [t.numpy() for t in tips_h]
         wts = np.ascontiguousarray(w.pattern_weights)
+        d_res = torch.zeros(1 + nn, dtype=torch.float64, device="cuda")
+        h_res = torch.zeros(1 + nn, dtype=torch.float64).pin_memory()
+        nstep = [0]
 
         def e2e_step():
-            inst.set_tip_states_all(tips_np)
+            k = nstep[0]
+            nstep[0] += 1
             inst.set_pattern_weights(wts)
             inst.set_model_async(0, w.model, w.params, w.freqs)
             inst.update_matrices(0, v, lengths, dp)
             inst.update_partials(post)
-            lg = inst.root_loglik(nn - 1, 0)
-            g = inst.pre_order_gradient(pre, nn, 0)
-            return lg, g
+            inst.root_loglik_dev(nn - 1, 0, d_res.data_ptr())
+            inst.pre_order_gradient_dev(pre, nn, 0, d_res.data_ptr() + 8)
+            inst.set_tip_states_all_async(tips_np[(k + 1) % 2])
+            h_res.copy_(d_res, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            return float(h_res[0]), h_res[1:].numpy()
 
+        inst.set_tip_states_all_async(tips_np[0])
         for _ in range(3):
             e2e_step()
         torch.cuda.synchronize()
@@ -869,9 +884,10 @@ def main() -> None:
         if dist:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         t_e2e = float(te.item())
-        # tips + padded weights + model parameters + (rates, branch lengths);
-        # op lists and matrix indices are unchanged between steps and stay
-        # resident (the library skips identical uploads)
+        # tips (one upload per step, for the next step) + padded weights +
+        # model parameters + (rates, branch lengths); op lists and matrix
+        # indices are unchanged between steps and stay resident (the library
+        # skips identical uploads)
         h2d = (N * P + 8 * ((P + 31) // 32 * 32) + 8 * (len(w.params) + np.size(w.freqs))
                + 8 * (R + nn - 1))
         e2e = {"value": world * P * (N - 1) / t_e2e, "unit": UNIT, "ms_per_step": 1e3 * t_e2e,

@@ -172,6 +172,20 @@ int tl_set_tip_partials(tl_instance* inst, int tip, const double* partials);
  * copied with one 2-D transfer (full speed from page-locked host memory);
  * synchronises the stream before returning. */
 int tl_set_tip_states_all(tl_instance* inst, const int8_t* states);
+/* Like tl_set_tip_states_all, but asynchronous and double-buffered, so the
+ * upload of the next evaluation's tip states overlaps the kernels of the
+ * current one: the copy runs on the instance's own copy stream into a
+ * second tip-state pool (allocated on the first call), after the kernels
+ * that last read that pool; the next call that launches work on the
+ * instance (update_partials, root log-likelihood, pre-order, edge
+ * derivatives, adjoint) makes the instance stream wait for the copy and
+ * switches to that pool. states: host, [n_tips][n_patterns] int8 as for
+ * tl_set_tip_states_all; it must be page-locked for the copy to be
+ * asynchronous and must stay valid and unchanged until that next call's
+ * work has been queued and the copy has finished (tl_sync, or the
+ * instance stream, orders after it). A second call before the pool is
+ * used replaces the pending upload. Errors as tl_set_tip_states_all. */
+int tl_set_tip_states_all_async(tl_instance* inst, const int8_t* states);
 /* Pattern weights [n_patterns] (non-negative, finite). Default 1. */
 int tl_set_pattern_weights(tl_instance* inst, const double* weights);
 /* Category rates rho_r [n_categories] (>= 0) and weights w_r (>= 0, summing

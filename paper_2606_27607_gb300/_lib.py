@@ -77,6 +77,7 @@ SIGNATURES = {
     "tl_edge_derivatives": [_VP, _VP, _I, _I, _VP, _I],
     "tl_get_partials": [_VP, _I, _VP, _VP],
     "tl_set_tip_states_all": [_VP, _VP],
+    "tl_set_tip_states_all_async": [_VP, _VP],
     "tl_set_model_async": [_VP, _I, _I, _VP, _I, _VP, _I],
     "tl_launch_count": [_VP, C.POINTER(C.c_ulonglong)],
     "tl_root_loglik_static": [_VP, _VP, _VP, _VP, _VP, _I, _I, _I, _VP, _VP],
@@ -243,6 +244,18 @@ class Instance:
         if a.shape != (self.n_tips, self.n_patterns):
             raise ValueError("states must be [n_tips, n_patterns]")
         _check(load().tl_set_tip_states_all(self.h, _ptr(a)), self.h)
+
+    def set_tip_states_all_async(self, states) -> None:
+        """tl_set_tip_states_all_async: states must be a C-contiguous int8
+        [n_tips, n_patterns] array in page-locked memory that stays valid
+        until the next evaluation on this instance has been queued and the
+        copy has finished (no copy is made here)."""
+        if not (isinstance(states, np.ndarray) and states.dtype == np.int8
+                and states.flags.c_contiguous):
+            raise ValueError("states must be a C-contiguous int8 array (page-locked)")
+        if states.shape != (self.n_tips, self.n_patterns):
+            raise ValueError("states must be [n_tips, n_patterns]")
+        _check(load().tl_set_tip_states_all_async(self.h, _ptr(states)), self.h)
 
     def launch_count(self) -> int:
         n = C.c_ulonglong()

@@ -257,6 +257,14 @@ struct Extra {
     int ring_next = 0;
     OpArea areas[6];
     cudaEvent_t order_ev = nullptr;  // orders this stream against a batch stream
+    // double-buffered tip states (tl_set_tip_states_all_async): pool[i] and
+    // the events ordering each copy against the kernels that read the pool
+    int8_t* tip_pools[2] = {nullptr, nullptr};
+    int tip_active = 0;              // the pool I->tip_pool points to
+    int tip_pending = -1;            // a pool being filled for the next call
+    cudaStream_t tip_stream = nullptr;
+    cudaEvent_t tip_copied[2] = {nullptr, nullptr};   // copy into pool i done
+    cudaEvent_t tip_free[2] = {nullptr, nullptr};     // last kernel reading pool i done
     std::vector<void*> gen_q;     // generic path: scratch pre-order buffers
     double* d_out = nullptr;      // small result area
     size_t out_cap = 0;
@@ -708,6 +716,30 @@ int plan_pre(Instance* I, const tl_pre_op* ops, int n, int n_grad, bool store_al
     return TL_OK;
 }
 
+// A pool filled by tl_set_tip_states_all_async becomes the instance's tip
+// pool at the next call that launches work: the instance stream waits for
+// the copy, and the pool it leaves is marked free once the work queued so
+// far (the last readers of that pool) is done.
+int activate_tip_pool(Instance* I) {
+    Extra& X = extra(I);
+    if (X.tip_pending < 0) return TL_OK;
+    const int nxt = X.tip_pending, old = X.tip_active;
+    X.tip_pending = -1;
+    cudaError_t e = cudaStreamWaitEvent(I->stream, X.tip_copied[nxt], 0);
+    if (e == cudaSuccess) e = cudaEventRecord(X.tip_free[old], I->stream);
+    if (e != cudaSuccess) return cuda_check(I, e, "tip pool switch");
+    X.tip_active = nxt;
+    I->tip_pool = X.tip_pools[nxt];
+    for (int t = 0; t < I->n_tips; ++t) {
+        I->h_tipst[t] = I->tip_pool + (size_t)t * I->Ppad;
+        I->h_buf[t] = nullptr;
+        I->tip_set[t] = 1;
+    }
+    int rc;
+    if ((rc = h2d(I, I->d_tipst, I->h_tipst.data(), sizeof(int8_t*) * I->n_tips))) return rc;
+    return h2d(I, I->d_buf, I->h_buf.data(), sizeof(void*) * I->n_tips);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -770,6 +802,15 @@ int tl_destroy(tl_instance* inst) {
         for (auto& s : X->ring) give_pinned(s);
         for (auto& A : X->areas) fr(A.d);
         if (X->order_ev) cudaEventDestroy(X->order_ev);
+        if (X->tip_stream) {
+            cudaStreamSynchronize(X->tip_stream);
+            cudaStreamDestroy(X->tip_stream);
+        }
+        for (int i = 0; i < 2; ++i) {
+            if (X->tip_pools[i] && X->tip_pools[i] != I->tip_pool) fr(X->tip_pools[i]);
+            if (X->tip_copied[i]) cudaEventDestroy(X->tip_copied[i]);
+            if (X->tip_free[i]) cudaEventDestroy(X->tip_free[i]);
+        }
         for (void* p : X->gen_q) fr(p);
         fr(X->d_out);
         delete X;
@@ -936,8 +977,10 @@ int tl_set_tip_states(tl_instance* inst, int tip, const int8_t* states) {
     Instance* I = reinterpret_cast<Instance*>(inst);
     if (tip < 0 || tip >= I->n_tips) return fail(I, TL_ERR_INDEX, "tip %d out of range", tip);
     if (!states) return fail(I, TL_ERR_ARG, "states is null");
+    int rc = activate_tip_pool(I);
+    if (rc) return rc;
     int8_t* dst = I->tip_pool + (size_t)tip * I->Ppad;
-    int rc = h2d(I, dst, states, (size_t)I->P);
+    rc = h2d(I, dst, states, (size_t)I->P);
     if (rc) return rc;
     if (I->h_tipst[tip] != dst || I->h_buf[tip] != nullptr) {
         I->h_tipst[tip] = dst;
@@ -949,10 +992,52 @@ int tl_set_tip_states(tl_instance* inst, int tip, const int8_t* states) {
     return TL_OK;
 }
 
+int tl_set_tip_states_all_async(tl_instance* inst, const int8_t* states) {
+    CHECK_INST(inst);
+    Instance* I = reinterpret_cast<Instance*>(inst);
+    if (!states) return fail(I, TL_ERR_ARG, "states is null");
+    Extra& X = extra(I);
+    cudaError_t e = cudaSuccess;
+    if (!X.tip_stream) {
+        e = cudaStreamCreateWithFlags(&X.tip_stream, cudaStreamNonBlocking);
+        for (int i = 0; e == cudaSuccess && i < 2; ++i) {
+            e = cudaEventCreateWithFlags(&X.tip_copied[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&X.tip_free[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_check(I, e, "tl_set_tip_states_all_async set-up");
+        X.tip_pools[0] = I->tip_pool;
+        X.tip_active = 0;
+        // nothing has read the second pool yet
+        if ((e = cudaEventRecord(X.tip_free[1], X.tip_stream)) != cudaSuccess)
+            return cuda_check(I, e, "tl_set_tip_states_all_async set-up");
+    }
+    if (!X.tip_pools[1]) {
+        int rc = dev_alloc(I, reinterpret_cast<void**>(&X.tip_pools[1]), (size_t)I->n_tips * I->Ppad,
+                           "second tip pool");
+        if (rc) return rc;
+        // padding patterns read as ambiguous, as in the first pool
+        e = cudaMemsetAsync(X.tip_pools[1], 0xff, (size_t)I->n_tips * I->Ppad, I->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(X.tip_free[1], I->stream);
+        if (e != cudaSuccess) return cuda_check(I, e, "second tip pool");
+    }
+    // fill the pool that is neither active nor already pending
+    const int tgt = X.tip_pending >= 0 ? X.tip_pending : 1 - X.tip_active;
+    e = cudaStreamWaitEvent(X.tip_stream, X.tip_free[tgt], 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(X.tip_pools[tgt], I->Ppad, states, I->P, I->P, I->n_tips,
+                              cudaMemcpyHostToDevice, X.tip_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(X.tip_copied[tgt], X.tip_stream);
+    if (e != cudaSuccess) return cuda_check(I, e, "tl_set_tip_states_all_async");
+    X.tip_pending = tgt;
+    return TL_OK;
+}
+
 int tl_set_tip_states_all(tl_instance* inst, const int8_t* states) {
     CHECK_INST(inst);
     Instance* I = reinterpret_cast<Instance*>(inst);
     if (!states) return fail(I, TL_ERR_ARG, "states is null");
+    int rc0 = activate_tip_pool(I);   // a pending asynchronous upload is superseded
+    if (rc0) return rc0;
     cudaError_t e = cudaMemcpy2DAsync(I->tip_pool, I->Ppad, states, I->P, I->P, I->n_tips,
                                       cudaMemcpyHostToDevice, I->stream);
     if (e != cudaSuccess) return cuda_check(I, e, "tl_set_tip_states_all");
@@ -1292,6 +1377,7 @@ int tl_adjoint(tl_instance* inst, const tl_adj_op* ops, int count, int model, un
                double* out_grad, int n_grad, double* out_dQ, double* out_dtheta, int n_theta) {
     CHECK_INST(inst);
     Instance* I = reinterpret_cast<Instance*>(inst);
+    if (int rc0 = activate_tip_pool(I)) return rc0;
     if (model < 0 || model >= I->n_models || !I->models[model].ready)
         return fail(I, TL_ERR_STATE, "model %d not set", model);
     if (count < 0 || (count > 0 && !ops)) return fail(I, TL_ERR_ARG, "bad op list");
@@ -1455,6 +1541,7 @@ int tl_get_partials(tl_instance* inst, int buf, double* out, int32_t* exponents)
 int tl_update_partials(tl_instance* inst, const tl_op* ops, int count) {
     CHECK_INST(inst);
     Instance* I = reinterpret_cast<Instance*>(inst);
+    if (int rc0 = activate_tip_pool(I)) return rc0;
     if (count < 0 || (count > 0 && !ops)) return fail(I, TL_ERR_ARG, "bad op list");
     if (count == 0) return TL_OK;
     int rc;
@@ -1591,6 +1678,7 @@ static int root_common(Instance* I, int root, int model, double* d_site, double*
 int tl_root_loglik(tl_instance* inst, int root, int model, double* out_logl, double* out_site) {
     CHECK_INST(inst);
     Instance* I = reinterpret_cast<Instance*>(inst);
+    if (int rc0 = activate_tip_pool(I)) return rc0;
     if (!out_logl) return fail(I, TL_ERR_ARG, "out_logl is null");
     int rc;
     if ((rc = ensure_out(I, 1 + (size_t)I->Ppad))) return rc;
@@ -1607,6 +1695,7 @@ int tl_root_loglik(tl_instance* inst, int root, int model, double* out_logl, dou
 int tl_root_loglik_dev(tl_instance* inst, int root, int model, double* out_logl_dev) {
     CHECK_INST(inst);
     Instance* I = reinterpret_cast<Instance*>(inst);
+    if (int rc0 = activate_tip_pool(I)) return rc0;
     if (!out_logl_dev) return fail(I, TL_ERR_ARG, "out is null");
     return root_common(I, root, model, nullptr, out_logl_dev);
 }
@@ -1680,6 +1769,7 @@ static int pre_common(Instance* I, const tl_pre_op* ops, int count, int model, i
 int tl_update_pre_partials(tl_instance* inst, const tl_pre_op* ops, int count, int model) {
     CHECK_INST(inst);
     Instance* I = reinterpret_cast<Instance*>(inst);
+    if (int rc0 = activate_tip_pool(I)) return rc0;
     for (int k = 0; k < count; ++k)
         for (int c = 0; c < 2; ++c)
             if (ops[k].edge[c] >= 0)
@@ -1694,6 +1784,7 @@ int tl_pre_order_gradient(tl_instance* inst, const tl_pre_op* ops, int count, in
                           double* out_grad, int n_grad) {
     CHECK_INST(inst);
     Instance* I = reinterpret_cast<Instance*>(inst);
+    if (int rc0 = activate_tip_pool(I)) return rc0;
     if (!out_grad && n_grad > 0) return fail(I, TL_ERR_ARG, "out_grad is null");
     int rc;
     if ((rc = ensure_out(I, (size_t)2 * std::max(n_grad, 1) + 16))) return rc;
@@ -1709,6 +1800,7 @@ int tl_pre_order_derivative(tl_instance* inst, const tl_pre_op* ops, int count, 
                             double* out, int n_out) {
     CHECK_INST(inst);
     Instance* I = reinterpret_cast<Instance*>(inst);
+    if (int rc0 = activate_tip_pool(I)) return rc0;
     if (!out && n_out > 0) return fail(I, TL_ERR_ARG, "out is null");
     // the FP64 generic path always forms u . (dmat p) from the stored
     // derivative matrix, so it needs no switch for general derivatives
@@ -1759,6 +1851,7 @@ int tl_pre_order_gradient_dev(tl_instance* inst, const tl_pre_op* ops, int count
                               double* out_grad_dev, int n_grad) {
     CHECK_INST(inst);
     Instance* I = reinterpret_cast<Instance*>(inst);
+    if (int rc0 = activate_tip_pool(I)) return rc0;
     if (!out_grad_dev && n_grad > 0) return fail(I, TL_ERR_ARG, "out_grad_dev is null");
     return pre_common(I, ops, count, model, n_grad, false, out_grad_dev);
 }
@@ -1767,6 +1860,7 @@ int tl_edge_derivatives(tl_instance* inst, const tl_edge* edges, int count, int 
                         double* out_grad, int n_grad) {
     CHECK_INST(inst);
     Instance* I = reinterpret_cast<Instance*>(inst);
+    if (int rc0 = activate_tip_pool(I)) return rc0;
     if (count < 0 || (count > 0 && !edges) || (n_grad > 0 && !out_grad))
         return fail(I, TL_ERR_ARG, "bad arguments");
     if (model < 0 || model >= I->n_models || !I->models[model].ready)

@@ -38,6 +38,9 @@ constexpr int kBChunk = kTcN * 32 * 4;      // 8 KB
 // Stage: A (2 x 16 KB) and B (2 x 8 KB) = 48 KB, four stages; with split
 // matrices a stage also holds B_lo (64 KB), so three fit; with split
 // partials also A_lo (96 KB), two stages.
+// Per-warp staging for coalesced stores of the epilogue's rows: 32 half rows.
+constexpr int kOutWarpBytes = 32 * 128;
+
 template <bool SPLIT, bool SPLITA>
 struct TcPipe {
     static constexpr int stages = SPLITA ? 2 : (SPLIT ? 3 : 4);
@@ -246,6 +249,7 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     // 128-byte swizzle atoms must start on 1024-byte shared-memory addresses
     unsigned char* stages = smem_tc + ((1024u - (smem_u32(smem_tc) & 1023u)) & 1023u);
+    unsigned char* wout = stages + kSt * kStB + (threadIdx.x >> 5) * kOutWarpBytes;
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;      // bit 0 empty, 1 full, 2 done wait gave up
@@ -543,18 +547,36 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
         // stored partials: TF32-rounded (the tensor core reads them exactly),
         // or full FP32 when A is split on chip
         auto rnd = [](float x) { return SPLITA ? x : to_tf32(x); };
-        auto store16 = [&](float* dst, const float* v, float f1, float f2) {
-            float4* o = reinterpret_cast<float4*>(dst);
+        // A 64-float row per thread (pattern), scaled and rounded, stored
+        // through the warp's staging area: half rows written with their
+        // 16-byte units XOR-swizzled by the row, read back four half rows
+        // per instruction and stored as whole cache lines (a plain store of
+        // one row per thread touches 32 lines per instruction).
+        // tile_base: row 0 of this warp's 32 patterns (row stride 64 floats).
+        auto store_row = [&](float* tile_base, const float* v, float f1, float f2) {
+            const int ln = tid & 31;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                float4 w;
-                w.x = rnd(v[4 * u] * f1 * f2);
-                w.y = rnd(v[4 * u + 1] * f1 * f2);
-                w.z = rnd(v[4 * u + 2] * f1 * f2);
-                w.w = rnd(v[4 * u + 3] * f1 * f2);
-                o[u] = w;
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int i = h * 32 + 4 * j;
+                    *reinterpret_cast<float4*>(wout + ln * 128 + ((j ^ (ln & 7)) << 4)) =
+                        make_float4(rnd(v[i] * f1 * f2), rnd(v[i + 1] * f1 * f2),
+                                    rnd(v[i + 2] * f1 * f2), rnd(v[i + 3] * f1 * f2));
+                }
+                __syncwarp();
+                const int u = ln & 7;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = 4 * i + (ln >> 3);
+                    const float4 f =
+                        *reinterpret_cast<const float4*>(wout + rr * 128 + ((u ^ (rr & 7)) << 4));
+                    *reinterpret_cast<float4*>(tile_base + (size_t)rr * kTcN + h * 32 + 4 * u) = f;
+                }
+                __syncwarp();
             }
         };
+        const size_t wrow0 = (size_t)(p0 + warp * 32) * kTcN;   // this warp's first row
         const bool real = p < a.Ppad;  // always true (tiles cover Ppad)
         const float wp = (p < a.Ppad) ? (float)a.patw[p] : 0.f;
 
@@ -579,13 +601,11 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
             float f1 = 1.f, f2 = 1.f;
             if (a.rescale) cum += scale_of(m, &f1, &f2);
             // pass 2: rescale, round to TF32, store
-            float* dst = a.pool + (size_t)op.dest * a.bstride + (size_t)p * kTcN;
+            float* dst = a.pool + (size_t)op.dest * a.bstride + wrow0;
             for (int r = 0; r < R; ++r) {
                 float z[64];
                 tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN), z);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, z + 16 * q, f1, f2);
+                store_row(dst + (size_t)r * a.Ppad * kTcN, z, f1, f2);
             }
             a.epool[(size_t)op.dest * a.Ppad + p] = cum;
         } else if (MODE == kPre1) {
@@ -661,13 +681,11 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                 if (op.uout[c] < 0) continue;
                 float f1, f2;
                 const int e = scale_of(mu[c], &f1, &f2);
-                float* dst = a.pool + (size_t)op.uout[c] * a.bstride + (size_t)p * kTcN;
+                float* dst = a.pool + (size_t)op.uout[c] * a.bstride + wrow0;
                 for (int r = 0; r < R; ++r) {
                     float u[64];
                     tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN + c * kTcN), u);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, u + 16 * q, f1, f2);
+                    store_row(dst + (size_t)r * a.Ppad * kTcN, u, f1, f2);
                 }
                 float d = den;
                 if (e != 0) d = (-e >= -126 && -e <= 126) ? den * pow2f(-e)
@@ -707,13 +725,11 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
             }
             float f1, f2;
             scale_of(m, &f1, &f2);
-            float* dst = a.pool + (size_t)op.dest * a.bstride + (size_t)p * kTcN;
+            float* dst = a.pool + (size_t)op.dest * a.bstride + wrow0;
             for (int r = 0; r < R; ++r) {
                 float x[64];
                 tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN), x);
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, x + 16 * q, f1, f2);
+                store_row(dst + (size_t)r * a.Ppad * kTcN, x, f1, f2);
             }
         }
         (void)real;
@@ -858,8 +874,8 @@ __global__ void k_q_tc(const double* __restrict__ Q, float* __restrict__ dst, in
 
 template <int MODE, bool SPLIT, bool SPLITA>
 void launch_mode_t(Instance* I, const TcOp* d, int n, TcArgs a) {
-    const size_t smem =
-        (size_t)TcPipe<SPLIT, SPLITA>::stages * TcPipe<SPLIT, SPLITA>::bytes + 1024;
+    const size_t smem = (size_t)TcPipe<SPLIT, SPLITA>::stages * TcPipe<SPLIT, SPLITA>::bytes +
+                        4 * kOutWarpBytes + 1024;
     cudaFuncSetAttribute(k_tc<MODE, SPLIT, SPLITA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int sms = 0, dev_id = 0;
@@ -930,17 +946,26 @@ struct __align__(16) FuseOp {
     int look[2];      // float offset of P^T, category 0 (tip lookups)
     int dest;         // output buffer (pool index)
     int prev;         // the child (0, 1) that is the previous op's result; -1 none
-    int pad[6];
+    int src[2];       // op of this list that stores child c (read from HBM); -1 none
+    int tbrow[2];     // matrix-map row of P^T, category 0 (tip lookups from shared memory)
+    int pad[2];
 };
 static_assert(sizeof(FuseOp) == kTcOpBytes, "fused descriptor size");
 
 constexpr int kFuseThreads = 192;
 constexpr int kPrevCols = 256;   // TMEM columns of the on-chip result
 
+// MMA stages (A, B, B_lo), then a two-slot ring of P^T blocks (P^T_lo)
+// for the epilogue's tip lookups.
 template <bool SPLIT>
 struct FusePipe {
-    static constexpr int stages = SPLIT ? 3 : 4;
+    static constexpr int stages = SPLIT ? 2 : 3;
     static constexpr int bytes = 2 * kAChunk + (SPLIT ? 4 : 2) * kBChunk;
+    static constexpr int tip_slots = 2;
+    static constexpr int tip_bytes = (SPLIT ? 4 : 2) * kBChunk;
+    static constexpr int out_bytes = 4 * 32 * 128;   // per epilogue warp: 32 half rows
+    static constexpr size_t smem =
+        (size_t)stages * bytes + (size_t)tip_slots * tip_bytes + out_bytes;
 };
 
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, unsigned parity,
@@ -966,6 +991,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __device__ __forceinline__ void st_release_cta(unsigned* p, unsigned v) {
     asm volatile("st.release.cta.shared::cta.u32 [%0], %1;\n" ::"r"(smem_u32(p)), "r"(v) : "memory");
 }
+// Generic-proxy global stores made visible to later async-proxy (TMA) reads.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;\n" ::: "memory");
+}
 __device__ __forceinline__ unsigned ld_acquire_cta(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];\n" : "=r"(v) : "r"(smem_u32(p)) : "memory");
@@ -989,15 +1018,16 @@ k_tc_fused(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ 
     constexpr int kSt = FusePipe<SPLIT>::stages;
     constexpr int kStB = FusePipe<SPLIT>::bytes;
     constexpr int kBOff = 2 * kAChunk;
-    const size_t kLoFloats = (size_t)2 * a.R * kTcN * kTcN;  // hi block -> lo block
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     unsigned char* stages = smem_tc + ((1024u - (smem_u32(smem_tc) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2],
-        done;
+        tip_full[2], tip_empty[2], done;
+    unsigned char* tip_area = stages + kSt * kStB;
+    unsigned char* out_area = tip_area + FusePipe<SPLIT>::tip_slots * FusePipe<SPLIT>::tip_bytes;
     __shared__ uint32_t tmem_base_sh;
-    __shared__ int abort_sh;          // bit 0 empty, 1 full, 2 acc_empty, 3 acc_full, 4 op-done
+    __shared__ int abort_sh;  // bit 0 empty, 1 full, 2 acc_empty, 3 acc_full, 4/6 op done
     __shared__ unsigned ready_sh[4];  // ops each epilogue warp has finished
-    __shared__ unsigned loads_sh, used_sh;
+    __shared__ unsigned loads_sh, used_sh, tip_loads_sh, tip_used_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     volatile int* abort_v = &abort_sh;
 
@@ -1017,11 +1047,13 @@ k_tc_fused(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ 
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], 4);   // one arrival per epilogue warp
+            mbar_init(&tip_full[b], 1);
+            mbar_init(&tip_empty[b], 4);
         }
         mbar_init(&done, 1);
         abort_sh = 0;
         for (int w = 0; w < 4; ++w) ready_sh[w] = 0;
-        loads_sh = used_sh = 0;
+        loads_sh = used_sh = tip_loads_sh = tip_used_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     tc_fence_before();
@@ -1036,13 +1068,50 @@ k_tc_fused(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ 
     if (warp == 0) {
         // ---- TMA producer ----------------------------------------------------
         if (lane == 0) {
-            unsigned g = 0;
-            for (int tile = blockIdx.x; tile < a.n_tiles && !*abort_v; tile += gridDim.x) {
+            unsigned g = 0, gt = 0, base = 0;   // base: ops of earlier tiles
+            for (int tile = blockIdx.x; tile < a.n_tiles && !*abort_v; tile += gridDim.x,
+                     base += (unsigned)n_ops) {
                 const int q0 = tile * kTcM;
                 for (int k = 0; k < n_ops && !*abort_v; ++k) {
                     const FuseOp o = ops[k];
+                    // a child this launch stores is read only after the
+                    // epilogue of the op that stores it is done with it
+                    for (int c = 0; c < 2; ++c) {
+                        if (o.src[c] < 0 || o.prev == c) continue;
+                        const unsigned need = base + (unsigned)o.src[c] + 1;
+                        const unsigned long long t0 = global_ns();
+                        for (int w = 0; w < 4 && !*abort_v; ++w)
+                            while (ld_acquire_cta(&ready_sh[w]) < need) {
+                                if (*abort_v || global_ns() - t0 > kWaitNs) {
+                                    atomicOr(&abort_sh, 64);
+                                    break;
+                                }
+                            }
+                        fence_proxy_async_global();
+                    }
                     for (int r = 0; r < R && !*abort_v; ++r)
                         for (int c = 0; c < 2; ++c) {
+                            if (o.kind[c] == kTipStates) {
+                                // the P^T block (and its lo block) of the tip's
+                                // edge for the epilogue's row lookups
+                                const int ts = gt % 2;
+                                if (!mbar_wait_or_abort(&tip_empty[ts], ((gt / 2) & 1) ^ 1, abort_v)) {
+                                    atomicOr(&abort_sh, 1);
+                                    break;
+                                }
+                                unsigned char* tb = tip_area + ts * FusePipe<SPLIT>::tip_bytes;
+                                mbar_expect_tx(&tip_full[ts], FusePipe<SPLIT>::tip_bytes);
+                                const int trow = o.tbrow[c] + r * kTcN;
+                                tma_load_2d(tb, &tm_mat, 0, trow, &tip_full[ts]);
+                                tma_load_2d(tb + kBChunk, &tm_mat, 32, trow, &tip_full[ts]);
+                                if (SPLIT) {
+                                    const int lrow = trow + 2 * R * kTcN;
+                                    tma_load_2d(tb + 2 * kBChunk, &tm_mat, 0, lrow, &tip_full[ts]);
+                                    tma_load_2d(tb + 3 * kBChunk, &tm_mat, 32, lrow, &tip_full[ts]);
+                                }
+                                ++gt;
+                                continue;
+                            }
                             if (!on_mma(o, c)) continue;
                             const int s = g % kSt;
                             if (!mbar_wait_or_abort(&empty[s], ((g / kSt) & 1) ^ 1, abort_v)) {
@@ -1072,6 +1141,7 @@ k_tc_fused(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ 
                 }
             }
             loads_sh = g;
+            tip_loads_sh = gt;
         }
     } else if (warp == 1) {
         // ---- MMA issuer ------------------------------------------------------
@@ -1149,58 +1219,108 @@ k_tc_fused(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ 
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         unsigned cat = 0, nop = 0;
         bool ok = true;
-        auto store16 = [&](float* dst, const float* v) {
-            float4* o4 = reinterpret_cast<float4*>(dst);
+        // Stores go out through a per-warp shared-memory transpose: each
+        // thread holds one pattern's row (256 bytes), and a store of the
+        // rows as they are would touch 32 cache lines per instruction. Half
+        // rows (128 bytes) are written with the 16-byte units XOR-swizzled by
+        // the row (j ^ (row & 7): 4-way conflicts instead of 32), read back
+        // four whole half rows per instruction and stored as full lines.
+        unsigned char* wout = out_area + quarter * 32 * 128;
+        auto store_row = [&](float* tile_base, const float* z) {
+            // tile_base: row 0 of this warp's 32 rows (row stride 64 floats)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) o4[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    *reinterpret_cast<float4*>(wout + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+                        make_float4(z[h * 32 + 4 * j], z[h * 32 + 4 * j + 1], z[h * 32 + 4 * j + 2],
+                                    z[h * 32 + 4 * j + 3]);
+                __syncwarp();
+                const int u = lane & 7;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int rr = 4 * i + (lane >> 3);
+                    const float4 f =
+                        *reinterpret_cast<const float4*>(wout + rr * 128 + ((u ^ (rr & 7)) << 4));
+                    *reinterpret_cast<float4*>(tile_base + (size_t)rr * kTcN + h * 32 + 4 * u) = f;
+                }
+                __syncwarp();
+            }
+        };
+        unsigned gt = 0;   // tip blocks consumed
+        // per-pattern inputs of an op: tip state codes and exponents of the
+        // children read from HBM, loaded one op ahead
+        auto op_inputs = [&](const FuseOp& o, int p, int* sv, int* ev) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                sv[c] = o.kind[c] == kTipStates ? (int)a.tips[(size_t)o.child[c] * a.Ppad + p] : 0;
+                ev[c] = (o.kind[c] == kInternal && o.prev != c)
+                            ? a.epool[(size_t)o.child[c] * a.Ppad + p] : 0;
+            }
         };
         for (int tile = blockIdx.x; ok && tile < a.n_tiles; tile += gridDim.x) {
             const int p = tile * kTcM + row;
             int cum_prev = 0;
+            int sv_n[2] = {0, 0}, ev_n[2] = {0, 0};
+            if (n_ops > 0) op_inputs(ops[0], p, sv_n, ev_n);
             for (int k = 0; ok && k < n_ops; ++k, ++nop) {
                 const FuseOp o = ops[k];
-                int cum = 0, sidx[2] = {0, 0};
+                int cum = 0, sidx[2] = {sv_n[0], sv_n[1]};
                 bool amb[2] = {false, false};
                 for (int c = 0; c < 2; ++c) {
-                    if (o.kind[c] == kInternal)
-                        cum += (o.prev == c) ? cum_prev : a.epool[(size_t)o.child[c] * a.Ppad + p];
-                    if (o.kind[c] == kTipStates) {
-                        const int s = a.tips[(size_t)o.child[c] * a.Ppad + p];
-                        amb[c] = !(s >= 0 && s < a.S);
-                        sidx[c] = s;
-                    }
+                    if (o.kind[c] == kInternal) cum += (o.prev == c) ? cum_prev : ev_n[c];
+                    if (o.kind[c] == kTipStates) amb[c] = !(sidx[c] >= 0 && sidx[c] < a.S);
                 }
-                // a tip's row of P^T (+ the lo row with split matrices), or
-                // the row sums of P for an ambiguous code
-                auto lookup64 = [&](int c, int r, float* v) {
-                    const int slot_base = o.look[c];
-                    const float* src =
-                        amb[c] ? a.rowsum + (size_t)(slot_base / ((SPLIT ? 4 : 2) * R * kTcN * kTcN)) *
-                                                R * kTcN + (size_t)r * kTcN
-                               : a.matw + (size_t)slot_base + (size_t)r * kTcN * kTcN +
-                                     (size_t)sidx[c] * kTcN;
-                    const float4* s4 = reinterpret_cast<const float4*>(src);
-                    float4 f[16];
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) f[u] = __ldg(s4 + u);
-                    if (SPLIT && !amb[c]) {
-                        const float4* l4 = reinterpret_cast<const float4*>(src + kLoFloats);
+                if (k + 1 < n_ops) op_inputs(ops[k + 1], p, sv_n, ev_n);
+                // a tip's row of P^T (+ the lo row with split matrices) from the
+                // block the TMA warp staged (128-byte swizzle: 16-byte unit j
+                // of row s sits at unit j ^ (s & 7)), or the row sums of P for
+                // an ambiguous code; false if the wait for the block gave up
+                auto lookup64 = [&](int c, int r, float* v) -> bool {
+                    const int ts = gt % 2;
+                    const bool got = mbar_wait_or_abort(&tip_full[ts], (gt / 2) & 1, abort_v);
+                    if (!__all_sync(0xffffffffu, got)) return false;
+                    const unsigned char* tb = tip_area + ts * FusePipe<SPLIT>::tip_bytes;
+                    if (amb[c]) {
+                        const float* src =
+                            a.rowsum + (size_t)(o.look[c] / ((SPLIT ? 4 : 2) * R * kTcN * kTcN)) *
+                                           R * kTcN + (size_t)r * kTcN;
+                        const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
                         for (int u = 0; u < 16; ++u) {
-                            const float4 l = __ldg(l4 + u);
-                            f[u].x += l.x;
-                            f[u].y += l.y;
-                            f[u].z += l.z;
-                            f[u].w += l.w;
+                            const float4 f = __ldg(s4 + u);
+                            v[4 * u] = f.x;
+                            v[4 * u + 1] = f.y;
+                            v[4 * u + 2] = f.z;
+                            v[4 * u + 3] = f.w;
                         }
-                    }
+                    } else {
+                        const int sr = sidx[c];
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        v[4 * u] = f[u].x;
-                        v[4 * u + 1] = f[u].y;
-                        v[4 * u + 2] = f[u].z;
-                        v[4 * u + 3] = f[u].w;
+                        for (int h = 0; h < 2; ++h)
+#pragma unroll
+                            for (int j = 0; j < 8; ++j) {
+                                const int off = h * kBChunk + sr * 128 + ((j ^ (sr & 7)) << 4);
+                                float4 f = *reinterpret_cast<const float4*>(tb + off);
+                                if (SPLIT) {
+                                    const float4 l =
+                                        *reinterpret_cast<const float4*>(tb + 2 * kBChunk + off);
+                                    f.x += l.x;
+                                    f.y += l.y;
+                                    f.z += l.z;
+                                    f.w += l.w;
+                                }
+                                const int i = h * 32 + j * 4;
+                                v[i] = f.x;
+                                v[i + 1] = f.y;
+                                v[i + 2] = f.z;
+                                v[i + 3] = f.w;
+                            }
                     }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tip_empty[ts]);
+                    ++gt;
+                    return true;
                 };
                 // pass 1: products of the two children per category, their
                 // maximum; the unscaled products go to the A columns
@@ -1219,10 +1339,16 @@ k_tc_fused(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ 
                     tc_fence_after();
                     float x[64], y[64];
                     const uint32_t acc = lane_base + (uint32_t)(kPrevCols + b * 2 * kTcN);
+                    bool got2 = true;
                     if (on_mma(o, 0)) tmem_ld64(acc, x);
-                    else lookup64(0, r, x);
-                    if (on_mma(o, 1)) tmem_ld64(acc + kTcN, y);
-                    else lookup64(1, r, y);
+                    else got2 = lookup64(0, r, x);
+                    if (got2 && on_mma(o, 1)) tmem_ld64(acc + kTcN, y);
+                    else if (got2) got2 = lookup64(1, r, y);
+                    if (!got2) {
+                        ok = false;
+                        if (lane == 0) atomicOr(&abort_sh, 128);
+                        break;
+                    }
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&acc_empty[b]);
@@ -1248,32 +1374,37 @@ k_tc_fused(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ 
                     }
                     cum += e;
                 }
-                float* dst = a.pool + (size_t)o.dest * a.bstride + (size_t)p * kTcN;
+                // row 0 of this warp's 32 patterns in the output buffer
+                float* dst = a.pool + (size_t)o.dest * a.bstride +
+                             (size_t)(tile * kTcM + quarter * 32) * kTcN;
                 for (int r = 0; r < R; ++r) {
                     float z[64];
                     tmem_ld64(lane_base + (uint32_t)(r * kTcN), z);
 #pragma unroll
                     for (int i = 0; i < 64; ++i) z[i] = to_tf32(z[i] * f1 * f2);
                     tmem_st64(lane_base + (uint32_t)(r * kTcN), z);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) store16(dst + (size_t)r * a.Ppad * kTcN + q * 16, z + 16 * q);
+                    store_row(dst + (size_t)r * a.Ppad * kTcN, z);
                 }
                 a.epool[(size_t)o.dest * a.Ppad + p] = cum;
                 cum_prev = cum;
                 // this warp's rows of the op are done and may be read from
-                // TMEM (each warp publishes its own count: no barrier among
-                // the epilogue warps, which an abort could leave unmatched)
+                // TMEM, and its stores by the copy engine (each warp
+                // publishes its own count: no barrier among the epilogue
+                // warps, which an abort could leave unmatched)
+                fence_proxy_async_global();
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) st_release_cta(&ready_sh[quarter], nop + 1);
             }
         }
+        if (warp == 2 && lane == 0) tip_used_sh = gt;
     }
     __syncthreads();
     if (abort_sh && tid == 0) {
         atomicOr(a.err, (abort_sh & 0xff) | (1 << 11));
         // bounded drain of copies still in flight
         for (unsigned g = used_sh; g < loads_sh; ++g) mbar_wait(&full[g % kSt], (g / kSt) & 1);
+        for (unsigned g = tip_used_sh; g < tip_loads_sh; ++g) mbar_wait(&tip_full[g % 2], (g / 2) & 1);
     }
     tc_fence_before();
     __syncthreads();
@@ -1369,6 +1500,8 @@ int tc_fused_enabled(const Instance* I) {
 int launch_post_tc_fused(Instance* I, const DevPostOp* plan_ops, int n, void* d_ops_area,
                          size_t cap) {
     std::vector<FuseOp> dev(n);
+    std::vector<int> writer(I->n_buffers, -1);   // op of this list storing each buffer
+    for (int k = 0; k < n; ++k) writer[plan_ops[k].dest] = k;
     for (int k = 0; k < n; ++k) {
         const DevPostOp& d = plan_ops[k];
         FuseOp& f = dev[k];
@@ -1379,7 +1512,12 @@ int launch_post_tc_fused(Instance* I, const DevPostOp* plan_ops, int n, void* d_
             f.kind[c] = d.kind[c];
             f.brow[c] = brow_of(I, d.mat[c], 0);
             f.look[c] = look_of(I, d.mat[c], 1);
-            if (d.kind[c] == kInternal && d.slot_in[c] == kFromRegisters) f.prev = c;
+            f.tbrow[c] = brow_of(I, d.mat[c], 1);
+            f.src[c] = -1;
+            if (d.kind[c] == kInternal) {
+                if (d.slot_in[c] == kFromRegisters) f.prev = c;
+                else f.src[c] = writer[d.child[c]] < k ? writer[d.child[c]] : -1;
+            }
         }
         f.dest = d.dest;
     }
@@ -1394,11 +1532,11 @@ int launch_post_tc_fused(Instance* I, const DevPostOp* plan_ops, int n, void* d_
     const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(I->tmaps.data());
     const FuseOp* d = reinterpret_cast<const FuseOp*>(d_ops_area);
     if (I->split) {
-        const size_t smem = (size_t)FusePipe<true>::stages * FusePipe<true>::bytes + 1024;
+        const size_t smem = FusePipe<true>::smem + 1024;
         cudaFuncSetAttribute(k_tc_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_tc_fused<true><<<grid, kFuseThreads, smem, I->stream>>>(m[0], m[1], m[2], d, n, a);
     } else {
-        const size_t smem = (size_t)FusePipe<false>::stages * FusePipe<false>::bytes + 1024;
+        const size_t smem = FusePipe<false>::smem + 1024;
         cudaFuncSetAttribute(k_tc_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_tc_fused<false><<<grid, kFuseThreads, smem, I->stream>>>(m[0], m[1], m[2], d, n, a);
     }
