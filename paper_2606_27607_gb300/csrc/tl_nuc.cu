@@ -70,6 +70,28 @@ template <typename T>
 __device__ __forceinline__ T vmax(V4<T> a) {
     return fmax(fmax(a.x, a.y), fmax(a.z, a.w));
 }
+// max(a, b, c) in one instruction for FP32 (sm_100 and later)
+__device__ __forceinline__ float max3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ double max3(double a, double b, double c) { return fmax(fmax(a, b), c); }
+// the largest of the CPL V4 values (a tree of three-input maxima)
+template <int CPL, typename T>
+__device__ __forceinline__ T vmax_all(const V4<T>* v) {
+    if constexpr (CPL == 4) {
+        const T a = max3(v[0].x, v[0].y, v[0].z), b = max3(v[0].w, v[1].x, v[1].y);
+        const T c = max3(v[1].z, v[1].w, v[2].x), d = max3(v[2].y, v[2].z, v[2].w);
+        const T e = max3(v[3].x, v[3].y, v[3].z);
+        return max3(max3(a, b, c), max3(d, e, v[3].w), T(0));
+    } else {
+        T m = vmax(v[0]);
+#pragma unroll
+        for (int j = 1; j < CPL; ++j) m = fmax(m, vmax(v[j]));
+        return m;
+    }
+}
 
 // ---- packed FP32 pairs (fma/mul/add .f32x2 of sm_100 and later): two
 // lanes of a V4<float> per instruction, each rounded exactly as the scalar
@@ -284,6 +306,13 @@ struct WarpPipe {
     Op* obuf;
     T* mbuf;
     int matf;
+    int per;       // 16-byte chunks per matrix
+    int m0, c0;    // this lane's first chunk: matrix m0, chunk c0 (lane = m0 per + c0)
+    __device__ __forceinline__ void init(int lane) {
+        per = matf * (int)sizeof(T) / 16;
+        m0 = lane / per;
+        c0 = lane - m0 * per;
+    }
     __device__ __forceinline__ void issue_op(const Op* ops, int j, int n, int lane) {
         constexpr int chunks = sizeof(Op) / 16;
         if (j < n && lane < chunks)
@@ -297,12 +326,13 @@ struct WarpPipe {
                                                int mat_stride, int lane) {
         if (j >= n) return;
         T* dst = mbuf + (j & 1) * NMAT * matf;
-        const int per = matf * (int)sizeof(T) / 16;
         int slots[NMAT];
 #pragma unroll
         for (int m = 0; m < NMAT; ++m) slots[m] = idx[m];
-        for (int q = lane; q < NMAT * per; q += 32) {
-            const int m = q / per, c = q % per;
+        // the lane's chunks lane, lane + 32, ... walked as (matrix, chunk)
+        // pairs: no division per chunk
+        int m = m0, c = c0;
+        while (m < NMAT) {
             int slot = slots[0];
 #pragma unroll
             for (int i = 1; i < NMAT; ++i)
@@ -310,7 +340,13 @@ struct WarpPipe {
             if (slot >= 0)
                 cp_async16(reinterpret_cast<char*>(dst + m * matf) + c * 16,
                            reinterpret_cast<const char*>(mat + (size_t)slot * mat_stride) + c * 16);
+            c += 32;
+            while (c >= per) {
+                c -= per;
+                ++m;
+            }
         }
+        (void)lane;
     }
     __device__ __forceinline__ const T* mats(int k) const { return mbuf + (k & 1) * NMAT * matf; }
 };
@@ -361,6 +397,7 @@ k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ 
     pipe.obuf = reinterpret_cast<DevPostOp*>(pipe_base + (size_t)warp * pipe_bytes<DevPostOp, T, 2>(R));
     pipe.mbuf = reinterpret_cast<T*>(pipe.obuf + 3);
     pipe.matf = kColStride * 4 * R;
+    pipe.init(lane);
     BatchJob<T>* stage = reinterpret_cast<BatchJob<T>*>(
         pipe_base + (size_t)kWarpsPerBlock * pipe_bytes<DevPostOp, T, 2>(R)) + warp;
     const NucArgs<T>& a = pick_args<BATCH>(a_, stage);
@@ -498,9 +535,7 @@ k_post4(const DevPostOp* __restrict__ ops_, int n_ops_, const __grid_constant__ 
 #pragma unroll
             for (int i = 0; i < PPL; ++i) {
                 if (a.rescale) {
-                    T m = vmax(acc[i][0]);
-#pragma unroll
-                    for (int j = 1; j < CPL; ++j) m = fmax(m, vmax(acc[i][j]));
+                    T m = vmax_all<CPL>(acc[i]);
 #pragma unroll
                     for (int o = 1; o < LPP; o <<= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
                     const int e = frexp_exp(m);
@@ -669,6 +704,7 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
     pipe.obuf = reinterpret_cast<DevPreOp*>(pipe_base + (size_t)warp * pipe_bytes<DevPreOp, T, 4>(R));
     pipe.mbuf = reinterpret_cast<T*>(pipe.obuf + 3);
     pipe.matf = kColStride * 4 * R;
+    pipe.init(lane);
     BatchJob<T>* stage = reinterpret_cast<BatchJob<T>*>(
         pipe_base + (size_t)kWarpsPerBlock * pipe_bytes<DevPreOp, T, 4>(R)) + warp;
     // gradient terms of up to kEdgeBuf edges, [edge][lane] (row stride 33),
@@ -851,31 +887,29 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
             }
             // q outputs: rescaled when out of range, then to a slot, the
             // op's buffer and/or the registers the next op reads
-    #pragma unroll
+#pragma unroll
             for (int c = 0; c < 2; ++c) {
                 if (!(c == 0 ? nq0 : nq1)) continue;
                 V4<T>* qc = c == 0 ? qa : qb;
-                T m = vmax(qc[0]);
-    #pragma unroll
-                for (int j = 1; j < CPL; ++j) m = fmax(m, vmax(qc[j]));
-    #pragma unroll
+                T m = vmax_all<CPL>(qc);
+#pragma unroll
                 for (int o = 1; o < LPP; o <<= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
                 const int e = frexp_exp(m);
                 if (e < -kQRange || e > kQRange) scale_by_pow2(qc, CPL, -e);
                 const int so = op.q_slot_out[c];
                 if (so >= 0) {
-    #pragma unroll
+#pragma unroll
                     for (int j = 0; j < CPL; ++j) slots[(so * CPL + j) * 32 + lane] = qc[j];
                 }
                 const int bo = op.q_buf_out[c];
                 if (bo >= 0) {
                     T* b = a.pool + (size_t)bo * a.bstride + off0;
-    #pragma unroll
+#pragma unroll
                     for (int j = 0; j < CPL; ++j)
                         if (act[j]) st4(b + j * offj, qc[j]);
                 }
                 if (op.q_reg == c) {
-    #pragma unroll
+#pragma unroll
                     for (int j = 0; j < CPL; ++j) prevq[j] = qc[j];
                 }
             }
