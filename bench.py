@@ -537,7 +537,7 @@ def serving_line(args) -> dict:
                 "served_vs_fp64_rel_err_p99": _pct(base_err, 99)}
     return {"metric": "serving requests/s and p50/p99 latency (s) at offered load",
             "value": capacity, "unit": "requests/s", "n_gpus": 1, "higher_is_better": True,
-            "dtype": "f32 (4-state), tf32x2 (codon)", "data": "synthetic",
+            "dtype": "f32 (4-state), tf32x3 (codon)", "data": "synthetic",
             "config": {"workload": "serving", "requests": len(reqs), "chains": len(chains),
                        "codon_requests": int(n_codon),
                        "gradient_requests": int(sum(r.gradient for r in reqs)),
@@ -571,8 +571,9 @@ def autograd_line(args) -> dict:
     out, methods = {}, {}
     eps = synth.random_effects()
     for name, base, precs, model in (("gtr_1024x50k", "gtr_1024x50k", ("f64", "f32"), "gtr"),
-                                     ("gy94_64x5k", "gy94_64x5k", ("f64", "tf32", "tf32x2"), "gy94"),
-                                     ("gy94re_64x5k", "gy94_64x5k", ("f64", "tf32x2"), "gy94re")):
+                                     ("gy94_64x5k", "gy94_64x5k", ("f64", "tf32", "tf32x2", "tf32x3"),
+                                      "gy94"),
+                                     ("gy94re_64x5k", "gy94_64x5k", ("f64", "tf32x3"), "gy94re")):
         w = synth.workload(base)
         params = np.r_[w.params, eps] if model == "gy94re" else np.asarray(w.params, float)
         res, ref = {}, None
@@ -603,6 +604,8 @@ def autograd_line(args) -> dict:
                 r["rel_err_grad_t"] = float(np.linalg.norm(gt - ref[1]) / np.linalg.norm(ref[1]))
                 r["rel_err_grad_theta"] = float(np.max(np.abs(gk - ref[2])) /
                                                 np.max(np.abs(ref[2])))
+                r["grad_err_per_component_t"] = per_component_err(gt, ref[1])
+                r["grad_err_per_component_theta"] = per_component_err(gk, ref[2])
             res[prec] = r
             if prec == precs[-1]:
                 # the substitution gradient of the backward by three methods
@@ -898,11 +901,18 @@ def main() -> None:
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (algorithmic bytes of one launch)
+    # roofline of the dominant kernel. Algorithmic bytes per unit (pattern x
+    # internal node) of the plain level-by-level formulation: post-order
+    # 131 B (an internal child's 64 B partial read, a tip's state byte, the
+    # 64 B partial and 2 B exponent written), pre-order and gradient 193 B
+    # per parent (q 64 B read, the children's partials 65 B, q 64 B
+    # written). The fused tile walks move less (children handed over on
+    # chip, q never stored): their compulsory bytes are in "compulsory".
     hbm, src = peaks()
     RS = R * 4 * 4  # bytes of one pattern's FP32 partial, all categories
-    alg = {"post": P * ((N - 1) * (RS + 4) + N * 1),
-           "pre": P * ((N - 2) * RS + N * 1) + 8 * (2 * N - 2) * ((P + 31) // 32)}
+    alg = {"post": 131 * P * (N - 1), "pre": 193 * P * (N - 1)}
+    comp = {"post": P * ((N - 1) * (RS + 4) + N * 1),
+            "pre": P * ((N - 2) * RS + N * 1) + 8 * (2 * N - 2) * ((P + 31) // 32)}
     dom = max(k_ms, key=k_ms.get)
     ach = alg[dom] / (k_ms[dom] * 1e-3) / 1e9
     lpp = int(os.environ.get("TL_NUC_LANES", "1"))
@@ -915,8 +925,12 @@ def main() -> None:
     roof = {"bound": "hbm", "kernel": kname, "achieved": ach, "peak": hbm, "unit": "GB/s",
             "frac": ach / hbm, "peak_source": src, "traffic": traffic,
             "algorithmic_bytes": alg[dom], "ms": k_ms[dom],
+            "bytes_per_unit": {"post": 131, "pre": 193, "units": P * (N - 1)},
             "other": {k: {"ms": k_ms[k], "GB/s": alg[k] / (k_ms[k] * 1e-3) / 1e9,
-                          "frac": alg[k] / (k_ms[k] * 1e-3) / 1e9 / hbm} for k in k_ms}}
+                          "frac": alg[k] / (k_ms[k] * 1e-3) / 1e9 / hbm,
+                          "compulsory_bytes": comp[k],
+                          "compulsory_frac": comp[k] / (k_ms[k] * 1e-3) / 1e9 / hbm}
+                      for k in k_ms}}
 
     codon = codon_split = codon_x3 = codon64 = fp64 = None
     if not args.no_codon and world == 1:

@@ -657,11 +657,13 @@ k_root4(int kind_, int root_, const __grid_constant__ NucArgs<T> a_, const doubl
 // ---------------------------------------------------------------------------
 // fused pre-order pass + branch-length gradient
 // ---------------------------------------------------------------------------
-// Pre-order partials are rescaled only when their per-pattern maximum
-// leaves [2^-kQRange, 2^kQRange]: the branch-length ratios do not depend on
-// the scale of q, so the exact power-of-two scaling only has to keep the
-// products away from underflow and overflow.
-constexpr int kQRange = 32;
+// Pre-order partials are rescaled to a per-pattern maximum in [0.5, 1)
+// (an exact power of two) after every op. The branch-length ratios do not
+// depend on the scale of q, but the ratio's denominator q . (v_a o v_b) must
+// stay inside the FP32 range: its states need not line up with q's maximum,
+// so a q left small (a lazier rescaling) drove it below the smallest normal
+// value on deep trees.
+constexpr int kQRange = 0;
 // Edges whose per-pattern gradient terms a warp buffers before summing them.
 constexpr int kEdgeBuf = 16;
 
@@ -895,7 +897,7 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
 #pragma unroll
                 for (int o = 1; o < LPP; o <<= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
                 const int e = frexp_exp(m);
-                if (e < -kQRange || e > kQRange) scale_by_pow2(qc, CPL, -e);
+                if (e < -kQRange || e > kQRange) scale_by_pow2(qc, CPL, -e);   // e != 0
                 const int so = op.q_slot_out[c];
                 if (so >= 0) {
 #pragma unroll
@@ -914,9 +916,10 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
                 }
             }
         };
-        // one call site (a second inlined copy could round FP64 differently
-        // from the first, and which copy an op took would depend on its
-        // position in the list)
+        // one call site: a second inlined copy of the op body costs registers
+        // (it spilled, 3.96 against 2.44 ms at 512 x 100k) and could round
+        // FP64 differently from the first (contractions are the compiler's
+        // choice there), with the copy an op took depending on its position
         for (int k = 0; k < n_ops; ++k) {
             op_body(k, xA, xB, tsA, tsB);
             tsA[0] = tsB[0];

@@ -136,6 +136,12 @@ class Server:
         self.inflight: list[_Group] = []
         self.stats = collections.Counter()
         self.group_sizes: list[int] = []
+        # FP64 re-evaluations run on a worker thread (the library calls
+        # release the interpreter lock) on a stream of their own, so the
+        # scheduling loop keeps serving while one runs
+        self._fb_pool = None
+        self._fb_stream = None
+        self._fallbacks: list = []   # (pending, group size, worker future, bytes, start)
 
     # chains ---------------------------------------------------------------
     def add_chain(self, data) -> int:
@@ -256,7 +262,8 @@ class Server:
         return f
 
     def pending(self) -> int:
-        return len(self.queue) + sum(len(g.items) for g in self.inflight)
+        return (len(self.queue) + sum(len(g.items) for g in self.inflight) +
+                len(self._fallbacks))
 
     def _complete(self) -> int:
         done = 0
@@ -278,23 +285,73 @@ class Server:
                 bad = not np.isfinite(logl) or (grad is not None and
                                                  not np.all(np.isfinite(grad)))
                 if bad and c.precision != "f64":
-                    # reduced precision can lose a pattern entirely: one
+                    # Reduced precision can lose a pattern entirely: one
                     # exponent per pattern spans all categories, so categories
                     # whose likelihoods differ by more than FP32's range at a
-                    # node underflow, and two children may keep disjoint ones.
-                    # The request is evaluated again in FP64 (its latency
+                    # node underflow, and two children may keep disjoint ones;
+                    # and a gradient ratio's denominator (the pattern
+                    # likelihood up to the scales of its factors) leaves the
+                    # FP32 range when the pre-order partial and the subtree
+                    # favour codons several changes apart. The request is
+                    # evaluated again in FP64 on the worker (its latency
                     # includes that evaluation).
-                    t0 = time.perf_counter()
-                    logl, grad = self._fp64(p)
-                    now = time.perf_counter()
-                    self.stats["fp64_fallback_s"] += now - t0
+                    kind = "codon" if c.data.n_states > 4 else "nuc"
+                    why = "logl" if not np.isfinite(logl) else "gradient"
+                    self.stats[f"fp64_fallback_{kind}_{why}"] += 1
+                    self._start_fallback(p, len(g.items))
+                    done += 1
+                    continue
                 if not np.isfinite(logl):
                     p.future.set_exception(FloatingPointError("non-finite log-likelihood"))
                 else:
                     p.future.set_result(Result(logl, grad, now - p.arrival, len(g.items)))
                 done += 1
         self.inflight = keep
+        # finished FP64 re-evaluations
+        still = []
+        for p, gsize, fut, extra, t0 in self._fallbacks:
+            if not fut.done():
+                still.append((p, gsize, fut, extra, t0))
+                continue
+            self.used -= extra
+            now = time.perf_counter()
+            self.stats["fp64_fallback_s"] += now - t0
+            try:
+                logl, grad = fut.result()
+            except Exception:   # reported to the request as a failure below
+                logl, grad = float("nan"), None
+            if not np.isfinite(logl):
+                p.future.set_exception(FloatingPointError("non-finite log-likelihood"))
+            else:
+                p.future.set_result(Result(logl, grad, now - p.arrival, gsize))
+            done += 1
+        self._fallbacks = still
         return done
+
+    def _start_fallback(self, p: _Pending, gsize: int) -> None:
+        """Queue the FP64 re-evaluation of p on the worker; its temporary
+        instance counts against the memory budget from now until it is done
+        (idle chains, p's own included, make room first; if even that is not
+        enough the device allocation decides)."""
+        import concurrent.futures as cf
+        c = self.chains[p.chain]
+        d = c.data
+        self.stats["fp64_fallback"] += 1
+        nbuf = c.n_buffers if c.band else None
+        extra = footprint(d.tree.n_tips, d.n_patterns, d.n_states, "f64", nbuf)
+        self._make_room(extra)
+        self.used += extra
+        if self._fb_pool is None:
+            self._fb_pool = cf.ThreadPoolExecutor(max_workers=1)
+            self._fb_stream = self.torch.cuda.Stream()
+        dev, stream = self.dev, self._fb_stream
+
+        def work():
+            self.torch.cuda.set_device(dev)
+            return self._fp64_eval(c, d, p.req, stream.cuda_stream)
+
+        self._fallbacks.append((p, gsize, self._fb_pool.submit(work), extra,
+                                time.perf_counter()))
 
     def _admit(self) -> list[_Pending]:
         picked, seen, rest = [], set(), collections.deque()
@@ -383,35 +440,19 @@ class Server:
 
         self._group(items, stream, launch)
 
-    def _fp64(self, p: _Pending):
-        """(logL, gradient or None) of one request on a temporary FP64
-        instance (the host waits); (nan, None) if that fails too."""
-        c = self.chains[p.chain]
-        d, r = c.data, p.req
-        self.stats["fp64_fallback"] += 1
-        # the temporary instance counts against the memory budget: idle
-        # chains (this one included) make room for it first, as for an
-        # admission; if even that is not enough it is tried anyway (the
-        # device allocation decides) rather than failing the request
-        nbuf = c.n_buffers if c.band else None
-        extra = footprint(d.tree.n_tips, d.n_patterns, d.n_states, "f64", nbuf)
-        self._make_room(extra)
-        self.used += extra
-        try:
-            return self._fp64_eval(c, d, r)
-        finally:
-            self.used -= extra
-
-    def _fp64_eval(self, c, d, r):
+    def _fp64_eval(self, c, d, r, stream: int):
+        """(logL, gradient or None) of request r of chain c on a temporary
+        FP64 instance on ``stream`` (the calling thread waits); (nan, None)
+        if that fails too."""
         from ._lib import TreelikError
         try:
             if c.band:   # a chain served with checkpointing keeps that form in FP64
                 tl = CheckpointedLikelihood(d.tree.n_tips, d.n_patterns, d.tree.children,
                                             d.n_states, R_CATEGORIES, "f64", band=c.band,
-                                            stream=c.stream.cuda_stream)
+                                            stream=stream)
             else:
                 tl = TreeLikelihood(d.tree.n_tips, d.n_patterns, d.n_states, R_CATEGORIES,
-                                    "f64", stream=c.stream.cuda_stream)
+                                    "f64", stream=stream)
         except TreelikError:
             return float("nan"), None
         try:
@@ -488,6 +529,8 @@ class Server:
                 time.sleep(20e-6)
 
     def close(self) -> None:
+        if self._fb_pool is not None:
+            self._fb_pool.shutdown(wait=True)
         self.torch.cuda.synchronize()
         for c in self.chains:
             if c.tl is not None:

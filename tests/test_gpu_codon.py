@@ -194,3 +194,45 @@ def test_fused_post_order_is_bit_identical_to_level_kernels(prec, monkeypatch):
     Q, pi, _ = om.build(w.model, w.params, w.freqs)
     want_l, _ = op.loglik(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights, w.tips)
     assert abs(out["1"][0] - want_l) <= 1e-5 * abs(want_l)
+
+
+@pytest.mark.slow
+def test_codon_128x20k_split_partials_full_size():
+    """The benchmark's codon configuration (GY94, 128 taxa x 20,000 patterns)
+    with split partials, every kernel launched over all patterns: per-pattern
+    log-likelihoods on 300 sampled patterns (the ragged tail among them)
+    within 2^-20 (N - 1) of the oracle, and, with pattern weights that select
+    those patterns, logL and every branch derivative against the oracle on
+    them alone (per-component bound)."""
+    import dataclasses
+
+    from oracle import gradient as og
+    from paper_2606_27607_gb300 import TreeLikelihood
+    w = synth.workload("gy94_128x20k")
+    rng = np.random.default_rng(12)
+    idx = np.sort(rng.choice(w.n_patterns, 300, replace=False))
+    idx[-1] = w.n_patterns - 1
+    Q, pi, _ = om.build(w.model, w.params, w.freqs)
+    logl, site = run(w, "tf32x3", site=True)
+    _, want_site = op.loglik_chunked(w.tree, Q, pi, w.rates, w.cat_weights, w.pattern_weights,
+                                     w.tips, patterns=idx)
+    assert np.max(np.abs(site[idx] - want_site)) <= 2.0 ** -20 * 127
+    wt = np.zeros(w.n_patterns)
+    wt[idx] = 1.0
+    small = dataclasses.replace(w, tips=w.tips[:, idx], pattern_weights=np.ones(len(idx)))
+    want_l, _ = op.loglik(small.tree, Q, pi, w.rates, w.cat_weights, small.pattern_weights,
+                          small.tips)
+    want_g = og.branch_gradient(small.tree, Q, pi, w.rates, w.cat_weights, small.pattern_weights,
+                                small.tips)
+    tl = TreeLikelihood(w.tree.n_tips, w.n_patterns, 61, 4, "tf32x3")
+    try:
+        tl.set_tips(w.tips)
+        tl.set_model("gy94", w.params, w.freqs)
+        tl.set_rates(w.rates, w.cat_weights)
+        tl.set_pattern_weights(wt)
+        tl.set_tree(w.tree.children, w.tree.edge_len)
+        lsel, g = tl.gradient()
+    finally:
+        tl.close()
+    assert abs(lsel - want_l) <= 1e-5 * abs(want_l)
+    assert_grad_close(g[:-1], want_g[:-1], 1e-3)
