@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtreelik.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["tl_api.cu", "tl_model.cu", "tl_nuc.cu", "tl_generic.cu", "tl_codon_tc.cu",
-           "tl_static.cu", "tl_adjoint.cu", "tl_ratio.cu"]
+           "tl_static.cu", "tl_adjoint.cu", "tl_adjoint_tc.cu", "tl_ratio.cu"]
 
 
 def nvcc() -> str:

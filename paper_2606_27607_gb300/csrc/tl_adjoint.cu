@@ -37,15 +37,6 @@
 
 namespace tl {
 
-struct AdjArgs {
-    const double* pi;     // [Spad]
-    const double* patw;   // [Ppad]
-    const double* coef;   // generic path: [n_ops][Ppad] w_p / L_p (scaled)
-    int* err;             // numeric flag (zero pattern likelihood)
-    int R, Ppad, Spad, S, chunk, n_chunks;
-    size_t n_rows;        // rows of the per-chunk outputs: listed edges x R x Spad^2
-    double catw[kMaxCat];
-};
 
 __device__ __forceinline__ void load4(const float* p, float* o) {
     float4 v = *reinterpret_cast<const float4*>(p);
@@ -419,204 +410,8 @@ static size_t adj_gen_smem(int elt) {
     return (size_t)elt * (2 * 64 * 64 + 2 * kGT * 64 + 2 * 64 * kGP + kGT * 64 + 2 * kGT * 64 + kGT);
 }
 
-// ---- TF32 instances: the same two products on the tensor cores ---------------
-// mma.sync m16n8k8 with TF32 operands and FP32 accumulators. The child
-// partials are stored TF32-rounded, so they enter exactly; P and U are split
-// as hi + lo (hi = TF32 nearest, lo = TF32 nearest of the remainder) and
-// each product is issued twice, which keeps about 21 bits of every operand.
-// Tiles of 16 patterns; 8 warps:
-//   v_c = x_c P_c^T  (warp: child w/4, output columns 16 (w%4) .. +16),
-//       written straight into U of the sibling: U_s = coef w_r q o v_c;
-//   M_c += U_c^T x_c (warp: child w/4, rows 16 (w%4) .. +16, all 64 columns,
-//       32 FP32 accumulators per thread across the chunk).
-// Fragment layouts (PTX ISA, mma.m16n8k8 .tf32): lane = 4 g + t;
-// A: a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4);
-// B: b0 (k=t, n=g), b1 (k=t+4, n=g); C: c0,c1 (g, 2t..2t+1), c2,c3 (g+8, ...).
-constexpr int kMT = 16;    // patterns per tile
-constexpr int kPP = 68;    // pitch of P and x rows (conflict-free row-g, column-t reads)
-constexpr int kUP = 72;    // pitch of U rows (conflict-free row-t, column-g reads)
-
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-        "{%8,%9}, {%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// SPLITX: the child partials are full FP32 (split-partials instances) and
-// are split as hi + lo like P and U: three products per contraction
-// (hi hi, hi lo, lo hi).
-template <bool SPLITX>
-__global__ void __launch_bounds__(256, 2) k_adj_mma(const AdjOp<float>* __restrict__ ops, AdjArgs a,
-                                                    double* __restrict__ mpart) {
-    extern __shared__ __align__(16) unsigned char sm_mma[];
-    uint32_t* Ph = reinterpret_cast<uint32_t*>(sm_mma);   // [2][64][kPP]  P_c[i][j] hi
-    uint32_t* Pl = Ph + 2 * 64 * kPP;                       // lo
-    float* X = reinterpret_cast<float*>(Pl + 2 * 64 * kPP); // [2][kMT][kPP] x_c[p][j]
-    float* Qs = X + 2 * kMT * kPP;                          // [kMT][kPP]
-    uint32_t* Uh = reinterpret_cast<uint32_t*>(Qs + kMT * kPP);  // [2][kMT][kUP] U_c[p][i]
-    uint32_t* Ul = Uh + 2 * kMT * kUP;
-    float* Cs = reinterpret_cast<float*>(Ul + 2 * kMT * kUP);    // [kMT]
-    const AdjOp<float>& op = ops[blockIdx.x];
-    const int r = blockIdx.y;
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int g = lane >> 2, tq = lane & 3;
-    const int S = a.S, Spad = a.Spad;
-    for (int idx = t; idx < 2 * 64 * 64; idx += blockDim.x) {
-        const int c = idx >> 12, i = (idx >> 6) & 63, j = idx & 63;
-        const double pv = (i < S && j < S) ? op.P[c][((size_t)r * Spad + i) * Spad + j] : 0.0;
-        const float pf = (float)pv;
-        const uint32_t h = tf32_rna(pf);
-        Ph[(c * 64 + i) * kPP + j] = h;
-        Pl[(c * 64 + i) * kPP + j] = tf32_rna(pf - __uint_as_float(h));
-    }
-    const float wr = (float)a.catw[r];
-    const int p_begin = blockIdx.z * a.chunk;
-    const int p_end = min(a.Ppad, p_begin + a.chunk);
-    const int wc = warp >> 2, wq = warp & 3;
-    float acc[8][4];
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[nt][k] = 0.f;
-    // Registers hold the next tile's loads while this tile is multiplied.
-    const int lp = t >> 4, lj4 = (t & 15) * 4;
-    float4 rx[2], rq;
-    double rc = 0.0;
-    auto fetch = [&](int p0) {
-        const int p = p0 + lp;
-        const size_t off = ((size_t)r * a.Ppad + p) * Spad + lj4;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            if (op.st[c]) {
-                const int s = op.st[c][p];
-                const bool amb = s < 0 || s >= S;
-                rx[c].x = (lj4 + 0 < S && (amb || s == lj4 + 0)) ? 1.f : 0.f;
-                rx[c].y = (lj4 + 1 < S && (amb || s == lj4 + 1)) ? 1.f : 0.f;
-                rx[c].z = (lj4 + 2 < S && (amb || s == lj4 + 2)) ? 1.f : 0.f;
-                rx[c].w = (lj4 + 3 < S && (amb || s == lj4 + 3)) ? 1.f : 0.f;
-            } else {
-                rx[c] = *reinterpret_cast<const float4*>(op.part[c] + off);
-            }
-        }
-        if (op.q) {
-            rq = *reinterpret_cast<const float4*>(op.q + off);
-        } else {
-            rq.x = lj4 + 0 < S ? (float)a.pi[lj4 + 0] : 0.f;
-            rq.y = lj4 + 1 < S ? (float)a.pi[lj4 + 1] : 0.f;
-            rq.z = lj4 + 2 < S ? (float)a.pi[lj4 + 2] : 0.f;
-            rq.w = lj4 + 3 < S ? (float)a.pi[lj4 + 3] : 0.f;
-        }
-        if (t < kMT) rc = a.coef[(size_t)blockIdx.x * a.Ppad + p0 + t];
-    };
-    if (p_begin < p_end) fetch(p_begin);
-    for (int p0 = p_begin; p0 < p_end; p0 += kMT) {
-        __syncthreads();  // the previous tile's readers are done
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-            *reinterpret_cast<float4*>(X + (c * kMT + lp) * kPP + lj4) = rx[c];
-        *reinterpret_cast<float4*>(Qs + lp * kPP + lj4) = rq;
-        if (t < kMT) Cs[t] = (float)rc * wr;
-        __syncthreads();
-        if (p0 + kMT < p_end) fetch(p0 + kMT);
-        {   // v_wc = x_wc P_wc^T on columns [16 wq, 16 wq + 16); U of the sibling
-            float v[2][4];
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) v[nt][k] = 0.f;
-            const float* xa = X + wc * kMT * kPP;
-            const uint32_t* ph = Ph + wc * 64 * kPP;
-            const uint32_t* pl = Pl + wc * 64 * kPP;
-#pragma unroll
-            for (int ks = 0; ks < 8; ++ks) {
-                const int k0 = ks * 8;
-                const float xf[4] = {xa[g * kPP + k0 + tq], xa[(g + 8) * kPP + k0 + tq],
-                                     xa[g * kPP + k0 + tq + 4], xa[(g + 8) * kPP + k0 + tq + 4]};
-                uint32_t af[4], afl[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    af[i] = SPLITX ? tf32_rna(xf[i]) : __float_as_uint(xf[i]);
-                    afl[i] = SPLITX ? tf32_rna(xf[i] - __uint_as_float(af[i])) : 0u;
-                }
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) {
-                    const int n = 16 * wq + 8 * nt + g;
-                    mma_tf32(v[nt], af, ph[n * kPP + k0 + tq], ph[n * kPP + k0 + tq + 4]);
-                    mma_tf32(v[nt], af, pl[n * kPP + k0 + tq], pl[n * kPP + k0 + tq + 4]);
-                    if (SPLITX)
-                        mma_tf32(v[nt], afl, ph[n * kPP + k0 + tq], ph[n * kPP + k0 + tq + 4]);
-                }
-            }
-            const int sib = 1 - wc;
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int p = g + (k >> 1) * 8, i = 16 * wq + 8 * nt + 2 * tq + (k & 1);
-                    const float u = Cs[p] * Qs[p * kPP + i] * v[nt][k];
-                    const uint32_t h = tf32_rna(u);
-                    Uh[(sib * kMT + p) * kUP + i] = h;
-                    Ul[(sib * kMT + p) * kUP + i] = tf32_rna(u - __uint_as_float(h));
-                }
-        }
-        __syncthreads();
-        {   // M_wc[16 wq .. +16][0 .. 64) += U_wc^T x_wc
-            const uint32_t* uh = Uh + wc * kMT * kUP;
-            const uint32_t* ul = Ul + wc * kMT * kUP;
-            const float* xb = X + wc * kMT * kPP;
-            const int m0 = 16 * wq;
-#pragma unroll
-            for (int ks = 0; ks < kMT / 8; ++ks) {
-                const int k0 = ks * 8;
-                uint32_t ah[4], al[4];
-                ah[0] = uh[(k0 + tq) * kUP + m0 + g];
-                ah[1] = uh[(k0 + tq) * kUP + m0 + g + 8];
-                ah[2] = uh[(k0 + tq + 4) * kUP + m0 + g];
-                ah[3] = uh[(k0 + tq + 4) * kUP + m0 + g + 8];
-                al[0] = ul[(k0 + tq) * kUP + m0 + g];
-                al[1] = ul[(k0 + tq) * kUP + m0 + g + 8];
-                al[2] = ul[(k0 + tq + 4) * kUP + m0 + g];
-                al[3] = ul[(k0 + tq + 4) * kUP + m0 + g + 8];
-#pragma unroll
-                for (int nt = 0; nt < 8; ++nt) {
-                    const float x0 = xb[(k0 + tq) * kPP + 8 * nt + g];
-                    const float x1 = xb[(k0 + tq + 4) * kPP + 8 * nt + g];
-                    const uint32_t b0 = SPLITX ? tf32_rna(x0) : __float_as_uint(x0);
-                    const uint32_t b1 = SPLITX ? tf32_rna(x1) : __float_as_uint(x1);
-                    mma_tf32(acc[nt], ah, b0, b1);
-                    mma_tf32(acc[nt], al, b0, b1);
-                    if (SPLITX)
-                        mma_tf32(acc[nt], ah, tf32_rna(x0 - __uint_as_float(b0)),
-                                 tf32_rna(x1 - __uint_as_float(b1)));
-                }
-            }
-        }
-    }
-    const int row = op.row[wc];
-    if (row < 0) return;
-    const int SS = Spad * Spad;
-#pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int i = 16 * wq + g + (k >> 1) * 8, j = 8 * nt + 2 * tq + (k & 1);
-            mpart[(size_t)blockIdx.z * a.n_rows + (size_t)(row * a.R + r) * SS + i * Spad + j] =
-                (double)acc[nt][k];
-        }
-}
-
-static size_t adj_mma_smem() {
-    return sizeof(uint32_t) * (4 * 64 * kPP + 2 * kMT * kPP + kMT * kPP + 4 * kMT * kUP + kMT);
-}
-
 static bool adj_nuc(const Instance* I) { return I->S == 4 && (I->prec == kF32 || I->prec == kF64); }
+static bool adj_tc(const Instance* I) { return I->prec == kTF32 && I->Spad == 64; }
 static int adj_lpp(int R) { return R <= 1 ? 1 : R <= 2 ? 2 : R <= 4 ? 4 : 8; }
 
 // Pattern chunks per parent: enough blocks for a few waves on the device,
@@ -625,7 +420,7 @@ static int adj_lpp(int R) { return R <= 1 ? 1 : R <= 2 ? 2 : R <= 4 ? 4 : 8; }
 int adj_chunks(const Instance* I, int n_ops) {
     const int sms = 152;
     const int per = adj_nuc(I) ? n_ops : n_ops * I->R;
-    const int step = adj_nuc(I) ? 128 : kGT;
+    const int step = (adj_nuc(I) || adj_tc(I)) ? 128 : kGT;
     int n = std::max(1, (4 * sms + per - 1) / std::max(per, 1));
     const int cap = adj_nuc(I) ? (I->elt == 4 ? 2048 : (1 << 30)) : 4096;
     n = std::max(n, (I->Ppad + cap - 1) / cap);
@@ -634,7 +429,7 @@ int adj_chunks(const Instance* I, int n_ops) {
 }
 
 static int adj_chunk_len(const Instance* I, int n_chunks) {
-    const int step = adj_nuc(I) ? 128 : kGT;
+    const int step = (adj_nuc(I) || adj_tc(I)) ? 128 : kGT;
     const int len = (I->Ppad + n_chunks - 1) / n_chunks;
     return ((len + step - 1) / step) * step;
 }
@@ -647,6 +442,7 @@ static int adj_accumulate_t(Instance* I, const void* d_ops, int n_ops, int n_chu
     a.patw = I->d_patw;
     a.coef = d_coef;
     a.err = I->d_err + 1;
+    a.timeout = I->d_err + 2;
     a.R = I->R;
     a.Ppad = I->Ppad;
     a.Spad = I->Spad;
@@ -669,14 +465,11 @@ static int adj_accumulate_t(Instance* I, const void* d_ops, int n_ops, int n_chu
     }
     k_adj_coef<T><<<dim3(n_ops, (I->Ppad + kCoefPat - 1) / kCoefPat), 256, 0, I->stream>>>(
         ops, a, d_coef);
-    if (I->prec == kTF32 && I->Spad == 64) {
-        const size_t smem = adj_mma_smem();
-        const auto kern = I->split_partials ? k_adj_mma<true> : k_adj_mma<false>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        kern<<<dim3(n_ops, I->R, n_chunks), 256, smem, I->stream>>>(
-            reinterpret_cast<const AdjOp<float>*>(d_ops), a, d_mpart);
-        I->launches += 2;
-        return cuda_check(I, cudaGetLastError(), "adjoint (tensor cores)");
+    if (adj_tc(I)) {
+        I->launches += 1;
+        if (int rc = cuda_check(I, cudaGetLastError(), "adjoint coefficients")) return rc;
+        return launch_adj_tc(I, reinterpret_cast<const AdjOp<float>*>(d_ops), n_ops, n_chunks, a,
+                             d_mpart);
     }
     const size_t smem = adj_gen_smem(sizeof(T));
     if constexpr (sizeof(T) == 8) {  // FP64 instances; FP32 storage is four-state or TF32

@@ -352,7 +352,7 @@ int check_numeric_flag(Instance* I) {
     if (h[2]) {
         cudaMemsetAsync(I->d_err + 2, 0, sizeof(int), I->stream);
         return fail(I, TL_ERR_TIMEOUT, "a tensor-core kernel wait gave up (code 0x%x: bits 0-2 "
-                    "empty/full/done barrier, bits 8-10 post/pre1/pre2 kernel)", h[2]);
+                    "empty/full/done barrier, bits 8-10 post/pre1/pre2 kernel, bit 11 adjoint)", h[2]);
     }
     if (h[0] || h[1]) {
         cudaMemsetAsync(I->d_err, 0, 2 * sizeof(int), I->stream);

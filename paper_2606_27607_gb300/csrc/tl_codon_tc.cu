@@ -26,12 +26,12 @@
 #include <cstring>
 
 #include "tl_internal.cuh"
+#include "tl_tcgen05.cuh"
 
 namespace tl {
 namespace {
+using namespace tc5;
 
-constexpr int kTcM = 128;                   // patterns per tile (TMEM lanes)
-constexpr int kTcN = 64;                    // padded states
 constexpr int kStages = 4;                  // most pipeline stages (barrier arrays)
 constexpr int kAChunk = kTcM * 32 * 4;      // 32 K-values of 128 rows: 16 KB
 constexpr int kBChunk = kTcN * 32 * 4;      // 8 KB
@@ -50,121 +50,7 @@ struct TcPipe {
     static constexpr int tx_bytes = 2 * kAChunk + (SPLIT ? 4 : 2) * kBChunk;
 };
 constexpr int kTmemCols = 512;
-constexpr unsigned long long kWaitNs = 2000000000ull;  // a wait gives up after 2 s
 
-// ---- PTX wrappers ----------------------------------------------------------
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-// Wait for the phase with the given parity; false once kWaitNs have passed
-// (try_wait may suspend the thread for a while on each poll, so the bound is
-// on elapsed time, not on the number of polls).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    const unsigned a = smem_u32(bar);
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        unsigned ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
-    }
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
-                                            uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-        : "memory");
-}
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart.
-__device__ __forceinline__ uint64_t sw128_desc(const void* p) {
-    const uint64_t addr = smem_u32(p);
-    uint64_t d = 0;
-    d |= (addr >> 4) & 0x3FFFull;           // start address
-    d |= (uint64_t)1 << 16;                 // leading byte offset (unused when swizzled)
-    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
-    d |= (uint64_t)1 << 46;                 // descriptor version
-    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
-    return d;
-}
-// Instruction descriptor: D f32, A and B tf32, both K-major, N = 64, M = 128.
-constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((kTcN >> 3) << 17) |
-                                ((kTcM >> 4) << 24);
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kIdescTf32), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-            smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-}
-// 64 consecutive 32-bit TMEM columns of this thread's lane: one load, one
-// wait (the epilogue's latency is in these round trips, not in bandwidth).
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
-    uint32_t r[64];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_st64(uint32_t taddr, const float* v) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64};\n"
-        ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31])), "r"(__float_as_uint(v[32])), "r"(__float_as_uint(v[33])), "r"(__float_as_uint(v[34])), "r"(__float_as_uint(v[35])), "r"(__float_as_uint(v[36])), "r"(__float_as_uint(v[37])), "r"(__float_as_uint(v[38])), "r"(__float_as_uint(v[39])), "r"(__float_as_uint(v[40])), "r"(__float_as_uint(v[41])), "r"(__float_as_uint(v[42])), "r"(__float_as_uint(v[43])), "r"(__float_as_uint(v[44])), "r"(__float_as_uint(v[45])), "r"(__float_as_uint(v[46])), "r"(__float_as_uint(v[47])), "r"(__float_as_uint(v[48])), "r"(__float_as_uint(v[49])), "r"(__float_as_uint(v[50])), "r"(__float_as_uint(v[51])), "r"(__float_as_uint(v[52])), "r"(__float_as_uint(v[53])), "r"(__float_as_uint(v[54])), "r"(__float_as_uint(v[55])), "r"(__float_as_uint(v[56])), "r"(__float_as_uint(v[57])), "r"(__float_as_uint(v[58])), "r"(__float_as_uint(v[59])), "r"(__float_as_uint(v[60])), "r"(__float_as_uint(v[61])), "r"(__float_as_uint(v[62])), "r"(__float_as_uint(v[63]))
-        : "memory");
-    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-}
-__device__ __forceinline__ float to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-// x with its 13 low mantissa bits cleared: a TF32 value, and x - tf32_trunc(x)
-// is exact in FP32
-__device__ __forceinline__ float tf32_trunc(float x) {
-    return __uint_as_float(__float_as_uint(x) & 0xffffe000u);
-}
-// Make generic-proxy shared-memory writes visible to the tensor cores'
-// (async-proxy) operand reads that follow a barrier.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
 __device__ __forceinline__ int frexp_exp_f(float m) {
     int E = (__float_as_int(m) >> 23) & 0xff;
     if (E == 0) {
@@ -175,6 +61,33 @@ __device__ __forceinline__ int frexp_exp_f(float m) {
 }
 __device__ __forceinline__ float pow2f(int k) {  // 2^k, k in [-126, 127]
     return __int_as_float((k + 127) << 23);
+}
+// Post-order partials are stored with their per-pattern maximum (over
+// categories and states) in [2^(K-1), 2^K), K = kPostExp. The product of two
+// stored children, and the pre-order ratio denominator q . (v_a o v_b)
+// formed from them, then sit 2^(2K) above the values a maximum near 1 would
+// give: underflow below FP32's smallest normal number needs a normalised
+// product below 2^-(126+2K). The largest value any kernel forms from stored
+// partials stays below 2^(2K+30) (products of two children, sums over 64
+// states and 8 categories, derivative matrices with entries below 2^20).
+// Power-of-two scaling commutes with rounding, so every result whose
+// intermediates stayed normal is unchanged.
+constexpr int kPostExp = 48;
+// Factors f1 f2 = 2^(K-e) that bring a maximum m = f 2^e, f in [0.5, 1), to
+// [2^(K-1), 2^K) (split in two when out of pow2f's range); returns the
+// exponent the stored values omit, e - K (0 for an all-zero pattern).
+__device__ __forceinline__ int post_scale(float m, float* f1, float* f2) {
+    *f1 = 1.f;
+    *f2 = 1.f;
+    if (m == 0.f) return 0;
+    const int kk = kPostExp - frexp_exp_f(m);
+    if (kk >= -126 && kk <= 126) {
+        *f1 = pow2f(kk);
+    } else {
+        *f1 = pow2f(kk / 2);
+        *f2 = pow2f(kk - kk / 2);
+    }
+    return -kk;
 }
 
 // ---- device op descriptor ----------------------------------------------------
@@ -599,7 +512,7 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                 tmem_st64(lane_base + (uint32_t)(r * 2 * kTcN), x);
             }
             float f1 = 1.f, f2 = 1.f;
-            if (a.rescale) cum += scale_of(m, &f1, &f2);
+            if (a.rescale) cum += post_scale(m, &f1, &f2);
             // pass 2: rescale, round to TF32, store
             float* dst = a.pool + (size_t)op.dest * a.bstride + wrow0;
             for (int r = 0; r < R; ++r) {
@@ -968,48 +881,6 @@ struct FusePipe {
         (size_t)stages * bytes + (size_t)tip_slots * tip_bytes + out_bytes;
 };
 
-__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, unsigned parity,
-                                                   volatile int* abort_flag) {
-    const unsigned addr = smem_u32(bar);
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        unsigned ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (*abort_flag) return false;
-        if (global_ns() - t0 > kWaitNs) return false;
-    }
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void st_release_cta(unsigned* p, unsigned v) {
-    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;\n" ::"r"(smem_u32(p)), "r"(v) : "memory");
-}
-// Generic-proxy global stores made visible to later async-proxy (TMA) reads.
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;\n" ::: "memory");
-}
-__device__ __forceinline__ unsigned ld_acquire_cta(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];\n" : "=r"(v) : "r"(smem_u32(p)) : "memory");
-    return v;
-}
-// A (M = 128 x K = 8, tf32) from tensor memory, B from shared memory.
-__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc,
-                                            uint32_t accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "r"(tmem_a), "l"(bdesc), "r"(kIdescTf32), "r"(accumulate)
-        : "memory");
-}
-
 template <bool SPLIT>
 __global__ void __launch_bounds__(kFuseThreads, 1)
 k_tc_fused(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtensorMap tm_tip,
@@ -1362,18 +1233,7 @@ k_tc_fused(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ 
                 if (!ok) break;
                 // pass 2: rescale, round to TF32, keep on chip and store
                 float f1 = 1.f, f2 = 1.f;
-                if (a.rescale) {
-                    const int e = frexp_exp_f(m);
-                    if (e != 0) {
-                        const int kk = -e;
-                        if (kk >= -126 && kk <= 126) f1 = pow2f(kk);
-                        else {
-                            f1 = pow2f(kk / 2);
-                            f2 = pow2f(kk - kk / 2);
-                        }
-                    }
-                    cum += e;
-                }
+                if (a.rescale) cum += post_scale(m, &f1, &f2);
                 // row 0 of this warp's 32 patterns in the output buffer
                 float* dst = a.pool + (size_t)o.dest * a.bstride +
                              (size_t)(tile * kTcM + quarter * 32) * kTcN;

@@ -312,6 +312,20 @@ struct __align__(16) AdjOp {
     const double* P[2];    // FP64 transition matrices of the edges [R][Spad][Spad]
     int row[2];            // output row of each edge (-1: not listed)
 };
+struct AdjArgs {
+    const double* pi;     // [Spad]
+    const double* patw;   // [Ppad]
+    const double* coef;   // generic path: [n_ops][Ppad] w_p / L_p (scaled)
+    int* err;             // numeric flag (zero pattern likelihood)
+    int* timeout;         // tensor-core wait flag (bit 11: the adjoint kernel)
+    int R, Ppad, Spad, S, chunk, n_chunks;
+    size_t n_rows;        // rows of the per-chunk outputs: listed edges x R x Spad^2
+    double catw[kMaxCat];
+};
+// tl_adjoint_tc.cu: both accumulation products of a TF32 instance (Spad 64)
+// on the 5th-generation tensor cores
+int launch_adj_tc(Instance* I, const AdjOp<float>* d_ops, int n_ops, int n_chunks,
+                  const AdjArgs& a, double* d_mpart);
 struct AdjEdge {           // one listed edge for the eigenbasis finish
     const double* P;       // [R][Spad][Spad]
     double t;
