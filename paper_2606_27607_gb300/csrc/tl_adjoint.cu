@@ -754,45 +754,47 @@ int launch_adj_finish(Instance* I, int model, const double* d_M, const AdjEdge* 
 //   dlogL/deps = Q_ij (dQ_ij - dQ_ii) + Q_ji (dQ_ji - dQ_jj)
 //                - (pi_i Q_ij + pi_j Q_ji) <dQ, Q>
 // (the derivative of exp(eps) s_ij pi_j and of the normaliser).
-__global__ void __launch_bounds__(256) k_adj_params(int S, int Spad, const double* __restrict__ V,
-                                                    const double* __restrict__ Vinv,
-                                                    const double* __restrict__ G, int first_order,
+// dlogL/dQ = V^-T G V^T (exact form) or G itself (first order): block i forms
+// row i, Y_i = sum_k Vinv[k][i] G[k][.], then D[i][j] = sum_l Y_i[l] V[j][l]
+// (a thread per column; the rows run on separate SMs).
+__global__ void __launch_bounds__(64) k_adj_dq(int S, int Spad, const double* __restrict__ V,
+                                               const double* __restrict__ Vinv,
+                                               const double* __restrict__ G, int first_order,
+                                               double* __restrict__ dQ) {
+    __shared__ double Y[64];
+    const int i = blockIdx.x, t = threadIdx.x;
+    if (first_order) {
+        if (t < Spad) dQ[i * Spad + t] = G[i * Spad + t];
+        return;
+    }
+    double acc = 0.0;
+    if (t < Spad)
+        for (int k = 0; k < S; ++k) acc += Vinv[k * Spad + i] * G[k * Spad + t];
+    Y[t] = acc;
+    __syncthreads();
+    if (t >= Spad) return;
+    double d = 0.0;
+    if (i < S && t < S)
+        for (int l = 0; l < S; ++l) d += Y[l] * V[t * Spad + l];
+    dQ[i * Spad + t] = d;
+}
+
+// Every substitution parameter from D = dlogL/dQ: <D, dQ/dtheta_k> for the
+// stored derivative matrices (fixed-order block sums), and the closed forms
+// of the general reversible model's exchangeabilities and of the
+// random-effect pairs, which need <D, Q>.
+__global__ void __launch_bounds__(256) k_adj_params(int S, int Spad, const double* __restrict__ D,
                                                     const double* __restrict__ Q,
                                                     const double* __restrict__ pi,
                                                     const double* __restrict__ dQk, int n_dq,
                                                     const int* __restrict__ pairs, int n_pairs,
                                                     int n_exch, const double* __restrict__ mu,
-                                                    double* __restrict__ dQ,
                                                     double* __restrict__ theta) {
-    extern __shared__ double sm_par[];
     const int SS = Spad * Spad;
-    double* Y = sm_par;       // [Spad][Spad]
-    double* D = Y + SS;       // dQ
     __shared__ double red[256];
     __shared__ double gq;
     const int t = threadIdx.x, nt = blockDim.x;
-    if (first_order) {
-        for (int idx = t; idx < SS; idx += nt) D[idx] = G[idx];
-    } else {
-        // Y = V^-T G  (Y_il = sum_k Vinv_ki G_kl), D = Y V^T (D_ij = sum_l Y_il V_jl)
-        for (int idx = t; idx < SS; idx += nt) {
-            const int i = idx / Spad, l = idx % Spad;
-            double acc = 0.0;
-            for (int k = 0; k < S; ++k) acc += Vinv[k * Spad + i] * G[k * Spad + l];
-            Y[idx] = acc;
-        }
-        __syncthreads();
-        for (int idx = t; idx < SS; idx += nt) {
-            const int i = idx / Spad, j = idx % Spad;
-            double acc = 0.0;
-            if (i < S && j < S)
-                for (int l = 0; l < S; ++l) acc += Y[i * Spad + l] * V[j * Spad + l];
-            D[idx] = acc;
-        }
-    }
-    __syncthreads();
-    for (int idx = t; idx < SS; idx += nt) dQ[idx] = D[idx];
-    // <dQ, M> for M = dQ/dtheta_k (k < n_dq), then M = Q
+    // <D, M> for M = dQ/dtheta_k (k < n_dq), then M = Q
     for (int k = 0; k <= n_dq; ++k) {
         const double* Mk = (k < n_dq) ? dQk + (size_t)k * SS : Q;
         double acc = 0.0;
@@ -832,14 +834,12 @@ __global__ void __launch_bounds__(256) k_adj_params(int S, int Spad, const doubl
 int launch_adj_params(Instance* I, int model, const double* d_G, bool first_order, double* d_dQ,
                       double* d_theta) {
     ModelDev& M = I->models[model];
-    const size_t smem = 2 * (size_t)I->Spad * I->Spad * sizeof(double);
-    cudaFuncSetAttribute(k_adj_params, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int n_pairs = M.kind == TL_MODEL_GY94RE ? TL_GY94_PAIRS : 0;
     const int n_exch = M.kind == TL_MODEL_REV ? I->S * I->S : 0;
-    k_adj_params<<<1, 256, smem, I->stream>>>(I->S, I->Spad, M.V, M.Vinv, d_G, first_order, M.Q,
-                                              M.pi, M.dQ, M.n_dq, M.pairs, n_pairs, n_exch, M.mu,
-                                              d_dQ, d_theta);
-    I->launches += 1;
+    k_adj_dq<<<I->Spad, 64, 0, I->stream>>>(I->S, I->Spad, M.V, M.Vinv, d_G, first_order, d_dQ);
+    k_adj_params<<<1, 256, 0, I->stream>>>(I->S, I->Spad, d_dQ, M.Q, M.pi, M.dQ, M.n_dq, M.pairs,
+                                           n_pairs, n_exch, M.mu, d_theta);
+    I->launches += 2;
     return cuda_check(I, cudaGetLastError(), "adjoint parameters");
 }
 
