@@ -646,6 +646,167 @@ __global__ void __launch_bounds__(256) k_adj_finish(int S, int Spad, int R, int 
     }
 }
 
+// The finish of a TF32 instance with the two eigenbasis products in
+// double-float arithmetic on the FP32 cores (FP64 issue is a small fraction of
+// FP32 on this part): every value of V, V^-1, M and Y as hi + lo, two FP32
+// numbers; each multiply-add takes the product's rounding error from an FMA
+// and the sum's from TwoSum (Knuth), both collected in a compensation term,
+// which keeps about 2^-48 of each sum's terms. W then enters the same FP64
+// arithmetic as the FP64 kernel, with Phi_ij = (e^{a_i} - e^{a_j}) / (a_i - a_j)
+// from the exponentials (a series in d = a_i - a_j below |d| = 2^-10).
+struct df2 {
+    float hi, lo;
+};
+__device__ __forceinline__ df2 df_of(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+// (s, c) += a * b; the intrinsics keep the compiler from contracting or
+// reassociating the error terms
+__device__ __forceinline__ void df_mac(float& s, float& c, df2 a, df2 b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float t = __fadd_rn(s, p);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+}
+__device__ __forceinline__ df2 df_norm(float s, float c) {
+    const float h = __fadd_rn(s, c);
+    return {h, __fsub_rn(c, __fsub_rn(h, s))};
+}
+
+__global__ void __launch_bounds__(256) k_adj_finish_df(int S, int Spad, int R, int E,
+                                                       const double* __restrict__ V,
+                                                       const double* __restrict__ Vinv,
+                                                       const double* __restrict__ lam,
+                                                       const double* __restrict__ rates,
+                                                       const double* __restrict__ Mall,
+                                                       const AdjEdge* __restrict__ edges,
+                                                       int first_order, double* __restrict__ gpart,
+                                                       double* __restrict__ grad) {
+    extern __shared__ __align__(16) unsigned char sm_fin[];
+    constexpr int L = 64, LP = 65;
+    df2* Vs = reinterpret_cast<df2*>(sm_fin);   // [L][LP]
+    df2* Vi = Vs + L * LP;
+    df2* Ms = Vi + L * LP;
+    df2* Ys = Ms + L * LP;
+    __shared__ double ea[64], la[64], gsum[8];
+    const int e = blockIdx.x, t = threadIdx.x, nt = blockDim.x;
+    const int ti = t >> 4, tj = t & 15;
+    const int SS = Spad * Spad;
+    const AdjEdge ed = edges[e];
+    for (int idx = t; idx < L * L; idx += nt) {
+        const int i = idx >> 6, j = idx & 63;
+        const bool in = i < S && j < S;
+        Vs[i * LP + j] = df_of(in ? V[i * Spad + j] : 0.0);
+        Vi[i * LP + j] = df_of(in ? Vinv[i * Spad + j] : 0.0);
+    }
+    double g[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) g[a][b] = 0.0;
+    double dsum = 0.0;
+    for (int r = 0; r < R; ++r) {
+        const double rt = rates[r] * ed.t;
+        __syncthreads();
+        for (int idx = t; idx < L * L; idx += nt) {
+            const int i = idx >> 6, j = idx & 63;
+            Ms[i * LP + j] =
+                df_of((i < S && j < S) ? Mall[((size_t)e * R + r) * SS + i * Spad + j] : 0.0);
+        }
+        if (t < 64) {
+            la[t] = t < S ? lam[t] * rt : 0.0;
+            ea[t] = t < S ? exp(la[t]) : 0.0;
+        }
+        __syncthreads();
+        // Y = V^T M: Y[i][l] = sum_k V[k][i] M[k][l]
+        float ys[4][4], yc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) ys[a][b] = yc[a][b] = 0.f;
+        for (int k = 0; k < S; ++k) {
+            df2 va[4], mb[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) va[a] = Vs[k * LP + 4 * ti + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) mb[b] = Ms[k * LP + 4 * tj + b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) df_mac(ys[a][b], yc[a][b], va[a], mb[b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) Ys[(4 * ti + a) * LP + 4 * tj + b] = df_norm(ys[a][b], yc[a][b]);
+        __syncthreads();
+        // W = Y V^-T: W[i][j] = sum_l Y[i][l] Vinv[j][l]
+        float ws[4][4], wc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) ws[a][b] = wc[a][b] = 0.f;
+        for (int l = 0; l < S; ++l) {
+            df2 ya[4], vb[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) ya[a] = Ys[(4 * ti + a) * LP + l];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) vb[b] = Vi[(4 * tj + b) * LP + l];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) df_mac(ws[a][b], wc[a][b], ya[a], vb[b]);
+        }
+        // the edge derivative (diagonal of W) and this edge's share of G
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int i = 4 * ti + a, j = 4 * tj + b;
+                if (i >= S || j >= S) continue;
+                const double w = (double)ws[a][b] + (double)wc[a][b];
+                if (i == j) dsum += w * rates[r] * lam[i] * ea[i];
+                if (!first_order) {
+                    const double d = la[i] - la[j];
+                    const double phi =
+                        fabs(d) < 0x1p-10
+                            ? ea[j] * (1.0 + d * (0.5 + d * (1.0 / 6 + d * (1.0 / 24 + d * (1.0 / 120)))))
+                            : (ea[i] - ea[j]) / d;
+                    g[a][b] += rt * w * phi;
+                } else {
+                    const double* P = ed.P + (size_t)r * SS;
+                    double mp = 0.0;
+                    for (int l = 0; l < S; ++l) {
+                        const df2 m = Ms[i * LP + l];
+                        mp += ((double)m.hi + (double)m.lo) * P[j * Spad + l];
+                    }
+                    g[a][b] += rt * mp;
+                }
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = 4 * ti + a, j = 4 * tj + b;
+            if (i < Spad && j < Spad) gpart[(size_t)(i * Spad + j) * E + e] = g[a][b];
+        }
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    if ((t & 31) == 0) gsum[t >> 5] = dsum;
+    __syncthreads();
+    if (t == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (nt >> 5); ++w) s += gsum[w];
+        grad[e] = s;
+    }
+}
+
 // Small state spaces (S <= 16): a thread per entry of Y and W.
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_finish_small(int S, int Spad, int R, int E,
@@ -734,6 +895,13 @@ int launch_adj_finish(Instance* I, int model, const double* d_M, const AdjEdge* 
         k_adj_finish_small<double><<<E, 256, smem, I->stream>>>(
             I->S, I->Spad, I->R, E, M.V, M.Vinv, M.lam, d_rates, d_M, d_edges, first_order,
             d_gpart, d_grad);
+    } else if (I->prec == kTF32 && !first_order) {
+        const size_t smem = 4 * (size_t)64 * 65 * sizeof(df2);
+        cudaFuncSetAttribute(k_adj_finish_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        k_adj_finish_df<<<E, 256, smem, I->stream>>>(I->S, I->Spad, I->R, E, M.V, M.Vinv, M.lam,
+                                                     d_rates, d_M, d_edges, first_order, d_gpart,
+                                                     d_grad);
     } else {
         const size_t smem = 4 * (size_t)64 * 65 * sizeof(double);
         cudaFuncSetAttribute(k_adj_finish<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
