@@ -40,6 +40,10 @@ constexpr int kBChunk = kTcN * 32 * 4;      // 8 KB
 // partials also A_lo (96 KB), two stages.
 // Per-warp staging for coalesced stores of the epilogue's rows: 32 half rows.
 constexpr int kOutWarpBytes = 32 * 128;
+// The level kernels run eight warps: two per TMEM lane quarter (thread =
+// pattern = lane), each taking half of the rate categories; per-pattern
+// partial results (maxima, sums over categories) meet in shared memory.
+constexpr int kTcThreads = 256;
 
 template <bool SPLIT, bool SPLITA>
 struct TcPipe {
@@ -128,13 +132,15 @@ static_assert(sizeof(TcOp) == kTcOpBytes, "descriptor size");
 enum TcMode { kPost = 0, kPre1 = 1, kPre2 = 2 };
 
 // Fixed-order sum over the 128 threads; thread 0 gets the total.
-__device__ __forceinline__ float block_sum128(float v, float* red) {
+// Sum of v over the block's eight warps (fixed order); the result in thread 0.
+__device__ __forceinline__ float block_sum256(float v, float* red) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     float t = 0.f;
-    if (threadIdx.x == 0) t = (red[0] + red[1]) + (red[2] + red[3]);
+    if (threadIdx.x == 0)
+        t = ((red[0] + red[1]) + (red[2] + red[3])) + ((red[4] + red[5]) + (red[6] + red[7]));
     __syncthreads();
     return t;
 }
@@ -150,7 +156,7 @@ __device__ __forceinline__ float block_sum128(float v, float* red) {
 // A_hi B_hi + A_hi B_lo + A_lo B_hi, which keeps about 21 bits of both
 // operands (the A_lo B_lo term is below FP32 rounding of the sum).
 template <int MODE, bool SPLIT, bool SPLITA>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
 k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtensorMap tm_tip,
      const __grid_constant__ CUtensorMap tm_mat, const TcOp* __restrict__ ops, int n_ops,
      TcArgs a) {
@@ -163,11 +169,14 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
     // 128-byte swizzle atoms must start on 1024-byte shared-memory addresses
     unsigned char* stages = smem_tc + ((1024u - (smem_u32(smem_tc) & 1023u)) & 1023u);
     unsigned char* wout = stages + kSt * kStB + (threadIdx.x >> 5) * kOutWarpBytes;
+    // per-pattern partial results of the two category halves: [5][2][128]
+    // floats at the start of the staging area (idle until the stores of pass 2)
+    float* xch = reinterpret_cast<float*>(stages + kSt * kStB);
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;      // bit 0 empty, 1 full, 2 done wait gave up
     __shared__ unsigned produced_sh, consumed_sh;
-    __shared__ float red[4];
+    __shared__ float red[8];
     const int tid = threadIdx.x, warp = tid >> 5;
 
     if (warp == 0) {
@@ -276,7 +285,7 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                 float4* A4 = reinterpret_cast<float4*>(st);
                 float4* L4 = reinterpret_cast<float4*>(st + 2 * kAChunk);
 #pragma unroll 4
-                for (int i = tid; i < 2 * kAChunk / 16; i += 128) {
+                for (int i = tid; i < 2 * kAChunk / 16; i += kTcThreads) {
                     const float4 v = A4[i];
                     float4 h, l;
                     h.x = tf32_trunc(v.x);
@@ -377,9 +386,16 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
         }
         pairs_done += n_pairs;
 
-        // ---- epilogue: lane tid <-> pattern p0 + tid -----------------------
-        const int p = p0 + tid;
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        // ---- epilogue: lane (tid & 127) <-> pattern p0 + (tid & 127); warp
+        // half hf takes categories [rb, re) ----------------------------------
+        const int pl = tid & 127, hf = warp >> 2;
+        const int p = p0 + pl;
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const int rb = hf ? (R + 1) / 2 : 0, re = hf ? R : (R + 1) / 2;
+        // partial k of this half into the exchange area, then (after a
+        // barrier) both halves' values of this pattern
+        auto put_x = [&](int k, float v) { xch[(k * 2 + hf) * 128 + pl] = v; };
+        auto get_x = [&](int k, int h) { return xch[(k * 2 + h) * 128 + pl]; };
         int sidx[2] = {0, 0};
         bool amb[2] = {false, false};
         for (int c = 0; c < 2; ++c)
@@ -489,7 +505,7 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                 __syncwarp();
             }
         };
-        const size_t wrow0 = (size_t)(p0 + warp * 32) * kTcN;   // this warp's first row
+        const size_t wrow0 = (size_t)(p0 + (warp & 3) * 32) * kTcN;   // this warp's first row
         const bool real = p < a.Ppad;  // always true (tiles cover Ppad)
         const float wp = (p < a.Ppad) ? (float)a.patw[p] : 0.f;
 
@@ -500,7 +516,7 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
             // pass 1: the products of all categories and their maximum; each
             // category's products replace operand 0's accumulator in TMEM
             float m = 0.f;
-            for (int r = 0; r < R; ++r) {
+            for (int r = rb; r < re; ++r) {
                 float x[64], y[64];
                 operand64(0, r, x);
                 operand64(1, r, y);
@@ -511,16 +527,20 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                 }
                 tmem_st64(lane_base + (uint32_t)(r * 2 * kTcN), x);
             }
+            put_x(0, m);
+            __syncthreads();
+            m = fmaxf(get_x(0, 0), get_x(0, 1));
+            __syncthreads();   // the exchange area is the stores' staging area
             float f1 = 1.f, f2 = 1.f;
             if (a.rescale) cum += post_scale(m, &f1, &f2);
             // pass 2: rescale, round to TF32, store
             float* dst = a.pool + (size_t)op.dest * a.bstride + wrow0;
-            for (int r = 0; r < R; ++r) {
+            for (int r = rb; r < re; ++r) {
                 float z[64];
                 tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN), z);
                 store_row(dst + (size_t)r * a.Ppad * kTcN, z, f1, f2);
             }
-            a.epool[(size_t)op.dest * a.Ppad + p] = cum;
+            if (hf == 0) a.epool[(size_t)op.dest * a.Ppad + p] = cum;
         } else if (MODE == kPre1) {
             // pass 1 over categories: den, the maxima of u_a = q o v_b and
             // u_b = q o v_a, tip numerators u_c . dP_c[:, s]; u of internal
@@ -528,7 +548,7 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
             float den = 0.f, mu[2] = {0.f, 0.f}, num[2] = {0.f, 0.f};
             const bool tipg[2] = {op.kind[0] == kTipStates && op.edge[0] >= 0,
                                   op.kind[1] == kTipStates && op.edge[1] >= 0};
-            for (int r = 0; r < R; ++r) {
+            for (int r = rb; r < re; ++r) {
                 float x[64], y[64];
                 operand64(0, r, x);
                 operand64(1, r, y);
@@ -583,9 +603,22 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                 if (op.uout[0] >= 0) tmem_st64(lane_base + (uint32_t)(r * 2 * kTcN), x);
                 if (op.uout[1] >= 0) tmem_st64(lane_base + (uint32_t)(r * 2 * kTcN + kTcN), y);
             }
+            put_x(0, den);
+            put_x(1, mu[0]);
+            put_x(2, mu[1]);
+            put_x(3, num[0]);
+            put_x(4, num[1]);
+            __syncthreads();
+            den = get_x(0, 0) + get_x(0, 1);
+            mu[0] = fmaxf(get_x(1, 0), get_x(1, 1));
+            mu[1] = fmaxf(get_x(2, 0), get_x(2, 1));
+            num[0] = get_x(3, 0) + get_x(3, 1);
+            num[1] = get_x(4, 0) + get_x(4, 1);
+            __syncthreads();
             for (int c = 0; c < 2; ++c) {
                 if (!tipg[c]) continue;
-                const float g = block_sum128(wp * ((amb[c] ? 0.f : num[c]) / den), red);
+                const float g =
+                    block_sum256(hf == 0 ? wp * ((amb[c] ? 0.f : num[c]) / den) : 0.f, red);
                 if (tid == 0) a.gpart[(size_t)op.edge[c] * a.n_tiles + tile] = (double)g;
             }
             // pass 2: each internal child's u, rescaled, to its pre buffer;
@@ -595,7 +628,7 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                 float f1, f2;
                 const int e = scale_of(mu[c], &f1, &f2);
                 float* dst = a.pool + (size_t)op.uout[c] * a.bstride + wrow0;
-                for (int r = 0; r < R; ++r) {
+                for (int r = rb; r < re; ++r) {
                     float u[64];
                     tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN + c * kTcN), u);
                     store_row(dst + (size_t)r * a.Ppad * kTcN, u, f1, f2);
@@ -603,14 +636,14 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                 float d = den;
                 if (e != 0) d = (-e >= -126 && -e <= 126) ? den * pow2f(-e)
                                                          : den * pow2f(-e / 2) * pow2f(-e - (-e / 2));
-                a.epool[(size_t)op.uout[c] * a.Ppad + p] = __float_as_int(d);
+                if (hf == 0) a.epool[(size_t)op.uout[c] * a.Ppad + p] = __float_as_int(d);
             }
         } else {  // kPre2: operand 0 = q_c = u_c P_c (B = P^T), operand 1 = Q x_c
                   // (or dP x_c for a general derivative, paired with u_c)
             const float den = __int_as_float(a.epool[(size_t)op.dest * a.Ppad + p]);
             const float* ub = a.pool + (size_t)op.dest * a.bstride + (size_t)p * kTcN;
             float num = 0.f, m = 0.f;
-            for (int r = 0; r < R; ++r) {
+            for (int r = rb; r < re; ++r) {
                 float x[64], y[64];
                 tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN), x);
                 tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN + kTcN), y);
@@ -632,14 +665,20 @@ k_tc(const __grid_constant__ CUtensorMap tm_part, const __grid_constant__ CUtens
                 for (int i = 0; i < 64; ++i) m = fmaxf(m, x[i]);
                 num += a.catw[r] * (a.dgen ? 1.f : a.rates[r]) * nr;
             }
+            put_x(0, num);
+            put_x(1, m);
+            __syncthreads();
+            num = get_x(0, 0) + get_x(0, 1);
+            m = fmaxf(get_x(1, 0), get_x(1, 1));
+            __syncthreads();
             if (op.edge[0] >= 0) {
-                const float g = block_sum128(wp * (num / den), red);
+                const float g = block_sum256(hf == 0 ? wp * (num / den) : 0.f, red);
                 if (tid == 0) a.gpart[(size_t)op.edge[0] * a.n_tiles + tile] = (double)g;
             }
             float f1, f2;
             scale_of(m, &f1, &f2);
             float* dst = a.pool + (size_t)op.dest * a.bstride + wrow0;
-            for (int r = 0; r < R; ++r) {
+            for (int r = rb; r < re; ++r) {
                 float x[64];
                 tmem_ld64(lane_base + (uint32_t)(r * 2 * kTcN), x);
                 store_row(dst + (size_t)r * a.Ppad * kTcN, x, f1, f2);
@@ -788,7 +827,7 @@ __global__ void k_q_tc(const double* __restrict__ Q, float* __restrict__ dst, in
 template <int MODE, bool SPLIT, bool SPLITA>
 void launch_mode_t(Instance* I, const TcOp* d, int n, TcArgs a) {
     const size_t smem = (size_t)TcPipe<SPLIT, SPLITA>::stages * TcPipe<SPLIT, SPLITA>::bytes +
-                        4 * kOutWarpBytes + 1024;
+                        (kTcThreads / 32) * kOutWarpBytes + 1024;
     cudaFuncSetAttribute(k_tc<MODE, SPLIT, SPLITA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     int sms = 0, dev_id = 0;
@@ -797,7 +836,7 @@ void launch_mode_t(Instance* I, const TcOp* d, int n, TcArgs a) {
     const CUtensorMap* m = reinterpret_cast<const CUtensorMap*>(I->tmaps.data());
     const int items = n * a.n_tiles;
     const int grid = std::max(1, std::min(items, sms));
-    k_tc<MODE, SPLIT, SPLITA><<<grid, 128, smem, I->stream>>>(m[0], m[1], m[2], d, n, a);
+    k_tc<MODE, SPLIT, SPLITA><<<grid, kTcThreads, smem, I->stream>>>(m[0], m[1], m[2], d, n, a);
     I->launches += 1;
 }
 
