@@ -318,6 +318,19 @@ __device__ void smem_gemm64(const double* A, const double* B, double* C, int n, 
     __syncthreads();
 }
 
+// The same products on many SMs, a block per row of Z (a thread per column):
+// Z = X Y or X^T Y (row stride LD), or with ns the Newton-Schulz factor
+// (3 I - X^T Y) / 2; each element summed as in smem_gemm64.
+__global__ void __launch_bounds__(64) k_eig_gemm(int n, int LD, const double* __restrict__ X,
+                                                 const double* __restrict__ Y,
+                                                 double* __restrict__ Z, int transX, int ns) {
+    const int i = blockIdx.x, j = threadIdx.x;
+    if (j >= n) return;
+    double acc = 0.0;
+    for (int k = 0; k < n; ++k) acc += (transX ? X[k * LD + i] : X[i * LD + k]) * Y[k * LD + j];
+    Z[i * LD + j] = ns ? 0.5 * ((i == j ? 3.0 : 0.0) - acc) : acc;
+}
+
 // Eigensystem of the reversible Q through the symmetric form
 // A = D^1/2 Q D^-1/2 (D = diag(pi)), A = U diag(lambda) U^T, so
 // V = D^-1/2 U and Vinv = U^T D^1/2. One block, in two precisions: cyclic
@@ -326,10 +339,17 @@ __device__ void smem_gemm64(const double* A, const double* B, double* C, int n, 
 // FP64 accuracy by two Newton-Schulz steps U <- U (3 I - U^T U) / 2, A is
 // transformed to U^T A U in FP64, and FP64 Jacobi sweeps (accumulated onto
 // U) finish it, converging quadratically from the FP32 starting point.
+//
+// phase 0 runs all of it in the one block; for large S the FP64 products run
+// on many SMs instead: phase 1 stops after the FP32 sweeps and writes A and
+// U (row stride Spad) to scratch[0] and scratch[1]; k_eig_gemm forms the
+// Newton-Schulz steps and U^T A U (each element summed in the same order as
+// here, so the result is the same); phase 2 reads U from scratch[1] and
+// U^T A U from scratch[3] and runs the FP64 sweeps.
 __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
                         const double* __restrict__ pi, double* __restrict__ V,
                         double* __restrict__ Vinv, double* __restrict__ lam,
-                        int* __restrict__ err) {
+                        int* __restrict__ err, int phase, double* __restrict__ scratch) {
     extern __shared__ double sm[];
     constexpr int LD = 65;
     double* A = sm;                   // [64][LD] FP64
@@ -353,6 +373,15 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
         if (!(p > 0.0)) err[0] = 2;
     }
     __syncthreads();
+    if (phase == 2) {
+        const size_t SS = (size_t)Spad * Spad;
+        for (int idx = t; idx < n * n; idx += nt) {
+            const int i = idx / n, j = idx % n;
+            U[i * LD + j] = scratch[SS + i * Spad + j];
+            A[i * LD + j] = 0.5 * (scratch[3 * SS + i * Spad + j] + scratch[3 * SS + j * Spad + i]);
+        }
+        __syncthreads();
+    } else {
     for (int idx = t; idx < n * n; idx += nt) {
         int i = idx / n, j = idx % n;
         // symmetrise: (D^1/2 Q D^-1/2 + transpose) / 2
@@ -373,6 +402,15 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
         U[i * LD + j] = (double)U32[i * LD + j];
     }
     __syncthreads();
+    if (phase == 1) {
+        const size_t SS = (size_t)Spad * Spad;
+        for (int idx = t; idx < n * n; idx += nt) {
+            const int i = idx / n, j = idx % n;
+            scratch[i * Spad + j] = A[i * LD + j];
+            scratch[SS + i * Spad + j] = U[i * LD + j];
+        }
+        return;
+    }
     for (int it = 0; it < 2; ++it) {
         smem_gemm64(U, U, T1, n, LD, true);          // T1 = U^T U
         for (int idx = t; idx < n * n; idx += nt) {
@@ -395,6 +433,7 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
         A[i * LD + j] = 0.5 * (T2[i * LD + j] + T2[j * LD + i]);
     }
     __syncthreads();
+    }
     // FP64: stop once off(A)^2 <= 1e-28 diag(A)^2 (off-diagonal at 1e-14 of
     // the diagonal; from the FP32 start one or two sweeps); fail above 1e-24
     const bool conv = jacobi_sweeps<double>(A, U, n, LD, 40, 1e-28, 1e-24, 1, 0.0, s_c, s_s, s_p,
@@ -619,12 +658,39 @@ int launch_build_model(Instance* I, int m, int kind, const double* d_params, int
     return launch_eigen_from_q(I, m, check);
 }
 
+// above this many states the eigensystem's FP64 products run on many SMs
+constexpr int kEigSplitS = 32;
+
 int launch_eigen_from_q(Instance* I, int m, bool check) {
     ModelDev& M = I->models[m];
+    M.basis_ready = false;   // V changes (and the basis area may serve as scratch)
     const size_t smem = 4 * 64 * 65 * sizeof(double) + 2 * 64 * 65 * sizeof(float);
     cudaFuncSetAttribute(k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_eigen<<<1, 256, smem, I->stream>>>(I->S, I->Spad, M.Q, M.pi, M.V, M.Vinv, M.lam, I->d_err);
-    I->launches += 1;
+    if (I->S <= kEigSplitS) {
+        k_eigen<<<1, 256, smem, I->stream>>>(I->S, I->Spad, M.Q, M.pi, M.V, M.Vinv, M.lam,
+                                             I->d_err, 0, nullptr);
+        I->launches += 1;
+    } else {
+        // the parameter basis area is scratch here (the model change voids it)
+        const int n = I->S, L = I->Spad;
+        const size_t SS = (size_t)L * L;
+        double* sA = M.G;
+        double* sU = M.G + SS;
+        double* s1 = M.G + 2 * SS;
+        double* s2 = M.G + 3 * SS;
+        k_eigen<<<1, 256, smem, I->stream>>>(I->S, I->Spad, M.Q, M.pi, M.V, M.Vinv, M.lam,
+                                             I->d_err, 1, M.G);
+        // two Newton-Schulz steps U <- U (3 I - U^T U) / 2, then U^T A U
+        k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sU, sU, s1, 1, 1);
+        k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sU, s1, s2, 0, 0);
+        k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, s2, s2, s1, 1, 1);
+        k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, s2, s1, sU, 0, 0);
+        k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sA, sU, s1, 0, 0);
+        k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sU, s1, s2, 1, 0);
+        k_eigen<<<1, 256, smem, I->stream>>>(I->S, I->Spad, M.Q, M.pi, M.V, M.Vinv, M.lam,
+                                             I->d_err, 2, M.G);
+        I->launches += 8;
+    }
     int rc = cuda_check(I, cudaGetLastError(), "eigen");
     if (rc) return rc;
     if (check && (rc = model_check_err(I, "eigendecomposition"))) return rc;

@@ -2,8 +2,9 @@
 exponential's derivative) against the FP64 oracle: dlogL/dt for every
 branch, dlogL/dQ, dlogL/dtheta for every model parameter (including the 265
 of random-effects GY94), and the first-order approximation, on the
-four-state kernels, the FP64 generic path and the split tensor-core codon
-path, every component within |x - x*| <= tol max(|x*|, 1e-3 |x*|_inf)."""
+four-state kernels, the FP64 generic path and the tensor-core codon path
+(split partials, and TF32-stored partials at their own bound), every
+component within |x - x*| <= tol max(|x*|, 1e-3 |x*|_inf)."""
 import dataclasses
 
 import numpy as np
@@ -153,6 +154,19 @@ def test_codon_adjoint(prec, tol, n_tips, n_pat):
     V = D^-1/2 U scale by 1/sqrt(pi_min)."""
     w = synth.workload("gy94_64x5k", n_tips=n_tips, n_patterns=n_pat)
     check(w, prec, tol)
+
+
+@pytest.mark.parametrize("prec", ["tf32", "tf32x2"])
+@pytest.mark.parametrize("n_tips,n_pat", [(7, 161), (20, 300)])
+def test_codon_adjoint_tf32_storage(prec, n_tips, n_pat):
+    """The tensor-core adjoint on TF32-stored partials (the accumulation
+    kernel's variant without the x_lo products). Partials rounded to 11 bits
+    give per-component gradient errors up to 1e-2 of a component on small
+    trees (terms that cancel keep an absolute error of order 2^-11 sqrt(P) of
+    their size); measured up to 3.4e-3 here, so the bound is 1e-2, while a
+    wrong operand layout or a dropped product errs by order one."""
+    w = synth.workload("gy94_64x5k", n_tips=n_tips, n_patterns=n_pat)
+    check(w, prec, 1e-2)
 
 
 @pytest.mark.parametrize("prec,tol", [("f64", 1e-9), ("tf32x3", 1e-3)])
