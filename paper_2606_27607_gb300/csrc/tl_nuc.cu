@@ -849,13 +849,17 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
                     const int cj = j * LPP * 4;
                     const T wr = a.catw[r0 + j * LPP];
                     const V4<T> q = prevq[j];
-                    // v_c = P_c p_c and dP_c p_c (columns of P and dP for a tip state)
-                    const V4<T> v0 = TIP0 ? lds4(mP0 + tc0 + cj) : matvec(mP0 + cj, cs, xc[0][j]);
-                    const V4<T> v1 = TIP1 ? lds4(mP1 + tc1 + cj) : matvec(mP1 + cj, cs, xc[1][j]);
+                    // v_c = P_c p_c and dP_c p_c (columns of P and dP for a tip state).
+                    // The scalar chain (matvec<T>, the same bits as the packed
+                    // FP32 form): issued here it is faster than the packed form,
+                    // whose broadcast operand pairs cost moves (2.47 -> 2.40 ms at
+                    // 512 x 100k); the post-order kernel is faster packed.
+                    const V4<T> v0 = TIP0 ? lds4(mP0 + tc0 + cj) : matvec<T>(mP0 + cj, cs, xc[0][j]);
+                    const V4<T> v1 = TIP1 ? lds4(mP1 + tc1 + cj) : matvec<T>(mP1 + cj, cs, xc[1][j]);
                     const V4<T> u0 = mul(q, v1), u1 = mul(q, v0);
                     den_l += wr * dot(u0, v0);
-                    const V4<T> d0 = TIP0 ? lds4(mD0 + tc0 + cj) : matvec(mD0 + cj, cs, xc[0][j]);
-                    const V4<T> d1 = TIP1 ? lds4(mD1 + tc1 + cj) : matvec(mD1 + cj, cs, xc[1][j]);
+                    const V4<T> d0 = TIP0 ? lds4(mD0 + tc0 + cj) : matvec<T>(mD0 + cj, cs, xc[0][j]);
+                    const V4<T> d1 = TIP1 ? lds4(mD1 + tc1 + cj) : matvec<T>(mD1 + cj, cs, xc[1][j]);
                     num0 += wr * dot(u0, d0);
                     num1 += wr * dot(u1, d1);
                     // q of a tip only when it is asked for (materialised q)
