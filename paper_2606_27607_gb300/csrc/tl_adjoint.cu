@@ -32,6 +32,7 @@
 // relative over 64 states for TF32 storage, 1e-16 in FP64).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "tl_internal.cuh"
 
@@ -304,7 +305,10 @@ __global__ void __launch_bounds__(256) k_adj_coef(const AdjOp<T>* __restrict__ o
     const int p = blockIdx.y * kCoefPat + half;
     const bool inb = p < a.Ppad;
     const int pl = inb ? p : 0;
-    double den = 0.0;
+    // FP32 instances sum the categories in FP32 (FP64 issue is a small fraction
+    // of FP32 on this part; the coefficient feeds TF32 products), FP64 ones in FP64
+    using Acc = typename std::conditional<sizeof(T) == 4, float, double>::type;
+    Acc den = Acc(0);
     for (int r = 0; r < a.R; ++r) {
         T s = T(0);
         for (int i0 = 4 * l16; i0 < a.Spad; i0 += 64) {
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(256) k_adj_coef(const AdjOp<T>* __restrict__ o
         }
 #pragma unroll
         for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        den += a.catw[r] * (double)s;
+        den += (Acc)a.catw[r] * (Acc)s;
     }
     if (l16 == 0 && inb) {
         const double wp = a.patw[p];
@@ -329,7 +333,7 @@ __global__ void __launch_bounds__(256) k_adj_coef(const AdjOp<T>* __restrict__ o
         if (wp != 0.0) {
             int sn = op.en ? op.en[p] : 0;
             for (int c = 0; c < 2; ++c) sn -= op.ec[c] ? op.ec[c][p] : 0;
-            if (den > 0.0) cf = ldexp(wp / den, -sn);
+            if (den > Acc(0)) cf = ldexp((double)((Acc)wp / den), -sn);
             else atomicOr(a.err, 1);
         }
         coef[(size_t)blockIdx.x * a.Ppad + p] = cf;
