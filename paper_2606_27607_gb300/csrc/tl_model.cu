@@ -46,6 +46,7 @@ __global__ void k_build_model(int kind, int S, int Spad, const double* __restric
     __shared__ double s_pi[64];
     __shared__ double s_red[256];
     __shared__ double s_mu[1 + kMaxDq];
+    __shared__ double s_q[64 * 64];   // off-diagonal rates (S <= 64)
     const int t = threadIdx.x;
     const int nt = blockDim.x;
 
@@ -146,14 +147,15 @@ __global__ void k_build_model(int kind, int S, int Spad, const double* __restric
             }
         }
         Q[idx] = r;
+        if (i < S && j < 64) s_q[i * 64 + j] = r;
         for (int k = 0; k < n_dq; ++k) dQ[(size_t)k * Spad * Spad + idx] = d[k];
     }
     __syncthreads();
-    // diagonals (row sums) of R and of each dR
+    // diagonals (row sums) of R (from the shared copy) and of each dR
     for (int i = t; i < S; i += nt) {
         double acc = 0;
         for (int j = 0; j < S; ++j)
-            if (j != i) acc += Q[i * Spad + j];
+            if (j != i) acc += s_q[i * 64 + j];
         Q[i * Spad + i] = -acc;
         for (int k = 0; k < n_dq; ++k) {
             double* D = dQ + (size_t)k * Spad * Spad;
@@ -181,11 +183,14 @@ __global__ void k_build_model(int kind, int S, int Spad, const double* __restric
     const double mu = s_mu[0];
     if (t == 0 && !(mu > 0.0 && isfinite(mu))) err[0] = 1;
     if (t == 0) mu_out[0] = mu;
+    // Q / mu exactly; the derivatives (which only feed parameter gradients)
+    // through one reciprocal, not a division per element and parameter
+    const double inv_mu = 1.0 / mu, inv_mu2 = inv_mu * inv_mu;
     for (int idx = t; idx < Spad * Spad; idx += nt) {
         double r = Q[idx];
         for (int k = 0; k < n_dq; ++k) {
             double* D = dQ + (size_t)k * Spad * Spad;
-            D[idx] = D[idx] / mu - r * s_mu[k + 1] / (mu * mu);
+            D[idx] = D[idx] * inv_mu - r * s_mu[k + 1] * inv_mu2;
         }
         Q[idx] = r / mu;
     }
@@ -358,7 +363,7 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
     double* T2 = T1 + 64 * LD;        // [64][LD] scratch
     float* A32 = reinterpret_cast<float*>(T2 + 64 * LD);   // [64][LD]
     float* U32 = A32 + 64 * LD;                            // [64][LD]
-    __shared__ double s_sq[64];
+    __shared__ double s_sq[64], s_isq[64];   // sqrt(pi_i) and its reciprocal
     __shared__ double s_c[32], s_s[32];
     __shared__ float s_cf[32], s_sf[32];
     __shared__ int s_p[32], s_q[32];
@@ -370,6 +375,7 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
     for (int i = t; i < n; i += nt) {
         double p = pi[i];
         s_sq[i] = sqrt(p);
+        s_isq[i] = 1.0 / s_sq[i];
         if (!(p > 0.0)) err[0] = 2;
     }
     __syncthreads();
@@ -385,8 +391,8 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
     for (int idx = t; idx < n * n; idx += nt) {
         int i = idx / n, j = idx % n;
         // symmetrise: (D^1/2 Q D^-1/2 + transpose) / 2
-        double a = s_sq[i] * Q[i * Spad + j] / s_sq[j];
-        double b = s_sq[j] * Q[j * Spad + i] / s_sq[i];
+        double a = s_sq[i] * Q[i * Spad + j] * s_isq[j];
+        double b = s_sq[j] * Q[j * Spad + i] * s_isq[i];
         const double v = 0.5 * (a + b);
         A[i * LD + j] = v;
         A32[i * LD + j] = (float)v;
@@ -443,7 +449,7 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
         int i = idx / Spad, k = idx % Spad;
         double v = 0, vi = 0;
         if (i < n && k < n) {
-            v = U[i * LD + k] / s_sq[i];   // V = D^-1/2 U
+            v = U[i * LD + k] * s_isq[i];   // V = D^-1/2 U
             vi = U[k * LD + i] * s_sq[k];  // Vinv[i][k] = U[k][i] sqrt(pi_k)
         }
         V[idx] = v;
