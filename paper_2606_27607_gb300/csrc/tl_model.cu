@@ -196,6 +196,37 @@ __global__ void k_build_model(int kind, int S, int Spad, const double* __restric
     }
 }
 
+// off(A)^2 and diag(A)^2 of the n x n block A (leading dimension LD), summed
+// in FP64 (a tree over the block's threads); every thread gets both.
+template <typename T>
+__device__ void off_diag_sums(const T* A, int n, int LD, double* s_red, double& offs,
+                              double& dgs) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    double off = 0, dg = 0;
+    for (int idx = t; idx < n * n; idx += nt) {
+        int i = idx / n, j = idx % n;
+        double a = (double)A[i * LD + j];
+        if (i == j) dg += a * a;
+        else off += a * a;
+    }
+    s_red[t] = off;
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+        if (t < w) s_red[t] += s_red[t + w];
+        __syncthreads();
+    }
+    offs = s_red[0];
+    __syncthreads();
+    s_red[t] = dg;
+    __syncthreads();
+    for (int w = nt / 2; w > 0; w >>= 1) {
+        if (t < w) s_red[t] += s_red[t + w];
+        __syncthreads();
+    }
+    dgs = s_red[0];
+    __syncthreads();
+}
+
 // One block-wide sweep set of cyclic Jacobi in tournament order on the
 // symmetric n x n matrix A (leading dimension LD), accumulating the
 // rotations into the columns of U. Each round rotates m / 2 disjoint pairs
@@ -270,33 +301,14 @@ __device__ bool jacobi_sweeps(T* A, T* U, int n, int LD, int max_sweeps, double 
             __syncthreads();
         }
         // convergence: off-diagonal mass relative to the diagonal
-        double off = 0, dg = 0;
-        for (int idx = t; idx < n * n; idx += nt) {
-            int i = idx / n, j = idx % n;
-            double a = (double)A[i * LD + j];
-            if (i == j) dg += a * a;
-            else off += a * a;
-        }
-        s_red[t] = off;
-        __syncthreads();
-        for (int w = nt / 2; w > 0; w >>= 1) {
-            if (t < w) s_red[t] += s_red[t + w];
-            __syncthreads();
-        }
-        double offs = s_red[0];
-        __syncthreads();
-        s_red[t] = dg;
-        __syncthreads();
-        for (int w = nt / 2; w > 0; w >>= 1) {
-            if (t < w) s_red[t] += s_red[t + w];
-            __syncthreads();
-        }
+        double offs, dgs;
+        off_diag_sums(A, n, LD, s_red, offs, dgs);
         if (t == 0) {
-            s_flag[0] = offs <= done_tol * s_red[0];
-            s_flag[1] = offs <= conv_tol * s_red[0];
+            s_flag[0] = offs <= done_tol * dgs;
+            s_flag[1] = offs <= conv_tol * dgs;
             // stalled: within 1e-8 of the diagonal and no longer shrinking fast
             s_flag[2] = stall > 0.0 && prev >= 0.0 && offs > stall * prev &&
-                        offs <= 1e-8 * s_red[0];
+                        offs <= 1e-8 * dgs;
             prev = offs;
         }
         __syncthreads();
@@ -336,6 +348,39 @@ __global__ void __launch_bounds__(64) k_eig_gemm(int n, int LD, const double* __
     Z[i * LD + j] = ns ? 0.5 * ((i == j ? 3.0 : 0.0) - acc) : acc;
 }
 
+// Largest rotation sine a simultaneous refinement step takes; a pair whose
+// rotation is larger (eigenvalues close on the scale of their coupling) is
+// left to the Jacobi sweeps that follow.
+constexpr double kRefineMaxSine = 1e-3;
+
+// All the Jacobi rotations of a nearly diagonal symmetric A at once:
+// G = I + Theta with Theta antisymmetric, Theta_pq = s_pq (p < q) the sine
+// of the plane rotation that zeroes A_pq, signed as the rotations of
+// jacobi_sweeps (U <- U J, J_pq = s, J_qp = -s). To first order G^T A G
+// has no off-diagonal part; the second-order remainder is about
+// off(A)^2 / gap, so each step squares the relative off-diagonal size
+// (a block per row, a thread per column).
+__global__ void __launch_bounds__(64) k_eig_rot(int n, int LD, const double* __restrict__ A,
+                                                double* __restrict__ G) {
+    const int i = blockIdx.x, j = threadIdx.x;
+    if (j >= n) return;
+    double g = 1.0;
+    if (i != j) {
+        const int p = min(i, j), q = max(i, j);
+        const double apq = 0.5 * (A[p * LD + q] + A[q * LD + p]);
+        double s = 0.0;
+        if (fabs(apq) > 1e-300) {
+            const double theta = (A[q * LD + q] - A[p * LD + p]) / (2.0 * apq);
+            double t = 1.0 / (fabs(theta) + sqrt(theta * theta + 1.0));
+            if (theta < 0) t = -t;
+            s = t / sqrt(t * t + 1.0);
+            if (fabs(s) > kRefineMaxSine) s = 0.0;
+        }
+        g = (i == p) ? s : -s;
+    }
+    G[i * LD + j] = g;
+}
+
 // Eigensystem of the reversible Q through the symmetric form
 // A = D^1/2 Q D^-1/2 (D = diag(pi)), A = U diag(lambda) U^T, so
 // V = D^-1/2 U and Vinv = U^T D^1/2. One block, in two precisions: cyclic
@@ -349,8 +394,11 @@ __global__ void __launch_bounds__(64) k_eig_gemm(int n, int LD, const double* __
 // on many SMs instead: phase 1 stops after the FP32 sweeps and writes A and
 // U (row stride Spad) to scratch[0] and scratch[1]; k_eig_gemm forms the
 // Newton-Schulz steps and U^T A U (each element summed in the same order as
-// here, so the result is the same); phase 2 reads U from scratch[1] and
-// U^T A U from scratch[3] and runs the FP64 sweeps.
+// here, so the result is the same) and two simultaneous-rotation steps
+// (k_eig_rot) refine U and U^T A U; phase 2 reads U from scratch[1] and
+// U^T A U from scratch[3] and runs the FP64 sweeps only if the off-diagonal
+// part is still above their stopping threshold (eigenvalues too close for
+// the refinement).
 __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
                         const double* __restrict__ pi, double* __restrict__ V,
                         double* __restrict__ Vinv, double* __restrict__ lam,
@@ -442,7 +490,12 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
     }
     // FP64: stop once off(A)^2 <= 1e-28 diag(A)^2 (off-diagonal at 1e-14 of
     // the diagonal; from the FP32 start one or two sweeps); fail above 1e-24
-    const bool conv = jacobi_sweeps<double>(A, U, n, LD, 40, 1e-28, 1e-24, 1, 0.0, s_c, s_s, s_p,
+    // (phase 2: the refinement steps before it usually leave A below that
+    // already, and then no sweep runs)
+    double offs = 1.0, dgs = 0.0;
+    if (phase == 2) off_diag_sums(A, n, LD, s_red, offs, dgs);
+    const bool conv = (phase == 2 && offs <= 1e-28 * dgs) ||
+                      jacobi_sweeps<double>(A, U, n, LD, 40, 1e-28, 1e-24, 1, 0.0, s_c, s_s, s_p,
                                             s_q, s_red, s_flag);
     if (t == 0 && !conv) err[0] = 3;
     for (int idx = t; idx < Spad * Spad; idx += nt) {
@@ -693,9 +746,29 @@ int launch_eigen_from_q(Instance* I, int m, bool check) {
         k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, s2, s1, sU, 0, 0);
         k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sA, sU, s1, 0, 0);
         k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sU, s1, s2, 1, 0);
+        // two refinement steps, each: G = I + Theta (k_eig_rot), made
+        // orthogonal by two Newton-Schulz steps, U <- U G, A <- G^T A G
+        // (the second step writes back to U's and A's slots)
+        double* sG = M.G + 4 * SS;
+        double* sG2 = M.G + 5 * SS;
+        double* alt[2][2] = {{M.G + 6 * SS, M.G + 7 * SS}, {sU, s2}};
+        double *cu = sU, *ca = s2;
+        for (int step = 0; step < 2; ++step) {
+            double *nu = alt[step][0], *na = alt[step][1];
+            k_eig_rot<<<n, 64, 0, I->stream>>>(n, L, ca, sG);
+            k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sG, sG, s1, 1, 1);
+            k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sG, s1, sG2, 0, 0);
+            k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sG2, sG2, s1, 1, 1);
+            k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sG2, s1, sG, 0, 0);
+            k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, cu, sG, nu, 0, 0);
+            k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, ca, sG, s1, 0, 0);
+            k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sG, s1, na, 1, 0);
+            cu = nu;
+            ca = na;
+        }
         k_eigen<<<1, 256, smem, I->stream>>>(I->S, I->Spad, M.Q, M.pi, M.V, M.Vinv, M.lam,
                                              I->d_err, 2, M.G);
-        I->launches += 8;
+        I->launches += 8 + 2 * 8;
     }
     int rc = cuda_check(I, cudaGetLastError(), "eigen");
     if (rc) return rc;

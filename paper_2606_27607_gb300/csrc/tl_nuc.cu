@@ -217,6 +217,10 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// a / b for the gradient ratios: FP32 by the fast division (at most 2 ulp,
+// b well inside the normal range here), FP64 exactly
+__device__ __forceinline__ float ratio_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double ratio_div(double a, double b) { return a / b; }
 __device__ __forceinline__ int tip_col(int8_t s) { return (s >= 0 && s < 4) ? (int)s : 4; }
 
 // ---------------------------------------------------------------------------
@@ -752,6 +756,7 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
             nbuf = 0;
         };
         // a child's post-order partial (memory, or tip partials), prefetched
+        // (a tip with states is read as matrix columns, its x left unset)
         auto child_x = [&](int child, int kind, V4<T>* x) {
             if (kind == kTipStates || kind < 0) {
 #pragma unroll
@@ -843,9 +848,13 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
                 constexpr bool TIP0 = decltype(tip0_c)::value, TIP1 = decltype(tip1_c)::value;
 #pragma unroll
                 for (int j = 0; j < CPL; ++j) {
-                    qa[j] = zero;
-                    qb[j] = zero;
-                    if (!act[j]) continue;
+                    // qa / qb of a tip are set only when asked for, and read
+                    // only then
+                    if (!act[j]) {
+                        qa[j] = zero;
+                        qb[j] = zero;
+                        continue;
+                    }
                     const int cj = j * LPP * 4;
                     const T wr = a.catw[r0 + j * LPP];
                     const V4<T> q = prevq[j];
@@ -877,7 +886,8 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
                 else categories(no{}, no{});
             }
             if (e0 || e1) {
-                const T wden = wpt / group_sum<LPP>(den_l);  // both children's ratios share it
+                // both children's ratios share it (FP32: the fast division, 2 ulp)
+                const T wden = ratio_div(wpt, group_sum<LPP>(den_l));
                 if (e0) {
                     const T num = group_sum<LPP>(num0);
                     gbuf[nbuf * 33 + lane] = (r0 == 0) ? num * wden : T(0);
