@@ -34,6 +34,7 @@
 #include <cmath>
 #include <type_traits>
 
+#include "tl_df.cuh"
 #include "tl_internal.cuh"
 
 namespace tl {
@@ -651,38 +652,10 @@ __global__ void __launch_bounds__(256) k_adj_finish(int S, int Spad, int R, int 
 }
 
 // The finish of a TF32 instance with the two eigenbasis products in
-// double-float arithmetic on the FP32 cores (FP64 issue is a small fraction of
-// FP32 on this part): every value of V, V^-1, M and Y as hi + lo, two FP32
-// numbers; each multiply-add takes the product's rounding error from an FMA
-// and the sum's from TwoSum (Knuth), both collected in a compensation term,
-// which keeps about 2^-48 of each sum's terms. W then enters the same FP64
-// arithmetic as the FP64 kernel, with Phi_ij = (e^{a_i} - e^{a_j}) / (a_i - a_j)
-// from the exponentials (a series in d = a_i - a_j below |d| = 2^-10).
-struct df2 {
-    float hi, lo;
-};
-__device__ __forceinline__ df2 df_of(double x) {
-    const float h = (float)x;
-    return {h, (float)(x - (double)h)};
-}
-// (s, c) += a * b; the intrinsics keep the compiler from contracting or
-// reassociating the error terms
-__device__ __forceinline__ void df_mac(float& s, float& c, df2 a, df2 b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    const float t = __fadd_rn(s, p);
-    const float bp = __fsub_rn(t, s);
-    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
-    s = t;
-    c = __fadd_rn(c, __fadd_rn(err, e));
-}
-__device__ __forceinline__ df2 df_norm(float s, float c) {
-    const float h = __fadd_rn(s, c);
-    return {h, __fsub_rn(c, __fsub_rn(h, s))};
-}
-
+// double-float arithmetic (tl_df.cuh): every value of V, V^-1, M and Y as
+// hi + lo. W then enters the same FP64 arithmetic as the FP64 kernel, with
+// Phi_ij = (e^{a_i} - e^{a_j}) / (a_i - a_j) from the exponentials (a series
+// in d = a_i - a_j below |d| = 2^-10).
 __global__ void __launch_bounds__(256) k_adj_finish_df(int S, int Spad, int R, int E,
                                                        const double* __restrict__ V,
                                                        const double* __restrict__ Vinv,

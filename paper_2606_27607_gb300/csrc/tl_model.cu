@@ -12,6 +12,9 @@
 // kernels that consume them.
 #include <cmath>
 
+#include <type_traits>
+
+#include "tl_df.cuh"
 #include "tl_internal.cuh"
 
 namespace tl {
@@ -381,6 +384,11 @@ __global__ void __launch_bounds__(64) k_eig_rot(int n, int LD, const double* __r
     G[i * LD + j] = g;
 }
 
+// Threads of the eigensolver's block: 256 for up to 32 states; above that
+// 1,024, so that a Jacobi round's rotations (up to 32) each get a warp and
+// the block-wide passes over the matrix have four times the threads.
+constexpr int kEigThreadsMax = 1024;
+
 // Eigensystem of the reversible Q through the symmetric form
 // A = D^1/2 Q D^-1/2 (D = diag(pi)), A = U diag(lambda) U^T, so
 // V = D^-1/2 U and Vinv = U^T D^1/2. One block, in two precisions: cyclic
@@ -399,7 +407,7 @@ __global__ void __launch_bounds__(64) k_eig_rot(int n, int LD, const double* __r
 // U^T A U from scratch[3] and runs the FP64 sweeps only if the off-diagonal
 // part is still above their stopping threshold (eigenvalues too close for
 // the refinement).
-__global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
+__global__ void __launch_bounds__(kEigThreadsMax) k_eigen(int S, int Spad, const double* __restrict__ Q,
                         const double* __restrict__ pi, double* __restrict__ V,
                         double* __restrict__ Vinv, double* __restrict__ lam,
                         int* __restrict__ err, int phase, double* __restrict__ scratch) {
@@ -415,7 +423,7 @@ __global__ void k_eigen(int S, int Spad, const double* __restrict__ Q,
     __shared__ double s_c[32], s_s[32];
     __shared__ float s_cf[32], s_sf[32];
     __shared__ int s_p[32], s_q[32];
-    __shared__ double s_red[256];
+    __shared__ double s_red[kEigThreadsMax];
     __shared__ int s_flag[3];
     const int t = threadIdx.x, nt = blockDim.x;
     const int n = S;
@@ -626,6 +634,10 @@ __device__ void write_layout(const double* Pm, int slot, int r, int S, int Spad,
 //  layout 1: FP64 transposed layout [R][Spad+1][Spad]: W[j][i] = P[i][j], row Spad = row sums
 //  layout 2: TF32 row-major [R][Spad][Spad] floats (rounded) + row sums [R][Spad]
 //  layout 3: layout 2 as hi and lo TF32 terms (TL_SPLIT_MATRICES)
+// The TF32 layouts take the S^3 product in double-float arithmetic on the
+// FP32 cores (about 2^-48 of the sum of the terms' magnitudes, far inside
+// what TF32 hi + lo storage keeps; FP64 issue was this kernel's limit);
+// the FP64 matrix each writes is that sum rounded to FP64.
 template <typename T>
 __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
                       const double* __restrict__ Vinv, const double* __restrict__ lam,
@@ -648,7 +660,13 @@ __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
         e[k] = (k < S) ? expm1(lam[k] * rt) : 0.0;
         de[k] = (k < S) ? rates[r] * lam[k] * exp(lam[k] * rt) : 0.0;
     }
-    for (int idx = t; idx < Spad * Spad; idx += nt) Vi[idx] = Vinv[idx];
+    const bool dfp = std::is_same<T, float>::value && layout >= 2;
+    df2* Vid = reinterpret_cast<df2*>(Vi);   // the same storage, as hi + lo pairs
+    df2* Wd = reinterpret_cast<df2*>(W);
+    for (int idx = t; idx < Spad * Spad; idx += nt) {
+        if (dfp) Vid[idx] = df_of(Vinv[idx]);
+        else Vi[idx] = Vinv[idx];
+    }
     __syncthreads();
     for (int pass = 0; pass < 2; ++pass) {
         const int slot = (pass == 0) ? pidx[b] : (dpidx ? dpidx[b] : -1);
@@ -656,14 +674,26 @@ __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
         const double* ev = (pass == 0) ? e : de;
         // W = V diag(ev), rounded as the product V_ik ev_k was before each
         // term's fused multiply-add
-        for (int idx = t; idx < Spad * Spad; idx += nt) W[idx] = V[idx] * ev[idx % Spad];
+        for (int idx = t; idx < Spad * Spad; idx += nt) {
+            const double w = V[idx] * ev[idx % Spad];
+            if (dfp) Wd[idx] = df_of(w);
+            else W[idx] = w;
+        }
         __syncthreads();
         double* out = mat64 + ((size_t)slot * R + r) * Spad * Spad;
         for (int idx = t; idx < Spad * Spad; idx += nt) {
             int i = idx / Spad, j = idx % Spad;
             double acc = 0.0;
-            if (i < S && j < S)
-                for (int k = 0; k < S; ++k) acc += W[i * Spad + k] * Vi[k * Spad + j];
+            if (i < S && j < S) {
+                if (dfp) {
+                    float sh = 0.f, sc = 0.f;
+                    for (int k = 0; k < S; ++k) df_mac(sh, sc, Wd[i * Spad + k], Vid[k * Spad + j]);
+                    const df2 d = df_norm(sh, sc);
+                    acc = (double)d.hi + (double)d.lo;
+                } else {
+                    for (int k = 0; k < S; ++k) acc += W[i * Spad + k] * Vi[k * Spad + j];
+                }
+            }
             if (pass == 0 && i == j && i < S) acc += 1.0;
             out[idx] = acc;
             Pm[idx] = acc;
@@ -737,8 +767,8 @@ int launch_eigen_from_q(Instance* I, int m, bool check) {
         double* sU = M.G + SS;
         double* s1 = M.G + 2 * SS;
         double* s2 = M.G + 3 * SS;
-        k_eigen<<<1, 256, smem, I->stream>>>(I->S, I->Spad, M.Q, M.pi, M.V, M.Vinv, M.lam,
-                                             I->d_err, 1, M.G);
+        k_eigen<<<1, kEigThreadsMax, smem, I->stream>>>(I->S, I->Spad, M.Q, M.pi, M.V, M.Vinv,
+                                                        M.lam, I->d_err, 1, M.G);
         // two Newton-Schulz steps U <- U (3 I - U^T U) / 2, then U^T A U
         k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sU, sU, s1, 1, 1);
         k_eig_gemm<<<n, 64, 0, I->stream>>>(n, L, sU, s1, s2, 0, 0);
@@ -766,8 +796,8 @@ int launch_eigen_from_q(Instance* I, int m, bool check) {
             cu = nu;
             ca = na;
         }
-        k_eigen<<<1, 256, smem, I->stream>>>(I->S, I->Spad, M.Q, M.pi, M.V, M.Vinv, M.lam,
-                                             I->d_err, 2, M.G);
+        k_eigen<<<1, kEigThreadsMax, smem, I->stream>>>(I->S, I->Spad, M.Q, M.pi, M.V, M.Vinv,
+                                                        M.lam, I->d_err, 2, M.G);
         I->launches += 8 + 2 * 8;
     }
     int rc = cuda_check(I, cudaGetLastError(), "eigen");

@@ -115,6 +115,39 @@ def test_device_model_matches_oracle(kind):
                 assert np.allclose(dP[r], rho * Q @ want, rtol=0, atol=1e-12 * max(1, rho))
 
 
+@pytest.mark.parametrize("prec", ["tf32", "tf32x2"])
+def test_codon_matrices_of_tf32_instances(prec):
+    """A TF32 instance forms P and dP/dt with a double-float S^3 product:
+    each entry within 2^-44 of the sum of its terms' magnitudes,
+    S * max|V| * max|Vinv| * max|e| (a factor 16 above the 2^-48 the
+    arithmetic keeps per term)."""
+    from paper_2606_27607_gb300 import Instance
+    rng = np.random.default_rng(11)
+    params, freqs = [2.0, 0.3], np.stack([rng.dirichlet(np.ones(4)) for _ in range(3)])
+    Q, pi, _ = om.build("gy94", params, freqs)
+    S = 61
+    rates = synth.gamma_rates(0.5)
+    t = np.array([0.0, 0.01, 0.1, 0.7, 3.0])
+    d = np.sqrt(pi)
+    A = d[:, None] * Q / d[None, :]
+    lam = np.linalg.eigvalsh(0.5 * (A + A.T))
+    vmax, vimax = 1.0 / d.min(), d.max()
+    with Instance(4, 8, S, 4, 4, 10, 1, prec) as inst:
+        inst.set_model(0, "gy94", params, freqs)
+        inst.set_category_rates(rates)
+        inst.update_matrices(0, np.arange(5), t, np.arange(5) + 5)
+        for b, tb in enumerate(t):
+            P, dP = inst.get_matrix(b), inst.get_matrix(5 + b)
+            for r, rho in enumerate(rates):
+                want = op.transition_matrices(Q, np.array([tb]), [rho])[0, 0]
+                emax = np.abs(np.expm1(lam * rho * tb)).max()
+                demax = np.abs(rho * lam * np.exp(lam * rho * tb)).max()
+                tol_p = S * vmax * vimax * emax * 2.0 ** -44 + 1e-13
+                tol_d = S * vmax * vimax * demax * 2.0 ** -44 + 1e-12 * max(1, rho)
+                assert np.abs(P[r] - want).max() <= tol_p, (b, r)
+                assert np.abs(dP[r] - rho * Q @ want).max() <= tol_d, (b, r)
+
+
 def test_set_eigen_and_rate_matrix_paths():
     from paper_2606_27607_gb300 import Instance
     pi = np.array([0.1, 0.2, 0.3, 0.4])
