@@ -806,13 +806,12 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
             if (k + 1 < n_ops) issue_mats(k + 1);
             cp_async_commit();
             // op k + 1's inputs, first read by the next op
-            {
-                const int4 hn = op_head(ops, k + 1, n_ops);
-                tsn[0] = tip_state(a, hn.x, hn.z, p);
-                tsn[1] = tip_state(a, hn.y, hn.w, p);
-            }
+            // (children and kinds from the descriptor copy in shared memory,
+            // not a global load whose result the addresses wait for)
             if (k + 1 < n_ops) {
                 const DevPreOp& o1 = pipe.obuf[(k + 1) % 3];
+                tsn[0] = tip_state(a, o1.child[0], o1.kind[0], p);
+                tsn[1] = tip_state(a, o1.child[1], o1.kind[1], p);
                 child_x(o1.child[0], o1.kind[0], xn[0]);
                 child_x(o1.child[1], o1.kind[1], xn[1]);
             }
