@@ -148,6 +148,42 @@ def test_codon_matrices_of_tf32_instances(prec):
                 assert np.abs(dP[r] - rho * Q @ want).max() <= tol_d, (b, r)
 
 
+@pytest.mark.parametrize("case", ["gy94_degenerate", "rev40"])
+def test_eigensystem_above_32_states(case):
+    """Above 32 states the FP64 eigensystem comes from FP32 Jacobi, the
+    simultaneous-rotation refinement and, where eigenvalues are too close
+    for it, FP64 Jacobi sweeps. Uniform codon frequencies with kappa = omega
+    = 1 give a spectrum of highly repeated eigenvalues (every pair of the
+    repeated ones left to the sweeps); a 40-state general reversible model a
+    generic one. P against the oracle at the FP64 path's tolerance."""
+    from paper_2606_27607_gb300 import Instance
+    rng = np.random.default_rng(17)
+    if case == "gy94_degenerate":
+        kind, S = "gy94", 61
+        params, freqs = [1.0, 1.0], np.full((3, 4), 0.25)
+    else:
+        kind, S = "rev", 40
+        ex = rng.exponential(1.0, size=(S, S))
+        params, freqs = 0.5 * (ex + ex.T), rng.dirichlet(np.ones(S))
+    Q, pi, _ = om.build(kind, params, freqs)
+    d = np.sqrt(pi)
+    lam = np.linalg.eigvalsh(0.5 * (d[:, None] * Q / d[None, :] + (d[:, None] * Q / d[None, :]).T))
+    if case == "gy94_degenerate":
+        assert np.sum(np.diff(np.sort(lam)) < 1e-9 * np.abs(lam).max()) > 10
+    with Instance(4, 8, S, 4, 4, 10, 1, "f64") as inst:
+        inst.set_model(0, kind, params, freqs)
+        rates = synth.gamma_rates(0.5)
+        inst.set_category_rates(rates)
+        t = np.array([0.0, 0.01, 0.1, 0.7, 3.0])
+        inst.update_matrices(0, np.arange(5), t, np.arange(5) + 5)
+        for b, tb in enumerate(t):
+            P, dP = inst.get_matrix(b), inst.get_matrix(5 + b)
+            for r, rho in enumerate(rates):
+                want = op.transition_matrices(Q, np.array([tb]), [rho])[0, 0]
+                assert np.abs(P[r] - want).max() <= 1e-13, (b, r)
+                assert np.abs(dP[r] - rho * Q @ want).max() <= 1e-12 * max(1, rho), (b, r)
+
+
 def test_set_eigen_and_rate_matrix_paths():
     from paper_2606_27607_gb300 import Instance
     pi = np.array([0.1, 0.2, 0.3, 0.4])
