@@ -784,6 +784,8 @@ int tl_destroy(tl_instance* inst) {
         fr(M.pi);
         fr(M.V);
         fr(M.Vinv);
+        fr(M.Vdf);
+        fr(M.Vinvdf);
         fr(M.lam);
         fr(M.dQ);
         fr(M.G);
@@ -946,6 +948,10 @@ int tl_create(int n_tips, int n_patterns, int n_states, int n_categories, int n_
             (rc = dev_alloc(I, &M.Qw, (size_t)I->elt * SS, "Q copy")) ||
             (rc = dev_alloc(I, &M.pairs, sizeof(int) * 2 * TL_GY94_PAIRS, "pair table")) ||
             (rc = dev_alloc(I, &M.mu, sizeof(double), "mean rate")))
+            return bail(rc);
+        if (prec != kF64 &&
+            ((rc = dev_alloc(I, &M.Vdf, 2 * sizeof(float) * SS, "V pairs")) ||
+             (rc = dev_alloc(I, &M.Vinvdf, 2 * sizeof(float) * SS, "Vinv pairs"))))
             return bail(rc);
     }
     if (prec == kTF32) {

@@ -27,6 +27,16 @@ __device__ __forceinline__ void df_mac(float& s, float& c, df2 a, df2 b) {
     s = t;
     c = __fadd_rn(c, __fadd_rn(err, e));
 }
+// a * b rounded to a double-float (the lo * lo term, 2^-48 of the
+// product, dropped)
+__device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float h = __fadd_rn(p, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
 __device__ __forceinline__ df2 df_norm(float s, float c) {
     const float h = __fadd_rn(s, c);
     return {h, __fsub_rn(c, __fsub_rn(h, s))};

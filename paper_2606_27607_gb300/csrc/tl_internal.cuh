@@ -132,6 +132,8 @@ struct ModelDev {
     double* G = nullptr;      // [kMaxDq][Spad][Spad]: Vinv dQ V, then as much scratch
     void* piw = nullptr;      // pi in working precision [Spad]
     void* Qw = nullptr;       // Q in working precision [Spad][Spad]
+    void* Vdf = nullptr;      // reduced precision: V and Vinv as double-float pairs
+    void* Vinvdf = nullptr;   // (two floats per entry) [Spad][Spad] for the matrix products
     int* pairs = nullptr;     // GY94RE: [TL_GY94_PAIRS][2] codon indices (i < j)
     double* mu = nullptr;     // [1] mean rate of the unnormalised Q (tl_set_model)
     int n_dq = 0;

@@ -529,6 +529,16 @@ __device__ __forceinline__ float trunc_tf32(float x) {
     return __uint_as_float(__float_as_uint(x) & 0xffffe000u);
 }
 
+// Double-float copies of V and Vinv for the reduced-precision matrix
+// products (k_tpm).
+__global__ void k_df_pairs(int n, const double* __restrict__ V, const double* __restrict__ Vinv,
+                           df2* __restrict__ Vdf, df2* __restrict__ Vinvdf) {
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        Vdf[idx] = df_of(V[idx]);
+        Vinvdf[idx] = df_of(Vinv[idx]);
+    }
+}
+
 // Working-precision copies of pi and Q.
 template <typename T>
 __global__ void k_model_working(int S, int Spad, const double* __restrict__ Q,
@@ -629,6 +639,54 @@ __device__ void write_layout(const double* Pm, int slot, int r, int S, int Spad,
 
 }
 
+// write_layout for the TF32 layouts (2, 3) from FP32 values in shared
+// memory (the double-float sums rounded to FP32); the row sums are formed
+// from the same rounded values, in the same order, as write_layout's. The
+// transposed copies go through a padded shared-memory tile (tr, Spad rows
+// of Spad + 1 floats, which fits the Spad x Spad doubles it reuses) so
+// that every global store is coalesced.
+template <typename T>
+__device__ void write_layout_f(const float* Pf, int slot, int r, int S, int Spad, int R,
+                               T* __restrict__ matw, size_t matw_stride, int layout,
+                               T* __restrict__ rowsum, float* tr) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int TLD = Spad + 1;
+    T* w = matw + (size_t)slot * matw_stride;
+    for (int part = 0; part < (layout == 3 ? 2 : 1); ++part) {   // P_hi, then P_lo
+        T* wp = w + ((size_t)2 * part * R + r) * Spad * Spad;
+        T* wt = w + ((size_t)(2 * part + 1) * R + r) * Spad * Spad;
+        for (int idx = t; idx < Spad * Spad; idx += nt) {
+            const int i = idx / Spad, j = idx % Spad;
+            const float f = Pf[idx];
+            const float hi = round_tf32(f);
+            const float v = part == 0 ? hi : trunc_tf32(f - hi);
+            wp[idx] = (T)v;
+            tr[i * TLD + j] = v;
+        }
+        __syncthreads();
+        for (int idx = t; idx < Spad * Spad; idx += nt) {
+            const int j = idx / Spad, i = idx % Spad;
+            wt[idx] = (T)tr[i * TLD + j];
+        }
+        __syncthreads();
+    }
+    for (int i = t; i < Spad; i += nt) {
+        T v;
+        if (layout == 3) {
+            const float f0 = Pf[i * Spad], h0 = round_tf32(f0);
+            v = (T)h0 + (T)trunc_tf32(f0 - h0);
+            for (int q = 1; q < S; ++q) {
+                const float f = Pf[i * Spad + q], h = round_tf32(f);
+                v = v + ((T)h + (T)trunc_tf32(f - h));
+            }
+        } else {
+            v = (T)round_tf32(Pf[i * Spad]);
+            for (int q = 1; q < S; ++q) v = v + (T)round_tf32(Pf[i * Spad + q]);
+        }
+        rowsum[((size_t)slot * R + r) * Spad + i] = v;
+    }
+}
+
 // P and dP/dt for `count` edges; grid (count, R).
 //  layout 0: four-state column layout [R][5][4] of T: column j of P, then row sums
 //  layout 1: FP64 transposed layout [R][Spad+1][Spad]: W[j][i] = P[i][j], row Spad = row sums
@@ -636,11 +694,14 @@ __device__ void write_layout(const double* Pm, int slot, int r, int S, int Spad,
 //  layout 3: layout 2 as hi and lo TF32 terms (TL_SPLIT_MATRICES)
 // The TF32 layouts take the S^3 product in double-float arithmetic on the
 // FP32 cores (about 2^-48 of the sum of the terms' magnitudes, far inside
-// what TF32 hi + lo storage keeps; FP64 issue was this kernel's limit);
-// the FP64 matrix each writes is that sum rounded to FP64.
+// what TF32 hi + lo storage keeps; FP64 issue was this kernel's limit),
+// from the model's double-float copies of V and Vinv (Vdf, Vinvdf) and
+// W = V diag(e) formed as double-float products; the FP64 matrix each
+// writes is that sum rounded to FP64, the working copy its FP32 rounding.
 template <typename T>
 __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
-                      const double* __restrict__ Vinv, const double* __restrict__ lam,
+                      const double* __restrict__ Vinv, const df2* __restrict__ Vdf,
+                      const df2* __restrict__ Vinvdf, const double* __restrict__ lam,
                       const int* __restrict__ pidx, const int* __restrict__ dpidx,
                       const double* __restrict__ len, const double* __restrict__ rates,
                       double* __restrict__ mat64, T* __restrict__ matw, size_t matw_stride,
@@ -663,8 +724,10 @@ __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
     const bool dfp = std::is_same<T, float>::value && layout >= 2;
     df2* Vid = reinterpret_cast<df2*>(Vi);   // the same storage, as hi + lo pairs
     df2* Wd = reinterpret_cast<df2*>(W);
+    float* Pf = reinterpret_cast<float*>(Pm);   // dfp: the FP32 working values
+    __shared__ df2 evd[64];
     for (int idx = t; idx < Spad * Spad; idx += nt) {
-        if (dfp) Vid[idx] = df_of(Vinv[idx]);
+        if (dfp) Vid[idx] = Vinvdf[idx];
         else Vi[idx] = Vinv[idx];
     }
     __syncthreads();
@@ -672,34 +735,48 @@ __global__ void k_tpm(int S, int Spad, int R, const double* __restrict__ V,
         const int slot = (pass == 0) ? pidx[b] : (dpidx ? dpidx[b] : -1);
         if (slot < 0) continue;
         const double* ev = (pass == 0) ? e : de;
-        // W = V diag(ev), rounded as the product V_ik ev_k was before each
-        // term's fused multiply-add
-        for (int idx = t; idx < Spad * Spad; idx += nt) {
-            const double w = V[idx] * ev[idx % Spad];
-            if (dfp) Wd[idx] = df_of(w);
-            else W[idx] = w;
+        // W = V diag(ev): FP64, rounded as the product V_ik ev_k was before
+        // each term's fused multiply-add; double-float products for dfp
+        if (dfp) {
+            for (int k = t; k < Spad; k += nt) evd[k] = df_of(ev[k]);
+            __syncthreads();
+            for (int idx = t; idx < Spad * Spad; idx += nt) Wd[idx] = df_mul(Vdf[idx], evd[idx % Spad]);
+        } else {
+            for (int idx = t; idx < Spad * Spad; idx += nt) W[idx] = V[idx] * ev[idx % Spad];
         }
         __syncthreads();
         double* out = mat64 + ((size_t)slot * R + r) * Spad * Spad;
         for (int idx = t; idx < Spad * Spad; idx += nt) {
             int i = idx / Spad, j = idx % Spad;
             double acc = 0.0;
-            if (i < S && j < S) {
-                if (dfp) {
+            if (dfp) {
+                float f = 0.f;
+                if (i < S && j < S) {
                     float sh = 0.f, sc = 0.f;
                     for (int k = 0; k < S; ++k) df_mac(sh, sc, Wd[i * Spad + k], Vid[k * Spad + j]);
                     const df2 d = df_norm(sh, sc);
                     acc = (double)d.hi + (double)d.lo;
-                } else {
-                    for (int k = 0; k < S; ++k) acc += W[i * Spad + k] * Vi[k * Spad + j];
+                    f = d.hi;
                 }
+                if (pass == 0 && i == j && i < S) {
+                    acc += 1.0;
+                    f = (float)acc;
+                }
+                out[idx] = acc;
+                Pf[idx] = f;
+                continue;
             }
+            if (i < S && j < S)
+                for (int k = 0; k < S; ++k) acc += W[i * Spad + k] * Vi[k * Spad + j];
             if (pass == 0 && i == j && i < S) acc += 1.0;
             out[idx] = acc;
             Pm[idx] = acc;
         }
         __syncthreads();
-        write_layout(Pm, slot, r, S, Spad, R, matw, matw_stride, layout, rowsum);
+        if (dfp)
+            write_layout_f(Pf, slot, r, S, Spad, R, matw, matw_stride, layout, rowsum,
+                           reinterpret_cast<float*>(W));   // W is free until the next pass
+        else write_layout(Pm, slot, r, S, Spad, R, matw, matw_stride, layout, rowsum);
         __syncthreads();
     }
 }
@@ -824,6 +901,9 @@ int launch_model_working_copies(Instance* I, int m) {
         k_model_working<float><<<1, 256, 0, I->stream>>>(I->S, I->Spad, M.Q, M.pi,
                                                          (float*)M.Qw, (float*)M.piw,
                                                          I->prec == kTF32);
+        k_df_pairs<<<16, 256, 0, I->stream>>>(I->Spad * I->Spad, M.V, M.Vinv, (df2*)M.Vdf,
+                                              (df2*)M.Vinvdf);
+        I->launches += 1;
     }
     I->launches += 1;
     int rc = cuda_check(I, cudaGetLastError(), "model working copies");
@@ -845,13 +925,15 @@ int launch_update_matrices(Instance* I, int m, const int* d_pidx, const int* d_d
                  : (I->prec == kF64 ? 1 : (I->split ? 3 : 2));
     if (I->prec == kF64) {
         cudaFuncSetAttribute(k_tpm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_tpm<double><<<grid, 256, smem, I->stream>>>(I->S, I->Spad, I->R, M.V, M.Vinv, M.lam,
+        k_tpm<double><<<grid, 256, smem, I->stream>>>(I->S, I->Spad, I->R, M.V, M.Vinv, nullptr,
+                                                      nullptr, M.lam,
                                                       d_pidx, d_dpidx, d_len, d_rates, I->d_mat64,
                                                       (double*)I->d_matw, I->matw_stride, layout,
                                                       nullptr);
     } else {
         cudaFuncSetAttribute(k_tpm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_tpm<float><<<grid, 256, smem, I->stream>>>(I->S, I->Spad, I->R, M.V, M.Vinv, M.lam,
+        k_tpm<float><<<grid, 256, smem, I->stream>>>(I->S, I->Spad, I->R, M.V, M.Vinv,
+                                                     (const df2*)M.Vdf, (const df2*)M.Vinvdf, M.lam,
                                                      d_pidx, d_dpidx, d_len, d_rates, I->d_mat64,
                                                      (float*)I->d_matw, I->matw_stride, layout,
                                                      I->d_rowsum);
