@@ -802,10 +802,7 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
                            int (&tsn)[2]) {
             cp_async_wait_all();
             __syncwarp();
-            pipe.issue_op(ops, k + 2, n_ops, lane);
-            if (k + 1 < n_ops) issue_mats(k + 1);
-            cp_async_commit();
-            // op k + 1's inputs, first read by the next op
+            // op k + 1's inputs, first read by the next op, issued first
             // (children and kinds from the descriptor copy in shared memory,
             // not a global load whose result the addresses wait for)
             if (k + 1 < n_ops) {
@@ -815,6 +812,9 @@ k_pre4(const DevPreOp* __restrict__ ops_, int n_ops_, const __grid_constant__ Nu
                 child_x(o1.child[0], o1.kind[0], xn[0]);
                 child_x(o1.child[1], o1.kind[1], xn[1]);
             }
+            pipe.issue_op(ops, k + 2, n_ops, lane);
+            if (k + 1 < n_ops) issue_mats(k + 1);
+            cp_async_commit();
             const DevPreOp& op = pipe.obuf[k % 3];
             const int kd0 = op.kind[0], kd1 = op.kind[1], qsrc = op.q_src;
             const bool e0 = op.edge[0] >= 0, e1 = op.edge[1] >= 0;
