@@ -901,9 +901,13 @@ int launch_model_working_copies(Instance* I, int m) {
         k_model_working<float><<<1, 256, 0, I->stream>>>(I->S, I->Spad, M.Q, M.pi,
                                                          (float*)M.Qw, (float*)M.piw,
                                                          I->prec == kTF32);
-        k_df_pairs<<<16, 256, 0, I->stream>>>(I->Spad * I->Spad, M.V, M.Vinv, (df2*)M.Vdf,
-                                              (df2*)M.Vinvdf);
-        I->launches += 1;
+        // only the TF32 matrix layouts take the double-float products (the
+        // four-state FP32 layout is formed from the FP64 eigensystem)
+        if (!(I->S == 4 && I->prec == kF32)) {
+            k_df_pairs<<<16, 256, 0, I->stream>>>(I->Spad * I->Spad, M.V, M.Vinv, (df2*)M.Vdf,
+                                                  (df2*)M.Vinvdf);
+            I->launches += 1;
+        }
     }
     I->launches += 1;
     int rc = cuda_check(I, cudaGetLastError(), "model working copies");
